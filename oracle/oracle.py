@@ -1,0 +1,238 @@
+"""ctypes wrapper around the serial FP64 oracle (pbf_oracle.cpp).
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the CPU-baseline leg of the
+benchmark may import this module; the GPU library never does. It marshals plain Python
+dicts (as produced by the package's `inputs` module) into the oracle's own C structs.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "pbf_oracle.cpp")
+LIB = os.path.join(HERE, "_build", "libpbf_oracle.so")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (no FMA contraction, so rounding follows the source)."""
+    if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
+        os.makedirs(os.path.dirname(LIB), exist_ok=True)
+        tmp = LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-o", tmp, SRC])
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class _Desc(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("ntree", C.c_int * 3), ("tree_h", C.c_double * 3),
+                ("degree", C.c_int), ("max_level", C.c_int), ("tree_exists", C.c_void_p),
+                ("active_top_z", C.c_double), ("dirichlet_faces", C.c_uint),
+                ("n_regions", C.c_int), ("regions", C.c_void_p),
+                ("powder_z0", C.c_double), ("powder_z1", C.c_double)]
+
+
+class _Mat(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("rho", "c", "k0", "k1", "Tk0", "Tk1", "latent", "Tm",
+                                          "sigma", "powder_k_scale", "T_dirichlet")]
+
+
+class _Laser(C.Structure):
+    _fields_ = [("n_seg", C.c_int), ("seg", C.c_void_p), ("power", C.c_void_p),
+                ("eta", C.c_double), ("radius", C.c_double), ("volumetric", C.c_int),
+                ("h_powder", C.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        L = _lib
+        L.or_mesh_build.restype = C.c_void_p
+        L.or_mesh_build.argtypes = [C.POINTER(_Desc)]
+        L.or_mesh_free.argtypes = [C.c_void_p]
+        L.or_lambda_max.restype = C.c_double
+        L.or_adjoint.restype = C.c_double
+        L.or_objective.restype = C.c_double
+        L.or_capp.restype = C.c_double
+        L.or_cond.restype = C.c_double
+        L.or_implicit.restype = C.c_int
+    return _lib
+
+
+def _ptr(a):
+    return C.c_void_p(a.ctypes.data) if a is not None else C.c_void_p(0)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def material(m: dict) -> _Mat:
+    return _Mat(*[float(m[n]) for n, _ in _Mat._fields_])
+
+
+class _LaserHolder:
+    def __init__(self, ls: dict, instance: int = 0):
+        self.seg = _f64(ls["seg"])
+        pw = np.atleast_2d(_f64(ls["power"]))
+        self.power = np.ascontiguousarray(pw[instance])
+        self.s = _Laser(self.seg.shape[0], _ptr(self.seg), _ptr(self.power), ls["eta"], ls["radius"],
+                        int(ls.get("volumetric", 0)), float(ls.get("h_powder", 40e-6)))
+
+    @property
+    def ref(self):
+        return C.byref(self.s)
+
+
+class Mesh:
+    """Oracle mesh built from a descriptor dict (see inputs.mesh_desc)."""
+
+    def __init__(self, desc: dict):
+        self.desc = desc
+        regs = np.zeros((max(1, len(desc["regions"])), 9))
+        for i, (k, a, b, r, lv) in enumerate(desc["regions"]):
+            regs[i] = [k, *a, *b, r, lv]
+        self._regs = regs
+        te = desc.get("tree_exists")
+        self._te = None if te is None else np.ascontiguousarray(te, np.uint8)
+        d = _Desc((C.c_double * 3)(*desc["origin"]), (C.c_int * 3)(*desc["ntree"]),
+                  (C.c_double * 3)(*desc["tree_h"]), desc["degree"], desc["max_level"],
+                  _ptr(self._te), desc["active_top_z"], desc["dirichlet_faces"],
+                  len(desc["regions"]), _ptr(regs), desc["powder_z0"], desc["powder_z1"])
+        self.h = lib().or_mesh_build(C.byref(d))
+        cnt = np.zeros(8, np.int64)
+        lib().or_mesh_counts(C.c_void_p(self.h), _ptr(cnt))
+        (self.n_leaves, self.n_active, self.n_dofs, self.n_hanging, self.n_con, self.n_colours,
+         self.n_top, self.npc) = (int(v) for v in cnt)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.or_mesh_free(C.c_void_p(self.h))
+            self.h = None
+
+    def tables(self) -> dict:
+        t = dict(leaves=np.zeros((self.n_leaves, 5), np.int64),
+                 material=np.zeros(self.n_leaves, np.uint8),
+                 cell_dofs=np.zeros((self.n_active, self.npc), np.int32),
+                 con_ptr=np.zeros(self.n_hanging + 1, np.int32),
+                 con_idx=np.zeros(self.n_con, np.int32),
+                 con_w=np.zeros(self.n_con, np.float64),
+                 hang_coord=np.zeros((self.n_hanging, 3), np.int64),
+                 dof_coord=np.zeros((self.n_dofs, 3), np.int64),
+                 dirichlet=np.zeros(self.n_dofs, np.uint8),
+                 colour=np.zeros(self.n_active, np.int32),
+                 top=np.zeros(self.n_active, np.uint8))
+        lib().or_mesh_tables(C.c_void_p(self.h), *[_ptr(t[k]) for k in
+                             ("leaves", "material", "cell_dofs", "con_ptr", "con_idx", "con_w",
+                              "hang_coord", "dof_coord", "dirichlet", "colour", "top")])
+        return t
+
+    def dof_xyz(self) -> np.ndarray:
+        """Physical dof coordinates [n][3] (for building smooth seeded fields)."""
+        c = self.tables()["dof_coord"].astype(np.float64)
+        d = self.desc
+        L, p = d["max_level"], d["degree"]
+        return np.array(d["origin"]) + np.array(d["tree_h"]) * c / (p * 2.0 ** L)
+
+    def set_material(self, mat_active: np.ndarray):
+        m = np.ascontiguousarray(mat_active, np.uint8)
+        lib().or_mesh_set_material(C.c_void_p(self.h), _ptr(m))
+
+    # ---- operators -------------------------------------------------------------------
+    def residual(self, mat, T, ls=None, t=0.0, s=1.0, instance=0):
+        T = _f64(T)
+        fd, fv, Cm = (np.zeros(self.n_dofs) for _ in range(3))
+        lh = _LaserHolder(ls, instance) if ls is not None else None
+        lib().or_residual(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(T),
+                          lh.ref if lh else None, C.c_double(t), _ptr(fd), _ptr(fv), _ptr(Cm))
+        return fd, fv, Cm
+
+    def explicit(self, mat, T, ls, t0, dt, nsteps, s=1.0, instance=0):
+        T = _f64(T).copy()
+        lh = _LaserHolder(ls, instance) if ls is not None else None
+        lib().or_explicit(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(T),
+                          lh.ref if lh else None, C.c_double(t0), C.c_double(dt), C.c_int(nsteps))
+        return T
+
+    def lambda_max(self, mat, x0, max_iter=200, rtol=1e-6, s=1.0):
+        x0 = _f64(x0)
+        it = C.c_int(0)
+        lam = lib().or_lambda_max(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(x0),
+                                  C.c_int(max_iter), C.c_double(rtol), C.byref(it))
+        return lam, it.value
+
+    def lumped_capacity(self, mat, T):
+        out = np.zeros(self.n_dofs)
+        lib().or_lumped_capacity(C.c_void_p(self.h), C.byref(material(mat)), _ptr(_f64(T)), _ptr(out))
+        return out
+
+    def apply_implicit(self, mat, dt, x):
+        y = np.zeros(self.n_dofs)
+        lib().or_apply_implicit(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), _ptr(_f64(x)), _ptr(y))
+        return y
+
+    def implicit_diagonal(self, mat, dt):
+        y = np.zeros(self.n_dofs)
+        lib().or_implicit_diagonal(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), _ptr(y))
+        return y
+
+    def chebyshev(self, mat, dt, degree, lmin, lmax, r):
+        z = np.zeros(self.n_dofs)
+        lib().or_chebyshev(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), C.c_int(degree),
+                           C.c_double(lmin), C.c_double(lmax), _ptr(_f64(r)), _ptr(z))
+        return z
+
+    def lanczos_bounds(self, mat, dt, b, n_iter=30):
+        out = np.zeros(2)
+        lib().or_lanczos_bounds(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), _ptr(_f64(b)),
+                                C.c_int(n_iter), _ptr(out))
+        return float(out[0]), float(out[1])
+
+    def implicit(self, mat, T, dt, nsteps, rtol, max_it, degree, lmin, lmax):
+        T = _f64(T).copy()
+        iters = np.zeros(nsteps, np.int32)
+        st = lib().or_implicit(C.c_void_p(self.h), C.byref(material(mat)), _ptr(T), C.c_double(dt),
+                               C.c_int(nsteps), C.c_double(rtol), C.c_int(max_it), C.c_int(degree),
+                               C.c_double(lmin), C.c_double(lmax), _ptr(iters))
+        return T, iters, st
+
+    def adjoint(self, mat, T0, ls, t0, dt, nsteps, T_target=2300.0, p_exp=16.0, s=1.0, instance=0):
+        lh = _LaserHolder(ls, instance)
+        grad = np.zeros(lh.seg.shape[0] + 1)
+        J = lib().or_adjoint(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(_f64(T0)), lh.ref,
+                             C.c_double(t0), C.c_double(dt), C.c_int(nsteps), C.c_double(T_target),
+                             C.c_double(p_exp), _ptr(grad))
+        return J, grad
+
+    def objective(self, mat, T0, ls, t0, dt, nsteps, T_target=2300.0, p_exp=16.0, s=1.0, instance=0):
+        lh = _LaserHolder(ls, instance)
+        return lib().or_objective(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(_f64(T0)),
+                                  lh.ref, C.c_double(t0), C.c_double(dt), C.c_int(nsteps),
+                                  C.c_double(T_target), C.c_double(p_exp))
+
+    def surface_weights(self):
+        w = np.zeros(self.n_dofs)
+        lib().or_surface_weights(C.c_void_p(self.h), _ptr(w))
+        return w
+
+
+def transfer(old: Mesh, T_old, new: Mesh, T_init):
+    out = np.zeros(new.n_dofs)
+    lib().or_transfer(C.c_void_p(old.h), _ptr(_f64(T_old)), C.c_void_p(new.h), C.c_double(T_init), _ptr(out))
+    return out
+
+
+def capp(mat, T):
+    return lib().or_capp(C.byref(material(mat)), C.c_double(T))
+
+
+def cond(mat, T, mat_id=0, s=1.0):
+    return lib().or_cond(C.byref(material(mat)), C.c_double(T), C.c_int(mat_id), C.c_double(s))

@@ -1,0 +1,180 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module only describes workloads: mesh descriptors, material constants, laser paths and
+seeded random fields. It holds none of the method's arithmetic, so both the CUDA path and the
+oracle can take their inputs from it without sharing any computation.
+
+Workloads (synthetic stand-ins shaped like the paper's; no paper dataset is used):
+  c1  uniform Q1 brick 64x32x16 cells on 1.0x0.5x0.25 mm, constant Ti-6Al-4V-like material,
+      one scan track (y = 0.25 mm, +x at 0.8 m/s), Dirichlet bottom.
+  c2  Q2 octree mesh on 2x2x1 mm (40 um trees, 3 levels -> 5 um cells) refined inside a
+      150 um ball around the laser spot, nonlinear k(T) and apparent capacity, 10 serpentine
+      hatch tracks at 100 um spacing, v = 1 m/s.
+  c3  the c1 brick with an extra tree row above it, used for a newly activated powder layer
+      of three cells (46.875 um) and an implicit cool-down.
+  c4  Q2 brick 1.0x0.5x0.25 mm refined to 7.8 um within a distance of the scan line,
+      16 laser-power segments and a conductivity scale per instance.
+Material constants of the paper's bridge example (Table mat_params) are given as BRIDGE.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# region kinds
+BALL = 0
+BOX = 1
+
+DIRICHLET_BOTTOM = 1 << 4
+
+# ---------------------------------------------------------------------------------------
+# materials: rho, c, conductivity ramp (k0 at Tk0 .. k1 at Tk1), latent heat Gaussian
+# (latent, Tm, sigma; sigma = 0 disables it), powder conductivity factor, Dirichlet value,
+# and T_ref, the offset the FP32 operator subtracts before rounding.
+# ---------------------------------------------------------------------------------------
+
+TI64_CONST = dict(rho=4430.0, c=526.0, k0=6.7, k1=6.7, Tk0=300.0, Tk1=300.0,
+                  latent=0.0, Tm=1903.0, sigma=0.0, powder_k_scale=0.1,
+                  T_dirichlet=353.0, T_ref=353.0)
+
+TI64_NONLIN = dict(rho=4430.0, c=526.0, k0=6.7, k1=28.0, Tk0=300.0, Tk1=1928.0,
+                   latent=2.86e5, Tm=1903.0, sigma=12.5, powder_k_scale=0.1,
+                   T_dirichlet=353.0, T_ref=353.0)
+
+# Paper, Table mat_params (stainless steel, bridge example): k = 20, rho = 7430, c = 965
+BRIDGE = dict(rho=7430.0, c=965.0, k0=20.0, k1=20.0, Tk0=303.0, Tk1=303.0,
+              latent=0.0, Tm=1700.0, sigma=0.0, powder_k_scale=0.01,
+              T_dirichlet=303.0, T_ref=303.0)
+
+T0 = 353.0
+
+
+def mesh_desc(ntree, tree_h, degree, max_level, regions=(), origin=(0.0, 0.0, 0.0),
+              active_top_z=1e30, dirichlet_faces=DIRICHLET_BOTTOM, tree_exists=None,
+              powder_z0=1e30, powder_z1=1e30):
+    """Plain dict describing a forest of axis-aligned octrees on a brick of trees.
+
+    regions: sequence of (kind, a[3], b[3], radius, level). A leaf is refined to `level`
+    when its box lies closer than `radius` to the region core (a point for BALL, the box
+    [a, b] for BOX)."""
+    return dict(origin=tuple(float(v) for v in origin), ntree=tuple(int(v) for v in ntree),
+                tree_h=tuple(float(v) for v in tree_h), degree=int(degree),
+                max_level=int(max_level),
+                regions=[(int(k), tuple(map(float, a)), tuple(map(float, b)), float(r), int(lv))
+                         for (k, a, b, r, lv) in regions],
+                active_top_z=float(active_top_z), dirichlet_faces=int(dirichlet_faces),
+                tree_exists=None if tree_exists is None else np.ascontiguousarray(tree_exists, np.uint8),
+                powder_z0=float(powder_z0), powder_z1=float(powder_z1))
+
+
+def uniform_region(level, big=1e6):
+    """A box region covering any domain, refining every leaf to `level`."""
+    return (BOX, (-big, -big, -big), (big, big, big), 1e-9, level)
+
+
+def laser(segments, power, eta=0.35, radius=40e-6, volumetric=False, h_powder=40e-6):
+    """segments [n][6] = (x0, y0, x1, y1, t0, t1); power [n] or [batch][n] in W."""
+    return dict(seg=np.ascontiguousarray(segments, np.float64),
+                power=np.ascontiguousarray(power, np.float64), eta=float(eta),
+                radius=float(radius), volumetric=int(bool(volumetric)), h_powder=float(h_powder))
+
+
+def track(x0, y, x1, v, t0=0.0):
+    return (x0, y, x1, y, t0, t0 + abs(x1 - x0) / v)
+
+
+# ---------------------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------------------
+
+def c1_mesh(ntree_z=4, active_top_z=1e30):
+    return mesh_desc((16, 8, ntree_z), (62.5e-6,) * 3, 1, 2, [uniform_region(2)],
+                     active_top_z=active_top_z)
+
+
+def c1_laser(power=200.0):
+    return laser([track(0.0, 0.25e-3, 1.0e-3, 0.8)], [power], eta=0.35, radius=40e-6)
+
+
+def c2_spot_regions(x, y, z_top=1.0e-3, radius=150e-6, level=3):
+    return [(BALL, (x, y, z_top), (x, y, z_top), radius, level)]
+
+
+def c2_mesh(spot=(0.5e-3, 0.55e-3)):
+    return mesh_desc((50, 50, 25), (40e-6,) * 3, 2, 3, c2_spot_regions(*spot))
+
+
+def c2_laser(power=200.0, v=1.0, n_tracks=10):
+    segs, t = [], 0.0
+    for k in range(n_tracks):
+        y = 0.55e-3 + 1e-4 * k
+        a, b = (0.5e-3, 1.5e-3) if k % 2 == 0 else (1.5e-3, 0.5e-3)
+        segs.append(track(a, y, b, v, t))
+        t = segs[-1][5]
+    return laser(segs, [power] * n_tracks, eta=0.35, radius=40e-6)
+
+
+def c3_mesh(active_top_z=0.25e-3):
+    """c1 brick plus one more tree row; cells above active_top_z are inactive."""
+    return c1_mesh(ntree_z=5, active_top_z=active_top_z)
+
+
+C3_LAYER_TOP = 0.25e-3 + 3 * 15.625e-6
+
+
+def c4_mesh(radius=80e-6):
+    line = (BOX, (0.0, 0.25e-3, 0.25e-3), (1.0e-3, 0.25e-3, 0.25e-3), radius, 3)
+    return mesh_desc((16, 8, 4), (62.5e-6,) * 3, 2, 3, [uniform_region(1), line])
+
+
+def c4_laser(powers, v=0.8, n_seg=16, steps_per_seg=125, dt=None, y=0.25e-3):
+    """Single track split into n_seg pieces of equal duration; powers [batch][n_seg]."""
+    powers = np.atleast_2d(np.asarray(powers, np.float64))
+    if dt is None:
+        seg_len = 1.0e-3 / n_seg
+        segs = [track(k * seg_len, y, (k + 1) * seg_len, v, k * seg_len / v) for k in range(n_seg)]
+    else:
+        dur = steps_per_seg * dt
+        segs = [(v * k * dur, y, v * (k + 1) * dur, y, k * dur, (k + 1) * dur) for k in range(n_seg)]
+    return laser(segs, powers, eta=0.35, radius=40e-6)
+
+
+def c4_params(batch, n_seg=16, seed=2302):
+    """Per-instance laser powers P ~ U[150, 250] W and conductivity scales s ~ U[0.8, 1.2]."""
+    rng = np.random.default_rng(seed)
+    P = rng.uniform(150.0, 250.0, size=(batch, n_seg))
+    s = rng.uniform(0.8, 1.2, size=batch)
+    return P, s
+
+
+# ---------------------------------------------------------------------------------------
+# seeded fields
+# ---------------------------------------------------------------------------------------
+
+def random_field(n, seed, lo=T0, hi=2600.0, batch=None):
+    rng = np.random.default_rng(seed)
+    shape = (n,) if batch is None else (n, batch)
+    return rng.uniform(lo, hi, size=shape)
+
+
+def smooth_field(coords, seed, lo=T0, hi=2600.0, batch=None):
+    """Smooth seeded temperature field from dof coordinates (physical units, [n][3]):
+    a sum of a few random Gaussian bumps, clipped to [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    nb = 1 if batch is None else batch
+    out = np.empty((coords.shape[0], nb))
+    ext = coords.max(axis=0) - coords.min(axis=0) + 1e-12
+    for b in range(nb):
+        v = np.full(coords.shape[0], lo)
+        for _ in range(4):
+            c = coords.min(axis=0) + rng.uniform(0, 1, 3) * ext
+            w = rng.uniform(0.1, 0.4) * ext.max()
+            amp = rng.uniform(0.3, 1.0) * (hi - lo)
+            d2 = ((coords - c) ** 2).sum(axis=1)
+            v = v + amp * np.exp(-d2 / (w * w))
+        out[:, b] = np.clip(v, lo, hi)
+    return out[:, 0] if batch is None else out
+
+
+def start_vector(n, seed=7):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=n)

@@ -1,0 +1,320 @@
+"""Pins of the oracle's finite-element operator, time steppers, solvers and adjoint against
+what the paper and the mathematics fix: textbook element matrices, closed forms, the paper's
+printed critical time step, conservation, exact polynomial reproduction and finite
+differences. A plausible slip anywhere in the oracle (dropped term, wrong sign, transposed
+index, wrong metric factor) fails at least one of these."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from paper_2302_05164_gb300 import inputs as I
+from tests import textbook as TB
+
+def golden(name):
+    out = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                out[k] = float(v)
+    return out
+
+
+UNIT = dict(rho=1.0, c=1.0, k0=1.0, k1=1.0, Tk0=0.0, Tk1=0.0, latent=0.0, Tm=0.0, sigma=0.0,
+            powder_k_scale=0.1, T_dirichlet=0.0)
+
+
+def amr_desc(p, dirichlet=0, top=1e30):
+    regions = [(I.BALL, (0.35, 0.4, 0.9), (0, 0, 0), 0.45, 3),
+               (I.BOX, (1.2, 0.2, 0.3), (1.3, 0.3, 0.5), 0.05, 2)]
+    return I.mesh_desc((2, 1, 1), (1.0, 1.0, 1.0), p, 3, regions, dirichlet_faces=dirichlet, active_top_z=top)
+
+
+def interior(m, desc):
+    c = m.tables()["dof_coord"]
+    N = np.array(desc["ntree"]) * desc["degree"] << desc["max_level"]
+    return np.all((c > 0) & (c < N), axis=1)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_operator_equals_textbook_kronecker(oracle_mod, p):
+    ntree, L = (3, 2, 1), 1
+    th = (0.4, 0.3, 0.5)
+    d = I.mesh_desc(ntree, th, p, L, [I.uniform_region(L)])
+    m = oracle_mod.Mesh(d)
+    ncell = [n << L for n in ntree]
+    h = [t / (1 << L) for t in th]
+    K, M = TB.brick_matrices(p, ncell, h)
+    lex = TB.lex_index(m.tables()["dof_coord"], p, ncell)
+    mat = dict(UNIT, k0=2.5, k1=2.5, rho=3.0, c=0.7)
+    T = np.random.default_rng(0).normal(size=m.n_dofs)
+    Tl = np.zeros(K.shape[0])
+    Tl[lex] = T
+    fd, fv, Cm = m.residual(mat, T)
+    ref = -2.5 * (K @ Tl)[lex]
+    assert np.max(np.abs(fd - ref)) <= 1e-12 * np.max(np.abs(ref))
+    assert np.allclose(Cm, 3.0 * 0.7 * M.sum(axis=1)[lex], rtol=1e-13, atol=0)
+    assert np.all(fv == 0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_patch_test_across_hanging_faces(oracle_mod, p):
+    d = amr_desc(p)
+    m = oracle_mod.Mesh(d)
+    assert m.n_hanging > 0
+    x = m.dof_xyz()
+    inner = interior(m, d)
+    k = 1.7
+    mat = dict(UNIT, k0=k, k1=k)
+    if p == 1:
+        # linear field: zero residual on every interior dof
+        u = 0.3 + 1.1 * x[:, 0] - 0.7 * x[:, 1] + 2.0 * x[:, 2]
+        fd, _, Cm = m.residual(mat, u)
+        assert np.max(np.abs(fd[inner])) < 1e-12
+    else:
+        # quadratic field, Laplacian 2*(1 + 2 - 0.5): f_i = k lap(u) int N_i on interior dofs
+        u = x[:, 0] ** 2 + 2 * x[:, 1] ** 2 - 0.5 * x[:, 2] ** 2 + 0.3 * x[:, 0] * x[:, 1] + x[:, 2]
+        fd, _, Cm = m.residual(mat, u)
+        lap = 2 * (1 + 2 - 0.5)
+        err = fd[inner] - k * lap * Cm[inner]
+        assert np.max(np.abs(err)) < 1e-12 * np.max(np.abs(fd[inner]))
+
+
+def test_nonlinear_conductivity_closed_form(oracle_mod):
+    """u = Ta + a x with k(T) linear on the ramp: div(k grad u) = k' a^2 exactly (Q2)."""
+    d = amr_desc(2)
+    m = oracle_mod.Mesh(d)
+    x = m.dof_xyz()
+    mat = dict(UNIT, k0=6.7, k1=28.0, Tk0=300.0, Tk1=1928.0)
+    a = 400.0
+    u = 700.0 + a * x[:, 0]  # 700..1500 K over x in [0, 2]: inside the ramp
+    fd, _, Cm = m.residual(mat, u)
+    inner = interior(m, d)
+    kp = (28.0 - 6.7) / (1928.0 - 300.0)
+    ref = kp * a * a * Cm[inner]
+    assert np.max(np.abs(fd[inner] - ref)) < 1e-10 * np.max(np.abs(ref))
+    # powder cells scale k; a conductivity scale s scales f_diff linearly
+    fd2, _, _ = m.residual(mat, u, s=1.3)
+    assert np.allclose(fd2, 1.3 * fd, rtol=1e-12, atol=1e-12 * np.abs(fd).max())
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_conservation_symmetry_capacity(oracle_mod, p):
+    d = amr_desc(p, top=0.8)
+    m = oracle_mod.Mesh(d)
+    rng = np.random.default_rng(1)
+    mat = dict(I.TI64_NONLIN)
+    T = rng.uniform(300, 2600, m.n_dofs)
+    fd, _, Cm = m.residual(mat, T)
+    assert abs(fd.sum()) < 1e-12 * np.abs(fd).sum()          # K 1 = 0: no flux leaves
+    lin = dict(UNIT, k0=2.0, k1=2.0)
+    xa, xb = rng.normal(size=(2, m.n_dofs))
+    ka, _, _ = m.residual(lin, xa)
+    kb, _, _ = m.residual(lin, xb)
+    assert abs(xb @ ka - xa @ kb) < 1e-12 * abs(xb @ ka)      # symmetric stiffness
+    Cc = m.lumped_capacity(dict(UNIT, rho=2.0, c=3.0), T)
+    lv = m.tables()["leaves"]
+    vol = float(((0.5 ** lv[:, 3]) ** 3 * lv[:, 4]).sum())   # union of active cells
+    assert np.all(Cc > 0) and abs(Cc.sum() - 6.0 * vol) < 1e-12 * 6.0 * vol
+
+
+def test_apparent_capacity_integrates_latent_heat(oracle_mod):
+    mat = I.TI64_NONLIN
+    T = np.linspace(mat["Tm"] - 20 * mat["sigma"], mat["Tm"] + 20 * mat["sigma"], 40001)
+    c = np.array([oracle_mod.capp(mat, t) for t in T])
+    lat = np.trapezoid(c - mat["c"], T)
+    assert abs(lat - mat["latent"]) < 1e-8 * mat["latent"]
+    peak = mat["c"] + mat["latent"] / (mat["sigma"] * math.sqrt(2 * math.pi))
+    assert abs(oracle_mod.capp(mat, mat["Tm"]) - peak) < 1e-9 * peak
+    # conductivity: clamped linear ramp
+    assert oracle_mod.cond(mat, 100.0) == 6.7 and oracle_mod.cond(mat, 5000.0) == 28.0
+    assert abs(oracle_mod.cond(mat, 1114.0) - (6.7 + 21.3 * 0.5)) < 1e-12
+    assert abs(oracle_mod.cond(mat, 1114.0, 1, 1.2) - 0.1 * 1.2 * (6.7 + 21.3 * 0.5)) < 1e-12
+    # uniform state: lumped capacity integrates rho c_app(T*)
+    m = oracle_mod.Mesh(amr_desc(2))
+    Cm = m.lumped_capacity(mat, np.full(m.n_dofs, 1900.0))
+    assert abs(Cm.sum() - mat["rho"] * oracle_mod.capp(mat, 1900.0) * 2.0) < 1e-10 * Cm.sum()
+
+
+def test_laser_total_power(oracle_mod):
+    """The surface Gaussian 2 eta P/(pi r^2) exp(-2 d^2/r^2) integrates to eta P."""
+    d = I.mesh_desc((4, 4, 1), (100e-6, 100e-6, 100e-6), 2, 3, [I.uniform_region(3)])
+    m = oracle_mod.Mesh(d)
+    ls = I.laser([(0.2e-3, 0.2e-3, 0.2e-3, 0.2e-3, 0.0, 1.0)], [200.0], eta=0.35, radius=40e-6)
+    _, fv, _ = m.residual(I.TI64_CONST, np.full(m.n_dofs, 353.0), ls, t=0.5)
+    assert abs(fv.sum() - 70.0) < 1e-4 * 70.0
+    # off-time: no source; segment timing is [t0, t1)
+    _, fv0, _ = m.residual(I.TI64_CONST, np.full(m.n_dofs, 353.0), ls, t=1.0)
+    assert np.all(fv0 == 0)
+
+
+def test_critical_time_step_closed_form_and_paper_value(oracle_mod):
+    # uniform Q1, lumped capacity, Neumann: lambda_max(C~^-1 K) = 4 alpha / h^2 exactly
+    d = I.mesh_desc((2, 2, 2), (1.0, 1.0, 1.0), 1, 2, [I.uniform_region(2)], dirichlet_faces=0)
+    m = oracle_mod.Mesh(d)
+    mat = dict(UNIT, k0=3.0, k1=3.0, rho=2.0, c=1.5)
+    lam, it = m.lambda_max(mat, I.start_vector(m.n_dofs), max_iter=2000, rtol=1e-13)
+    alpha, h = 3.0 / 3.0, 0.25
+    assert abs(lam - 4 * alpha / h ** 2) < 1e-6 * lam
+    # Paper, Sec. 5.1: bridge material (Table mat_params) on 40 um Q1 cells gives
+    # dt_max = 2.9e-4 s from Eq. (explicit_time_step)
+    g = golden("bridge_critical_dt.txt")
+    mat = dict(I.BRIDGE, k0=g["k_W_per_mK"], k1=g["k_W_per_mK"], rho=g["rho_kg_per_m3"], c=g["c_J_per_kgK"])
+    d = I.mesh_desc((2, 2, 2), (4 * g["h_m"],) * 3, 1, 2, [I.uniform_region(2)])
+    m = oracle_mod.Mesh(d)
+    lam, it = m.lambda_max(mat, I.start_vector(m.n_dofs), max_iter=3000, rtol=1e-10)
+    dt = 2.0 / lam
+    assert round(dt, 5) == g["dt_max_s"]
+
+
+def test_explicit_cosine_mode_multiplier(oracle_mod):
+    """Q1 lumped, Neumann: cos(pi x) at the nodes is an eigenvector of C~^-1 K with
+    eigenvalue alpha (2/h^2)(1 - cos(pi h)); one Euler step multiplies it by 1 - dt lambda."""
+    n = 16
+    d = I.mesh_desc((n, 1, 1), (1.0 / n,) * 3, 1, 0, [], dirichlet_faces=0)
+    m = oracle_mod.Mesh(d)
+    x = m.dof_xyz()[:, 0]
+    h = 1.0 / n
+    mat = dict(UNIT, k0=0.8, k1=0.8, rho=2.0, c=0.5)
+    alpha = 0.8
+    lam = alpha * 2 / h ** 2 * (1 - math.cos(math.pi * h))
+    dt = 0.9 / (4 * alpha / h ** 2)  # stable: dt lambda_max = 0.9 < 2
+    T0 = 10.0 + np.cos(math.pi * x)
+    T1 = m.explicit(mat, T0, None, 0.0, dt, 3)
+    assert np.max(np.abs(T1 - (10.0 + (1 - dt * lam) ** 3 * np.cos(math.pi * x)))) < 1e-13
+
+
+def test_explicit_q2_converges_to_exact_decay(oracle_mod):
+    errs = []
+    for n in (4, 8):
+        d = I.mesh_desc((n, 1, 1), (1.0 / n,) * 3, 2, 0, [], dirichlet_faces=0)
+        m = oracle_mod.Mesh(d)
+        x = m.dof_xyz()[:, 0]
+        lam, _ = m.lambda_max(UNIT, I.start_vector(m.n_dofs), max_iter=500, rtol=1e-10)
+        t_end = 0.02
+        nst = int(math.ceil(t_end / (0.25 / lam)))
+        dt = t_end / nst
+        T = m.explicit(UNIT, np.cos(math.pi * x), None, 0.0, dt, nst)
+        errs.append(np.max(np.abs(T - math.exp(-math.pi ** 2 * t_end) * np.cos(math.pi * x))))
+    assert errs[1] < errs[0] / 3.5
+
+
+def kron_implicit(p, ntree, L, th, mat, dt):
+    ncell = [n << L for n in ntree]
+    h = [t / (1 << L) for t in th]
+    K, M = TB.brick_matrices(p, ncell, h)
+    return mat["rho"] * mat["c"] / dt * M + mat["k0"] * K
+
+
+def test_implicit_step_matches_dense_solve(oracle_mod):
+    p, ntree, L, th = 1, (2, 2, 1), 2, (1e-4, 1e-4, 1e-4)
+    d = I.mesh_desc(ntree, th, p, L, [I.uniform_region(L)])
+    m = oracle_mod.Mesh(d)
+    mat = dict(I.TI64_CONST)
+    dt = 1e-2
+    A = kron_implicit(p, ntree, L, th, mat, dt)
+    t = m.tables()
+    lex = TB.lex_index(t["dof_coord"], p, [n << L for n in ntree])
+    free = t["dirichlet"] == 0
+    rng = np.random.default_rng(5)
+    T = 353.0 + np.where(free, rng.uniform(0, 1000, m.n_dofs), 0.0)
+    lmin, lmax = m.lanczos_bounds(mat, dt, I.start_vector(m.n_dofs))
+    T1, iters, st = m.implicit(mat, T, dt, 1, 1e-13, 200, 5, lmin, 1.1 * lmax)
+    assert st == 0
+    # dense: (C/dt + K) dT = -K T on free rows, dT = 0 on Dirichlet rows
+    Al = np.zeros_like(A)
+    Al[np.ix_(lex, lex)] = 0
+    P = np.zeros((m.n_dofs, A.shape[0]))
+    P[np.arange(m.n_dofs), lex] = 1.0
+    Ad = P @ A @ P.T
+    Kd = P @ (kron_implicit(p, ntree, L, th, dict(mat, rho=0.0), dt)) @ P.T
+    rhs = -(Kd @ T)
+    f = free
+    dT = np.zeros(m.n_dofs)
+    dT[f] = np.linalg.solve(Ad[np.ix_(f, f)], rhs[f])
+    assert np.max(np.abs(T1 - (T + dT))) < 1e-9 * np.max(np.abs(dT))
+    assert iters[0] < 60
+
+
+def test_chebyshev_is_the_shifted_chebyshev_polynomial(oracle_mod):
+    p, ntree, L, th = 1, (2, 1, 1), 1, (1e-4, 1e-4, 1e-4)
+    d = I.mesh_desc(ntree, th, p, L, [I.uniform_region(L)])
+    m = oracle_mod.Mesh(d)
+    mat = dict(I.TI64_CONST)
+    dt = 1e-3
+    t = m.tables()
+    lex = TB.lex_index(t["dof_coord"], p, [n << L for n in ntree])
+    P = np.zeros((m.n_dofs, len(lex)))
+    P[np.arange(m.n_dofs), lex] = 1.0
+    A = P @ kron_implicit(p, ntree, L, th, mat, dt) @ P.T
+    f = t["dirichlet"] == 0
+    Af = A[np.ix_(f, f)]
+    D = np.diag(Af).copy()
+    assert np.allclose(m.implicit_diagonal(mat, dt)[f], D, rtol=1e-13)
+    S = Af / np.sqrt(np.outer(D, D))
+    ev, V = np.linalg.eigh(S)
+    lmin, lmax = 0.9 * ev.min(), 1.1 * ev.max()
+    r = np.zeros(m.n_dofs)
+    r[f] = np.random.default_rng(2).normal(size=f.sum())
+    deg = 5
+    z = m.chebyshev(mat, dt, deg, lmin, lmax, r)
+    theta, delta = (lmax + lmin) / 2, (lmax - lmin) / 2
+    kdeg = deg + 1  # residual polynomial degree after deg+1 Chebyshev steps
+    resid = np.cos(kdeg * np.arccos(np.clip((theta - ev) / delta, -1, 1))) / np.cosh(kdeg * np.arccosh(theta / delta))
+    poly = (1 - resid) / ev                     # z = p(D^-1 A) D^-1 r, 1 - lambda p = residual
+    zs = V @ (poly * (V.T @ (r[f] / np.sqrt(D))))
+    zref = zs / np.sqrt(D)
+    assert np.max(np.abs(z[f] - zref)) < 1e-10 * np.max(np.abs(zref))
+    # Lanczos bounds from 30 Jacobi-PCG steps approach the extreme eigenvalues of D^-1 A
+    lo, hi = m.lanczos_bounds(mat, dt, I.start_vector(m.n_dofs), 30)
+    assert abs(hi - ev.max()) < 1e-6 * ev.max() and abs(lo - ev.min()) < 1e-6 * ev.min()
+
+
+def test_adjoint_matches_central_differences(oracle_mod):
+    d = I.mesh_desc((4, 2, 2), (62.5e-6,) * 3, 1, 1, [I.uniform_region(1)])
+    m = oracle_mod.Mesh(d)
+    mat = dict(I.TI64_NONLIN)
+    T0 = I.smooth_field(m.dof_xyz(), seed=11, lo=353.0, hi=2400.0)
+    dt, nst = 2e-7, 12
+    ls = I.c4_laser([[180.0, 220.0, 240.0]], n_seg=3, steps_per_seg=4, dt=dt, v=0.5, y=0.25e-3)
+    s = 1.05
+    J, g = m.adjoint(mat, T0, ls, 0.0, dt, nst, s=s)
+    assert J > 0 and np.all(np.isfinite(g))
+    for k in range(4):
+        pw = ls["power"].copy()
+        if k < 3:
+            h = 1e-4 * pw[0, k]
+            lp, lm = dict(ls, power=pw.copy()), dict(ls, power=pw.copy())
+            lp["power"][0, k] += h
+            lm["power"][0, k] -= h
+            fd = (m.objective(mat, T0, lp, 0.0, dt, nst, s=s) - m.objective(mat, T0, lm, 0.0, dt, nst, s=s)) / (2 * h)
+        else:
+            h = 1e-4 * s
+            fd = (m.objective(mat, T0, ls, 0.0, dt, nst, s=s + h) - m.objective(mat, T0, ls, 0.0, dt, nst, s=s - h)) / (2 * h)
+        assert abs(g[k] - fd) < 1e-5 * max(abs(fd), 1e-3 * np.abs(g).max()), (k, g[k], fd)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_transfer_reproduces_polynomials_and_fills_new_cells(oracle_mod, p):
+    a = oracle_mod.Mesh(amr_desc(p, top=0.75))
+    regions = [(I.BALL, (1.5, 0.5, 0.9), (0, 0, 0), 0.3, 3)]
+    b = oracle_mod.Mesh(I.mesh_desc((2, 1, 1), (1.0,) * 3, p, 3, regions, active_top_z=0.875))
+    rng = np.random.default_rng(4)
+    coef = rng.normal(size=(p + 1, p + 1, p + 1))
+
+    def u(x):
+        return sum(coef[i, j, k] * x[:, 0] ** i * x[:, 1] ** j * x[:, 2] ** k
+                   for i in range(p + 1) for j in range(p + 1) for k in range(p + 1))
+    xa, xb = a.dof_xyz(), b.dof_xyz()
+    Tb = oracle_mod.transfer(a, u(xa), b, -7.0)
+    lv = a.tables()["leaves"]
+    act = lv[lv[:, 4] == 1]
+    lo = act[:, :3] * p
+    hi = lo + p * (1 << (3 - act[:, 3]))[:, None]
+    cb = b.tables()["dof_coord"]
+    old = np.array([np.any(np.all((lo <= c) & (c <= hi), axis=1)) for c in cb])
+    assert old.sum() < b.n_dofs
+    assert np.max(np.abs(Tb[old] - u(xb[old]))) < 1e-12 * np.abs(u(xb)).max()
+    assert np.all(Tb[~old] == -7.0)
