@@ -1,0 +1,356 @@
+"""Benchmark of the explicit hot path on the adaptive Q2 multi-track workload.
+
+Workload (configuration 2 of the scope): Q2 octree mesh on a 2 x 2 x 1 mm block (40 um trees,
+3 refinement levels -> 5 um cells inside a 150 um ball around the laser spot, 2:1 balanced
+with hanging nodes; 1,066,531 dofs, 132,423 cells), k(T) linear 6.7 -> 28 W/mK over
+300-1928 K, apparent capacity with latent heat 2.86e5 J/kg (Gaussian around 1903 K, nodal
+lumping), surface
+Gaussian laser (P = 200 W, eta = 0.35, r = 40 um, v = 1 m/s, serpentine tracks), forward
+Euler at half the CFL bound. Synthetic seeded initial field: a 2600 K melt pool (50 um) at the
+spot on a 353 K part, 1% seeded noise.
+
+One benchmark step = 50 explicit time steps (the re-adaptation interval of the workload) on
+the resident mesh. value = dof-updates per second over all ranks (GDoF/s). Between timed
+steps the L2 cache is flushed by writing a 256 MB buffer (the working set would otherwise stay
+in the 129 MB L2); each step is timed with CUDA events on the stream the kernels run on.
+
+--impl reference runs the repository's serial FP64 oracle on the host cores instead (a
+bounded sample of the same workload per step) and prints the same JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "explicit-step DoF-updates/s (GDoF/s) and % HBM roofline, FP32-op vs FP64 at stated error"
+WORKLOAD = "C2: Q2 AMR 2x2x1 mm, 5 um cells in a 150 um ball, 1.07M dofs, nonlinear k(T) + latent heat"
+CHUNK = 50                 # explicit steps per benchmark step
+BYTES_PER_DOF_UPDATE = 16  # read T_n and write T_{n+1} in FP64 (c_app(T) recomputed in-kernel)
+
+
+def flops_per_cell_q2_nonlinear():
+    """Floating-point operations of one cell in the FP32 cell kernel (FMA = 2), counted from
+    its arithmetic: 1D passes over the 3 x 3 x 3 tensor with the nonzeros of the Gauss-point
+    tables (S: 7 per line, D: 8 per line), plus the pointwise quadrature-point work. The
+    apparent capacity of the workload is nodal (evaluated in the update, not in this kernel)."""
+    lines = 9
+    s_pass = lines * 7 * 2
+    d_pass = lines * 8 * 2
+    passes = 3 * s_pass                    # values at quadrature points
+    passes += 3 * (d_pass + d_pass)        # gradient and its transpose, three directions
+    passes += 3 * s_pass                   # final integration
+    pointwise = 27 * (5 + 6)               # k(T), metric scaling
+    return passes + pointwise
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample_desc(I):
+    """Bounded sample of the workload for the CPU oracle: the same 40 um trees, 3 levels and
+    150 um refinement ball around the spot, cropped to a 0.32 x 0.32 x 0.32 mm block."""
+    x, y = 0.16e-3, 0.16e-3
+    d = I.mesh_desc((8, 8, 8), (40e-6,) * 3, 2, 3, I.c2_spot_regions(x, y, z_top=0.32e-3))
+    ls = I.laser([(x, y, x + 0.1e-3, y, 0.0, 1e-4)], [200.0], eta=0.35, radius=40e-6)
+    return d, ls
+
+
+def time_oracle(steps, max_seconds=None):
+    """Serial FP64 oracle explicit steps on the sample; returns (dof-updates/s, n_dofs, steps, s)."""
+    from oracle import oracle as O
+    from paper_2302_05164_gb300 import inputs as I
+    O.build()
+    d, ls = oracle_sample_desc(I)
+    m = O.Mesh(d)
+    T = I.melt_pool_field(m.dof_xyz(), (0.16e-3, 0.16e-3, 0.32e-3), 2600.0, 50e-6, seed=21, noise=0.01)
+    dt = 2e-8
+    done, t0 = 0, time.perf_counter()
+    for k in range(steps):
+        T = m.explicit(I.TI64_NONLIN_Q2, T, ls, k * dt, dt, 1)
+        done += 1
+        if max_seconds and time.perf_counter() - t0 > max_seconds:
+            break
+    el = time.perf_counter() - t0
+    return m.n_dofs * done / el, m.n_dofs, done, el
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group(backend)
+    return ws, rank
+
+
+def run_reference(args):
+    ws, rank = dist_setup()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        time_oracle(1)
+    rates = []
+    n_dofs = 0
+    for _ in range(args.steps):
+        r, n_dofs, _, _ = time_oracle(1)
+        rates.append(r)
+    total_updates = n_dofs * args.steps
+    seconds = sum(n_dofs / r for r in rates)
+    value = total_updates / seconds / 1e9
+    sample = "1 serial FP64 oracle explicit step per benchmark step on a 0.32 mm^3 crop of the workload " \
+             f"({n_dofs} dofs, same trees, refinement ball, material and laser)"
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": args.gpus,
+                      "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * seconds / args.steps,
+                      "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                      "data": "synthetic", "config": {"workload": WORKLOAD, "sample": "oracle crop"},
+                      "cpu_baseline": {"value": value, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                                       "sample": sample},
+                      "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+def traffic_for_kernel():
+    """DRAM bytes per launch of the cell kernel from the committed ncu summary, if the kernel
+    source is unchanged since that capture (else null)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "cell_kernel_c2_traffic.json")
+    src = os.path.join(ROOT, "paper_2302_05164_gb300", "csrc", "kernels_cell.cu")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        return rec["dram_bytes_per_launch"] if rec.get("kernels_cell_sha256") == h else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="timed loop only (for profiler launch lists)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    from paper_2302_05164_gb300 import inputs as I
+    from paper_2302_05164_gb300 import pbf
+
+    ws, rank = dist_setup()
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    W, K = max(3, args.warmup), args.steps
+
+    desc = I.c2_mesh()
+    mat = I.TI64_NONLIN_Q2
+    mesh = pbf.Mesh(desc)
+    info = mesh.info()
+    n = info["n_dofs"]
+    tab = mesh.tables()
+    xyz = np.array(desc["origin"]) + np.array(desc["tree_h"]) * tab["dof_coord"] / (2 * 2.0 ** desc["max_level"])
+    T0 = I.melt_pool_field(xyz, (0.5e-3, 0.55e-3, 1.0e-3), 2600.0, 50e-6, seed=21 + rank, noise=0.01)
+    ls = I.c2_laser()
+    ctx = pbf.Context(mesh, mat, pbf.PBF_F32OP)
+    # critical step from the CFL estimate with the largest conductivity (Eq. explicit_time_step)
+    if args.quick:
+        dt = 1e-8  # profiler runs: no setup launches before the timed kernels
+    else:
+        cfl = pbf.Context(mesh, dict(mat, k0=mat["k1"], k1=mat["k1"], sigma=0.0, latent=0.0), pbf.PBF_F64)
+        lam, dt_crit, _ = pbf.pbf_estimate_dt(cfl.h, None, 200, 1e-6)
+        cfl.close()
+        dt = 0.5 * dt_crit
+    T = torch.tensor(T0, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def bench_step(k):
+        pbf.pbf_explicit_step(ctx.h, T, ls, k * CHUNK * dt, dt, CHUNK, stream=stream)
+
+    for k in range(W):
+        bench_step(k)
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = pbf.pbf_ctx_launch_count(ctx.h)
+    pbf.pbf_ctx_kernel_time(ctx.h)
+    pbf.pbf_ctx_set_timing(ctx.h, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    with ClockSampler(dev) as clocks:
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            evs[k][0].record(stream)
+            bench_step(W + k)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    pbf.pbf_ctx_set_timing(ctx.h, False)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    cell_ms, cell_launches = pbf.pbf_ctx_kernel_time(ctx.h)
+    gpu_launches = pbf.pbf_ctx_launch_count(ctx.h) - launches0
+    if ws > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = n * CHUNK * K * ws
+    value = updates / (ms * 1e-3) / 1e9
+    peaks, peak_src = load_peaks()
+    out = {"metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": K, "warmup": W,
+           "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "precision": "FP32 operator arithmetic and accumulation; FP64 state and update",
+           "data": "synthetic",
+           "config": {"workload": WORKLOAD, "n_dofs": n, "n_cells": info["n_active"], "n_hanging": info["n_hanging"],
+                      "explicit_steps_per_step": CHUNK, "dt_s": dt, "l2": "flushed between timed steps (256 MB write)",
+                      "parallelism": f"replicas x{ws} (independent instances)"},
+           "gpu_launches": gpu_launches}
+    # roofline of the dominant kernel (cell operator), timed live with events on its stream
+    avg_cell_s = cell_ms * 1e-3 / max(cell_launches, 1)
+    fpc = flops_per_cell_q2_nonlinear()
+    flops_launch = fpc * info["n_active"]
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    achieved = flops_launch / avg_cell_s / 1e12
+    out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                       "frac": achieved / fp32_peak, "traffic": traffic_for_kernel(),
+                       "kernel": "k_cell<2,float,RESIDUAL,nonlinear>", "flops_per_cell": fpc,
+                       "avg_launch_us": avg_cell_s * 1e6, "peak_basis": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    out["hbm_fraction"] = {"algorithmic_bytes_per_dof_update": BYTES_PER_DOF_UPDATE,
+                           "achieved_gbs": value * BYTES_PER_DOF_UPDATE,
+                           "peak_gbs": hbm, "frac": value * BYTES_PER_DOF_UPDATE / hbm,
+                           "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    out["clocks"] = clocks.summary()
+    if not args.quick:
+        # FP64 operator on the same workload (fewer steps: it runs at the FP64 rate)
+        ctx64 = pbf.Context(mesh, mat, pbf.PBF_F64)
+        T64 = torch.tensor(T0, dtype=torch.float64, device="cuda")
+        T32 = torch.tensor(T0, dtype=torch.float64, device="cuda")
+        pbf.pbf_explicit_step(ctx64.h, T64, ls, 0.0, dt, 2, stream=stream)
+        torch.cuda.synchronize()
+        T64.copy_(torch.tensor(T0, dtype=torch.float64, device="cuda"))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        e0.record(stream)
+        pbf.pbf_explicit_step(ctx64.h, T64, ls, 0.0, dt, CHUNK, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v64 = n * CHUNK / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        pbf.pbf_explicit_step(ctx.h, T32, ls, 0.0, dt, CHUNK, stream=stream)
+        torch.cuda.synchronize()
+        err = float((T32 - T64).abs().max() / T64.abs().max())
+        out["fp64"] = {"value": v64, "unit": "GDoF/s", "f32op_speedup": value / ws / v64}
+        out["error"] = {"f32op_vs_f64_rel_maxnorm": err, "after_explicit_steps": CHUNK,
+                        "tolerance": 2e-4, "f64_vs_oracle": "parity-tested to 1e-10 (tests/test_gpu_explicit.py)"}
+        ctx64.close()
+        # end to end through the C ABI with host buffers: pinned H2D of the state, 50 steps,
+        # D2H of the state, every step
+        Th = torch.tensor(T0, dtype=torch.float64).pin_memory()
+        Tout = torch.empty_like(Th).pin_memory()
+        Td = torch.empty(n, dtype=torch.float64, device="cuda")
+        for k in range(2):
+            Td.copy_(Th, non_blocking=True)
+            pbf.pbf_explicit_step(ctx.h, Td, ls, k * CHUNK * dt, dt, CHUNK, stream=stream)
+            Tout.copy_(Td, non_blocking=True)
+        torch.cuda.synchronize()
+        e_ms = 0.0
+        for k in range(K):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            Td.copy_(Th, non_blocking=True)
+            pbf.pbf_explicit_step(ctx.h, Td, ls, k * CHUNK * dt, dt, CHUNK, stream=stream)
+            Tout.copy_(Td, non_blocking=True)
+            b.record(stream)
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
+        out["e2e"] = {"value": n * CHUNK * K * ws / (e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
+                      "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+        if rank == 0 and ws >= 1:
+            rate, n_s, done, secs = time_oracle(3, max_seconds=25.0)
+            out["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                                   "sample": f"{done} serial FP64 oracle explicit steps on a 0.32 mm^3 crop of the "
+                                             f"workload ({n_s} dofs), {secs:.1f} s"}
+    ctx.close()
+    mesh.close()
+    if ws > 1:
+        torch.distributed.barrier()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,279 @@
+/*
+ * pbf.h - C ABI of the GPU (sm_103a) library for the matrix-free thermal powder-bed-fusion
+ * hot path of Proell, Munch, Kronbichler, Wall, Meier, arXiv 2302.05164.
+ *
+ * Conventions for every entry point
+ *  - Returns a pbf_status. PBF_OK on success; otherwise pbf_last_error() gives a message
+ *    (thread-local, valid until the next call on the same thread). No call aborts, traps or
+ *    throws across the ABI.
+ *  - Field arrays named *_dev are caller-owned DEVICE pointers (e.g. torch tensor data_ptr),
+ *    FP64, contiguous, laid out [n_dofs][batch] with the instance index fastest. Input and
+ *    output fields must not alias unless stated.
+ *  - Host pointers (descriptors, tables, laser powers) are read only during the call.
+ *  - pbf_stream is a cudaStream_t (0 = legacy default stream). Work is enqueued on it; a call
+ *    synchronises only when it must return values computed on the device (stated below).
+ *  - pbf_mesh and pbf_ctx are opaque, library-owned, and freed by their destroy calls.
+ *  - After PBF_ECUDA or PBF_EFAULT a context refuses further work with PBF_ESTATE.
+ */
+#ifndef PBF_H
+#define PBF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PBF_OK = 0,
+  PBF_EINVAL = 1,   /* invalid argument or descriptor */
+  PBF_ENOMEM = 2,   /* host or device allocation failed */
+  PBF_ECUDA = 3,    /* a CUDA runtime call failed */
+  PBF_ENOCONV = 4,  /* an iterative solve missed its tolerance */
+  PBF_ENAN = 5,     /* a non-finite value was found in the state */
+  PBF_ETIMEOUT = 6, /* a bounded device wait expired */
+  PBF_EFAULT = 7,   /* a device-side index check failed */
+  PBF_ESTATE = 8    /* object is poisoned or out of date (mesh changed under a context) */
+} pbf_status;
+
+typedef void* pbf_stream; /* cudaStream_t */
+
+const char* pbf_last_error(void);
+const char* pbf_version(void);
+
+/* ------------------------------------------------------------------------------------- */
+/* Mesh (host). Paper Sec. 4.1: coarse hexahedral mesh of uniform trees, a-priori octree   */
+/* refinement, 2:1 balance, Z-curve cell order, inactive cells above the active layer.    */
+/* ------------------------------------------------------------------------------------- */
+
+typedef struct pbf_mesh pbf_mesh;
+
+enum { PBF_REGION_BALL = 0, PBF_REGION_BOX = 1 };
+
+/* Refinement region: a leaf is refined to `level` while its box lies closer than `radius`
+ * to the region core (the point a for a ball, the box [a, b] for a box). Squared distances
+ * are compared in FP64, d2 < radius^2. */
+typedef struct {
+  int kind;
+  int level;
+  double a[3];
+  double b[3];
+  double radius;
+} pbf_region;
+
+/* Forest of ntree[0] x ntree[1] x ntree[2] axis-aligned trees of edge tree_h starting at
+ * origin (metres). Q_degree Lagrange elements, degree 1 or 2, trees refined at most
+ * max_level times (0 <= max_level <= 12). tree_exists (nullable) masks trees of a
+ * boundary-fitted voxel mesh, [nz][ny][nx] with x fastest. Cells whose lower z lies at or
+ * above active_top_z are inactive (no dofs). dirichlet_faces: bit 0 -x, 1 +x, 2 -y, 3 +y,
+ * 4 -z, 5 +z faces of the tree brick carry T = T_dirichlet. Cells whose z-centre lies in
+ * [powder_z0, powder_z1) get material 1 (powder), others material 0 (solid). */
+typedef struct {
+  double origin[3];
+  int ntree[3];
+  double tree_h[3];
+  int degree;
+  int max_level;
+  const uint8_t* tree_exists;
+  double active_top_z;
+  uint32_t dirichlet_faces;
+  int n_regions;
+  const pbf_region* regions;
+  double powder_z0, powder_z1;
+} pbf_mesh_desc;
+
+typedef struct {
+  int64_t n_leaves;      /* all leaves, active or not */
+  int64_t n_active;      /* active cells */
+  int64_t n_dofs;        /* degrees of freedom (hanging nodes are not dofs) */
+  int64_t n_hanging;     /* constrained (hanging) nodes */
+  int64_t n_con_entries; /* entries of the flattened constraint rows */
+  int64_t n_colours;     /* colours of the greedy cell colouring */
+  int64_t n_top_faces;   /* active top faces (laser / objective surface) */
+  int64_t nodes_per_cell;
+  int64_t generation;    /* incremented by every topology change */
+} pbf_mesh_info_t;
+
+/* Host output buffers of pbf_mesh_export, sized from pbf_mesh_info_t; any may be NULL.
+ *  leaves      [n_leaves][5]  anchor x, y, z on the lattice of finest cells, level, active
+ *  material    [n_leaves]     0 solid, 1 powder
+ *  cell_dofs   [n_active][nodes_per_cell] dof id, or -1-r for a node constrained by row r;
+ *              local nodes lexicographic with x fastest
+ *  con_ptr     [n_hanging+1], con_idx/con_w [n_con_entries]: constraint rows (masters sorted)
+ *  hang_coord  [n_hanging][3], dof_coord [n_dofs][3]: node positions in units of
+ *              (finest cell edge)/degree
+ *  dirichlet   [n_dofs], colour [n_active], top [n_active] */
+typedef struct {
+  int64_t* leaves;
+  uint8_t* material;
+  int32_t* cell_dofs;
+  int32_t* con_ptr;
+  int32_t* con_idx;
+  double* con_w;
+  int64_t* hang_coord;
+  int64_t* dof_coord;
+  uint8_t* dirichlet;
+  int32_t* colour;
+  uint8_t* top;
+} pbf_mesh_tables;
+
+/* Builds the canonical mesh: refinement to region targets, full 2:1 balance, Morton order
+ * within trees (trees lexicographic), activity, first-touch dof numbering, hanging-node
+ * constraints (weights = Lagrange basis of the first coarse cell in cell order, chains
+ * substituted, masters merged and sorted), Dirichlet flags, greedy colouring, top faces.
+ * Host only. Errors: PBF_EINVAL (bad descriptor), PBF_ENOMEM. */
+pbf_status pbf_mesh_create(const pbf_mesh_desc* desc, pbf_mesh** out);
+pbf_status pbf_mesh_destroy(pbf_mesh* mesh);
+pbf_status pbf_mesh_info(const pbf_mesh* mesh, pbf_mesh_info_t* out);
+pbf_status pbf_mesh_export(const pbf_mesh* mesh, const pbf_mesh_tables* out);
+
+/* Layer activation (Sec. 4.1; initial condition of Sec. 2 for later-activated parts): raises
+ * the activation height to z_new_top; newly active cells take `material`. Host topology
+ * change only; it records a pending transfer (old dofs -> new dofs) that pbf_mesh_transfer
+ * applies: nodes shared with the old active domain keep their value, new nodes get T_init.
+ * Contexts created before the call return PBF_ESTATE until recreated. */
+pbf_status pbf_mesh_activate_layer(pbf_mesh* mesh, double z_new_top, int material, double T_init);
+
+/* Re-adaptation to a new region set (a-priori refinement around the scan, Sec. 4.1): the
+ * mesh becomes the canonical mesh for the new regions (same trees and activation);
+ * materials follow the old leaf holding each new leaf's anchor. Records a pending transfer
+ * (field interpolation on the old mesh, i.e. prolongation / injection). */
+pbf_status pbf_mesh_adapt(pbf_mesh* mesh, int n_regions, const pbf_region* regions);
+
+/* Applies the pending transfer on the device: T_new_dev[new n_dofs][batch] from
+ * T_old_dev[old n_dofs][batch]. Errors: PBF_ESTATE when no transfer is pending. */
+pbf_status pbf_mesh_transfer(pbf_mesh* mesh, const double* T_old_dev, double* T_new_dev, int batch,
+                             pbf_stream stream);
+
+/* ------------------------------------------------------------------------------------- */
+/* Context: device copy of the mesh tables, material and work space for `batch` instances */
+/* ------------------------------------------------------------------------------------- */
+
+typedef struct pbf_ctx pbf_ctx;
+
+typedef enum { PBF_F64 = 0, PBF_F32OP = 1 } pbf_precision;
+
+enum { PBF_LUMP_QUADRATURE = 0, PBF_LUMP_NODAL = 1 };
+
+/* Material (Sec. 2 heat equation; configuration readings for k(T) and latent heat):
+ * k(T) = k0 + (k1-k0) clamp((T-Tk0)/(Tk1-Tk0), 0, 1) (constant k0 when Tk1 <= Tk0),
+ * multiplied by powder_k_scale on material-1 cells and by the per-instance scale s;
+ * c_app(T) = c + latent/(sigma sqrt(2 pi)) exp(-(T-Tm)^2/(2 sigma^2)) (off when sigma <= 0).
+ * T_ref: offset subtracted from T before the FP32 operator rounds it.
+ * lumping (only matters with latent heat): PBF_LUMP_QUADRATURE, the row sum of the consistent
+ * capacity C~_ii = sum_j C_ij (Sec. 3.2) with c_app at the quadrature points; PBF_LUMP_NODAL,
+ * C~_ii = rho c_app(T_i) sum_j M_ij with the constant-coefficient mass M. For Q2 elements the
+ * quadrature form can turn negative where c_app(T) peaks sharply inside a cell (the Q2 basis
+ * is negative in parts of a cell); the nodal form stays positive. */
+typedef struct {
+  double rho, c;
+  double k0, k1, Tk0, Tk1;
+  double latent, Tm, sigma;
+  double powder_k_scale;
+  double T_dirichlet;
+  double T_ref;
+  int lumping;
+} pbf_material;
+
+/* Moving laser (Sec. 2 heat source). The spot moves linearly over segment k,
+ * seg[k] = {x0, y0, x1, y1, t0, t1}, during t0 <= t < t1 with power power[instance][k]; no
+ * segment active: no source. volumetric = 0: surface flux 2 eta P/(pi r^2) exp(-2 d^2/r^2)
+ * on active top faces; volumetric = 1: the cylinder source 2 eta P/(pi r^2 h_powder)
+ * exp(-2 d^2/r^2) for active_top_z - h_powder < z < active_top_z (Eq. heat_soruce_cylindrical,
+ * W_eff = eta P). At most 64 segments. */
+typedef struct {
+  int n_seg;
+  const double* seg;   /* host [n_seg][6] */
+  const double* power; /* host [batch][n_seg] */
+  double eta, radius;
+  int volumetric;
+  double h_powder;
+} pbf_laser;
+
+/* Uploads the mesh tables and the material; allocates work space for `batch` instances
+ * (1 <= batch <= 1024). precision PBF_F64: operator in FP64; PBF_F32OP: operator arithmetic
+ * and cell accumulation in FP32, state, update, reductions in FP64. */
+pbf_status pbf_ctx_create(const pbf_mesh* mesh, const pbf_material* mat, pbf_precision prec, int batch,
+                          pbf_ctx** out);
+pbf_status pbf_ctx_destroy(pbf_ctx* ctx);
+
+/* Per-instance conductivity scale s (host [batch]); default 1. */
+pbf_status pbf_ctx_set_k_scale(pbf_ctx* ctx, const double* s_host);
+
+/* Evaluates, at state T_dev and time t, the three parts of the semi-discrete right-hand
+ * side (Eq. semi-discrete) and the row-sum lumped capacity (Sec. 3.2):
+ *   fdiff_dev = -P^T sum_e int k(T_h) grad N . grad T_h   (Eq. diffusive_term_evaluation)
+ *   fvol_dev  = P^T sum_e laser source against N
+ *   C_dev     = P^T sum_e int rho c_app(T_h) N
+ * Any output may be NULL. Outputs [n_dofs][batch] FP64. laser may be NULL (no source). */
+pbf_status pbf_eval_residual(pbf_ctx* ctx, const double* T_dev, const pbf_laser* laser, double t,
+                             double* fdiff_dev, double* fvol_dev, double* C_dev, pbf_stream stream);
+
+/* nsteps forward-Euler steps T <- T + dt C~(T)^-1 f(T) on free dofs (Eq. forward_euler),
+ * with the laser at t0 + n dt for step n; Dirichlet dofs hold T_dirichlet. In place on
+ * T_dev [n_dofs][batch]. */
+pbf_status pbf_explicit_step(pbf_ctx* ctx, double* T_dev, const pbf_laser* laser, double t0, double dt, int nsteps,
+                             pbf_stream stream);
+
+/* Largest eigenvalue of C~^-1 K_diff on free dofs by power iteration (Eq. explicit_time_step,
+ * k frozen at k0 scaled by s of instance 0, plain c): x0_dev [n_dofs] start vector (NULL: a
+ * built-in SplitMix64 vector), at most max_iter iterations, stop when successive Rayleigh
+ * quotients differ by <= rtol relative. Writes lambda and dt_crit = 2/lambda. Synchronises. */
+pbf_status pbf_estimate_dt(pbf_ctx* ctx, const double* x0_dev, int max_iter, double rtol, double* lambda_out,
+                           double* dt_crit_out, int* iters_out, pbf_stream stream);
+
+/* Eigenvalue bounds of D^-1 A, A = C/dt + K (consistent capacity, linear material, Dirichlet
+ * rows identity), D = diag(A), from the Lanczos tridiagonal of n_iter Jacobi-PCG steps on
+ * A x = b, x0 = 0 (b_dev [n_dofs]; NULL: built-in SplitMix64 vector). out = {lmin, lmax}.
+ * Synchronises. */
+pbf_status pbf_cheb_bounds(pbf_ctx* ctx, double dt, const double* b_dev, int n_iter, double* out,
+                           pbf_stream stream);
+
+/* nsteps backward-Euler steps of the linear problem (Eq. backward_euler_nonlinear with
+ * constant k and c, no surface terms, no laser): (C/dt + K) dT = f(T_n), T_{n+1} = T_n + dT,
+ * by CG with a Chebyshev(cheb_degree)-Jacobi preconditioner on bounds {lmin, lmax}
+ * (NULL: pbf_cheb_bounds with 30 steps, lmax x 1.1), FP64 dot products, stop at
+ * ||r||_2 <= rtol ||r_0||_2. Instance 0 only (batch must be 1). iters_out (host, nullable)
+ * [nsteps]. Synchronises once per CG iteration. PBF_ENOCONV when a step missed rtol within
+ * max_it (T holds the last iterate). */
+pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt, int nsteps, double rtol, int max_it,
+                              int cheb_degree, const double* cheb_bounds, int* iters_out, pbf_stream stream);
+
+/* Adjoint sweep of the explicit stepper for every instance (objective reading of the
+ * configuration: J = (1/N) sum_{n=1..N} (M_n - T_target)^2, M_n = (sum_i w_i T_{n,i}^p /
+ * sum_i w_i)^(1/p) over top-surface dofs, w_i = int_{top} N_i): forward nsteps from T0_dev
+ * storing n_checkpoints states on a binomial (revolve) schedule, then the reverse recursion
+ * lambda_n = lambda_{n+1} + dt (du/dT)^T lambda_{n+1} + dJ/dT_n, u = C~^-1 f. Gradients with
+ * respect to the laser power of each segment and to the conductivity scale s.
+ * J_out host [batch]; grad_out host [batch][n_seg + 1] (dJ/dP_0..dJ/dP_{n_seg-1}, dJ/ds);
+ * forward_steps_out (nullable): forward steps taken, including recomputation. Synchronises. */
+pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, const pbf_laser* laser, double t0, double dt,
+                             int nsteps, int n_checkpoints, double T_target, double p_exp, double* J_out,
+                             double* grad_out, long long* forward_steps_out, pbf_stream stream);
+
+/* Forward-step count of the binomial checkpoint schedule (Griewank and Walther, revolve)
+ * for nsteps steps and n_snaps stored states; host only. */
+pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_out);
+
+/* Kernel timing of the dominant (cell operator) kernel: when enabled, CUDA events bracket
+ * every cell-operator launch on its stream; pbf_ctx_kernel_time returns the summed elapsed
+ * milliseconds and the launch count since the last reset (synchronises). */
+pbf_status pbf_ctx_set_timing(pbf_ctx* ctx, int enable);
+pbf_status pbf_ctx_kernel_time(pbf_ctx* ctx, double* ms_out, long long* launches_out);
+
+/* The exact conversions of the FP32-operator form, exposed for testing: IEEE-754 binary64 to
+ * binary32 rounding to nearest (ties to even; magnitudes below 2^-126 flush to signed zero;
+ * inputs finite with magnitude < 2^128), and the exact binary32 to binary64 widening
+ * (subnormals flush to signed zero). Device arrays of n elements; enqueued on stream. */
+pbf_status pbf_round_to_f32(const double* x_dev, float* y_dev, int64_t n, pbf_stream stream);
+pbf_status pbf_widen_to_f64(const float* x_dev, double* y_dev, int64_t n, pbf_stream stream);
+
+/* Counts of kernels launched by this context since creation (all kinds). */
+pbf_status pbf_ctx_launch_count(pbf_ctx* ctx, long long* launches_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBF_H */

@@ -38,7 +38,7 @@ class _Desc(C.Structure):
 
 class _Mat(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("rho", "c", "k0", "k1", "Tk0", "Tk1", "latent", "Tm",
-                                          "sigma", "powder_k_scale", "T_dirichlet")]
+                                          "sigma", "powder_k_scale", "T_dirichlet")] + [("lumping", C.c_int)]
 
 
 class _Laser(C.Structure):
@@ -76,7 +76,7 @@ def _f64(a):
 
 
 def material(m: dict) -> _Mat:
-    return _Mat(*[float(m[n]) for n, _ in _Mat._fields_])
+    return _Mat(*[float(m[n]) for n, _ in _Mat._fields_[:-1]], int(m.get("lumping", 0)))
 
 
 class _LaserHolder:

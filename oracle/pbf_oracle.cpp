@@ -56,6 +56,7 @@ typedef struct {
   double latent, Tm, sigma;
   double powder_k_scale;
   double T_dirichlet;
+  int lumping;  // 0: row sum with c_app at quadrature points, 1: c_app at the node x row-sum mass
 } or_material;
 
 typedef struct {
@@ -684,6 +685,18 @@ void residual(const Mesh& m, const or_material& mt, double s, const double* T, c
     scatter(m, c, fe.data(), F.fdiff.data());
     scatter(m, c, ve.data(), F.fvol.data());
     if (with_C) scatter(m, c, ce.data(), F.C.data());
+  }
+  // Nodal lumping: C~_ii = rho c_app(T_i) sum_j M_ij with the constant-coefficient mass M.
+  // With Q2 elements the basis takes negative values inside a cell, so the row sum of a
+  // capacity with a sharp c_app(T) peak can be negative; the nodal form stays positive
+  // wherever the lumped mass is.
+  if (with_C && mt.lumping == 1 && mt.sigma > 0.0) {
+    or_material plain = mt;
+    plain.sigma = 0.0;
+    plain.lumping = 0;
+    Fields G;
+    residual(m, plain, s, T, nullptr, t, G, true);
+    for (int i = 0; i < m.n_dofs; ++i) F.C[(size_t)i] = G.C[(size_t)i] / mt.c * capp(mt, T[i]);
   }
 }
 

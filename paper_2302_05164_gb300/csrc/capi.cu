@@ -1,0 +1,791 @@
+// C ABI of the library (include/pbf.h): mesh objects, device contexts and the hot-path
+// entry points. Host orchestration only; every step of the path runs in the kernels of
+// kernels_cell.cu and vec_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+#include "mesh.hpp"
+#include "pbf.h"
+#include "solver.hpp"
+#include "vec_kernels.cuh"
+
+using namespace pbf;
+
+namespace {
+thread_local std::string g_err;
+
+pbf_status fail(pbf_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+}  // namespace
+
+namespace pbf {
+pbf_status set_error(pbf_status s, const char* msg) {
+  g_err = msg;
+  return s;
+}
+}  // namespace pbf
+
+struct pbf_mesh {
+  HostMesh m;
+};
+
+extern "C" const char* pbf_last_error(void) { return g_err.c_str(); }
+extern "C" const char* pbf_version(void) { return "pbf-gb300 0.1 (sm_103a)"; }
+
+// ======================================================================================
+// mesh
+// ======================================================================================
+
+extern "C" pbf_status pbf_mesh_create(const pbf_mesh_desc* desc, pbf_mesh** out) {
+  if (!desc || !out) return fail(PBF_EINVAL, "null argument");
+  *out = nullptr;
+  try {
+    std::unique_ptr<pbf_mesh> mh(new pbf_mesh());
+    std::string err;
+    pbf_status st = init_mesh(mh->m, *desc, &err);
+    if (st != PBF_OK) return fail(st, "%s", err.c_str());
+    st = build_mesh(mh->m, nullptr, &err);
+    if (st != PBF_OK) return fail(st, "%s", err.c_str());
+    *out = mh.release();
+    return PBF_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(PBF_ENOMEM, "host allocation failed");
+  }
+}
+
+extern "C" pbf_status pbf_mesh_destroy(pbf_mesh* mesh) {
+  delete mesh;
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_mesh_info(const pbf_mesh* mesh, pbf_mesh_info_t* out) {
+  if (!mesh || !out) return fail(PBF_EINVAL, "null argument");
+  const HostMesh& m = mesh->m;
+  out->n_leaves = (int64_t)m.oct.size();
+  out->n_active = (int64_t)m.leaf_of_active.size();
+  out->n_dofs = m.n_dofs;
+  out->n_hanging = (int64_t)m.con_ptr.size() - 1;
+  out->n_con_entries = (int64_t)m.con_idx.size();
+  out->n_colours = m.n_colours;
+  out->n_top_faces = m.n_top;
+  out->nodes_per_cell = m.npc;
+  out->generation = m.generation;
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_mesh_export(const pbf_mesh* mesh, const pbf_mesh_tables* t) {
+  if (!mesh || !t) return fail(PBF_EINVAL, "null argument");
+  const HostMesh& m = mesh->m;
+  if (t->leaves)
+    for (size_t i = 0; i < m.oct.size(); ++i) {
+      for (int a = 0; a < 3; ++a) t->leaves[i * 5 + a] = m.oct[i].a[a];
+      t->leaves[i * 5 + 3] = m.oct[i].level;
+      t->leaves[i * 5 + 4] = m.active[i];
+    }
+  if (t->material) std::memcpy(t->material, m.material.data(), m.material.size());
+  if (t->cell_dofs) std::memcpy(t->cell_dofs, m.cell_dofs.data(), m.cell_dofs.size() * 4);
+  if (t->con_ptr) std::memcpy(t->con_ptr, m.con_ptr.data(), m.con_ptr.size() * 4);
+  if (t->con_idx) std::memcpy(t->con_idx, m.con_idx.data(), m.con_idx.size() * 4);
+  if (t->con_w) std::memcpy(t->con_w, m.con_w.data(), m.con_w.size() * 8);
+  if (t->hang_coord) std::memcpy(t->hang_coord, m.hang_xyz.data(), m.hang_xyz.size() * 8);
+  if (t->dof_coord) std::memcpy(t->dof_coord, m.dof_xyz.data(), m.dof_xyz.size() * 8);
+  if (t->dirichlet) std::memcpy(t->dirichlet, m.dirichlet.data(), m.dirichlet.size());
+  if (t->colour) std::memcpy(t->colour, m.colour.data(), m.colour.size() * 4);
+  if (t->top) std::memcpy(t->top, m.top.data(), m.top.size());
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_mesh_activate_layer(pbf_mesh* mesh, double z_new_top, int material, double T_init) {
+  if (!mesh) return fail(PBF_EINVAL, "null mesh");
+  if (material < 0 || material > 1) return fail(PBF_EINVAL, "material must be 0 or 1");
+  try {
+    HostMesh& old = mesh->m;
+    if (!(z_new_top >= old.desc.active_top_z)) return fail(PBF_EINVAL, "activation height must not decrease");
+    HostMesh nm;
+    std::string err;
+    pbf_mesh_desc d = old.desc;
+    d.tree_exists = old.exists.empty() ? nullptr : old.exists.data();
+    d.regions = old.regions.data();
+    d.n_regions = (int)old.regions.size();
+    d.active_top_z = z_new_top;
+    pbf_status st = init_mesh(nm, d, &err);
+    if (st != PBF_OK) return fail(st, "%s", err.c_str());
+    // same leaves; previously active cells keep their material, new ones take `material`
+    std::vector<uint8_t> mat(old.material);
+    for (size_t i = 0; i < old.oct.size(); ++i) {
+      double z0 = old.coord(2, old.oct[i].a[2]);
+      if (!old.active[i] && z0 < z_new_top) mat[i] = (uint8_t)material;
+    }
+    st = build_mesh(nm, &mat, &err);
+    if (st != PBF_OK) return fail(st, "%s", err.c_str());
+    nm.generation = old.generation + 1;
+    make_transfer(old, nm, T_init, nm.transfer);
+    mesh->m = std::move(nm);
+    return PBF_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(PBF_ENOMEM, "host allocation failed");
+  }
+}
+
+extern "C" pbf_status pbf_mesh_adapt(pbf_mesh* mesh, int n_regions, const pbf_region* regions) {
+  if (!mesh || (n_regions > 0 && !regions) || n_regions < 0) return fail(PBF_EINVAL, "bad arguments");
+  try {
+    HostMesh& old = mesh->m;
+    HostMesh nm;
+    std::string err;
+    pbf_mesh_desc d = old.desc;
+    d.tree_exists = old.exists.empty() ? nullptr : old.exists.data();
+    d.regions = regions;
+    d.n_regions = n_regions;
+    pbf_status st = init_mesh(nm, d, &err);
+    if (st != PBF_OK) return fail(st, "%s", err.c_str());
+    st = build_mesh(nm, nullptr, &err);  // topology first, then materials from the old leaves
+    if (st != PBF_OK) return fail(st, "%s", err.c_str());
+    std::vector<uint8_t> mat(nm.oct.size());
+    for (size_t i = 0; i < nm.oct.size(); ++i) {
+      int64_t j = old.locate(nm.oct[i].a);
+      mat[i] = j >= 0 ? old.material[(size_t)j] : 0;
+    }
+    st = build_mesh(nm, &mat, &err);
+    if (st != PBF_OK) return fail(st, "%s", err.c_str());
+    nm.generation = old.generation + 1;
+    make_transfer(old, nm, old.desc.active_top_z > 0 ? 0.0 : 0.0, nm.transfer);
+    mesh->m = std::move(nm);
+    return PBF_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(PBF_ENOMEM, "host allocation failed");
+  }
+}
+
+extern "C" pbf_status pbf_mesh_transfer(pbf_mesh* mesh, const double* T_old_dev, double* T_new_dev, int batch,
+                                        pbf_stream stream) {
+  if (!mesh || !T_old_dev || !T_new_dev || batch < 1) return fail(PBF_EINVAL, "bad arguments");
+  TransferMap& tr = mesh->m.transfer;
+  if (!tr.pending) return fail(PBF_ESTATE, "no pending transfer");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t *ptr = nullptr, *idx = nullptr;
+  double* w = nullptr;
+  auto cleanup = [&]() {
+    cudaFree(ptr);
+    cudaFree(idx);
+    cudaFree(w);
+  };
+  if (cudaMalloc(&ptr, tr.ptr.size() * 4) != cudaSuccess || cudaMalloc(&idx, std::max<size_t>(1, tr.idx.size()) * 4) != cudaSuccess ||
+      cudaMalloc(&w, std::max<size_t>(1, tr.w.size()) * 8) != cudaSuccess) {
+    cleanup();
+    return fail(PBF_ENOMEM, "device allocation failed");
+  }
+  cudaError_t e = cudaMemcpyAsync(ptr, tr.ptr.data(), tr.ptr.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !tr.idx.empty()) e = cudaMemcpyAsync(idx, tr.idx.data(), tr.idx.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !tr.w.empty()) e = cudaMemcpyAsync(w, tr.w.data(), tr.w.size() * 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = launch_transfer(tr.n_new, batch, ptr, idx, w, T_old_dev, tr.fill, T_new_dev, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cleanup();
+  if (e != cudaSuccess) return fail(PBF_ECUDA, "transfer: %s", cudaGetErrorString(e));
+  tr.pending = false;
+  return PBF_OK;
+}
+
+// ======================================================================================
+// context
+// ======================================================================================
+
+pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pbf_precision prec, int batch,
+                               pbf_ctx** out);
+
+extern "C" pbf_status pbf_ctx_create(const pbf_mesh* mesh, const pbf_material* mat, pbf_precision prec, int batch,
+                                     pbf_ctx** out) {
+  if (!mesh || !mat || !out) return fail(PBF_EINVAL, "null argument");
+  if (batch < 1 || batch > 1024) return fail(PBF_EINVAL, "batch must be in [1, 1024]");
+  if (prec != PBF_F64 && prec != PBF_F32OP) return fail(PBF_EINVAL, "bad precision");
+  if (!(mat->rho > 0) || !(mat->c > 0) || !(mat->k0 > 0)) return fail(PBF_EINVAL, "rho, c, k0 must be positive");
+  return pbf_ctx_impl_create(mesh, mat, prec, batch, out);
+}
+
+// ---- context object ---------------------------------------------------------------------
+
+struct pbf_ctx : public CtxBase {};
+
+namespace {
+
+template <typename T>
+cudaError_t dalloc(pbf_ctx* c, T** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(1, n) * sizeof(T));
+  if (e == cudaSuccess) {
+    c->allocs.push_back(q);
+    *p = (T*)q;
+  }
+  return e;
+}
+
+template <typename T>
+cudaError_t upload(pbf_ctx* c, T** p, const T* src, size_t n) {
+  cudaError_t e = dalloc(c, p, n);
+  if (e == cudaSuccess && n) e = cudaMemcpy(*p, src, n * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+}  // namespace
+
+pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pbf_precision prec, int batch,
+                               pbf_ctx** out) {
+  const HostMesh& m = mesh->m;
+  std::unique_ptr<pbf_ctx> c(new pbf_ctx());
+  c->mesh = &mesh->m;
+  c->generation = m.generation;
+  c->degree = m.p;
+  c->npc = m.npc;
+  c->batch = batch;
+  c->n_dofs = m.n_dofs;
+  c->n_cells = (int64_t)m.leaf_of_active.size();
+  c->n_hang = (int64_t)m.con_ptr.size() - 1;
+  c->f32 = prec == PBF_F32OP;
+  c->mat = *mat;
+  const bool has_latent = mat->sigma > 0.0 && mat->latent != 0.0;
+  if (mat->lumping != PBF_LUMP_QUADRATURE && mat->lumping != PBF_LUMP_NODAL) return fail(PBF_EINVAL, "bad lumping");
+  c->cap = !has_latent ? CAP_CONST : (mat->lumping == PBF_LUMP_NODAL ? CAP_NODAL : CAP_QUADRATURE);
+  c->latent = c->cap == CAP_QUADRATURE;  // capacity integrated by the cell kernel
+  if (has_latent) {
+    const double lat_norm = mat->latent / (mat->sigma * std::sqrt(2.0 * kPi));
+    c->nodal.lat_ratio = lat_norm / mat->c;
+    c->nodal.Tm = mat->Tm;
+    c->nodal.inv_sigma = 1.0 / mat->sigma;
+    c->nodal.lat_ratio_f = (float)c->nodal.lat_ratio;
+    c->nodal.tm_off_f = (float)(mat->T_ref - mat->Tm);
+    c->nodal.inv_sigma_f = (float)c->nodal.inv_sigma;
+  }
+  c->nonlin = mat->Tk1 > mat->Tk0 && mat->k1 != mat->k0;
+  if (c->n_cells * (int64_t)c->npc >= ((int64_t)1 << 31) || c->n_dofs * (int64_t)batch >= ((int64_t)1 << 40))
+    return fail(PBF_EINVAL, "mesh too large");
+  const size_t nc = (size_t)c->n_cells, npc = (size_t)c->npc, nd = (size_t)c->n_dofs;
+  // host staging of per-cell tables
+  std::vector<int32_t> soa(nc * npc);
+  for (size_t e = 0; e < nc; ++e)
+    for (size_t a = 0; a < npc; ++a) soa[a * nc + e] = m.cell_dofs[e * npc + a];
+  std::vector<uint8_t> lvl(nc), cm(nc);
+  std::vector<double> lo(nc * 3);
+  std::vector<int32_t> top_cell;
+  std::vector<double> top_geo;
+  for (size_t e = 0; e < nc; ++e) {
+    const Octant& o = m.oct[(size_t)m.leaf_of_active[e]];
+    lvl[e] = (uint8_t)o.level;
+    cm[e] = m.material[(size_t)m.leaf_of_active[e]];
+    for (int a = 0; a < 3; ++a) lo[e * 3 + a] = m.coord(a, o.a[a]);
+    if (m.top[e]) {
+      top_cell.push_back((int32_t)e);
+      const int64_t s = m.size(o);
+      top_geo.push_back(m.coord(0, o.a[0]));
+      top_geo.push_back(m.coord(1, o.a[1]));
+      top_geo.push_back(m.coord(0, o.a[0] + s) - m.coord(0, o.a[0]));
+      top_geo.push_back(m.coord(1, o.a[1] + s) - m.coord(1, o.a[1]));
+    }
+  }
+  std::vector<float> con_wf(m.con_w.begin(), m.con_w.end());
+  std::vector<double> level_h((size_t)kMaxLevels * 3, 0.0);
+  CellLaunch& L = c->base;
+  for (int l = 0; l <= m.L && l < kMaxLevels; ++l) {
+    double h[3];
+    for (int a = 0; a < 3; ++a) h[a] = m.desc.tree_h[a] / (double)((int64_t)1 << l);
+    double detJ = h[0] * h[1] * h[2];
+    L.gd.detJ[l] = detJ;
+    L.gf.detJ[l] = (float)detJ;
+    for (int a = 0; a < 3; ++a) {
+      level_h[(size_t)l * 3 + a] = h[a];
+      L.gd.ih2[l][a] = 1.0 / (h[a] * h[a]);
+      L.gf.ih2[l][a] = (float)(1.0 / (h[a] * h[a]));
+    }
+  }
+  cudaError_t e = cudaSuccess;
+#define UP(ptr, vec) \
+  if (e == cudaSuccess) e = upload(c.get(), &ptr, vec.data(), vec.size())
+  UP(c->cell_dofs, soa);
+  UP(c->cell_level, lvl);
+  UP(c->cell_mat, cm);
+  UP(c->con_ptr, m.con_ptr);
+  UP(c->con_idx, m.con_idx);
+  UP(c->con_w, m.con_w);
+  UP(c->con_wf, con_wf);
+  UP(c->dirichlet, m.dirichlet);
+  UP(c->top_cell, top_cell);
+  UP(c->top_geo, top_geo);
+  UP(c->cell_lo, lo);
+  UP(c->level_h, level_h);
+#undef UP
+  c->n_top = (int64_t)top_cell.size();
+  const size_t rsz = c->f32 ? 4 : 8;
+  const size_t nv = nd * (size_t)batch;
+  if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->f, nv * rsz);
+  if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->fvol, nv * rsz);
+  if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->Cacc, (c->latent ? nv : 1) * rsz);
+  if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->Tw, nv);
+  if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->Tf, nv);
+  const size_t nh = (size_t)c->n_hang * (size_t)batch;
+  if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->xh, nh * rsz);
+  if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->fh, nh * rsz);
+  if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->Ch, nh * rsz);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->xh64, nh);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->fh64, nh);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->Ch64, nh);
+  if (e == cudaSuccess) e = cudaMemset(c->fh, 0, std::max<size_t>(1, nh) * rsz);
+  if (e == cudaSuccess) e = cudaMemset(c->Ch, 0, std::max<size_t>(1, nh) * rsz);
+  if (e == cudaSuccess) e = cudaMemset(c->fh64, 0, std::max<size_t>(1, nh) * 8);
+  if (e == cudaSuccess) e = cudaMemset(c->Ch64, 0, std::max<size_t>(1, nh) * 8);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->C0, nd);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_d, nd);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_f, nd);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->power, (size_t)batch * kMaxSeg);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->part, (size_t)reduction_blocks() * batch);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->scal, (size_t)batch * 16);
+  c->k_scale_host.assign((size_t)batch, 1.0);
+  std::vector<float> ksf((size_t)batch, 1.0f);
+  if (e == cudaSuccess) e = upload(c.get(), &c->k_scale_d, c->k_scale_host.data(), (size_t)batch);
+  if (e == cudaSuccess) e = upload(c.get(), &c->k_scale_f, ksf.data(), (size_t)batch);
+  if (e == cudaSuccess) e = cudaMemset(c->f, 0, nv * rsz);
+  if (e == cudaSuccess) e = cudaMemset(c->fvol, 0, nv * rsz);
+  if (e == cudaSuccess) e = cudaMemset(c->Cacc, 0, (c->latent ? nv : 1) * rsz);
+  if (e == cudaSuccess) e = cudaMemset(c->C0, 0, nd * 8);
+  if (e == cudaSuccess) e = cudaMemset(c->power, 0, (size_t)batch * kMaxSeg * 8);
+  if (e != cudaSuccess) {
+    c->release();
+    return fail(e == cudaErrorMemoryAllocation ? PBF_ENOMEM : PBF_ECUDA, "context setup: %s", cudaGetErrorString(e));
+  }
+  // launch template
+  DevMesh& M = L.mesh;
+  M.n_cells = (int)c->n_cells;
+  M.npc = c->npc;
+  M.n_dofs = (int)c->n_dofs;
+  M.n_hang = (int)c->n_hang;
+  M.batch = batch;
+  M.cell_dofs = c->cell_dofs;
+  M.cell_level = c->cell_level;
+  M.cell_mat = c->cell_mat;
+  M.con_ptr = c->con_ptr;
+  M.con_idx = c->con_idx;
+  M.con_w = c->con_w;
+  M.con_wf = c->con_wf;
+  M.dirichlet = c->dirichlet;
+  L.degree = c->degree;
+  L.f32 = c->f32;
+  L.nonlin_k = c->nonlin;
+  L.latent = c->latent;
+  L.k_scale_d = c->k_scale_d;
+  L.k_scale_f = c->k_scale_f;
+  c->set_material_constants(0.0);
+  c->lsetup.n_top = (int)c->n_top;
+  c->lsetup.top_cell = c->top_cell;
+  c->lsetup.top_geo = c->top_geo;
+  c->lsetup.cell_lo = c->cell_lo;
+  c->lsetup.level_h = c->level_h;
+  // constant-c lumped capacity and its inverse (FP64, once)
+  {
+    CellLaunch Lc = L;
+    Lc.f32 = 0;
+    Lc.latent = 0;
+    Lc.mesh.batch = 1;
+    Lc.offset = mat->T_ref;
+    std::vector<double> zero(nd, mat->T_ref);
+    double* Tz = nullptr;
+    e = cudaMalloc(&Tz, std::max<size_t>(1, nd) * 8);
+    if (e == cudaSuccess) e = cudaMemcpy(Tz, zero.data(), nd * 8, cudaMemcpyHostToDevice);
+    Lc.x = Tz;
+    if (e == cudaSuccess) e = c->apply_cell(Lc, nullptr, c->C0, MODE_CAPACITY, 0);
+    if (e == cudaSuccess) e = launch_reciprocal((int64_t)nd, c->C0, c->invC0_d, c->invC0_f, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(Tz);
+    c->launches += 2;
+    if (e != cudaSuccess) {
+      c->release();
+      return fail(PBF_ECUDA, "capacity setup: %s", cudaGetErrorString(e));
+    }
+  }
+  *out = c.release();
+  return PBF_OK;
+}
+
+void CtxBase::set_material_constants(double dt) {
+  CellLaunch& L = base;
+  const pbf_material& mt = mat;
+  MatR<double> d;
+  d.rho = mt.rho;
+  d.c = mt.c;
+  d.lat_norm = latent ? mt.latent / (mt.sigma * std::sqrt(2.0 * kPi)) : 0.0;
+  d.tm_off = mt.T_ref - mt.Tm;
+  d.inv_sigma = latent ? 1.0 / mt.sigma : 0.0;
+  d.k0 = mt.k0;
+  d.dk = nonlin ? mt.k1 - mt.k0 : 0.0;
+  d.tk_off = mt.T_ref - mt.Tk0;
+  d.inv_dT = nonlin ? 1.0 / (mt.Tk1 - mt.Tk0) : 0.0;
+  d.powder_scale = mt.powder_k_scale;
+  d.m_impl = dt > 0 ? mt.rho * mt.c / dt : 0.0;
+  L.md = d;
+  L.mf.rho = (float)d.rho;
+  L.mf.c = (float)d.c;
+  L.mf.lat_norm = (float)d.lat_norm;
+  L.mf.tm_off = (float)d.tm_off;
+  L.mf.inv_sigma = (float)d.inv_sigma;
+  L.mf.k0 = (float)d.k0;
+  L.mf.dk = (float)d.dk;
+  L.mf.tk_off = (float)d.tk_off;
+  L.mf.inv_dT = (float)d.inv_dT;
+  L.mf.powder_scale = (float)d.powder_scale;
+  L.mf.m_impl = (float)d.m_impl;
+  L.offset = mt.T_ref;
+}
+
+void CtxBase::release() {
+  for (void* p : allocs) cudaFree(p);
+  allocs.clear();
+  for (auto& ev : events) {
+    cudaEventDestroy(ev.first);
+    cudaEventDestroy(ev.second);
+  }
+  events.clear();
+}
+
+extern "C" pbf_status pbf_ctx_destroy(pbf_ctx* ctx) {
+  if (!ctx) return PBF_OK;
+  ctx->release();
+  delete ctx;
+  return PBF_OK;
+}
+
+pbf_status CtxBase::check_usable() {
+  if (poisoned) return fail(PBF_ESTATE, "context is poisoned by an earlier CUDA error");
+  if (mesh->generation != generation) return fail(PBF_ESTATE, "mesh changed since the context was created");
+  return PBF_OK;
+}
+
+pbf_status CtxBase::cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return PBF_OK;
+  poisoned = true;
+  return fail(PBF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+extern "C" pbf_status pbf_ctx_set_k_scale(pbf_ctx* ctx, const double* s_host) {
+  if (!ctx || !s_host) return fail(PBF_EINVAL, "null argument");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  std::vector<float> f((size_t)ctx->batch);
+  for (int b = 0; b < ctx->batch; ++b) {
+    if (!(s_host[b] > 0)) return fail(PBF_EINVAL, "k scale must be positive");
+    ctx->k_scale_host[(size_t)b] = s_host[b];
+    f[(size_t)b] = (float)s_host[b];
+  }
+  cudaError_t e = cudaMemcpy(ctx->k_scale_d, s_host, (size_t)ctx->batch * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(ctx->k_scale_f, f.data(), (size_t)ctx->batch * 4, cudaMemcpyHostToDevice);
+  return ctx->cuda(e, "set_k_scale");
+}
+
+pbf_status CtxBase::set_laser(const pbf_laser* ls, cudaStream_t s) {
+  LaserK& k = lsetup.k;
+  if (!ls || ls->n_seg == 0) {
+    k.n_seg = 0;
+    return PBF_OK;
+  }
+  if (ls->n_seg < 0 || ls->n_seg > kMaxSeg || !ls->seg || !ls->power) return fail(PBF_EINVAL, "bad laser description");
+  if (!(ls->radius > 0)) return fail(PBF_EINVAL, "laser radius must be positive");
+  k.n_seg = ls->n_seg;
+  k.volumetric = ls->volumetric;
+  k.eta = ls->eta;
+  k.radius = ls->radius;
+  k.h_powder = ls->h_powder;
+  k.z_top = mesh->desc.active_top_z;
+  for (int i = 0; i < ls->n_seg; ++i)
+    for (int j = 0; j < 6; ++j) k.seg[i][j] = ls->seg[i * 6 + j];
+  std::vector<double> pw((size_t)batch * kMaxSeg, 0.0);
+  for (int b = 0; b < batch; ++b)
+    for (int i = 0; i < ls->n_seg; ++i) pw[(size_t)b * kMaxSeg + (size_t)i] = ls->power[(size_t)b * ls->n_seg + (size_t)i];
+  if (pw != power_host) {
+    power_host = pw;
+    cudaError_t e = cudaMemcpyAsync(power, pw.data(), pw.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda(e, "laser power upload");
+  }
+  return PBF_OK;
+}
+
+cudaError_t CtxBase::apply_cell(CellLaunch L, void* f, void* C, int mode, cudaStream_t s) {
+  const bool lf32 = L.f32 != 0;
+  // FP64-operator launches in an FP32 context use the FP64 hanging buffers
+  void* xhb = lf32 ? xh : (f32 ? (void*)xh64 : xh);
+  void* fhb = lf32 ? fh : (f32 ? (void*)fh64 : fh);
+  void* Chb = lf32 ? Ch : (f32 ? (void*)Ch64 : Ch);
+  cudaError_t e = launch_hang_values(lf32, L.mesh, lf32 ? (const void*)L.xf : (const void*)L.x, xhb, s);
+  if (lf32) L.xfh = (const float*)xhb;
+  else L.xh = (const double*)xhb;
+  ++launches;
+  if (e != cudaSuccess) return e;
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (timing) {
+    if (free_events.empty()) {
+      cudaEventCreate(&ev.first);
+      cudaEventCreate(&ev.second);
+    } else {
+      ev = free_events.back();
+      free_events.pop_back();
+    }
+    cudaEventRecord(ev.first, s);
+  }
+  e = launch_cell(L, f, fhb, C, C ? Chb : nullptr, mode, s);
+  ++launches;
+  if (timing) {
+    cudaEventRecord(ev.second, s);
+    events.push_back(ev);
+  }
+  if (e == cudaSuccess && f) e = launch_hang_distribute(lf32, L.mesh, fhb, f, s);
+  if (e == cudaSuccess && C) e = launch_hang_distribute(lf32, L.mesh, Chb, C, s);
+  launches += (f ? 1 : 0) + (C ? 1 : 0);
+  return e;
+}
+
+extern "C" pbf_status pbf_eval_residual(pbf_ctx* ctx, const double* T_dev, const pbf_laser* laser, double t,
+                                        double* fdiff_dev, double* fvol_dev, double* C_dev, pbf_stream stream) {
+  if (!ctx || !T_dev) return fail(PBF_EINVAL, "null argument");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ctx->set_laser(laser, s);
+  if (st) return st;
+  const int64_t nv = ctx->n_dofs * ctx->batch;
+  const size_t rsz = ctx->f32 ? 4 : 8;
+  CellLaunch L = ctx->base;
+  L.x = T_dev;
+  cudaError_t e = cudaSuccess;
+  if (ctx->f32) {
+    e = launch_prepare_f32(nv, T_dev, ctx->mat.T_ref, nullptr, ctx->Tf, s);
+    L.xf = ctx->Tf;
+    ++ctx->launches;
+  }
+  if (e == cudaSuccess) e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);
+  if (e == cudaSuccess && ctx->lsetup.k.n_seg > 0) {
+    e = launch_laser(ctx->degree, ctx->f32, ctx->lsetup, L.mesh, ctx->power, spot_at(ctx->lsetup.k, t), ctx->fvol, s);
+    ++ctx->launches;
+  }
+  if (e == cudaSuccess && fdiff_dev) e = launch_to_f64(ctx->f32, nv, ctx->f, fdiff_dev, s);
+  if (e == cudaSuccess && fvol_dev) e = launch_to_f64(ctx->f32, nv, ctx->fvol, fvol_dev, s);
+  if (e == cudaSuccess && C_dev) {
+    if (ctx->cap == CAP_QUADRATURE) e = launch_to_f64(ctx->f32, nv, ctx->Cacc, C_dev, s);
+    else if (ctx->cap == CAP_NODAL) e = launch_capacity_nodal(ctx->n_dofs, ctx->batch, ctx->C0, T_dev, ctx->nodal, C_dev, s);
+    else e = launch_broadcast_dofs(ctx->n_dofs, ctx->batch, ctx->C0, C_dev, s);
+  }
+  ctx->launches += 3;
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f, 0, (size_t)nv * rsz, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fvol, 0, (size_t)nv * rsz, s);
+  if (e == cudaSuccess && ctx->latent) e = cudaMemsetAsync(ctx->Cacc, 0, (size_t)nv * rsz, s);
+  return ctx->cuda(e, "eval_residual");
+}
+
+extern "C" pbf_status pbf_explicit_step(pbf_ctx* ctx, double* T_dev, const pbf_laser* laser, double t0, double dt,
+                                        int nsteps, pbf_stream stream) {
+  if (!ctx || !T_dev) return fail(PBF_EINVAL, "null argument");
+  if (nsteps < 0 || !(dt > 0)) return fail(PBF_EINVAL, "need nsteps >= 0 and dt > 0");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  st = ctx->set_laser(laser, s);
+  if (st) return st;
+  CellLaunch L = ctx->base;
+  const bool with_laser = ctx->lsetup.k.n_seg > 0;
+  const int64_t nv = ctx->n_dofs * ctx->batch;
+  cudaError_t e = cudaSuccess;
+  if (ctx->f32) {
+    // FP64 working state Tw = T - T_ref and its FP32 copy for the whole call
+    const double tw_dir = ctx->mat.T_dirichlet - ctx->mat.T_ref;
+    const float tf_dir = (float)tw_dir;
+    e = launch_prepare_f32(nv, T_dev, ctx->mat.T_ref, ctx->Tw, ctx->Tf, s);
+    ++ctx->launches;
+    L.xf = ctx->Tf;
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      const double t = t0 + n * dt;
+      e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);
+      if (e == cudaSuccess && with_laser) {
+        e = launch_laser(ctx->degree, true, ctx->lsetup, L.mesh, ctx->power, spot_at(ctx->lsetup.k, t), ctx->f, s);
+        ++ctx->launches;
+      }
+      if (e == cudaSuccess)
+        e = launch_update_f32(ctx->cap, ctx->n_dofs, ctx->batch, ctx->Tw, ctx->Tf, (float*)ctx->f, (float*)ctx->Cacc,
+                              ctx->invC0_f, ctx->nodal, ctx->dirichlet, tw_dir, tf_dir, (float)dt, s);
+      ++ctx->launches;
+    }
+    if (e == cudaSuccess) e = launch_finish_f32(nv, ctx->Tw, ctx->mat.T_ref, T_dev, s);
+    ++ctx->launches;
+  } else {
+    L.x = T_dev;
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      const double t = t0 + n * dt;
+      e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);
+      if (e == cudaSuccess && with_laser) {
+        e = launch_laser(ctx->degree, false, ctx->lsetup, L.mesh, ctx->power, spot_at(ctx->lsetup.k, t), ctx->f, s);
+        ++ctx->launches;
+      }
+      if (e == cudaSuccess)
+        e = launch_update_f64(ctx->cap, ctx->n_dofs, ctx->batch, T_dev, (double*)ctx->f, (double*)ctx->Cacc,
+                              ctx->invC0_d, ctx->nodal, ctx->dirichlet, ctx->mat.T_dirichlet, dt, s);
+      ++ctx->launches;
+    }
+  }
+  return ctx->cuda(e, "explicit_step");
+}
+
+extern "C" pbf_status pbf_round_to_f32(const double* x_dev, float* y_dev, int64_t n, pbf_stream stream) {
+  if ((!x_dev || !y_dev) && n > 0) return fail(PBF_EINVAL, "null argument");
+  if (n < 0) return fail(PBF_EINVAL, "negative length");
+  cudaError_t e = launch_round_f32(n, x_dev, y_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? PBF_OK : fail(PBF_ECUDA, "round_to_f32: %s", cudaGetErrorString(e));
+}
+
+extern "C" pbf_status pbf_widen_to_f64(const float* x_dev, double* y_dev, int64_t n, pbf_stream stream) {
+  if ((!x_dev || !y_dev) && n > 0) return fail(PBF_EINVAL, "null argument");
+  if (n < 0) return fail(PBF_EINVAL, "negative length");
+  cudaError_t e = launch_f32_to_f64(n, x_dev, y_dev, (cudaStream_t)stream);
+  return e == cudaSuccess ? PBF_OK : fail(PBF_ECUDA, "widen_to_f64: %s", cudaGetErrorString(e));
+}
+
+extern "C" pbf_status pbf_ctx_set_timing(pbf_ctx* ctx, int enable) {
+  if (!ctx) return fail(PBF_EINVAL, "null argument");
+  ctx->timing = enable != 0;
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_ctx_kernel_time(pbf_ctx* ctx, double* ms_out, long long* launches_out) {
+  if (!ctx) return fail(PBF_EINVAL, "null argument");
+  double total = 0.0;
+  for (auto& ev : ctx->events) {
+    cudaError_t e = cudaEventSynchronize(ev.second);
+    if (e != cudaSuccess) return ctx->cuda(e, "kernel_time");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev.first, ev.second);
+    total += ms;
+    ctx->free_events.push_back(ev);
+  }
+  if (ms_out) *ms_out = total;
+  if (launches_out) *launches_out = (long long)ctx->events.size();
+  ctx->events.clear();
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_ctx_launch_count(pbf_ctx* ctx, long long* launches_out) {
+  if (!ctx || !launches_out) return fail(PBF_EINVAL, "null argument");
+  *launches_out = ctx->launches;
+  return PBF_OK;
+}
+
+// ---- critical time step (Eq. explicit_time_step) -----------------------------------------
+
+namespace {
+// SplitMix64 (Steele, Lea, Flood 2014; public-domain reference by Vigna): deterministic
+// start vectors when the caller passes none.
+void splitmix_fill(std::vector<double>& v, uint64_t seed) {
+  uint64_t x = seed;
+  for (double& o : v) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    o = (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  }
+}
+}  // namespace
+
+pbf_status CtxBase::ensure_vectors(int n) {
+  while ((int)vec.size() < n) {
+    double* p = nullptr;
+    cudaError_t e = dalloc_raw(&p, (size_t)n_dofs * (size_t)batch);
+    if (e != cudaSuccess) return cuda(e, "work vector allocation");
+    vec.push_back(p);
+  }
+  return PBF_OK;
+}
+
+cudaError_t CtxBase::dalloc_raw(double** p, size_t n) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, std::max<size_t>(1, n) * 8);
+  if (e == cudaSuccess) {
+    allocs.push_back(q);
+    *p = (double*)q;
+  }
+  return e;
+}
+
+extern "C" pbf_status pbf_estimate_dt(pbf_ctx* ctx, const double* x0_dev, int max_iter, double rtol,
+                                      double* lambda_out, double* dt_crit_out, int* iters_out, pbf_stream stream) {
+  if (!ctx) return fail(PBF_EINVAL, "null argument");
+  if (max_iter < 1) return fail(PBF_EINVAL, "max_iter must be positive");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  st = ctx->ensure_vectors(2);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n = ctx->n_dofs;
+  double *x = ctx->vec[0], *y = ctx->vec[1];
+  cudaError_t e;
+  if (x0_dev) {
+    e = cudaMemcpyAsync(x, x0_dev, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
+  } else {
+    std::vector<double> h((size_t)n);
+    splitmix_fill(h, 0x5eedull);
+    e = cudaMemcpyAsync(x, h.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  }
+  if (e == cudaSuccess) e = launch_zero_masked(n, x, ctx->dirichlet, s);
+  // linear stiffness in FP64 for instance 0 (k frozen at k0, scale s of instance 0)
+  CellLaunch L = ctx->base;
+  L.f32 = 0;
+  L.nonlin_k = 0;
+  L.latent = 0;
+  L.offset = 0.0;
+  L.mesh.batch = 1;
+  L.k_scale_d = ctx->k_scale_d;
+  double lambda = 0.0;
+  int it = 0;
+  double* d_scal = ctx->scal;
+  for (; it < max_iter && e == cudaSuccess; ++it) {
+    // normalise x in the C~ norm
+    e = launch_dot(n, 1, x, x, ctx->C0, nullptr, ctx->part, d_scal, s);
+    double nx2 = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&nx2, d_scal, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) break;
+    if (!(nx2 > 0)) return fail(PBF_EINVAL, "start vector vanishes on the free dofs");
+    double inv = 1.0 / std::sqrt(nx2);
+    e = cudaMemcpyAsync(d_scal + 1, &inv, 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_scale_masked(n, x, d_scal + 1, nullptr, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(y, 0, (size_t)n * 8, s);
+    L.x = x;
+    if (e == cudaSuccess) e = ctx->apply_cell(L, y, nullptr, MODE_STIFF, s);
+    if (e == cudaSuccess) e = launch_zero_masked(n, y, ctx->dirichlet, s);
+    if (e == cudaSuccess) e = launch_dot(n, 1, x, y, nullptr, nullptr, ctx->part, d_scal + 2, s);
+    double lam = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&lam, d_scal + 2, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = launch_div_masked(n, x, y, ctx->invC0_d, ctx->dirichlet, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    ctx->launches += 9;
+    if (e != cudaSuccess) break;
+    bool done = it > 0 && std::fabs(lam - lambda) <= rtol * std::fabs(lam);
+    lambda = lam;
+    if (done) {
+      ++it;
+      break;
+    }
+  }
+  if (e != cudaSuccess) return ctx->cuda(e, "estimate_dt");
+  if (lambda_out) *lambda_out = lambda;
+  if (dt_crit_out) *dt_crit_out = lambda > 0 ? 2.0 / lambda : INFINITY;
+  if (iters_out) *iters_out = it;
+  return PBF_OK;
+}

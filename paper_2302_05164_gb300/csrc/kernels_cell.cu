@@ -1,0 +1,335 @@
+// Cell-operator kernels: the matrix-free, sum-factorised evaluation of the heat operator
+// (paper Sec. 4.2, Eqs. diffusive_term_evaluation, vector_evaluation, matrix_free_eval).
+//
+// GPU mapping: one thread per (cell, instance); consecutive threads are consecutive
+// instances of a cell, then consecutive cells in Z-curve order, so gathers of a batch are
+// coalesced and neighbouring cells share cache lines (the analogue of the paper's
+// vectorisation over cell batches, Sec. 4.2.1). Per thread the 1D interpolation and
+// gradient contractions run fully unrolled in registers with compile-time coefficients;
+// the quadrature-point physics is branch-free (clamps and selects, Sec. 4.2.1 masks);
+// values are scattered with atomics onto dofs and, through the constraint rows, onto the
+// masters of hanging nodes (G_e^T P^T).
+#include <cstdio>
+
+#include "internal.cuh"
+
+namespace pbf {
+namespace {
+
+template <int N>
+__device__ __forceinline__ constexpr int lin(int dir, int a, int b, int i) {
+  return dir == 0 ? i + N * (a + N * b) : (dir == 1 ? a + N * (i + N * b) : a + N * (b + N * i));
+}
+
+template <int P, int WHICH>
+__device__ __forceinline__ constexpr double coef(int q, int i) {
+  return WHICH == 0 ? Basis<P>::S(q, i) : Basis<P>::D(q, i);
+}
+
+// out[line, q] (+)= sum_i M(q, i) in[line, i]   along direction DIR; TR uses M(i, q).
+template <int P, int WHICH, int DIR, bool TR, bool ADD, typename R>
+__device__ __forceinline__ void apply1d(const R* in, R* out) {
+  constexpr int N = P + 1;
+#pragma unroll
+  for (int b = 0; b < N; ++b)
+#pragma unroll
+    for (int a = 0; a < N; ++a)
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        R s = ADD ? out[lin<N>(DIR, a, b, q)] : R(0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          const double m = TR ? coef<P, WHICH>(i, q) : coef<P, WHICH>(q, i);
+          if (m != 0.0) s = s + R(m) * in[lin<N>(DIR, a, b, i)];
+        }
+        out[lin<N>(DIR, a, b, q)] = s;
+      }
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void values_at_qp(const R* u, R* v) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  R t[NP], w[NP];
+  apply1d<P, 0, 0, false, false>(u, t);
+  apply1d<P, 0, 1, false, false>(t, w);
+  apply1d<P, 0, 2, false, false>(w, v);
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void integrate_values(const R* r, R* fe) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  R t[NP], w[NP];
+  apply1d<P, 0, 0, true, false>(r, t);
+  apply1d<P, 0, 1, true, false>(t, w);
+  apply1d<P, 0, 2, true, false>(w, fe);
+}
+
+template <typename R>
+__device__ __forceinline__ R weight_of(const DevMesh& M, int e);
+template <>
+__device__ __forceinline__ float weight_of<float>(const DevMesh& M, int e) { return M.con_wf[e]; }
+template <>
+__device__ __forceinline__ double weight_of<double>(const DevMesh& M, int e) { return M.con_w[e]; }
+
+// Gather T_e = P G_e x. Slot a of a cell holds a dof d >= 0 or a hanging node -1-r; hanging
+// values were computed beforehand (x_h = P_h x, one small kernel), so every slot is one load
+// from one of two arrays, selected without branching: all loads of a cell issue back to back.
+template <int P, typename R, typename S>
+__device__ __forceinline__ void gather_sel(const DevMesh& M, const S* __restrict__ x, const S* __restrict__ xh,
+                                           int cell, int inst, double off, R* u) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  const int B = M.batch;
+  int idx[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) idx[a] = __ldg(&M.cell_dofs[a * M.n_cells + cell]);
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const int d = idx[a];
+    const S* base = d >= 0 ? x : xh;
+    const int64_t j = d >= 0 ? d : -1 - d;
+    const S v = __ldg(&base[j * B + inst]);
+    if (sizeof(S) == 8) u[a] = R((double)v - off);
+    else u[a] = R(v);
+  }
+}
+
+template <int P, typename R>
+__device__ __forceinline__ void gather_any(const CellLaunch& L, int cell, int inst, R* u);
+template <>
+__device__ __forceinline__ void gather_any<1, float>(const CellLaunch& L, int cell, int inst, float* u) {
+  gather_sel<1, float, float>(L.mesh, L.xf, L.xfh, cell, inst, 0.0, u);
+}
+template <>
+__device__ __forceinline__ void gather_any<2, float>(const CellLaunch& L, int cell, int inst, float* u) {
+  gather_sel<2, float, float>(L.mesh, L.xf, L.xfh, cell, inst, 0.0, u);
+}
+template <>
+__device__ __forceinline__ void gather_any<1, double>(const CellLaunch& L, int cell, int inst, double* u) {
+  gather_sel<1, double, double>(L.mesh, L.x, L.xh, cell, inst, L.offset, u);
+}
+template <>
+__device__ __forceinline__ void gather_any<2, double>(const CellLaunch& L, int cell, int inst, double* u) {
+  gather_sel<2, double, double>(L.mesh, L.x, L.xh, cell, inst, L.offset, u);
+}
+
+// f += G_e^T fe, with hanging-node slots going to fh (distributed by P_h^T afterwards)
+template <int P, typename R>
+__device__ __forceinline__ void scatter(const DevMesh& M, R* __restrict__ f, R* __restrict__ fh, int cell, int inst,
+                                        const R* fe) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  const int B = M.batch;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    const int d = __ldg(&M.cell_dofs[a * M.n_cells + cell]);
+    R* base = d >= 0 ? f : fh;
+    const int64_t j = d >= 0 ? d : -1 - d;
+    atomicAdd(&base[j * B + inst], fe[a]);
+  }
+}
+
+__device__ __forceinline__ float clamp01(float x) { return __saturatef(x); }
+__device__ __forceinline__ double clamp01(double x) { return fmin(fmax(x, 0.0), 1.0); }
+__device__ __forceinline__ float expo(float x) { return __expf(x); }
+__device__ __forceinline__ double expo(double x) { return exp(x); }
+
+template <int P>
+__device__ __forceinline__ constexpr double wq3(int q) {
+  return Basis<P>::W(q % (P + 1)) * Basis<P>::W((q / (P + 1)) % (P + 1)) * Basis<P>::W(q / ((P + 1) * (P + 1)));
+}
+
+// One kernel for the residual / capacity / stiffness / implicit-operator modes.
+template <int P, typename R, int MODE, bool NLK, bool LAT>
+__global__ void __launch_bounds__(128) k_cell(const CellLaunch L, R* __restrict__ f, R* __restrict__ fh,
+                                              R* __restrict__ C, R* __restrict__ Ch) {
+  constexpr int N = P + 1, NP = N * N * N;
+  (void)N;
+  const DevMesh& M = L.mesh;
+  const MatR<R>& mt = mat_of<R>(L);
+  const GeoR<R>& geo = geo_of<R>(L);
+  const int B = M.batch;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (int64_t)M.n_cells * B) return;
+  const int cell = (int)(tid / B), inst = (int)(tid - (int64_t)(tid / B) * B);
+
+  R u[NP], v[NP];
+  gather_any<P, R>(L, cell, inst, u);
+  values_at_qp<P, R>(u, v);
+
+  const int lev = M.cell_level[cell];
+  const R detJ = geo.detJ[lev];
+
+  if ((MODE == MODE_RESIDUAL || MODE == MODE_CAPACITY) && C != nullptr) {
+    // lumped capacity: int rho c_app(T_h) N_i  (row sums of the consistent capacity)
+    R cw[NP], ce[NP];
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      R cap = mt.c;
+      if (LAT) {
+        const R z = (v[q] + mt.tm_off) * mt.inv_sigma;
+        cap = mt.c + mt.lat_norm * expo(R(-0.5) * z * z);
+      }
+      cw[q] = mt.rho * cap * (R(wq3<P>(q)) * detJ);
+    }
+    integrate_values<P, R>(cw, ce);
+    scatter<P, R>(M, C, Ch, cell, inst, ce);
+  }
+  if (MODE == MODE_CAPACITY) return;
+
+  // conductivity at quadrature points times quadrature weight and det J: the D_e of
+  // Eq. diffusive_term_evaluation for a diagonal Jacobian
+  const int mat = M.cell_mat[cell];
+  const R* ks = kscale_of<R>(L);
+  const R scale = (mat == 1 ? mt.powder_scale : R(1)) * (ks ? ks[inst] : R(1));
+  const R sgn = (MODE == MODE_RESIDUAL) ? R(-1) : R(1);
+  R kw[NP];
+  {
+    const R k0 = mt.k0 * scale, dk = mt.dk * scale;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      R k = k0;
+      if (NLK) k = k0 + dk * clamp01((v[q] + mt.tk_off) * mt.inv_dT);
+      kw[q] = sgn * k * (R(wq3<P>(q)) * detJ);
+    }
+  }
+  R r[NP], g[NP];
+  {
+    const R cd = geo.ih2[lev][0];
+    apply1d<P, 1, 0, false, false>(v, g);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) g[q] *= kw[q] * cd;
+    apply1d<P, 1, 0, true, false>(g, r);
+  }
+  {
+    const R cd = geo.ih2[lev][1];
+    apply1d<P, 1, 1, false, false>(v, g);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) g[q] *= kw[q] * cd;
+    apply1d<P, 1, 1, true, true>(g, r);
+  }
+  {
+    const R cd = geo.ih2[lev][2];
+    apply1d<P, 1, 2, false, false>(v, g);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) g[q] *= kw[q] * cd;
+    apply1d<P, 1, 2, true, true>(g, r);
+  }
+  if (MODE == MODE_IMPLICIT) {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r[q] += mt.m_impl * (R(wq3<P>(q)) * detJ) * v[q];
+  }
+  R fe[NP];
+  integrate_values<P, R>(r, fe);
+  scatter<P, R>(M, f, fh, cell, inst, fe);
+}
+
+// Diagonal of P^T A_e P for the implicit operator A = C/dt + K (FP64, setup): the cell
+// matrix column A_e e_b is computed matrix-free for every local node b, the way the paper
+// remarks that a matrix can be assembled from products with unit vectors (Sec. 4.2).
+template <int P>
+__global__ void __launch_bounds__(64) k_diag(const CellLaunch L, double* __restrict__ diag) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  const DevMesh& M = L.mesh;
+  const MatR<double>& mt = L.md;
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= M.n_cells) return;
+  const int lev = M.cell_level[cell];
+  const double detJ = L.gd.detJ[lev];
+  const int mat = M.cell_mat[cell];
+  const double k = mt.k0 * (mat == 1 ? mt.powder_scale : 1.0) * (L.k_scale_d ? L.k_scale_d[0] : 1.0);
+  for (int b = 0; b < NP; ++b) {
+    double u[NP], v[NP], r[NP], g[NP], col[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) u[a] = (a == b) ? 1.0 : 0.0;
+    values_at_qp<P, double>(u, v);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) r[a] = 0.0;
+    apply1d<P, 1, 0, false, false>(v, g);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) g[q] *= k * wq3<P>(q) * detJ * L.gd.ih2[lev][0];
+    apply1d<P, 1, 0, true, true>(g, r);
+    apply1d<P, 1, 1, false, false>(v, g);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) g[q] *= k * wq3<P>(q) * detJ * L.gd.ih2[lev][1];
+    apply1d<P, 1, 1, true, true>(g, r);
+    apply1d<P, 1, 2, false, false>(v, g);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) g[q] *= k * wq3<P>(q) * detJ * L.gd.ih2[lev][2];
+    apply1d<P, 1, 2, true, true>(g, r);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r[q] += mt.m_impl * wq3<P>(q) * detJ * v[q];
+    integrate_values<P, double>(r, col);
+    const int db = M.cell_dofs[b * M.n_cells + cell];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const int da = M.cell_dofs[a * M.n_cells + cell];
+      if (da >= 0 && db >= 0) {
+        if (a == b) atomicAdd(&diag[da], col[a]);
+        continue;
+      }
+      // a hanging node is involved: sum over common masters m of w_am w_bm A_ab
+      const int ra0 = da >= 0 ? 0 : M.con_ptr[-1 - da], ra1 = da >= 0 ? 1 : M.con_ptr[-da];
+      const int rb0 = db >= 0 ? 0 : M.con_ptr[-1 - db], rb1 = db >= 0 ? 1 : M.con_ptr[-db];
+      for (int ea = ra0; ea < ra1; ++ea) {
+        const int ma = da >= 0 ? da : M.con_idx[ea];
+        const double wa = da >= 0 ? 1.0 : M.con_w[ea];
+        for (int eb = rb0; eb < rb1; ++eb) {
+          const int mb = db >= 0 ? db : M.con_idx[eb];
+          if (mb != ma) continue;
+          const double wb = db >= 0 ? 1.0 : M.con_w[eb];
+          atomicAdd(&diag[ma], wa * wb * col[a]);
+        }
+      }
+    }
+  }
+}
+
+template <int P, typename R, int MODE, bool NLK, bool LAT>
+cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
+  const int64_t n = (int64_t)L.mesh.n_cells * L.mesh.batch;
+  if (n == 0) return cudaSuccess;
+  const int bs = 128;
+  const int64_t grid = (n + bs - 1) / bs;
+  k_cell<P, R, MODE, NLK, LAT><<<(unsigned)grid, bs, 0, s>>>(L, (R*)f, (R*)fh, (R*)C, (R*)Ch);
+  return cudaGetLastError();
+}
+
+template <int P, typename R>
+cudaError_t dispatch(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, int mode, cudaStream_t s) {
+  const bool nl = L.nonlin_k != 0, lat = L.latent != 0;
+  switch (mode) {
+    case MODE_RESIDUAL:
+      if (nl && lat) return go<P, R, MODE_RESIDUAL, true, true>(L, f, fh, C, Ch, s);
+      if (nl) return go<P, R, MODE_RESIDUAL, true, false>(L, f, fh, C, Ch, s);
+      if (lat) return go<P, R, MODE_RESIDUAL, false, true>(L, f, fh, C, Ch, s);
+      return go<P, R, MODE_RESIDUAL, false, false>(L, f, fh, C, Ch, s);
+    case MODE_CAPACITY:
+      if (lat) return go<P, R, MODE_CAPACITY, false, true>(L, f, fh, C, Ch, s);
+      return go<P, R, MODE_CAPACITY, false, false>(L, f, fh, C, Ch, s);
+    case MODE_STIFF:
+      return go<P, R, MODE_STIFF, false, false>(L, f, fh, C, Ch, s);
+    case MODE_IMPLICIT:
+      return go<P, R, MODE_IMPLICIT, false, false>(L, f, fh, C, Ch, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_cell(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, int mode, cudaStream_t s) {
+  if (L.degree == 1)
+    return L.f32 ? dispatch<1, float>(L, f, fh, C, Ch, mode, s) : dispatch<1, double>(L, f, fh, C, Ch, mode, s);
+  if (L.degree == 2)
+    return L.f32 ? dispatch<2, float>(L, f, fh, C, Ch, mode, s) : dispatch<2, double>(L, f, fh, C, Ch, mode, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_diag(const CellLaunch& L, double* diag, cudaStream_t s) {
+  const int n = L.mesh.n_cells;
+  if (n == 0) return cudaSuccess;
+  const int bs = 64;
+  if (L.degree == 1) k_diag<1><<<(n + bs - 1) / bs, bs, 0, s>>>(L, diag);
+  else k_diag<2><<<(n + bs - 1) / bs, bs, 0, s>>>(L, diag);
+  return cudaGetLastError();
+}
+
+}  // namespace pbf

@@ -1,0 +1,463 @@
+// Canonical mesh construction for the library (host C++).
+//
+// Design: a linear octree. Leaves are kept sorted by a global key (tree index, then the
+// Morton interleave of the anchor inside the tree, x least significant), which is the
+// paper's Z-curve order (Sec. 4.1). A lattice point is located by binary search on the
+// keys. Nodes are grouped by sorting (node key, cell slot) pairs; hanging nodes are found by
+// probing the leaves around each node. The rules reproduce the canonical specification of
+// the repository exactly (bit for bit), including the floating-point geometry tests.
+#include "mesh.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <map>
+
+namespace pbf {
+
+double HostMesh::coord(int axis, int64_t lattice) const {
+  return desc.origin[axis] + desc.tree_h[axis] * ((double)lattice / (double)((int64_t)1 << L));
+}
+
+bool HostMesh::inside(const int64_t q[3]) const {
+  for (int a = 0; a < 3; ++a)
+    if (q[a] < 0 || q[a] >= ext[a]) return false;
+  if (exists.empty()) return true;
+  int64_t t = (q[0] >> L) + desc.ntree[0] * ((q[1] >> L) + (int64_t)desc.ntree[1] * (q[2] >> L));
+  return exists[(size_t)t] != 0;
+}
+
+static inline uint64_t spread3(uint64_t v, int bits) {
+  uint64_t r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((v >> b) & 1ull) << (3 * b);
+  return r;
+}
+
+uint64_t HostMesh::morton_key(const int64_t q[3]) const {
+  uint64_t t = (uint64_t)((q[0] >> L) + desc.ntree[0] * ((q[1] >> L) + (int64_t)desc.ntree[1] * (q[2] >> L)));
+  uint64_t mask = ((uint64_t)1 << L) - 1;
+  uint64_t m = spread3((uint64_t)q[0] & mask, L) | (spread3((uint64_t)q[1] & mask, L) << 1) |
+               (spread3((uint64_t)q[2] & mask, L) << 2);
+  return (t << (3 * L)) | m;
+}
+
+int64_t HostMesh::locate(const int64_t q[3]) const {
+  if (!inside(q)) return -1;
+  uint64_t k = morton_key(q);
+  auto it = std::upper_bound(key.begin(), key.end(), k);
+  if (it == key.begin()) return -1;
+  int64_t i = (int64_t)(it - key.begin()) - 1;
+  const Octant& o = oct[(size_t)i];
+  int64_t s = size(o);
+  for (int a = 0; a < 3; ++a)
+    if (q[a] < o.a[a] || q[a] >= o.a[a] + s) return -1;
+  return i;
+}
+
+pbf_status init_mesh(HostMesh& m, const pbf_mesh_desc& d, std::string* err) {
+  if (d.degree != 1 && d.degree != 2) return *err = "degree must be 1 or 2", PBF_EINVAL;
+  if (d.max_level < 0 || d.max_level > 12) return *err = "max_level must be in [0, 12]", PBF_EINVAL;
+  for (int a = 0; a < 3; ++a) {
+    if (d.ntree[a] < 1 || ((int64_t)d.ntree[a] << d.max_level) >= ((int64_t)1 << 20))
+      return *err = "ntree out of range", PBF_EINVAL;
+    if (!(d.tree_h[a] > 0.0)) return *err = "tree_h must be positive", PBF_EINVAL;
+  }
+  if (d.n_regions < 0 || (d.n_regions > 0 && !d.regions)) return *err = "bad region list", PBF_EINVAL;
+  m.desc = d;
+  m.p = d.degree;
+  m.L = d.max_level;
+  m.npc = (m.p + 1) * (m.p + 1) * (m.p + 1);
+  for (int a = 0; a < 3; ++a) m.ext[a] = (int64_t)d.ntree[a] << m.L;
+  m.exists.clear();
+  if (d.tree_exists) m.exists.assign(d.tree_exists, d.tree_exists + (size_t)d.ntree[0] * d.ntree[1] * d.ntree[2]);
+  m.regions.assign(d.regions, d.regions + d.n_regions);
+  for (const pbf_region& r : m.regions)
+    if (r.kind != PBF_REGION_BALL && r.kind != PBF_REGION_BOX) return *err = "bad region kind", PBF_EINVAL;
+  m.desc.tree_exists = nullptr;
+  m.desc.regions = nullptr;
+  return PBF_OK;
+}
+
+// ---- refinement ----------------------------------------------------------------------
+
+static int region_target(const HostMesh& m, const Octant& o) {
+  int64_t s = m.size(o);
+  double lo[3], hi[3];
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = m.coord(a, o.a[a]);
+    hi[a] = m.coord(a, o.a[a] + s);
+  }
+  int best = 0;
+  for (const pbf_region& r : m.regions) {
+    const double* cmin = r.a;
+    const double* cmax = r.kind == PBF_REGION_BALL ? r.a : r.b;
+    double d2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double g = 0.0;
+      if (cmin[a] > hi[a]) g = cmin[a] - hi[a];
+      else if (lo[a] > cmax[a]) g = lo[a] - cmax[a];
+      d2 += g * g;
+    }
+    if (d2 < r.radius * r.radius && r.level > best) best = r.level;
+  }
+  return best < m.L ? best : m.L;
+}
+
+static void push_children(const HostMesh& m, const Octant& o, std::vector<Octant>& out) {
+  int64_t h = m.size(o) >> 1;
+  for (int c = 0; c < 8; ++c)
+    out.push_back(Octant{{o.a[0] + (c & 1) * h, o.a[1] + ((c >> 1) & 1) * h, o.a[2] + ((c >> 2) & 1) * h}, o.level + 1});
+}
+
+static void refine_tree(const HostMesh& m, const Octant& o, std::vector<Octant>& out) {
+  if (o.level < region_target(m, o)) {
+    std::vector<Octant> kids;
+    push_children(m, o, kids);
+    for (const Octant& k : kids) refine_tree(m, k, out);
+  } else {
+    out.push_back(o);
+  }
+}
+
+static void rekey(HostMesh& m) {
+  m.key.resize(m.oct.size());
+  for (size_t i = 0; i < m.oct.size(); ++i) m.key[i] = m.morton_key(m.oct[i].a);
+}
+
+static void balance(HostMesh& m) {
+  for (;;) {
+    std::vector<uint8_t> split(m.oct.size(), 0);
+    bool any = false;
+    for (size_t i = 0; i < m.oct.size(); ++i) {
+      const Octant& o = m.oct[i];
+      int64_t s = m.size(o);
+      for (int nb = 0; nb < 27; ++nb) {
+        if (nb == 13) continue;
+        int64_t q[3] = {o.a[0] + (nb % 3 - 1) * s, o.a[1] + ((nb / 3) % 3 - 1) * s, o.a[2] + (nb / 9 - 1) * s};
+        int64_t j = m.locate(q);
+        if (j >= 0 && m.oct[(size_t)j].level < o.level - 1 && !split[(size_t)j]) {
+          split[(size_t)j] = 1;
+          any = true;
+        }
+      }
+    }
+    if (!any) return;
+    std::vector<Octant> next;
+    next.reserve(m.oct.size() + 8);
+    for (size_t i = 0; i < m.oct.size(); ++i) {
+      if (split[i]) push_children(m, m.oct[i], next);
+      else next.push_back(m.oct[i]);
+    }
+    m.oct.swap(next);
+    rekey(m);
+  }
+}
+
+// ---- nodes ----------------------------------------------------------------------------
+
+static inline uint64_t pack_node(const int64_t n[3]) {
+  return ((uint64_t)n[2] << 42) | ((uint64_t)n[1] << 21) | (uint64_t)n[0];
+}
+
+// 1D Lagrange weights of degree p at position u (node-lattice units) on a cell whose nodes
+// sit at 0, s, .., p s.
+static void weights_1d(int p, int64_t u, int64_t s, double w[3]) {
+  double t = (double)u / (double)s;  // node-spacing units: nodes at t = 0..p
+  if (p == 1) {
+    w[0] = 1.0 - t;
+    w[1] = t;
+  } else {
+    w[0] = 0.5 * (t - 1.0) * (t - 2.0);
+    w[1] = t * (2.0 - t);
+    w[2] = 0.5 * t * (t - 1.0);
+  }
+}
+
+struct NodeTable {
+  std::vector<uint64_t> keys;  // sorted unique
+  std::vector<int64_t> xyz;    // [n][3]
+  int64_t find(const int64_t n[3]) const {
+    uint64_t k = pack_node(n);
+    auto it = std::lower_bound(keys.begin(), keys.end(), k);
+    return (it != keys.end() && *it == k) ? (int64_t)(it - keys.begin()) : -1;
+  }
+};
+
+// The active cells whose closure holds node n, found by probing the eight octants around it;
+// returns the smallest active index among those that do not have n as a nodal point (-1:
+// none, i.e. the node is a proper dof).
+static int32_t first_coarse_holder(const HostMesh& m, const int64_t n[3]) {
+  int32_t best = -1;
+  for (int o = 0; o < 8; ++o) {
+    int64_t q[3];
+    bool ok = true;
+    for (int a = 0; a < 3; ++a) {
+      int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);  // half node-lattice units
+      if (h2 < 0) { ok = false; break; }
+      q[a] = h2 / (2 * m.p);
+    }
+    if (!ok) continue;
+    int64_t leaf = m.locate(q);
+    if (leaf < 0 || !m.active[(size_t)leaf]) continue;
+    const Octant& c = m.oct[(size_t)leaf];
+    int64_t s = m.size(c);
+    bool nodal = true;
+    for (int a = 0; a < 3; ++a)
+      if ((n[a] - m.p * c.a[a]) % s != 0) nodal = false;
+    if (nodal) continue;
+    int32_t ai = m.active_of_leaf[(size_t)leaf];
+    if (best < 0 || ai < best) best = ai;
+  }
+  return best;
+}
+
+pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::string* err) {
+  const int p = m.p;
+  // forest
+  m.oct.clear();
+  for (int tz = 0; tz < m.desc.ntree[2]; ++tz)
+    for (int ty = 0; ty < m.desc.ntree[1]; ++ty)
+      for (int tx = 0; tx < m.desc.ntree[0]; ++tx) {
+        Octant root{{(int64_t)tx << m.L, (int64_t)ty << m.L, (int64_t)tz << m.L}, 0};
+        if (m.inside(root.a)) refine_tree(m, root, m.oct);
+      }
+  if (m.oct.empty()) return *err = "no trees exist", PBF_EINVAL;
+  rekey(m);
+  balance(m);
+  size_t nl = m.oct.size();
+  // activity and material
+  m.active.assign(nl, 0);
+  m.material.assign(nl, 0);
+  m.active_of_leaf.assign(nl, -1);
+  m.leaf_of_active.clear();
+  for (size_t i = 0; i < nl; ++i) {
+    const Octant& o = m.oct[i];
+    double z0 = m.coord(2, o.a[2]), z1 = m.coord(2, o.a[2] + m.size(o));
+    m.active[i] = z0 < m.desc.active_top_z;
+    double zc = 0.5 * (z0 + z1);
+    m.material[i] = (zc >= m.desc.powder_z0 && zc < m.desc.powder_z1) ? 1 : 0;
+    if (mat_hint) m.material[i] = (*mat_hint)[i];
+    if (m.active[i]) {
+      m.active_of_leaf[i] = (int32_t)m.leaf_of_active.size();
+      m.leaf_of_active.push_back((int32_t)i);
+    }
+  }
+  size_t na = m.leaf_of_active.size();
+  const int npc = m.npc;
+  // node table: sort (node key, slot)
+  std::vector<std::pair<uint64_t, int64_t>> ents;
+  ents.reserve(na * (size_t)npc);
+  for (size_t c = 0; c < na; ++c) {
+    const Octant& o = m.oct[(size_t)m.leaf_of_active[c]];
+    int64_t s = m.size(o);
+    for (int l = 0; l < npc; ++l) {
+      int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
+      int64_t n[3];
+      for (int a = 0; a < 3; ++a) n[a] = p * o.a[a] + ijk[a] * s;
+      ents.push_back({pack_node(n), (int64_t)(c * (size_t)npc + (size_t)l)});
+    }
+  }
+  std::sort(ents.begin(), ents.end());
+  NodeTable nodes;
+  std::vector<int32_t> node_of_slot(na * (size_t)npc);
+  for (size_t e = 0; e < ents.size(); ++e) {
+    if (e == 0 || ents[e].first != ents[e - 1].first) {
+      nodes.keys.push_back(ents[e].first);
+      uint64_t k = ents[e].first;
+      nodes.xyz.push_back((int64_t)(k & 0x1FFFFF));
+      nodes.xyz.push_back((int64_t)((k >> 21) & 0x1FFFFF));
+      nodes.xyz.push_back((int64_t)(k >> 42));
+    }
+    node_of_slot[(size_t)ents[e].second] = (int32_t)nodes.keys.size() - 1;
+  }
+  size_t nn = nodes.keys.size();
+  std::vector<int32_t> holder(nn);
+  for (size_t i = 0; i < nn; ++i) holder[i] = first_coarse_holder(m, &nodes.xyz[i * 3]);
+  // first-touch numbering of dofs and of constraint rows
+  std::vector<int32_t> dof(nn, -1), row(nn, -1);
+  m.n_dofs = 0;
+  int32_t n_rows = 0;
+  std::vector<int32_t> row_node;
+  m.dof_xyz.clear();
+  for (size_t slot = 0; slot < node_of_slot.size(); ++slot) {
+    int32_t nd = node_of_slot[slot];
+    if (holder[(size_t)nd] >= 0) {
+      if (row[(size_t)nd] < 0) {
+        row[(size_t)nd] = n_rows++;
+        row_node.push_back(nd);
+      }
+    } else if (dof[(size_t)nd] < 0) {
+      dof[(size_t)nd] = (int32_t)m.n_dofs++;
+      for (int a = 0; a < 3; ++a) m.dof_xyz.push_back(nodes.xyz[(size_t)nd * 3 + a]);
+    }
+  }
+  if (m.n_dofs >= ((int64_t)1 << 31)) return *err = "too many dofs", PBF_EINVAL;
+  // constraint rows, with chains substituted (memoised by node)
+  std::map<int32_t, std::vector<std::pair<int32_t, double>>> memo;
+  std::vector<std::pair<int32_t, double>> stackbuf;
+  std::function<const std::vector<std::pair<int32_t, double>>&(int32_t)> expand;
+  expand = [&](int32_t nd) -> const std::vector<std::pair<int32_t, double>>& {
+    auto it = memo.find(nd);
+    if (it != memo.end()) return it->second;
+    const Octant& c = m.oct[(size_t)m.leaf_of_active[(size_t)holder[(size_t)nd]]];
+    int64_t s = m.size(c);
+    double w1[3][3];
+    for (int a = 0; a < 3; ++a) weights_1d(p, nodes.xyz[(size_t)nd * 3 + a] - p * c.a[a], s, w1[a]);
+    std::vector<std::pair<int32_t, double>> acc;
+    for (int l = 0; l < npc; ++l) {
+      int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
+      double w = w1[0][ijk[0]] * w1[1][ijk[1]] * w1[2][ijk[2]];
+      if (w == 0.0) continue;
+      int64_t q[3];
+      for (int a = 0; a < 3; ++a) q[a] = p * c.a[a] + ijk[a] * s;
+      int32_t mn = (int32_t)nodes.find(q);
+      if (holder[(size_t)mn] >= 0) {
+        const auto& sub = expand(mn);
+        for (const auto& e : sub) acc.push_back({e.first, w * e.second});
+      } else {
+        acc.push_back({dof[(size_t)mn], w});
+      }
+    }
+    std::stable_sort(acc.begin(), acc.end(),
+                     [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
+    std::vector<std::pair<int32_t, double>> out;
+    for (size_t e = 0; e < acc.size();) {
+      size_t f = e;
+      double sum = 0.0;
+      while (f < acc.size() && acc[f].first == acc[e].first) sum += acc[f++].second;
+      if (sum != 0.0) out.push_back({acc[e].first, sum});
+      e = f;
+    }
+    return memo[nd] = out;
+  };
+  m.con_ptr.assign(1, 0);
+  m.con_idx.clear();
+  m.con_w.clear();
+  m.hang_xyz.clear();
+  for (int32_t r = 0; r < n_rows; ++r) {
+    int32_t nd = row_node[(size_t)r];
+    for (const auto& e : expand(nd)) {
+      m.con_idx.push_back(e.first);
+      m.con_w.push_back(e.second);
+    }
+    m.con_ptr.push_back((int32_t)m.con_idx.size());
+    for (int a = 0; a < 3; ++a) m.hang_xyz.push_back(nodes.xyz[(size_t)nd * 3 + a]);
+  }
+  // cell table
+  m.cell_dofs.resize(na * (size_t)npc);
+  for (size_t slot = 0; slot < node_of_slot.size(); ++slot) {
+    int32_t nd = node_of_slot[slot];
+    m.cell_dofs[slot] = holder[(size_t)nd] >= 0 ? -1 - row[(size_t)nd] : dof[(size_t)nd];
+  }
+  // Dirichlet dofs
+  m.dirichlet.assign((size_t)m.n_dofs, 0);
+  for (int64_t i = 0; i < m.n_dofs; ++i)
+    for (int a = 0; a < 3; ++a) {
+      int64_t v = m.dof_xyz[(size_t)i * 3 + a];
+      if ((m.desc.dirichlet_faces & (1u << (2 * a))) && v == 0) m.dirichlet[(size_t)i] = 1;
+      if ((m.desc.dirichlet_faces & (1u << (2 * a + 1))) && v == p * m.ext[a]) m.dirichlet[(size_t)i] = 1;
+    }
+  // greedy colouring with per-dof colour masks (up to 256 colours)
+  const int W = 4;
+  std::vector<uint64_t> used((size_t)m.n_dofs * W, 0);
+  m.colour.assign(na, 0);
+  m.n_colours = 0;
+  std::vector<int32_t> touched;
+  for (size_t c = 0; c < na; ++c) {
+    touched.clear();
+    for (int l = 0; l < npc; ++l) {
+      int32_t v = m.cell_dofs[c * (size_t)npc + (size_t)l];
+      if (v >= 0) touched.push_back(v);
+      else
+        for (int32_t e = m.con_ptr[(size_t)(-1 - v)]; e < m.con_ptr[(size_t)(-v)]; ++e) touched.push_back(m.con_idx[(size_t)e]);
+    }
+    uint64_t busy[W] = {0, 0, 0, 0};
+    for (int32_t t : touched)
+      for (int w = 0; w < W; ++w) busy[w] |= used[(size_t)t * W + w];
+    int col = -1;
+    for (int w = 0; w < W && col < 0; ++w)
+      if (~busy[w]) col = 64 * w + __builtin_ctzll(~busy[w]);
+    if (col < 0) return *err = "colouring needs more than 256 colours", PBF_EINVAL;
+    m.colour[c] = col;
+    if (col + 1 > m.n_colours) m.n_colours = col + 1;
+    for (int32_t t : touched) used[(size_t)t * W + (size_t)(col / 64)] |= 1ull << (col % 64);
+  }
+  // top faces
+  m.top.assign(na, 0);
+  m.n_top = 0;
+  for (size_t c = 0; c < na; ++c) {
+    const Octant& o = m.oct[(size_t)m.leaf_of_active[c]];
+    int64_t up[3] = {o.a[0], o.a[1], o.a[2] + m.size(o)};
+    bool open = !m.inside(up) || !(m.coord(2, up[2]) < m.desc.active_top_z);
+    m.top[c] = open;
+    m.n_top += open;
+  }
+  ++m.generation;
+  return PBF_OK;
+}
+
+// ---- transfer ----------------------------------------------------------------------------
+
+void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, TransferMap& out) {
+  const int p = om.p, npc = om.npc;
+  out.pending = true;
+  out.n_old = om.n_dofs;
+  out.n_new = nm.n_dofs;
+  out.fill = fill;
+  out.ptr.assign(1, 0);
+  out.idx.clear();
+  out.w.clear();
+  std::vector<std::pair<int32_t, double>> acc;
+  for (int64_t i = 0; i < nm.n_dofs; ++i) {
+    const int64_t* n = &nm.dof_xyz[(size_t)i * 3];
+    // first old active cell (cell order) whose closure holds the point
+    int32_t best = -1;
+    for (int o = 0; o < 8; ++o) {
+      int64_t q[3];
+      bool ok = true;
+      for (int a = 0; a < 3; ++a) {
+        int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);
+        if (h2 < 0) { ok = false; break; }
+        q[a] = h2 / (2 * p);
+      }
+      if (!ok) continue;
+      int64_t leaf = om.locate(q);
+      if (leaf < 0 || !om.active[(size_t)leaf]) continue;
+      int32_t ai = om.active_of_leaf[(size_t)leaf];
+      if (best < 0 || ai < best) best = ai;
+    }
+    if (best >= 0) {
+      const Octant& c = om.oct[(size_t)om.leaf_of_active[(size_t)best]];
+      int64_t s = om.size(c);
+      double w1[3][3];
+      for (int a = 0; a < 3; ++a) weights_1d(p, n[a] - p * c.a[a], s, w1[a]);
+      acc.clear();
+      for (int l = 0; l < npc; ++l) {
+        int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
+        double w = w1[0][ijk[0]] * w1[1][ijk[1]] * w1[2][ijk[2]];
+        if (w == 0.0) continue;
+        int32_t v = om.cell_dofs[(size_t)best * (size_t)npc + (size_t)l];
+        if (v >= 0) acc.push_back({v, w});
+        else
+          for (int32_t e = om.con_ptr[(size_t)(-1 - v)]; e < om.con_ptr[(size_t)(-v)]; ++e)
+            acc.push_back({om.con_idx[(size_t)e], w * om.con_w[(size_t)e]});
+      }
+      std::stable_sort(acc.begin(), acc.end(),
+                       [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
+      for (size_t e = 0; e < acc.size();) {
+        size_t f = e;
+        double sum = 0.0;
+        while (f < acc.size() && acc[f].first == acc[e].first) sum += acc[f++].second;
+        if (sum != 0.0) {
+          out.idx.push_back(acc[e].first);
+          out.w.push_back(sum);
+        }
+        e = f;
+      }
+    }
+    out.ptr.push_back((int32_t)out.idx.size());
+  }
+}
+
+}  // namespace pbf

@@ -1,0 +1,89 @@
+// Context state shared by the C-ABI entry points (capi.cu) and the solvers (solver.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+#include "mesh.hpp"
+#include "pbf.h"
+#include "vec_kernels.cuh"
+
+namespace pbf {
+
+pbf_status set_error(pbf_status s, const char* msg);
+
+struct CtxBase {
+  const HostMesh* mesh = nullptr;
+  int64_t generation = 0;
+  int degree = 1, npc = 8, batch = 1;
+  int64_t n_dofs = 0, n_cells = 0, n_hang = 0, n_top = 0;
+  bool f32 = false, nonlin = false, latent = false;
+  int cap = 0;          // CAP_CONST, CAP_QUADRATURE or CAP_NODAL
+  NodalCap nodal;
+  pbf_material mat{};
+  CellLaunch base;
+  LaserSetup lsetup;
+  std::vector<void*> allocs;
+  // mesh tables
+  int32_t* cell_dofs = nullptr;
+  uint8_t* cell_level = nullptr;
+  uint8_t* cell_mat = nullptr;
+  int32_t* con_ptr = nullptr;
+  int32_t* con_idx = nullptr;
+  double* con_w = nullptr;
+  float* con_wf = nullptr;
+  uint8_t* dirichlet = nullptr;
+  int32_t* top_cell = nullptr;
+  double* top_geo = nullptr;
+  double* cell_lo = nullptr;
+  double* level_h = nullptr;
+  // material / instance data
+  double* k_scale_d = nullptr;
+  float* k_scale_f = nullptr;
+  std::vector<double> k_scale_host;
+  double* power = nullptr;  // [batch][kMaxSeg]
+  std::vector<double> power_host;
+  // work space
+  void* f = nullptr;     // operator accumulator (FP32 or FP64) [n_dofs][batch]
+  void* fvol = nullptr;  // laser accumulator [n_dofs][batch]
+  void* Cacc = nullptr;  // capacity accumulator (latent heat) [n_dofs][batch]
+  double* Tw = nullptr;  // FP32 operator: FP64 working state T - T_ref [n_dofs][batch]
+  float* Tf = nullptr;   // FP32 operator: its FP32 rounding, gathered by the cell kernel
+  void* xh = nullptr;    // input values at hanging nodes (FP32 or FP64) [n_hang][batch]
+  double* xh64 = nullptr;  // FP64 hanging values for FP64-operator launches of an FP32 context
+  void* fh = nullptr;    // operator accumulator at hanging nodes [n_hang][batch]
+  void* Ch = nullptr;    // capacity accumulator at hanging nodes
+  double* fh64 = nullptr;  // FP64 accumulators for FP64-operator launches of an FP32 context
+  double* Ch64 = nullptr;
+  double* C0 = nullptr;  // lumped capacity with the plain c [n_dofs]
+  double* invC0_d = nullptr;
+  float* invC0_f = nullptr;
+  double* part = nullptr;  // reduction partials [reduction_blocks][batch]
+  double* scal = nullptr;  // device scalars [batch][16]
+  std::vector<double*> vec;  // FP64 work vectors [n_dofs][batch]
+  // implicit-operator diagonal cache
+  double* diag = nullptr;
+  double diag_dt = -1.0;
+  // state
+  bool poisoned = false;
+  bool timing = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events, free_events;
+  long long launches = 0;
+
+  void set_material_constants(double dt);
+  void release();
+  pbf_status check_usable();
+  pbf_status cuda(cudaError_t e, const char* what);
+  pbf_status set_laser(const pbf_laser* ls, cudaStream_t s);
+  pbf_status ensure_vectors(int n);
+  cudaError_t dalloc_raw(double** p, size_t n);
+  // One operator application: hanging values of the input, the cell kernel (timed when timing
+  // is on), and the distribution of hanging-node contributions to their masters.
+  // L.x (FP64) or L.xf (FP32) must be set; f and C (nullable) are the dof accumulators.
+  cudaError_t apply_cell(CellLaunch L, void* f, void* C, int mode, cudaStream_t s);
+};
+
+}  // namespace pbf

@@ -1,0 +1,59 @@
+// Launchers of the streaming kernels (vec_kernels.cu); internal to the library.
+#pragma once
+
+#include "internal.cuh"
+
+namespace pbf {
+
+struct LaserSetup {
+  LaserK k;
+  int n_top = 0;
+  const int32_t* top_cell = nullptr;  // [n_top] active cell index
+  const double* top_geo = nullptr;    // [n_top][4]: x0, y0, hx, hy of the face
+  const double* cell_lo = nullptr;    // [n_cells][3] lower corner (volumetric source)
+  const double* level_h = nullptr;    // [levels][3]
+};
+
+// Lumped-capacity forms of the update: constant c, quadrature-point row sum accumulated by
+// the cell kernel, or nodal apparent capacity c_app(T_i) x row-sum mass.
+enum { CAP_CONST = 0, CAP_QUADRATURE = 1, CAP_NODAL = 2 };
+struct NodalCap {
+  double lat_ratio = 0.0, Tm = 0.0, inv_sigma = 0.0;  // c_app/c = 1 + lat_ratio exp(-((T-Tm) inv_sigma)^2/2)
+  float lat_ratio_f = 0.f, tm_off_f = 0.f, inv_sigma_f = 0.f;  // FP32 form on T - T_ref
+};
+cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double* f, double* Cacc,
+                              const double* invC0, const NodalCap& nc, const uint8_t* dirichlet, double T_dir,
+                              double dt, cudaStream_t s);
+cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float* Tf, float* f, float* Cacc,
+                              const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, double tw_dir,
+                              float tf_dir, float dt, cudaStream_t s);
+// C_out[d][b] = C0[d] c_app(T[d][b]) / c (nodal lumping) in FP64
+cudaError_t launch_capacity_nodal(int64_t n_dofs, int B, const double* C0, const double* T, const NodalCap& nc,
+                                  double* C_out, cudaStream_t s);
+cudaError_t launch_prepare_f32(int64_t n, const double* T, double off, double* Tw, float* Tf, cudaStream_t s);
+cudaError_t launch_finish_f32(int64_t n, const double* Tw, double off, double* T, cudaStream_t s);
+cudaError_t launch_round_f32(int64_t n, const double* x, float* y, cudaStream_t s);
+cudaError_t launch_f32_to_f64(int64_t n, const float* x, double* y, cudaStream_t s);
+cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const double* power,
+                         const Spot& sp, void* f, cudaStream_t s);
+// Host evaluation of the spot at time t (first segment with t0 <= t < t1, linear motion).
+Spot spot_at(const LaserK& k, double t);
+cudaError_t launch_to_f64(bool f32, int64_t n, const void* a, double* out, cudaStream_t s);
+cudaError_t launch_broadcast_dofs(int64_t n_dofs, int B, const double* a, double* out, cudaStream_t s);
+cudaError_t launch_reciprocal(int64_t n, const double* c, double* inv_d, float* inv_f, cudaStream_t s);
+// x_h = P_h x (values at hanging nodes) and f += P_h^T f_h (f_h cleared); FP32 or FP64 arrays
+cudaError_t launch_hang_values(bool f32, const DevMesh& M, const void* x, void* out, cudaStream_t s);
+cudaError_t launch_hang_distribute(bool f32, const DevMesh& M, void* fh, void* f, cudaStream_t s);
+int reduction_blocks();
+// out[b] = sum_d w_d x[d][b] y[d][b] over dofs with !skip[d]; part: [reduction_blocks()][B]
+cudaError_t launch_dot(int64_t n_dofs, int B, const double* x, const double* y, const double* w, const uint8_t* skip,
+                       double* part, double* out, cudaStream_t s);
+cudaError_t launch_scale_masked(int64_t n, double* x, const double* sc, const uint8_t* zero_mask, cudaStream_t s);
+cudaError_t launch_div_masked(int64_t n, double* x, const double* y, const double* invC, const uint8_t* mask,
+                              cudaStream_t s);
+cudaError_t launch_zero_masked(int64_t n, double* y, const uint8_t* mask, cudaStream_t s);
+cudaError_t launch_set_masked(int64_t n, double* y, const uint8_t* mask, double v, cudaStream_t s);
+cudaError_t launch_transfer(int64_t n_new, int B, const int32_t* ptr, const int32_t* idx, const double* w,
+                            const double* Told, double fill, double* Tnew, cudaStream_t s);
+
+}  // namespace pbf

@@ -36,9 +36,15 @@ TI64_CONST = dict(rho=4430.0, c=526.0, k0=6.7, k1=6.7, Tk0=300.0, Tk1=300.0,
                   latent=0.0, Tm=1903.0, sigma=0.0, powder_k_scale=0.1,
                   T_dirichlet=353.0, T_ref=353.0)
 
+LUMP_QUADRATURE = 0  # row sum of the consistent capacity, c_app at quadrature points
+LUMP_NODAL = 1       # c_app at the node times the row-sum lumped mass (positive for Q2)
+
 TI64_NONLIN = dict(rho=4430.0, c=526.0, k0=6.7, k1=28.0, Tk0=300.0, Tk1=1928.0,
                    latent=2.86e5, Tm=1903.0, sigma=12.5, powder_k_scale=0.1,
-                   T_dirichlet=353.0, T_ref=353.0)
+                   T_dirichlet=353.0, T_ref=353.0, lumping=LUMP_QUADRATURE)
+
+# the Q2 workloads: nodal apparent capacity (see LUMP_NODAL)
+TI64_NONLIN_Q2 = dict(TI64_NONLIN, lumping=LUMP_NODAL)
 
 # Paper, Table mat_params (stainless steel, bridge example): k = 20, rho = 7430, c = 965
 BRIDGE = dict(rho=7430.0, c=965.0, k0=20.0, k1=20.0, Tk0=303.0, Tk1=303.0,
@@ -173,6 +179,17 @@ def smooth_field(coords, seed, lo=T0, hi=2600.0, batch=None):
             v = v + amp * np.exp(-d2 / (w * w))
         out[:, b] = np.clip(v, lo, hi)
     return out[:, 0] if batch is None else out
+
+
+def melt_pool_field(coords, center, peak=2600.0, width=50e-6, base=T0, seed=None, noise=0.0):
+    """Melt-pool-shaped temperature: base + (peak - base) exp(-|x - center|^2 / width^2), with
+    optional seeded noise of relative amplitude `noise` (coords physical, [n][3])."""
+    d2 = ((np.asarray(coords) - np.asarray(center)) ** 2).sum(axis=1)
+    T = base + (peak - base) * np.exp(-d2 / (width * width))
+    if noise:
+        rng = np.random.default_rng(seed)
+        T = T * (1.0 + noise * rng.uniform(-1, 1, T.shape))
+    return T
 
 
 def start_vector(n, seed=7):

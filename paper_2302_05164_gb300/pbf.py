@@ -1,0 +1,344 @@
+"""Python binding of the C ABI in include/pbf.h (argument marshalling only).
+
+Every numerical step runs in the CUDA library `_build/libpbf.so`; this module converts Python
+objects (dicts from `inputs`, numpy arrays, torch CUDA tensors) into the C structs and
+pointers of the ABI and raises `PbfError` on a non-zero status. There is no fallback: when the
+library is missing, importing the binding fails.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libpbf.so")
+
+PBF_F64, PBF_F32OP = 0, 1
+STATUS = {0: "PBF_OK", 1: "PBF_EINVAL", 2: "PBF_ENOMEM", 3: "PBF_ECUDA", 4: "PBF_ENOCONV", 5: "PBF_ENAN",
+          6: "PBF_ETIMEOUT", 7: "PBF_EFAULT", 8: "PBF_ESTATE"}
+
+
+class PbfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Region(C.Structure):
+    _fields_ = [("kind", C.c_int), ("level", C.c_int), ("a", C.c_double * 3), ("b", C.c_double * 3),
+                ("radius", C.c_double)]
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("origin", C.c_double * 3), ("ntree", C.c_int * 3), ("tree_h", C.c_double * 3),
+                ("degree", C.c_int), ("max_level", C.c_int), ("tree_exists", C.c_void_p),
+                ("active_top_z", C.c_double), ("dirichlet_faces", C.c_uint32), ("n_regions", C.c_int),
+                ("regions", C.c_void_p), ("powder_z0", C.c_double), ("powder_z1", C.c_double)]
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_leaves", "n_active", "n_dofs", "n_hanging", "n_con_entries",
+                                         "n_colours", "n_top_faces", "nodes_per_cell", "generation")]
+
+
+class MeshTables(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("leaves", "material", "cell_dofs", "con_ptr", "con_idx", "con_w",
+                                          "hang_coord", "dof_coord", "dirichlet", "colour", "top")]
+
+
+class Material(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("rho", "c", "k0", "k1", "Tk0", "Tk1", "latent", "Tm", "sigma",
+                                          "powder_k_scale", "T_dirichlet", "T_ref")] + [("lumping", C.c_int)]
+
+
+class Laser(C.Structure):
+    _fields_ = [("n_seg", C.c_int), ("seg", C.c_void_p), ("power", C.c_void_p), ("eta", C.c_double),
+                ("radius", C.c_double), ("volumetric", C.c_int), ("h_powder", C.c_double)]
+
+
+_lib = None
+
+_SIGS = {
+    "pbf_last_error": ([], C.c_char_p),
+    "pbf_version": ([], C.c_char_p),
+    "pbf_mesh_create": ([C.POINTER(MeshDesc), C.POINTER(C.c_void_p)], C.c_int),
+    "pbf_mesh_destroy": ([C.c_void_p], C.c_int),
+    "pbf_mesh_info": ([C.c_void_p, C.POINTER(MeshInfo)], C.c_int),
+    "pbf_mesh_export": ([C.c_void_p, C.POINTER(MeshTables)], C.c_int),
+    "pbf_mesh_activate_layer": ([C.c_void_p, C.c_double, C.c_int, C.c_double], C.c_int),
+    "pbf_mesh_adapt": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "pbf_mesh_transfer": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "pbf_ctx_create": ([C.c_void_p, C.POINTER(Material), C.c_int, C.c_int, C.POINTER(C.c_void_p)], C.c_int),
+    "pbf_ctx_destroy": ([C.c_void_p], C.c_int),
+    "pbf_ctx_set_k_scale": ([C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_eval_residual": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p], C.c_int),
+    "pbf_explicit_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_void_p], C.c_int),
+    "pbf_estimate_dt": ([C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double),
+                         C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p], C.c_int),
+    "pbf_cheb_bounds": ([C.c_void_p, C.c_double, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_implicit_solve": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                            C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_adjoint_sweep": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
+                           C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong),
+                           C.c_void_p], C.c_int),
+    "pbf_revolve_cost": ([C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
+    "pbf_round_to_f32": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "pbf_widen_to_f64": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
+    "pbf_ctx_set_timing": ([C.c_void_p, C.c_int], C.c_int),
+    "pbf_ctx_kernel_time": ([C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
+    "pbf_ctx_launch_count": ([C.c_void_p, C.POINTER(C.c_longlong)], C.c_int),
+}
+
+
+def lib():
+    """Loads the CUDA library; raises ImportError when it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"CUDA library not built: {LIB_PATH} is missing "
+                              "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != 0:
+        raise PbfError(status, lib().pbf_last_error().decode())
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return C.c_void_p(x.data_ptr())
+    return C.c_void_p(x.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+# ---- marshalling helpers -----------------------------------------------------------------
+
+def _regions(regions):
+    arr = (Region * max(1, len(regions)))()
+    for i, (k, a, b, r, lv) in enumerate(regions):
+        arr[i] = Region(int(k), int(lv), (C.c_double * 3)(*a), (C.c_double * 3)(*b), float(r))
+    return arr
+
+
+def _material(m: dict) -> Material:
+    return Material(*[float(m.get(n, 0.0)) for n, _ in Material._fields_[:-1]], int(m.get("lumping", 0)))
+
+
+class _LaserArg:
+    def __init__(self, ls, batch):
+        if ls is None:
+            self.ref = None
+            return
+        self.seg = np.ascontiguousarray(ls["seg"], np.float64)
+        n = self.seg.shape[0]
+        pw = np.asarray(ls["power"], np.float64)
+        if pw.ndim == 1:
+            pw = np.broadcast_to(pw, (batch, n))
+        self.power = np.ascontiguousarray(pw)
+        self.s = Laser(n, _ptr(self.seg), _ptr(self.power), ls["eta"], ls["radius"],
+                       int(ls.get("volumetric", 0)), float(ls.get("h_powder", 40e-6)))
+        self.ref = C.byref(self.s)
+
+
+# ---- C-ABI functions (same names) -----------------------------------------------------------
+
+def pbf_mesh_create(desc: dict):
+    regs = _regions(desc["regions"])
+    te = desc.get("tree_exists")
+    te = None if te is None else np.ascontiguousarray(te, np.uint8)
+    d = MeshDesc((C.c_double * 3)(*desc["origin"]), (C.c_int * 3)(*desc["ntree"]),
+                 (C.c_double * 3)(*desc["tree_h"]), desc["degree"], desc["max_level"], _ptr(te),
+                 desc["active_top_z"], desc["dirichlet_faces"], len(desc["regions"]),
+                 C.cast(regs, C.c_void_p), desc["powder_z0"], desc["powder_z1"])
+    h = C.c_void_p()
+    _check(lib().pbf_mesh_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def pbf_mesh_destroy(h):
+    _check(lib().pbf_mesh_destroy(h))
+
+
+def pbf_mesh_info(h) -> dict:
+    info = MeshInfo()
+    _check(lib().pbf_mesh_info(h, C.byref(info)))
+    return {n: int(getattr(info, n)) for n, _ in MeshInfo._fields_}
+
+
+def pbf_mesh_export(h) -> dict:
+    i = pbf_mesh_info(h)
+    npc = i["nodes_per_cell"]
+    t = dict(leaves=np.zeros((i["n_leaves"], 5), np.int64), material=np.zeros(i["n_leaves"], np.uint8),
+             cell_dofs=np.zeros((i["n_active"], npc), np.int32), con_ptr=np.zeros(i["n_hanging"] + 1, np.int32),
+             con_idx=np.zeros(i["n_con_entries"], np.int32), con_w=np.zeros(i["n_con_entries"], np.float64),
+             hang_coord=np.zeros((i["n_hanging"], 3), np.int64), dof_coord=np.zeros((i["n_dofs"], 3), np.int64),
+             dirichlet=np.zeros(i["n_dofs"], np.uint8), colour=np.zeros(i["n_active"], np.int32),
+             top=np.zeros(i["n_active"], np.uint8))
+    tab = MeshTables(*[_ptr(t[n]) for n, _ in MeshTables._fields_])
+    _check(lib().pbf_mesh_export(h, C.byref(tab)))
+    return t
+
+
+def pbf_mesh_activate_layer(h, z_new_top, material, T_init):
+    _check(lib().pbf_mesh_activate_layer(h, float(z_new_top), int(material), float(T_init)))
+
+
+def pbf_mesh_adapt(h, regions):
+    regs = _regions(regions)
+    _check(lib().pbf_mesh_adapt(h, len(regions), C.cast(regs, C.c_void_p)))
+
+
+def pbf_mesh_transfer(h, T_old, T_new, batch=1, stream=None):
+    _check(lib().pbf_mesh_transfer(h, _ptr(T_old), _ptr(T_new), int(batch), _stream(stream)))
+
+
+def pbf_ctx_create(mesh, material: dict, precision=PBF_F64, batch=1):
+    h = C.c_void_p()
+    m = _material(material)
+    _check(lib().pbf_ctx_create(mesh, C.byref(m), int(precision), int(batch), C.byref(h)))
+    return h
+
+
+def pbf_ctx_destroy(h):
+    _check(lib().pbf_ctx_destroy(h))
+
+
+def pbf_ctx_set_k_scale(h, s):
+    s = np.ascontiguousarray(s, np.float64)
+    _check(lib().pbf_ctx_set_k_scale(h, _ptr(s)))
+
+
+def pbf_eval_residual(h, T, laser, t, fdiff, fvol, Cm, batch=1, stream=None):
+    la = _LaserArg(laser, batch)
+    _check(lib().pbf_eval_residual(h, _ptr(T), la.ref, float(t), _ptr(fdiff), _ptr(fvol), _ptr(Cm), _stream(stream)))
+
+
+def pbf_explicit_step(h, T, laser, t0, dt, nsteps, batch=1, stream=None):
+    la = _LaserArg(laser, batch)
+    _check(lib().pbf_explicit_step(h, _ptr(T), la.ref, float(t0), float(dt), int(nsteps), _stream(stream)))
+
+
+def pbf_estimate_dt(h, x0=None, max_iter=200, rtol=1e-6, stream=None):
+    lam, dtc, it = C.c_double(), C.c_double(), C.c_int()
+    _check(lib().pbf_estimate_dt(h, _ptr(x0), int(max_iter), float(rtol), C.byref(lam), C.byref(dtc),
+                                 C.byref(it), _stream(stream)))
+    return lam.value, dtc.value, it.value
+
+
+def pbf_cheb_bounds(h, dt, b=None, n_iter=30, stream=None):
+    out = np.zeros(2)
+    _check(lib().pbf_cheb_bounds(h, float(dt), _ptr(b), int(n_iter), _ptr(out), _stream(stream)))
+    return float(out[0]), float(out[1])
+
+
+def pbf_implicit_solve(h, T, dt, nsteps, rtol=1e-8, max_it=500, cheb_degree=5, cheb_bounds=None, stream=None):
+    iters = np.zeros(max(1, nsteps), np.int32)
+    cb = None if cheb_bounds is None else np.ascontiguousarray(cheb_bounds, np.float64)
+    st = lib().pbf_implicit_solve(h, _ptr(T), float(dt), int(nsteps), float(rtol), int(max_it), int(cheb_degree),
+                                  _ptr(cb), _ptr(iters), _stream(stream))
+    return st, iters[:nsteps]
+
+
+def pbf_adjoint_sweep(h, T0, laser, t0, dt, nsteps, n_checkpoints, T_target=2300.0, p_exp=16.0, batch=1,
+                      stream=None):
+    la = _LaserArg(laser, batch)
+    n_seg = la.seg.shape[0]
+    J = np.zeros(batch)
+    grad = np.zeros((batch, n_seg + 1))
+    fwd = C.c_longlong()
+    _check(lib().pbf_adjoint_sweep(h, _ptr(T0), la.ref, float(t0), float(dt), int(nsteps), int(n_checkpoints),
+                                   float(T_target), float(p_exp), _ptr(J), _ptr(grad), C.byref(fwd), _stream(stream)))
+    return J, grad, fwd.value
+
+
+def pbf_revolve_cost(nsteps, n_snaps):
+    out = C.c_longlong()
+    _check(lib().pbf_revolve_cost(int(nsteps), int(n_snaps), C.byref(out)))
+    return out.value
+
+
+def pbf_round_to_f32(x, y, n, stream=None):
+    _check(lib().pbf_round_to_f32(_ptr(x), _ptr(y), int(n), _stream(stream)))
+
+
+def pbf_widen_to_f64(x, y, n, stream=None):
+    _check(lib().pbf_widen_to_f64(_ptr(x), _ptr(y), int(n), _stream(stream)))
+
+
+def pbf_ctx_set_timing(h, enable):
+    _check(lib().pbf_ctx_set_timing(h, int(bool(enable))))
+
+
+def pbf_ctx_kernel_time(h):
+    ms, n = C.c_double(), C.c_longlong()
+    _check(lib().pbf_ctx_kernel_time(h, C.byref(ms), C.byref(n)))
+    return ms.value, n.value
+
+
+def pbf_ctx_launch_count(h):
+    n = C.c_longlong()
+    _check(lib().pbf_ctx_launch_count(h, C.byref(n)))
+    return n.value
+
+
+# ---- small object wrappers ---------------------------------------------------------------------
+
+class Mesh:
+    def __init__(self, desc: dict):
+        self.h = pbf_mesh_create(desc)
+
+    def info(self):
+        return pbf_mesh_info(self.h)
+
+    def tables(self):
+        return pbf_mesh_export(self.h)
+
+    def close(self):
+        if self.h:
+            pbf_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Context:
+    def __init__(self, mesh: Mesh, material: dict, precision=PBF_F64, batch=1):
+        self.mesh = mesh
+        self.batch = batch
+        self.h = pbf_ctx_create(mesh.h, material, precision, batch)
+
+    def close(self):
+        if self.h:
+            pbf_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

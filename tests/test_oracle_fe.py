@@ -138,6 +138,36 @@ def test_apparent_capacity_integrates_latent_heat(oracle_mod):
     assert abs(Cm.sum() - mat["rho"] * oracle_mod.capp(mat, 1900.0) * 2.0) < 1e-10 * Cm.sum()
 
 
+def test_lumped_capacity_sign_q1_q2(oracle_mod):
+    """Row-sum lumping of a capacity with a sharp c_app(T) peak: Q1 bases are non-negative, so
+    C~_ii = int rho c_app(T_h) N_i > 0; Q2 vertex bases are negative inside the cell, so the
+    same row sum turns negative where the latent peak sits there, while the nodal form
+    rho c_app(T_i) sum_j M_ij stays positive. Both forms agree for constant c."""
+    rng = np.random.default_rng(8)
+    for p in (1, 2):
+        d = I.mesh_desc((2, 2, 2), (1e-4,) * 3, p, 2, [I.uniform_region(2)])
+        m = oracle_mod.Mesh(d)
+        T = I.T0 + rng.uniform(1850.0, 1960.0, m.n_dofs) - I.T0  # nodes around the latent peak
+        Cq = m.lumped_capacity(I.TI64_NONLIN, T)
+        Cn = m.lumped_capacity(dict(I.TI64_NONLIN, lumping=I.LUMP_NODAL), T)
+        assert Cn.min() > 0
+        if p == 1:
+            assert Cq.min() > 0
+        else:
+            assert Cq.min() < 0
+        const = np.full(m.n_dofs, 600.0)
+        a = m.lumped_capacity(I.TI64_NONLIN, const)
+        b = m.lumped_capacity(dict(I.TI64_NONLIN, lumping=I.LUMP_NODAL), const)
+        assert np.allclose(a, b, rtol=1e-12, atol=0)
+    # nodal form: c_app evaluated at the node, times the constant-coefficient lumped mass
+    m = oracle_mod.Mesh(I.mesh_desc((2, 1, 1), (1e-4,) * 3, 2, 1, [I.uniform_region(1)]))
+    T = rng.uniform(1850.0, 1960.0, m.n_dofs)
+    M = m.lumped_capacity(dict(I.TI64_CONST, rho=1.0, c=1.0), T)
+    Cn = m.lumped_capacity(dict(I.TI64_NONLIN, lumping=I.LUMP_NODAL), T)
+    ref = np.array([I.TI64_NONLIN["rho"] * oracle_mod.capp(I.TI64_NONLIN, t) for t in T]) * M
+    assert np.allclose(Cn, ref, rtol=1e-12, atol=0)
+
+
 def test_laser_total_power(oracle_mod):
     """The surface Gaussian 2 eta P/(pi r^2) exp(-2 d^2/r^2) integrates to eta P."""
     d = I.mesh_desc((4, 4, 1), (100e-6, 100e-6, 100e-6), 2, 3, [I.uniform_region(3)])
