@@ -1174,6 +1174,16 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
   const int p = M.p, npc = M.npc(), nq = p + 1;
   double gx[3], gw[3];
   gauss(nq, gx, gw);
+  const bool nodal = mt->lumping == 1 && mt->sigma > 0.0;
+  std::vector<double> plainC;
+  if (nodal) {
+    or_material plain = *mt;
+    plain.sigma = 0.0;
+    plain.lumping = 0;
+    Fields G;
+    residual(M, plain, s, T0, nullptr, 0.0, G, true);
+    plainC = G.C;
+  }
   std::vector<double> Te(npc), ve(npc), me(npc), ge(npc), N(npc);
   std::vector<double> dN((size_t)npc * 3);
   for (int k = nsteps - 1; k >= 0; --k) {
@@ -1223,14 +1233,18 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
             }
             double kq = cond(*mt, Tq, mat, s), dk = cond_deriv(*mt, Tq, mat, s);
             double gvgT = gv[0] * gT[0] + gv[1] * gT[1] + gv[2] * gT[2];
+            double cap_term = nodal ? 0.0 : mt->rho * capp_deriv(*mt, Tq) * muq;
             for (int j = 0; j < npc; ++j) {
               double gjv = 0.0;
               for (int d = 0; d < 3; ++d) gjv += dN[3 * j + d] / geo.h[d] * gv[d];
-              ge[j] += W * (-kq * gjv - dk * gvgT * N[j] - mt->rho * capp_deriv(*mt, Tq) * muq * N[j]);
+              ge[j] += W * (-kq * gjv - dk * gvgT * N[j] - cap_term * N[j]);
             }
           }
       scatter(M, c, ge.data(), g.data());
     }
+    // nodal lumping: dC~_i/dT_j = delta_ij rho M_i c_app'(T_i), M the lumped mass
+    if (nodal)
+      for (size_t i = 0; i < n; ++i) g[i] -= mu[i] * plainC[i] / mt->c * capp_deriv(*mt, T[i]);
     std::vector<double> lam_new(n, 0.0);
     if (k > 0) {
       double Mn = pnorm_max(obj, T, &gM);

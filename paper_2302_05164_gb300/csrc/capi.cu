@@ -164,7 +164,7 @@ extern "C" pbf_status pbf_mesh_adapt(pbf_mesh* mesh, int n_regions, const pbf_re
     st = build_mesh(nm, &mat, &err);
     if (st != PBF_OK) return fail(st, "%s", err.c_str());
     nm.generation = old.generation + 1;
-    make_transfer(old, nm, old.desc.active_top_z > 0 ? 0.0 : 0.0, nm.transfer);
+    make_transfer(old, nm, 0.0, nm.transfer);  // same activation: every new dof lies in the old domain
     mesh->m = std::move(nm);
     return PBF_OK;
   } catch (const std::bad_alloc&) {
@@ -271,8 +271,10 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     c->nodal.inv_sigma_f = (float)c->nodal.inv_sigma;
   }
   c->nonlin = mat->Tk1 > mat->Tk0 && mat->k1 != mat->k0;
-  if (c->n_cells * (int64_t)c->npc >= ((int64_t)1 << 31) || c->n_dofs * (int64_t)batch >= ((int64_t)1 << 40))
-    return fail(PBF_EINVAL, "mesh too large");
+  // kernels index with 32-bit integers: every (entity x instance) count stays below 2^31
+  if (c->n_cells * (int64_t)c->npc >= ((int64_t)1 << 31) || c->n_dofs * (int64_t)batch >= ((int64_t)1 << 31) ||
+      c->n_cells * (int64_t)batch * c->npc >= ((int64_t)1 << 31) || c->n_hang * (int64_t)batch >= ((int64_t)1 << 31))
+    return fail(PBF_EINVAL, "mesh x batch too large for 32-bit indexing");
   const size_t nc = (size_t)c->n_cells, npc = (size_t)c->npc, nd = (size_t)c->n_dofs;
   // host staging of per-cell tables
   std::vector<int32_t> soa(nc * npc);
@@ -335,17 +337,17 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->Cacc, (c->latent ? nv : 1) * rsz);
   if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->Tw, nv);
   if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->Tf, nv);
-  const size_t nh = (size_t)c->n_hang * (size_t)batch;
+  const size_t nh = std::max<size_t>(1, (size_t)c->n_hang * (size_t)batch);
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->xh, nh * rsz);
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->fh, nh * rsz);
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->Ch, nh * rsz);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->xh64, nh);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->fh64, nh);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->Ch64, nh);
-  if (e == cudaSuccess) e = cudaMemset(c->fh, 0, std::max<size_t>(1, nh) * rsz);
-  if (e == cudaSuccess) e = cudaMemset(c->Ch, 0, std::max<size_t>(1, nh) * rsz);
-  if (e == cudaSuccess) e = cudaMemset(c->fh64, 0, std::max<size_t>(1, nh) * 8);
-  if (e == cudaSuccess) e = cudaMemset(c->Ch64, 0, std::max<size_t>(1, nh) * 8);
+  if (e == cudaSuccess) e = cudaMemset(c->fh, 0, nh * rsz);
+  if (e == cudaSuccess) e = cudaMemset(c->Ch, 0, nh * rsz);
+  if (e == cudaSuccess) e = cudaMemset(c->fh64, 0, nh * 8);
+  if (e == cudaSuccess) e = cudaMemset(c->Ch64, 0, nh * 8);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->C0, nd);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_d, nd);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_f, nd);
@@ -362,6 +364,7 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   if (e == cudaSuccess) e = cudaMemset(c->C0, 0, nd * 8);
   if (e == cudaSuccess) e = cudaMemset(c->power, 0, (size_t)batch * kMaxSeg * 8);
   if (e != cudaSuccess) {
+    cudaGetLastError();  // do not leave the error for the next caller's launch check
     c->release();
     return fail(e == cudaErrorMemoryAllocation ? PBF_ENOMEM : PBF_ECUDA, "context setup: %s", cudaGetErrorString(e));
   }
@@ -410,6 +413,7 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     cudaFree(Tz);
     c->launches += 2;
     if (e != cudaSuccess) {
+      cudaGetLastError();
       c->release();
       return fail(PBF_ECUDA, "capacity setup: %s", cudaGetErrorString(e));
     }
@@ -473,6 +477,7 @@ pbf_status CtxBase::check_usable() {
 
 pbf_status CtxBase::cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return PBF_OK;
+  cudaGetLastError();
   poisoned = true;
   return fail(PBF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -553,6 +558,84 @@ cudaError_t CtxBase::apply_cell(CellLaunch L, void* f, void* C, int mode, cudaSt
   return e;
 }
 
+// f_diff, f_vol and C~ at T (laser already set); FP64 outputs, accumulators left at zero.
+cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_dev, double* fvol_dev, double* C_dev,
+                                  cudaStream_t s) {
+  const int64_t nv = n_dofs * batch;
+  const size_t rsz = f32 ? 4 : 8;
+  CellLaunch L = base;
+  L.x = T_dev;
+  cudaError_t e = cudaSuccess;
+  if (f32) {
+    e = launch_prepare_f32(nv, T_dev, mat.T_ref, nullptr, Tf, s);
+    L.xf = Tf;
+    ++launches;
+  }
+  if (e == cudaSuccess) e = apply_cell(L, f, latent ? Cacc : nullptr, MODE_RESIDUAL, s);
+  if (e == cudaSuccess && lsetup.k.n_seg > 0) {
+    e = launch_laser(degree, f32, lsetup, L.mesh, power, spot_at(lsetup.k, t), fvol, s);
+    ++launches;
+  }
+  if (e == cudaSuccess && fdiff_dev) e = launch_to_f64(f32, nv, f, fdiff_dev, s);
+  if (e == cudaSuccess && fvol_dev) e = launch_to_f64(f32, nv, fvol, fvol_dev, s);
+  if (e == cudaSuccess && C_dev) {
+    if (cap == CAP_QUADRATURE) e = launch_to_f64(f32, nv, Cacc, C_dev, s);
+    else if (cap == CAP_NODAL) e = launch_capacity_nodal(n_dofs, batch, C0, T_dev, nodal, C_dev, s);
+    else e = launch_broadcast_dofs(n_dofs, batch, C0, C_dev, s);
+  }
+  launches += 3;
+  if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, (size_t)nv * rsz, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(fvol, 0, (size_t)nv * rsz, s);
+  if (e == cudaSuccess && latent) e = cudaMemsetAsync(Cacc, 0, (size_t)nv * rsz, s);
+  return e;
+}
+
+// nsteps forward-Euler steps on T (laser already set)
+cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
+  CellLaunch L = base;
+  const bool with_laser = lsetup.k.n_seg > 0;
+  const int64_t nv = n_dofs * batch;
+  cudaError_t e = cudaSuccess;
+  if (nsteps <= 0) return e;
+  if (f32) {
+    // FP64 working state Tw = T - T_ref and its FP32 copy for the whole call
+    const double tw_dir = mat.T_dirichlet - mat.T_ref;
+    const float tf_dir = (float)tw_dir;
+    e = launch_prepare_f32(nv, T_dev, mat.T_ref, Tw, Tf, s);
+    ++launches;
+    L.xf = Tf;
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      const double t = t0 + n * dt;
+      e = apply_cell(L, f, latent ? Cacc : nullptr, MODE_RESIDUAL, s);
+      if (e == cudaSuccess && with_laser) {
+        e = launch_laser(degree, true, lsetup, L.mesh, power, spot_at(lsetup.k, t), f, s);
+        ++launches;
+      }
+      if (e == cudaSuccess)
+        e = launch_update_f32(cap, n_dofs, batch, Tw, Tf, (float*)f, (float*)Cacc, invC0_f, nodal, dirichlet, tw_dir,
+                              tf_dir, (float)dt, s);
+      ++launches;
+    }
+    if (e == cudaSuccess) e = launch_finish_f32(nv, Tw, mat.T_ref, T_dev, s);
+    ++launches;
+  } else {
+    L.x = T_dev;
+    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+      const double t = t0 + n * dt;
+      e = apply_cell(L, f, latent ? Cacc : nullptr, MODE_RESIDUAL, s);
+      if (e == cudaSuccess && with_laser) {
+        e = launch_laser(degree, false, lsetup, L.mesh, power, spot_at(lsetup.k, t), f, s);
+        ++launches;
+      }
+      if (e == cudaSuccess)
+        e = launch_update_f64(cap, n_dofs, batch, T_dev, (double*)f, (double*)Cacc, invC0_d, nodal, dirichlet,
+                              mat.T_dirichlet, dt, s);
+      ++launches;
+    }
+  }
+  return e;
+}
+
 extern "C" pbf_status pbf_eval_residual(pbf_ctx* ctx, const double* T_dev, const pbf_laser* laser, double t,
                                         double* fdiff_dev, double* fvol_dev, double* C_dev, pbf_stream stream) {
   if (!ctx || !T_dev) return fail(PBF_EINVAL, "null argument");
@@ -561,33 +644,7 @@ extern "C" pbf_status pbf_eval_residual(pbf_ctx* ctx, const double* T_dev, const
   cudaStream_t s = (cudaStream_t)stream;
   st = ctx->set_laser(laser, s);
   if (st) return st;
-  const int64_t nv = ctx->n_dofs * ctx->batch;
-  const size_t rsz = ctx->f32 ? 4 : 8;
-  CellLaunch L = ctx->base;
-  L.x = T_dev;
-  cudaError_t e = cudaSuccess;
-  if (ctx->f32) {
-    e = launch_prepare_f32(nv, T_dev, ctx->mat.T_ref, nullptr, ctx->Tf, s);
-    L.xf = ctx->Tf;
-    ++ctx->launches;
-  }
-  if (e == cudaSuccess) e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);
-  if (e == cudaSuccess && ctx->lsetup.k.n_seg > 0) {
-    e = launch_laser(ctx->degree, ctx->f32, ctx->lsetup, L.mesh, ctx->power, spot_at(ctx->lsetup.k, t), ctx->fvol, s);
-    ++ctx->launches;
-  }
-  if (e == cudaSuccess && fdiff_dev) e = launch_to_f64(ctx->f32, nv, ctx->f, fdiff_dev, s);
-  if (e == cudaSuccess && fvol_dev) e = launch_to_f64(ctx->f32, nv, ctx->fvol, fvol_dev, s);
-  if (e == cudaSuccess && C_dev) {
-    if (ctx->cap == CAP_QUADRATURE) e = launch_to_f64(ctx->f32, nv, ctx->Cacc, C_dev, s);
-    else if (ctx->cap == CAP_NODAL) e = launch_capacity_nodal(ctx->n_dofs, ctx->batch, ctx->C0, T_dev, ctx->nodal, C_dev, s);
-    else e = launch_broadcast_dofs(ctx->n_dofs, ctx->batch, ctx->C0, C_dev, s);
-  }
-  ctx->launches += 3;
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f, 0, (size_t)nv * rsz, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fvol, 0, (size_t)nv * rsz, s);
-  if (e == cudaSuccess && ctx->latent) e = cudaMemsetAsync(ctx->Cacc, 0, (size_t)nv * rsz, s);
-  return ctx->cuda(e, "eval_residual");
+  return ctx->cuda(ctx->residual_f64(T_dev, t, fdiff_dev, fvol_dev, C_dev, s), "eval_residual");
 }
 
 extern "C" pbf_status pbf_explicit_step(pbf_ctx* ctx, double* T_dev, const pbf_laser* laser, double t0, double dt,
@@ -599,47 +656,7 @@ extern "C" pbf_status pbf_explicit_step(pbf_ctx* ctx, double* T_dev, const pbf_l
   cudaStream_t s = (cudaStream_t)stream;
   st = ctx->set_laser(laser, s);
   if (st) return st;
-  CellLaunch L = ctx->base;
-  const bool with_laser = ctx->lsetup.k.n_seg > 0;
-  const int64_t nv = ctx->n_dofs * ctx->batch;
-  cudaError_t e = cudaSuccess;
-  if (ctx->f32) {
-    // FP64 working state Tw = T - T_ref and its FP32 copy for the whole call
-    const double tw_dir = ctx->mat.T_dirichlet - ctx->mat.T_ref;
-    const float tf_dir = (float)tw_dir;
-    e = launch_prepare_f32(nv, T_dev, ctx->mat.T_ref, ctx->Tw, ctx->Tf, s);
-    ++ctx->launches;
-    L.xf = ctx->Tf;
-    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      const double t = t0 + n * dt;
-      e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);
-      if (e == cudaSuccess && with_laser) {
-        e = launch_laser(ctx->degree, true, ctx->lsetup, L.mesh, ctx->power, spot_at(ctx->lsetup.k, t), ctx->f, s);
-        ++ctx->launches;
-      }
-      if (e == cudaSuccess)
-        e = launch_update_f32(ctx->cap, ctx->n_dofs, ctx->batch, ctx->Tw, ctx->Tf, (float*)ctx->f, (float*)ctx->Cacc,
-                              ctx->invC0_f, ctx->nodal, ctx->dirichlet, tw_dir, tf_dir, (float)dt, s);
-      ++ctx->launches;
-    }
-    if (e == cudaSuccess) e = launch_finish_f32(nv, ctx->Tw, ctx->mat.T_ref, T_dev, s);
-    ++ctx->launches;
-  } else {
-    L.x = T_dev;
-    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      const double t = t0 + n * dt;
-      e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);
-      if (e == cudaSuccess && with_laser) {
-        e = launch_laser(ctx->degree, false, ctx->lsetup, L.mesh, ctx->power, spot_at(ctx->lsetup.k, t), ctx->f, s);
-        ++ctx->launches;
-      }
-      if (e == cudaSuccess)
-        e = launch_update_f64(ctx->cap, ctx->n_dofs, ctx->batch, T_dev, (double*)ctx->f, (double*)ctx->Cacc,
-                              ctx->invC0_d, ctx->nodal, ctx->dirichlet, ctx->mat.T_dirichlet, dt, s);
-      ++ctx->launches;
-    }
-  }
-  return ctx->cuda(e, "explicit_step");
+  return ctx->cuda(ctx->explicit_steps(T_dev, t0, dt, nsteps, s), "explicit_step");
 }
 
 extern "C" pbf_status pbf_round_to_f32(const double* x_dev, float* y_dev, int64_t n, pbf_stream stream) {

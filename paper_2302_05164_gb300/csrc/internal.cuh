@@ -144,6 +144,15 @@ struct CellLaunch {
   const double* xh = nullptr;       // its values at hanging nodes [n_hang][batch]
   const float* xf = nullptr;        // input field rounded to FP32 (FP32 operator)
   const float* xfh = nullptr;       // FP32 values at hanging nodes
+  // adjoint: v = lambda / C~ and mu = lambda f / C~^2 (quadrature-point capacity only)
+  const double* v = nullptr;
+  const double* vh = nullptr;
+  const float* vf = nullptr;
+  const float* vfh = nullptr;
+  const double* mu = nullptr;
+  const double* muh = nullptr;
+  const float* muf = nullptr;
+  const float* mufh = nullptr;
   int degree = 1;
   int f32 = 0;
 };
@@ -174,7 +183,8 @@ cudaError_t launch_cell(const CellLaunch& L, void* f, void* fh, void* C, void* C
 // implicit-operator diagonal: diag += diag(P^T A_e P) over cells (FP64 output)
 cudaError_t launch_diag(const CellLaunch& L, double* diag, cudaStream_t s);
 
-// adjoint cell kernel: g += (df/dT)^T v - (dC/dT)^T mu at state x (FP64 or FP32 operator)
-cudaError_t launch_adjoint(const CellLaunch& L, const double* v, const double* mu, void* g, cudaStream_t s);
+// adjoint cell kernel at state x: g += (df_diff/dT)^T v - (dC~/dT)^T mu, the capacity term only
+// for the quadrature-point capacity (qp_capacity); g/gh accumulate over dofs / hanging nodes
+cudaError_t launch_adjoint(const CellLaunch& L, bool qp_capacity, void* g, void* gh, cudaStream_t s);
 
 }  // namespace pbf

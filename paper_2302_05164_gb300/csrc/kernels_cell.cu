@@ -86,7 +86,7 @@ __device__ __forceinline__ void gather_sel(const DevMesh& M, const S* __restrict
   for (int a = 0; a < NP; ++a) {
     const int d = idx[a];
     const S* base = d >= 0 ? x : xh;
-    const int64_t j = d >= 0 ? d : -1 - d;
+    const int j = d >= 0 ? d : -1 - d;
     const S v = __ldg(&base[j * B + inst]);
     if (sizeof(S) == 8) u[a] = R((double)v - off);
     else u[a] = R(v);
@@ -122,7 +122,7 @@ __device__ __forceinline__ void scatter(const DevMesh& M, R* __restrict__ f, R* 
   for (int a = 0; a < NP; ++a) {
     const int d = __ldg(&M.cell_dofs[a * M.n_cells + cell]);
     R* base = d >= 0 ? f : fh;
-    const int64_t j = d >= 0 ? d : -1 - d;
+    const int j = d >= 0 ? d : -1 - d;
     atomicAdd(&base[j * B + inst], fe[a]);
   }
 }
@@ -147,9 +147,9 @@ __global__ void __launch_bounds__(128) k_cell(const CellLaunch L, R* __restrict_
   const MatR<R>& mt = mat_of<R>(L);
   const GeoR<R>& geo = geo_of<R>(L);
   const int B = M.batch;
-  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (int64_t)M.n_cells * B) return;
-  const int cell = (int)(tid / B), inst = (int)(tid - (int64_t)(tid / B) * B);
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= M.n_cells * B) return;
+  const int cell = B == 1 ? tid : tid / B, inst = tid - cell * B;
 
   R u[NP], v[NP];
   gather_any<P, R>(L, cell, inst, u);
@@ -283,6 +283,103 @@ __global__ void __launch_bounds__(64) k_diag(const CellLaunch L, double* __restr
   }
 }
 
+// Adjoint of the explicit residual: for the state T and the vectors v, mu it accumulates
+//   g_j = sum_e [ -int k(T_h) grad v_h . grad N_j - int k'(T_h) N_j grad v_h . grad T_h
+//                 - int rho c_app'(T_h) mu_h N_j ]
+// i.e. the transpose of the linearised operator of Eq. matrix_free_eval (the D_e and L_e
+// parts) plus, for the quadrature-point capacity, the transposed capacity derivative.
+template <int P, typename R, bool NLK, bool QPC>
+__global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restrict__ g, R* __restrict__ gh) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  const DevMesh& M = L.mesh;
+  const MatR<R>& mt = mat_of<R>(L);
+  const GeoR<R>& geo = geo_of<R>(L);
+  const int B = M.batch;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= M.n_cells * B) return;
+  const int cell = B == 1 ? tid : tid / B, inst = tid - cell * B;
+  R u[NP], Tq[NP], vq[NP];
+  gather_any<P, R>(L, cell, inst, u);
+  values_at_qp<P, R>(u, Tq);
+  if (sizeof(R) == 4) gather_sel<P, R, float>(M, L.vf, L.vfh, cell, inst, 0.0, u);
+  else gather_sel<P, R, double>(M, L.v, L.vh, cell, inst, 0.0, u);
+  values_at_qp<P, R>(u, vq);
+  const int lev = M.cell_level[cell];
+  const R detJ = geo.detJ[lev];
+  const int mat = M.cell_mat[cell];
+  const R* ks = kscale_of<R>(L);
+  const R scale = (mat == 1 ? mt.powder_scale : R(1)) * (ks ? ks[inst] : R(1));
+  R kw[NP], val[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    const R W = R(wq3<P>(q)) * detJ;
+    const R sx = (Tq[q] + mt.tk_off) * mt.inv_dT;
+    R k = mt.k0 * scale;
+    if (NLK) k = k + mt.dk * scale * clamp01(sx);
+    kw[q] = -k * W;
+    // k'(T): slope inside the open ramp, zero outside (and at its ends)
+    val[q] = (NLK && sx > R(0) && sx < R(1)) ? -(mt.dk * scale * mt.inv_dT) * W : R(0);
+  }
+  if (QPC) {
+    if (sizeof(R) == 4) gather_sel<P, R, float>(M, L.muf, L.mufh, cell, inst, 0.0, u);
+    else gather_sel<P, R, double>(M, L.mu, L.muh, cell, inst, 0.0, u);
+    R mq[NP];
+    values_at_qp<P, R>(u, mq);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const R z = (Tq[q] + mt.tm_off) * mt.inv_sigma;
+      const R dc = -z * mt.inv_sigma * mt.lat_norm * expo(R(-0.5) * z * z);  // c_app'(T)
+      mq[q] = -mt.rho * dc * mq[q] * (R(wq3<P>(q)) * detJ);
+    }
+    // val holds -k'(T) W; the k' term needs grad v . grad T, added below
+#pragma unroll
+    for (int q = 0; q < NP; ++q) u[q] = mq[q];
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) u[q] = R(0);
+  }
+  R r[NP], gv[NP], gT[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) r[q] = R(0);
+#define ADJ_DIR(DIR)                                                         \
+  {                                                                          \
+    const R cd = geo.ih2[lev][DIR];                                          \
+    apply1d<P, 1, DIR, false, false>(vq, gv);                                \
+    if (NLK) apply1d<P, 1, DIR, false, false>(Tq, gT);                       \
+    _Pragma("unroll") for (int q = 0; q < NP; ++q) {                         \
+      if (NLK) u[q] += val[q] * cd * gv[q] * gT[q];                          \
+      gv[q] *= kw[q] * cd;                                                   \
+    }                                                                        \
+    apply1d<P, 1, DIR, true, true>(gv, r);                                   \
+  }
+  ADJ_DIR(0)
+  ADJ_DIR(1)
+  ADJ_DIR(2)
+#undef ADJ_DIR
+#pragma unroll
+  for (int q = 0; q < NP; ++q) r[q] += u[q];
+  R fe[NP];
+  integrate_values<P, R>(r, fe);
+  scatter<P, R>(M, g, gh, cell, inst, fe);
+}
+
+template <int P, typename R, bool NLK, bool QPC>
+cudaError_t go_adj(const CellLaunch& L, void* g, void* gh, cudaStream_t s) {
+  const int64_t n = (int64_t)L.mesh.n_cells * L.mesh.batch;
+  if (n == 0) return cudaSuccess;
+  k_adjoint<P, R, NLK, QPC><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(L, (R*)g, (R*)gh);
+  return cudaGetLastError();
+}
+
+template <int P, typename R>
+cudaError_t dispatch_adj(const CellLaunch& L, bool qpc, void* g, void* gh, cudaStream_t s) {
+  const bool nl = L.nonlin_k != 0;
+  if (nl && qpc) return go_adj<P, R, true, true>(L, g, gh, s);
+  if (nl) return go_adj<P, R, true, false>(L, g, gh, s);
+  if (qpc) return go_adj<P, R, false, true>(L, g, gh, s);
+  return go_adj<P, R, false, false>(L, g, gh, s);
+}
+
 template <int P, typename R, int MODE, bool NLK, bool LAT>
 cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
   const int64_t n = (int64_t)L.mesh.n_cells * L.mesh.batch;
@@ -320,6 +417,14 @@ cudaError_t launch_cell(const CellLaunch& L, void* f, void* fh, void* C, void* C
     return L.f32 ? dispatch<1, float>(L, f, fh, C, Ch, mode, s) : dispatch<1, double>(L, f, fh, C, Ch, mode, s);
   if (L.degree == 2)
     return L.f32 ? dispatch<2, float>(L, f, fh, C, Ch, mode, s) : dispatch<2, double>(L, f, fh, C, Ch, mode, s);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_adjoint(const CellLaunch& L, bool qp_capacity, void* g, void* gh, cudaStream_t s) {
+  if (L.degree == 1)
+    return L.f32 ? dispatch_adj<1, float>(L, qp_capacity, g, gh, s) : dispatch_adj<1, double>(L, qp_capacity, g, gh, s);
+  if (L.degree == 2)
+    return L.f32 ? dispatch_adj<2, float>(L, qp_capacity, g, gh, s) : dispatch_adj<2, double>(L, qp_capacity, g, gh, s);
   return cudaErrorInvalidValue;
 }
 

@@ -84,6 +84,15 @@ struct CtxBase {
   // is on), and the distribution of hanging-node contributions to their masters.
   // L.x (FP64) or L.xf (FP32) must be set; f and C (nullable) are the dof accumulators.
   cudaError_t apply_cell(CellLaunch L, void* f, void* C, int mode, cudaStream_t s);
+  // f_diff, f_vol and C~ at T in FP64 (laser set beforehand; any output may be null)
+  cudaError_t residual_f64(const double* T, double t, double* fd, double* fv, double* C, cudaStream_t s);
+  // nsteps forward-Euler steps in place on T (laser set beforehand)
+  cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
+  // adjoint work space
+  int32_t* surf_idx = nullptr;
+  double* surf_w = nullptr;
+  int n_surf = 0;
+  double surf_W = 0.0;
 };
 
 }  // namespace pbf

@@ -8,6 +8,9 @@ namespace {
 
 constexpr int kBS = 256;
 
+__device__ __forceinline__ float expo_r(float x) { return __expf(x); }
+__device__ __forceinline__ double expo_r(double x) { return exp(x); }
+
 inline unsigned grid_for(int64_t n, int bs = kBS) { return (unsigned)((n + bs - 1) / bs); }
 
 // ---- forward-Euler update -------------------------------------------------------------
@@ -19,9 +22,9 @@ template <int CAP>
 __global__ void k_update_f64(int64_t n, int B, double* __restrict__ T, double* __restrict__ f,
                              double* __restrict__ Cacc, const double* __restrict__ invC0, const NodalCap nc,
                              const uint8_t* __restrict__ dirichlet, double T_dir, double dt) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t d = i / B;
+  const int d = B == 1 ? i : i / B;
   const double fi = f[i];
   f[i] = 0.0;
   double ci = 0.0;
@@ -51,9 +54,9 @@ __global__ void k_update_f32(int64_t n, int B, double* __restrict__ Tw, float* _
                              float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
                              const NodalCap nc, const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir,
                              float dt) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int64_t d = i / B;
+  const int d = B == 1 ? i : i / B;
   const float fi = f[i];
   f[i] = 0.f;
   float ci = 0.f;
@@ -113,35 +116,34 @@ __global__ void k_laser_surface(int n_top, int B, const int32_t* __restrict__ to
                                 const double* __restrict__ top_geo, const DevMesh M, const LaserK ls,
                                 const double* __restrict__ power, Spot sp, R* __restrict__ f) {
   constexpr int N = P + 1;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)n_top * B) return;
-  const int face = (int)(i / B), inst = (int)(i - (int64_t)face * B);
-  const double lx = sp.x, ly = sp.y;
-  const int seg = sp.seg;
-  const double x0 = top_geo[4 * face + 0], y0 = top_geo[4 * face + 1];
-  const double hx = top_geo[4 * face + 2], hy = top_geo[4 * face + 3];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_top * B) return;
+  const int face = B == 1 ? i : i / B, inst = i - face * B;
+  // face corner relative to the spot (one FP64 subtraction per axis), then the operator
+  // precision: the integrand is smooth on the face and its weights sum to the face area
+  const double hxd = top_geo[4 * face + 2], hyd = top_geo[4 * face + 3];
+  const double ox = top_geo[4 * face + 0] - sp.x, oy = top_geo[4 * face + 1] - sp.y;
   const double r = ls.radius;
-  const double gx = fmax(0.0, fmax(x0 - lx, lx - (x0 + hx))), gy = fmax(0.0, fmax(y0 - ly, ly - (y0 + hy)));
+  const double gx = fmax(0.0, fmax(ox, -(ox + hxd))), gy = fmax(0.0, fmax(oy, -(oy + hyd)));
   if (gx * gx + gy * gy > 36.0 * r * r) return;
-  const double P0 = power[(int64_t)inst * kMaxSeg + seg];
-  const double amp = 2.0 * ls.eta * P0 / (kPi * r * r);
-  const double ir2 = 2.0 / (r * r);
-  double fe[N][N];
+  const R x0 = R(ox), y0 = R(oy), hx = R(hxd), hy = R(hyd);
+  const R amp = R(2.0 * ls.eta * power[inst * kMaxSeg + sp.seg] / (kPi * r * r));
+  const R ir2 = R(2.0 / (r * r));
+  R fe[N][N];
 #pragma unroll
   for (int j = 0; j < N; ++j)
 #pragma unroll
-    for (int k = 0; k < N; ++k) fe[j][k] = 0.0;
+    for (int k = 0; k < N; ++k) fe[j][k] = R(0);
 #pragma unroll
   for (int qy = 0; qy < N; ++qy)
 #pragma unroll
     for (int qx = 0; qx < N; ++qx) {
-      const double x = x0 + Basis<P>::X(qx) * hx, y = y0 + Basis<P>::X(qy) * hy;
-      const double d2 = (x - lx) * (x - lx) + (y - ly) * (y - ly);
-      const double q = amp * exp(-d2 * ir2) * Basis<P>::W(qx) * Basis<P>::W(qy) * hx * hy;
+      const R x = x0 + R(Basis<P>::X(qx)) * hx, y = y0 + R(Basis<P>::X(qy)) * hy;
+      const R q = amp * expo_r(-(x * x + y * y) * ir2) * R(Basis<P>::W(qx) * Basis<P>::W(qy)) * hx * hy;
 #pragma unroll
       for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int k = 0; k < N; ++k) fe[j][k] += q * Basis<P>::S(qy, j) * Basis<P>::S(qx, k);
+        for (int k = 0; k < N; ++k) fe[j][k] += q * R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
     }
   const int cell = top_cell[face];
 #pragma unroll
@@ -151,10 +153,10 @@ __global__ void k_laser_surface(int n_top, int B, const int32_t* __restrict__ to
       const int a = k + N * (j + N * P);  // local node (k, j, P) on the top face
       const int d = M.cell_dofs[a * M.n_cells + cell];
       if (d >= 0) {
-        atomicAdd(&f[(int64_t)d * B + inst], R(fe[j][k]));
+        atomicAdd(&f[d * B + inst], fe[j][k]);
       } else {
         for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
-          atomicAdd(&f[(int64_t)M.con_idx[e] * B + inst], R(M.con_w[e] * fe[j][k]));
+          atomicAdd(&f[M.con_idx[e] * B + inst], R(M.con_w[e]) * fe[j][k]);
       }
     }
 }
@@ -314,11 +316,11 @@ __global__ void k_set_masked(int64_t n, double* __restrict__ y, const uint8_t* _
 template <typename R>
 __global__ void k_hang_values(int n_hang, int B, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                               const R* __restrict__ w, const R* __restrict__ x, R* __restrict__ out) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)n_hang * B) return;
-  const int r = (int)(i / B), b = (int)(i - (int64_t)r * B);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_hang * B) return;
+  const int r = B == 1 ? i : i / B, b = i - r * B;
   R s = R(0);
-  for (int e = ptr[r]; e < ptr[r + 1]; ++e) s += w[e] * x[(int64_t)idx[e] * B + b];
+  for (int e = ptr[r]; e < ptr[r + 1]; ++e) s += w[e] * x[idx[e] * B + b];
   out[i] = s;
 }
 
@@ -326,13 +328,211 @@ __global__ void k_hang_values(int n_hang, int B, const int32_t* __restrict__ ptr
 template <typename R>
 __global__ void k_hang_distribute(int n_hang, int B, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                   const R* __restrict__ w, R* __restrict__ fh, R* __restrict__ f) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)n_hang * B) return;
-  const int r = (int)(i / B), b = (int)(i - (int64_t)r * B);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_hang * B) return;
+  const int r = B == 1 ? i : i / B, b = i - r * B;
   const R v = fh[i];
   if (v == R(0)) return;
   fh[i] = R(0);
-  for (int e = ptr[r]; e < ptr[r + 1]; ++e) atomicAdd(&f[(int64_t)idx[e] * B + b], w[e] * v);
+  for (int e = ptr[r]; e < ptr[r + 1]; ++e) atomicAdd(&f[idx[e] * B + b], w[e] * v);
+}
+
+// ---- CG and Chebyshev recurrences (FP64 vectors; Dirichlet rows held at zero) -----------------
+__global__ void k_axpy2(int64_t n, double alpha, const double* __restrict__ p, const double* __restrict__ Ap,
+                        double* __restrict__ x, double* __restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  x[i] += alpha * p[i];
+  r[i] -= alpha * Ap[i];
+}
+
+__global__ void k_xpby(int64_t n, const double* __restrict__ z, double beta, double* __restrict__ p) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = z[i] + beta * p[i];
+}
+
+// res = r, d = r / (theta diag), z = d
+__global__ void k_cheb_init(int64_t n, const double* __restrict__ r, const double* __restrict__ diag, double inv_theta,
+                            double* __restrict__ res, double* __restrict__ d, double* __restrict__ z,
+                            const uint8_t* __restrict__ mask) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double ri = mask[i] ? 0.0 : r[i];
+  res[i] = ri;
+  const double di = ri / diag[i] * inv_theta;
+  d[i] = di;
+  z[i] = di;
+}
+
+// res -= A d; d = a d + b res / diag; z += d
+__global__ void k_cheb_update(int64_t n, const double* __restrict__ Ad, double* __restrict__ res, double* __restrict__ d,
+                              double* __restrict__ z, const double* __restrict__ diag, double a, double b,
+                              const uint8_t* __restrict__ mask) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (mask[i]) {
+    res[i] = 0.0;
+    d[i] = 0.0;
+    return;
+  }
+  const double ri = res[i] - Ad[i];
+  res[i] = ri;
+  const double di = a * d[i] + b * ri / diag[i];
+  d[i] = di;
+  z[i] += di;
+}
+
+__global__ void k_jacobi(int64_t n, const double* __restrict__ r, const double* __restrict__ diag,
+                         double* __restrict__ z, const uint8_t* __restrict__ mask) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) z[i] = mask[i] ? 0.0 : r[i] / diag[i];
+}
+
+// y = -y on free rows, 0 on Dirichlet rows
+__global__ void k_neg_masked(int64_t n, double* __restrict__ y, const uint8_t* __restrict__ mask) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = mask[i] ? 0.0 : -y[i];
+}
+
+__global__ void k_add(int64_t n, double* __restrict__ T, const double* __restrict__ x) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) T[i] += x[i];
+}
+
+// ---- adjoint sweep ----------------------------------------------------------------------------
+// v = lambda / C~, mu = lambda f / C~^2, q1 = f_diff / C~, q2 = f_vol / C~ on free dofs
+__global__ void k_adj_prepare(int n, int B, const double* __restrict__ lam, const double* __restrict__ fd,
+                              const double* __restrict__ fv, const double* __restrict__ Cm,
+                              const uint8_t* __restrict__ dir, double* __restrict__ v, double* __restrict__ mu,
+                              double* __restrict__ q1, double* __restrict__ q2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * B) return;
+  const int d = B == 1 ? i : i / B;
+  if (dir[d]) {
+    v[i] = mu[i] = q1[i] = q2[i] = 0.0;
+    return;
+  }
+  const double ic = 1.0 / Cm[i];
+  v[i] = lam[i] * ic;
+  mu[i] = lam[i] * (fd[i] + fv[i]) * ic * ic;
+  q1[i] = fd[i] * ic;
+  q2[i] = fv[i] * ic;
+}
+
+__device__ __forceinline__ double power_of(double t, double p, int ip) {
+  if (ip <= 0) return pow(t, p);
+  double r = 1.0, b = t;
+  for (int e = ip; e; e >>= 1) {
+    if (e & 1) r *= b;
+    b *= b;
+  }
+  return r;
+}
+
+// part[blk][b] = sum over a slice of the surface list of w_k T[idx_k][b]^p
+__global__ void k_pnorm_partial(int ns, int B, const int32_t* __restrict__ sidx, const double* __restrict__ sw,
+                                const double* __restrict__ T, double p, int ip, double* __restrict__ part) {
+  __shared__ double sh[kBS];
+  const int per = (ns + gridDim.x - 1) / gridDim.x;
+  const int lo = blockIdx.x * per, hi = min(ns, lo + per);
+  for (int b = 0; b < B; ++b) {
+    double acc = 0.0;
+    for (int k = lo + threadIdx.x; k < hi; k += blockDim.x) acc += sw[k] * power_of(T[sidx[k] * B + b], p, ip);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x * B + b] = sh[0];
+    __syncthreads();
+  }
+}
+
+// M_b = (S_b / W)^(1/p); J_b += (M_b - T_t)^2 / N when accumulating;
+// coef_b = 2 (M_b - T_t) / N * M_b^(1-p) / W  (dJ/dT_i = coef_b w_i T_i^(p-1))
+__global__ void k_objective(int B, int nblk, const double* __restrict__ part, double W, double p, double Tt,
+                            double invN, int accumulate, double* __restrict__ J, double* __restrict__ coef) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  double S = 0.0;
+  for (int k = 0; k < nblk; ++k) S += part[k * B + b];
+  const double M = pow(S / W, 1.0 / p);
+  if (accumulate) J[b] += (M - Tt) * (M - Tt) * invN;
+  coef[b] = 2.0 * (M - Tt) * invN * pow(M, 1.0 - p) / W;
+}
+
+// lambda += coef_b w_k T^(p-1) on the surface dofs (not on Dirichlet dofs)
+__global__ void k_lambda_objective(int ns, int B, const int32_t* __restrict__ sidx, const double* __restrict__ sw,
+                                   const double* __restrict__ T, double p, int ip, const double* __restrict__ coef,
+                                   const uint8_t* __restrict__ dir, double* __restrict__ lam) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= ns * B) return;
+  const int k = B == 1 ? i : i / B, b = i - k * B;
+  const int d = sidx[k];
+  if (dir[d]) return;
+  lam[d * B + b] += coef[b] * sw[k] * power_of(T[d * B + b], p - 1.0, ip > 0 ? ip - 1 : 0);
+}
+
+// lambda_k = lambda_{k+1} + dt (g - [nodal] mu C0 c_app'(T)/c) on free dofs, 0 on Dirichlet
+template <typename R, bool NODAL>
+__global__ void k_lambda_update(int n, int B, double* __restrict__ lam, R* __restrict__ g,
+                                const double* __restrict__ mu, const double* __restrict__ C0,
+                                const double* __restrict__ T, const NodalCap nc, const uint8_t* __restrict__ dir,
+                                double dt) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * B) return;
+  const int d = B == 1 ? i : i / B;
+  double gi = (double)g[i];
+  g[i] = R(0);
+  if (dir[d]) {
+    lam[i] = 0.0;
+    return;
+  }
+  if (NODAL) {
+    const double z = (T[i] - nc.Tm) * nc.inv_sigma;
+    gi -= mu[i] * C0[d] * nc.lat_ratio * (-z * nc.inv_sigma) * exp(-0.5 * z * z);
+  }
+  lam[i] += dt * gi;
+}
+
+// grad[b][seg] += dt d2[b] / P[b][seg];  grad[b][nseg] += dt d1[b] / s_b
+__global__ void k_grad_accum(int B, int nseg, int seg, const double* __restrict__ d1, const double* __restrict__ d2,
+                             const double* __restrict__ s, const double* __restrict__ power, double dt,
+                             double* __restrict__ grad) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  grad[b * (nseg + 1) + nseg] += dt * d1[b] / s[b];
+  if (seg >= 0) grad[b * (nseg + 1) + seg] += dt * d2[b] / power[b * kMaxSeg + seg];
+}
+
+// w_i += int_top N_i dA over top faces ((P+1)^2 Gauss points), through the constraints
+template <int P>
+__global__ void k_surface_weights(int n_top, const int32_t* __restrict__ top_cell, const double* __restrict__ top_geo,
+                                  const DevMesh M, double* __restrict__ w) {
+  constexpr int N = P + 1;
+  const int face = blockIdx.x * blockDim.x + threadIdx.x;
+  if (face >= n_top) return;
+  const double area = top_geo[4 * face + 2] * top_geo[4 * face + 3];
+  const int cell = top_cell[face];
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      double wj = 0.0, wk = 0.0;
+#pragma unroll
+      for (int q = 0; q < N; ++q) {
+        wj += Basis<P>::W(q) * Basis<P>::S(q, j);
+        wk += Basis<P>::W(q) * Basis<P>::S(q, k);
+      }
+      const double val = wj * wk * area;
+      const int d = M.cell_dofs[(k + N * (j + N * P)) * M.n_cells + cell];
+      if (d >= 0) {
+        atomicAdd(&w[d], val);
+      } else {
+        for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e) atomicAdd(&w[M.con_idx[e]], M.con_w[e] * val);
+      }
+    }
 }
 
 // ---- field transfer -----------------------------------------------------------------------
@@ -487,6 +687,99 @@ cudaError_t launch_hang_distribute(bool f32, const DevMesh& M, void* fh, void* f
   if (n == 0) return cudaSuccess;
   if (f32) k_hang_distribute<float><<<grid_for(n), kBS, 0, s>>>(M.n_hang, M.batch, M.con_ptr, M.con_idx, M.con_wf, (float*)fh, (float*)f);
   else k_hang_distribute<double><<<grid_for(n), kBS, 0, s>>>(M.n_hang, M.batch, M.con_ptr, M.con_idx, M.con_w, (double*)fh, (double*)f);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy2(int64_t n, double alpha, const double* p, const double* Ap, double* x, double* r,
+                         cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_axpy2<<<grid_for(n), kBS, 0, s>>>(n, alpha, p, Ap, x, r);
+  return cudaGetLastError();
+}
+cudaError_t launch_xpby(int64_t n, const double* z, double beta, double* p, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_xpby<<<grid_for(n), kBS, 0, s>>>(n, z, beta, p);
+  return cudaGetLastError();
+}
+cudaError_t launch_cheb_init(int64_t n, const double* r, const double* diag, double inv_theta, double* res, double* d,
+                             double* z, const uint8_t* mask, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_cheb_init<<<grid_for(n), kBS, 0, s>>>(n, r, diag, inv_theta, res, d, z, mask);
+  return cudaGetLastError();
+}
+cudaError_t launch_cheb_update(int64_t n, const double* Ad, double* res, double* d, double* z, const double* diag,
+                               double a, double b, const uint8_t* mask, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_cheb_update<<<grid_for(n), kBS, 0, s>>>(n, Ad, res, d, z, diag, a, b, mask);
+  return cudaGetLastError();
+}
+cudaError_t launch_jacobi(int64_t n, const double* r, const double* diag, double* z, const uint8_t* mask,
+                          cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_jacobi<<<grid_for(n), kBS, 0, s>>>(n, r, diag, z, mask);
+  return cudaGetLastError();
+}
+cudaError_t launch_neg_masked(int64_t n, double* y, const uint8_t* mask, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_neg_masked<<<grid_for(n), kBS, 0, s>>>(n, y, mask);
+  return cudaGetLastError();
+}
+cudaError_t launch_add(int64_t n, double* T, const double* x, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_add<<<grid_for(n), kBS, 0, s>>>(n, T, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_prepare(int n, int B, const double* lam, const double* fd, const double* fv, const double* Cm,
+                               const uint8_t* dir, double* v, double* mu, double* q1, double* q2, cudaStream_t s) {
+  if (n * B == 0) return cudaSuccess;
+  k_adj_prepare<<<grid_for((int64_t)n * B), kBS, 0, s>>>(n, B, lam, fd, fv, Cm, dir, v, mu, q1, q2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_objective(int ns, int B, const int32_t* sidx, const double* sw, const double* T, double W, double p,
+                             double Tt, double invN, int accumulate, double* part, double* J, double* coef,
+                             cudaStream_t s) {
+  const int ip = (p == (double)(int)p && p >= 1 && p <= 64) ? (int)p : 0;
+  k_pnorm_partial<<<kRedBlocks, kBS, 0, s>>>(ns, B, sidx, sw, T, p, ip, part);
+  k_objective<<<(B + 63) / 64, 64, 0, s>>>(B, kRedBlocks, part, W, p, Tt, invN, accumulate, J, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_objective(int ns, int B, const int32_t* sidx, const double* sw, const double* T, double p,
+                                    const double* coef, const uint8_t* dir, double* lam, cudaStream_t s) {
+  if (ns * B == 0) return cudaSuccess;
+  const int ip = (p == (double)(int)p && p >= 1 && p <= 64) ? (int)p : 0;
+  k_lambda_objective<<<grid_for((int64_t)ns * B), kBS, 0, s>>>(ns, B, sidx, sw, T, p, ip, coef, dir, lam);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_update(bool f32, bool nodal, int n, int B, double* lam, void* g, const double* mu,
+                                 const double* C0, const double* T, const NodalCap& nc, const uint8_t* dir, double dt,
+                                 cudaStream_t s) {
+  if (n * B == 0) return cudaSuccess;
+  const unsigned gr = grid_for((int64_t)n * B);
+  if (f32) {
+    if (nodal) k_lambda_update<float, true><<<gr, kBS, 0, s>>>(n, B, lam, (float*)g, mu, C0, T, nc, dir, dt);
+    else k_lambda_update<float, false><<<gr, kBS, 0, s>>>(n, B, lam, (float*)g, mu, C0, T, nc, dir, dt);
+  } else {
+    if (nodal) k_lambda_update<double, true><<<gr, kBS, 0, s>>>(n, B, lam, (double*)g, mu, C0, T, nc, dir, dt);
+    else k_lambda_update<double, false><<<gr, kBS, 0, s>>>(n, B, lam, (double*)g, mu, C0, T, nc, dir, dt);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_accum(int B, int nseg, int seg, const double* d1, const double* d2, const double* sc,
+                              const double* power, double dt, double* grad, cudaStream_t s) {
+  k_grad_accum<<<(B + 63) / 64, 64, 0, s>>>(B, nseg, seg, d1, d2, sc, power, dt, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surface_weights(int degree, int n_top, const int32_t* top_cell, const double* top_geo,
+                                   const DevMesh& M, double* w, cudaStream_t s) {
+  if (n_top == 0) return cudaSuccess;
+  if (degree == 1) k_surface_weights<1><<<grid_for(n_top, 128), 128, 0, s>>>(n_top, top_cell, top_geo, M, w);
+  else k_surface_weights<2><<<grid_for(n_top, 128), 128, 0, s>>>(n_top, top_cell, top_geo, M, w);
   return cudaGetLastError();
 }
 

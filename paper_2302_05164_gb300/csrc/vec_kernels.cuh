@@ -44,6 +44,32 @@ cudaError_t launch_reciprocal(int64_t n, const double* c, double* inv_d, float* 
 // x_h = P_h x (values at hanging nodes) and f += P_h^T f_h (f_h cleared); FP32 or FP64 arrays
 cudaError_t launch_hang_values(bool f32, const DevMesh& M, const void* x, void* out, cudaStream_t s);
 cudaError_t launch_hang_distribute(bool f32, const DevMesh& M, void* fh, void* f, cudaStream_t s);
+cudaError_t launch_axpy2(int64_t n, double alpha, const double* p, const double* Ap, double* x, double* r,
+                         cudaStream_t s);
+cudaError_t launch_xpby(int64_t n, const double* z, double beta, double* p, cudaStream_t s);
+cudaError_t launch_cheb_init(int64_t n, const double* r, const double* diag, double inv_theta, double* res, double* d,
+                             double* z, const uint8_t* mask, cudaStream_t s);
+cudaError_t launch_cheb_update(int64_t n, const double* Ad, double* res, double* d, double* z, const double* diag,
+                               double a, double b, const uint8_t* mask, cudaStream_t s);
+cudaError_t launch_jacobi(int64_t n, const double* r, const double* diag, double* z, const uint8_t* mask,
+                          cudaStream_t s);
+cudaError_t launch_neg_masked(int64_t n, double* y, const uint8_t* mask, cudaStream_t s);
+cudaError_t launch_add(int64_t n, double* T, const double* x, cudaStream_t s);
+// adjoint sweep helpers (FP64)
+cudaError_t launch_adj_prepare(int n, int B, const double* lam, const double* fd, const double* fv, const double* Cm,
+                               const uint8_t* dir, double* v, double* mu, double* q1, double* q2, cudaStream_t s);
+cudaError_t launch_objective(int ns, int B, const int32_t* sidx, const double* sw, const double* T, double W, double p,
+                             double Tt, double invN, int accumulate, double* part, double* J, double* coef,
+                             cudaStream_t s);
+cudaError_t launch_lambda_objective(int ns, int B, const int32_t* sidx, const double* sw, const double* T, double p,
+                                    const double* coef, const uint8_t* dir, double* lam, cudaStream_t s);
+cudaError_t launch_lambda_update(bool f32, bool nodal, int n, int B, double* lam, void* g, const double* mu,
+                                 const double* C0, const double* T, const NodalCap& nc, const uint8_t* dir, double dt,
+                                 cudaStream_t s);
+cudaError_t launch_grad_accum(int B, int nseg, int seg, const double* d1, const double* d2, const double* sc,
+                              const double* power, double dt, double* grad, cudaStream_t s);
+cudaError_t launch_surface_weights(int degree, int n_top, const int32_t* top_cell, const double* top_geo,
+                                   const DevMesh& M, double* w, cudaStream_t s);
 int reduction_blocks();
 // out[b] = sum_d w_d x[d][b] y[d][b] over dofs with !skip[d]; part: [reduction_blocks()][B]
 cudaError_t launch_dot(int64_t n_dofs, int B, const double* x, const double* y, const double* w, const uint8_t* skip,

@@ -302,10 +302,11 @@ def test_chebyshev_is_the_shifted_chebyshev_polynomial(oracle_mod):
     assert abs(hi - ev.max()) < 1e-6 * ev.max() and abs(lo - ev.min()) < 1e-6 * ev.min()
 
 
-def test_adjoint_matches_central_differences(oracle_mod):
-    d = I.mesh_desc((4, 2, 2), (62.5e-6,) * 3, 1, 1, [I.uniform_region(1)])
+@pytest.mark.parametrize("p,lumping", [(1, I.LUMP_QUADRATURE), (2, I.LUMP_NODAL)])
+def test_adjoint_matches_central_differences(oracle_mod, p, lumping):
+    d = I.mesh_desc((4, 2, 2), (62.5e-6,) * 3, p, 1, [I.uniform_region(1)])
     m = oracle_mod.Mesh(d)
-    mat = dict(I.TI64_NONLIN)
+    mat = dict(I.TI64_NONLIN, lumping=lumping)
     T0 = I.smooth_field(m.dof_xyz(), seed=11, lo=353.0, hi=2400.0)
     dt, nst = 2e-7, 12
     ls = I.c4_laser([[180.0, 220.0, 240.0]], n_seg=3, steps_per_seg=4, dt=dt, v=0.5, y=0.25e-3)
