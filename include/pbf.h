@@ -256,6 +256,12 @@ pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, const pbf_laser
  * for nsteps steps and n_snaps stored states; host only. */
 pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_out);
 
+/* Autotuner of the launch shape of the FP32-operator cell kernel (threads per block and the
+ * register bound that sets resident blocks per SM): times every shape on `reps` residual
+ * evaluations at the state T_dev (not modified), keeps the fastest in the context and
+ * returns its index (0 = default). FP64 contexts keep the default. Synchronises. */
+pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, pbf_stream stream);
+
 /* Kernel timing of the dominant (cell operator) kernel: when enabled, CUDA events bracket
  * every cell-operator launch on its stream; pbf_ctx_kernel_time returns the summed elapsed
  * milliseconds and the launch count since the last reset (synchronises). */

@@ -163,7 +163,7 @@ class Mesh:
         return T
 
     def lambda_max(self, mat, x0, max_iter=200, rtol=1e-6, s=1.0):
-        x0 = _f64(x0)
+        x0 = _f64(x0)  # bound to a name: the array must outlive the C call
         it = C.c_int(0)
         lam = lib().or_lambda_max(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(x0),
                                   C.c_int(max_iter), C.c_double(rtol), C.byref(it))
@@ -171,12 +171,14 @@ class Mesh:
 
     def lumped_capacity(self, mat, T):
         out = np.zeros(self.n_dofs)
-        lib().or_lumped_capacity(C.c_void_p(self.h), C.byref(material(mat)), _ptr(_f64(T)), _ptr(out))
+        T = _f64(T)  # keep the (possibly copied) array alive during the call
+        lib().or_lumped_capacity(C.c_void_p(self.h), C.byref(material(mat)), _ptr(T), _ptr(out))
         return out
 
     def apply_implicit(self, mat, dt, x):
         y = np.zeros(self.n_dofs)
-        lib().or_apply_implicit(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), _ptr(_f64(x)), _ptr(y))
+        x = _f64(x)
+        lib().or_apply_implicit(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), _ptr(x), _ptr(y))
         return y
 
     def implicit_diagonal(self, mat, dt):
@@ -186,13 +188,15 @@ class Mesh:
 
     def chebyshev(self, mat, dt, degree, lmin, lmax, r):
         z = np.zeros(self.n_dofs)
+        r = _f64(r)
         lib().or_chebyshev(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), C.c_int(degree),
-                           C.c_double(lmin), C.c_double(lmax), _ptr(_f64(r)), _ptr(z))
+                           C.c_double(lmin), C.c_double(lmax), _ptr(r), _ptr(z))
         return z
 
     def lanczos_bounds(self, mat, dt, b, n_iter=30):
         out = np.zeros(2)
-        lib().or_lanczos_bounds(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), _ptr(_f64(b)),
+        b = _f64(b)
+        lib().or_lanczos_bounds(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(dt), _ptr(b),
                                 C.c_int(n_iter), _ptr(out))
         return float(out[0]), float(out[1])
 
@@ -207,14 +211,16 @@ class Mesh:
     def adjoint(self, mat, T0, ls, t0, dt, nsteps, T_target=2300.0, p_exp=16.0, s=1.0, instance=0):
         lh = _LaserHolder(ls, instance)
         grad = np.zeros(lh.seg.shape[0] + 1)
-        J = lib().or_adjoint(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(_f64(T0)), lh.ref,
+        T0 = _f64(T0)
+        J = lib().or_adjoint(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(T0), lh.ref,
                              C.c_double(t0), C.c_double(dt), C.c_int(nsteps), C.c_double(T_target),
                              C.c_double(p_exp), _ptr(grad))
         return J, grad
 
     def objective(self, mat, T0, ls, t0, dt, nsteps, T_target=2300.0, p_exp=16.0, s=1.0, instance=0):
         lh = _LaserHolder(ls, instance)
-        return lib().or_objective(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(_f64(T0)),
+        T0 = _f64(T0)
+        return lib().or_objective(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(T0),
                                   lh.ref, C.c_double(t0), C.c_double(dt), C.c_int(nsteps),
                                   C.c_double(T_target), C.c_double(p_exp))
 
@@ -226,7 +232,8 @@ class Mesh:
 
 def transfer(old: Mesh, T_old, new: Mesh, T_init):
     out = np.zeros(new.n_dofs)
-    lib().or_transfer(C.c_void_p(old.h), _ptr(_f64(T_old)), C.c_void_p(new.h), C.c_double(T_init), _ptr(out))
+    T_old = _f64(T_old)
+    lib().or_transfer(C.c_void_p(old.h), _ptr(T_old), C.c_void_p(new.h), C.c_double(T_init), _ptr(out))
     return out
 
 

@@ -299,6 +299,30 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     }
   }
   std::vector<float> con_wf(m.con_w.begin(), m.con_w.end());
+  std::vector<uint8_t> ctop(m.top.begin(), m.top.end());
+  std::vector<float> lof(lo.size());
+  for (size_t e = 0; e < nc; ++e)
+    for (int a = 0; a < 3; ++a) lof[e * 3 + a] = (float)lo[e * 3 + a];
+  // transposed constraint map: for each dof the hanging rows it is a master of
+  std::vector<int32_t> mptr((size_t)m.n_dofs + 1, 0), mrow;
+  std::vector<double> mw;
+  for (size_t e = 0; e < m.con_idx.size(); ++e) ++mptr[(size_t)m.con_idx[e] + 1];
+  for (size_t d = 0; d < (size_t)m.n_dofs; ++d) mptr[d + 1] += mptr[d];
+  mrow.resize(m.con_idx.size());
+  mw.resize(m.con_idx.size());
+  {
+    std::vector<int32_t> fill(mptr.begin(), mptr.end() - 1);
+    for (size_t r = 0; r + 1 < m.con_ptr.size(); ++r)
+      for (int32_t e = m.con_ptr[r]; e < m.con_ptr[r + 1]; ++e) {
+        const int32_t slot = fill[(size_t)m.con_idx[(size_t)e]]++;
+        mrow[(size_t)slot] = (int32_t)r;
+        mw[(size_t)slot] = m.con_w[(size_t)e];
+      }
+  }
+  std::vector<float> mwf(mw.begin(), mw.end());
+  int32_t *d_mptr = nullptr, *d_mrow = nullptr;
+  double* d_mw = nullptr;
+  float* d_mwf = nullptr;
   std::vector<double> level_h((size_t)kMaxLevels * 3, 0.0);
   CellLaunch& L = c->base;
   for (int l = 0; l <= m.L && l < kMaxLevels; ++l) {
@@ -308,6 +332,8 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     L.gd.detJ[l] = detJ;
     L.gf.detJ[l] = (float)detJ;
     for (int a = 0; a < 3; ++a) {
+      L.gd.h[l][a] = h[a];
+      L.gf.h[l][a] = (float)h[a];
       level_h[(size_t)l * 3 + a] = h[a];
       L.gd.ih2[l][a] = 1.0 / (h[a] * h[a]);
       L.gf.ih2[l][a] = (float)(1.0 / (h[a] * h[a]));
@@ -328,7 +354,19 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   UP(c->top_geo, top_geo);
   UP(c->cell_lo, lo);
   UP(c->level_h, level_h);
+  UP(c->cell_top, ctop);
+  UP(c->cell_lof, lof);
+  UP(d_mptr, mptr);
+  UP(d_mrow, mrow);
+  UP(d_mw, mw);
+  UP(d_mwf, mwf);
 #undef UP
+  if (c->n_hang > 0) {
+    c->pull.ptr = d_mptr;
+    c->pull.row = d_mrow;
+    c->pull.w = d_mw;
+    c->pull.wf = d_mwf;
+  }
   c->n_top = (int64_t)top_cell.size();
   const size_t rsz = c->f32 ? 4 : 8;
   const size_t nv = nd * (size_t)batch;
@@ -352,6 +390,7 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_d, nd);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_f, nd);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->power, (size_t)batch * kMaxSeg);
+  if (e == cudaSuccess) e = dalloc(c.get(), &c->powerf, (size_t)batch * kMaxSeg);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->part, (size_t)reduction_blocks() * batch);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->scal, (size_t)batch * 16);
   c->k_scale_host.assign((size_t)batch, 1.0);
@@ -383,6 +422,9 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   M.con_w = c->con_w;
   M.con_wf = c->con_wf;
   M.dirichlet = c->dirichlet;
+  M.cell_top = c->cell_top;
+  M.cell_lo = c->cell_lo;
+  M.cell_lof = c->cell_lof;
   L.degree = c->degree;
   L.f32 = c->f32;
   L.nonlin_k = c->nonlin;
@@ -518,7 +560,10 @@ pbf_status CtxBase::set_laser(const pbf_laser* ls, cudaStream_t s) {
     for (int i = 0; i < ls->n_seg; ++i) pw[(size_t)b * kMaxSeg + (size_t)i] = ls->power[(size_t)b * ls->n_seg + (size_t)i];
   if (pw != power_host) {
     power_host = pw;
+    std::vector<float> pf(pw.begin(), pw.end());
     cudaError_t e = cudaMemcpyAsync(power, pw.data(), pw.size() * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(powerf, pf.data(), pf.size() * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // host staging buffers go out of scope
     if (e != cudaSuccess) return cuda(e, "laser power upload");
   }
   return PBF_OK;
@@ -590,49 +635,89 @@ cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_d
   return e;
 }
 
-// nsteps forward-Euler steps on T (laser already set)
+// One fused forward-Euler step sequence on T (laser already set). Per step: hanging values of
+// the state (clearing the hanging accumulators), the cell kernel with the surface laser on
+// top faces, and the update, which pulls the hanging-node contributions to their masters.
 cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
   CellLaunch L = base;
   const bool with_laser = lsetup.k.n_seg > 0;
+  const bool volumetric = with_laser && lsetup.k.volumetric;
   const int64_t nv = n_dofs * batch;
   cudaError_t e = cudaSuccess;
   if (nsteps <= 0) return e;
+  PullMap pm = pull;
+  pm.fh = fh;
+  pm.Ch = latent ? Ch : nullptr;
+  const double tw_dir = mat.T_dirichlet - mat.T_ref;
+  const float tf_dir = (float)tw_dir;
   if (f32) {
     // FP64 working state Tw = T - T_ref and its FP32 copy for the whole call
-    const double tw_dir = mat.T_dirichlet - mat.T_ref;
-    const float tf_dir = (float)tw_dir;
     e = launch_prepare_f32(nv, T_dev, mat.T_ref, Tw, Tf, s);
     ++launches;
     L.xf = Tf;
-    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      const double t = t0 + n * dt;
-      e = apply_cell(L, f, latent ? Cacc : nullptr, MODE_RESIDUAL, s);
-      if (e == cudaSuccess && with_laser) {
-        e = launch_laser(degree, true, lsetup, L.mesh, power, spot_at(lsetup.k, t), f, s);
-        ++launches;
-      }
-      if (e == cudaSuccess)
-        e = launch_update_f32(cap, n_dofs, batch, Tw, Tf, (float*)f, (float*)Cacc, invC0_f, nodal, dirichlet, tw_dir,
-                              tf_dir, (float)dt, s);
-      ++launches;
-    }
-    if (e == cudaSuccess) e = launch_finish_f32(nv, Tw, mat.T_ref, T_dev, s);
-    ++launches;
+    L.xfh = (const float*)xh;
   } else {
     L.x = T_dev;
-    for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-      const double t = t0 + n * dt;
-      e = apply_cell(L, f, latent ? Cacc : nullptr, MODE_RESIDUAL, s);
-      if (e == cudaSuccess && with_laser) {
-        e = launch_laser(degree, false, lsetup, L.mesh, power, spot_at(lsetup.k, t), f, s);
-        ++launches;
+    L.xh = (const double*)xh;
+  }
+  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    const double t = t0 + n * dt;
+    const Spot sp = with_laser ? spot_at(lsetup.k, t) : Spot();
+    L.las = LaserInline();
+    if (with_laser && !volumetric && sp.seg >= 0) {
+      const double r = lsetup.k.radius;
+      L.las.on = 1;
+      L.las.seg = sp.seg;
+      L.las.sx = sp.x;
+      L.las.sy = sp.y;
+      L.las.amp = 2.0 * lsetup.k.eta / (kPi * r * r);
+      L.las.ir2 = 2.0 / (r * r);
+      L.las.cut2 = 36.0 * r * r;
+      L.las.power = power;
+      L.las.powerf = powerf;
+    }
+    e = launch_hang_values_zero(f32, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev, xh, fh, latent ? Ch : nullptr, s);
+    ++launches;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (timing && e == cudaSuccess) {
+      if (free_events.empty()) {
+        cudaEventCreate(&ev.first);
+        cudaEventCreate(&ev.second);
+      } else {
+        ev = free_events.back();
+        free_events.pop_back();
       }
-      if (e == cudaSuccess)
-        e = launch_update_f64(cap, n_dofs, batch, T_dev, (double*)f, (double*)Cacc, invC0_d, nodal, dirichlet,
-                              mat.T_dirichlet, dt, s);
+      cudaEventRecord(ev.first, s);
+    }
+    if (e == cudaSuccess) e = launch_cell(L, f, fh, latent ? Cacc : nullptr, latent ? Ch : nullptr, MODE_RESIDUAL, s);
+    ++launches;
+    if (timing && ev.first) {
+      cudaEventRecord(ev.second, s);
+      events.push_back(ev);
+    }
+    if (e == cudaSuccess && volumetric && sp.seg >= 0) {
+      e = launch_laser(degree, f32, lsetup, L.mesh, power, sp, f, s);
       ++launches;
     }
+    if (e == cudaSuccess) {
+      if (f32)
+        e = launch_update_f32(cap, n_dofs, batch, Tw, Tf, (float*)f, (float*)Cacc, invC0_f, nodal, dirichlet, tw_dir,
+                              tf_dir, (float)dt, s, pm);
+      else
+        e = launch_update_f64(cap, n_dofs, batch, T_dev, (double*)f, (double*)Cacc, invC0_d, nodal, dirichlet,
+                              mat.T_dirichlet, dt, s, pm);
+    }
+    ++launches;
   }
+  if (f32 && e == cudaSuccess) {
+    e = launch_finish_f32(nv, Tw, mat.T_ref, T_dev, s);
+    ++launches;
+  }
+  // the update pulls f_h without clearing it: clear it (and C_h) so that every accumulator is
+  // zero between calls, as the other operator paths expect
+  const size_t nh = (size_t)n_hang * (size_t)batch * (f32 ? 4 : 8);
+  if (e == cudaSuccess && nh) e = cudaMemsetAsync(fh, 0, nh, s);
+  if (e == cudaSuccess && nh && latent) e = cudaMemsetAsync(Ch, 0, nh, s);
   return e;
 }
 
@@ -671,6 +756,58 @@ extern "C" pbf_status pbf_widen_to_f64(const float* x_dev, double* y_dev, int64_
   if (n < 0) return fail(PBF_EINVAL, "negative length");
   cudaError_t e = launch_f32_to_f64(n, x_dev, y_dev, (cudaStream_t)stream);
   return e == cudaSuccess ? PBF_OK : fail(PBF_ECUDA, "widen_to_f64: %s", cudaGetErrorString(e));
+}
+
+extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out,
+                                       pbf_stream stream) {
+  if (!ctx || !T_dev || reps < 1) return fail(PBF_EINVAL, "bad arguments");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!ctx->f32) {
+    ctx->base.variant = 0;
+    if (variant_out) *variant_out = 0;
+    return PBF_OK;
+  }
+  const int64_t nv = ctx->n_dofs * ctx->batch;
+  CellLaunch L = ctx->base;
+  cudaError_t e = launch_prepare_f32(nv, T_dev, ctx->mat.T_ref, nullptr, ctx->Tf, s);
+  L.xf = ctx->Tf;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  int best = 0;
+  float best_ms = 0.f;
+  for (int v = 0; v < kCellVariants && e == cudaSuccess; ++v) {
+    L.variant = v;
+    e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    for (int r = 0; r < reps && e == cudaSuccess; ++r)
+      e = launch_cell(L, ctx->f, ctx->fh, ctx->latent ? ctx->Cacc : nullptr, ctx->latent ? ctx->Ch : nullptr,
+                      MODE_RESIDUAL, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
+      best = v;
+      best_ms = ms;
+    }
+    ctx->launches += reps + 3;
+  }
+  const size_t rsz = 4;
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f, 0, (size_t)nv * rsz, s);
+  const size_t nh = std::max<size_t>(1, (size_t)ctx->n_hang * ctx->batch);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fh, 0, nh * rsz, s);
+  if (e == cudaSuccess && ctx->latent) e = cudaMemsetAsync(ctx->Cacc, 0, (size_t)nv * rsz, s);
+  if (e == cudaSuccess && ctx->latent) e = cudaMemsetAsync(ctx->Ch, 0, nh * rsz, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (e != cudaSuccess) return ctx->cuda(e, "autotune");
+  ctx->base.variant = best;
+  if (variant_out) *variant_out = best;
+  return PBF_OK;
 }
 
 extern "C" pbf_status pbf_ctx_set_timing(pbf_ctx* ctx, int enable) {

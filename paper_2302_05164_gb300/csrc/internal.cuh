@@ -90,6 +90,9 @@ struct DevMesh {
   const double* con_w = nullptr;
   const float* con_wf = nullptr;
   const uint8_t* dirichlet = nullptr;
+  const uint8_t* cell_top = nullptr;  // 1 when the cell has an active top face
+  const double* cell_lo = nullptr;    // [n_cells][3] lower corner
+  const float* cell_lof = nullptr;    // the same in FP32
 };
 
 // Per-level geometry of axis-aligned cells (diagonal Jacobian J = diag(h)), precomputed on
@@ -98,6 +101,19 @@ template <typename R>
 struct GeoR {
   R detJ[kMaxLevels];
   R ih2[kMaxLevels][3];  // 1 / h_d^2
+  R h[kMaxLevels][3];    // h_d
+};
+
+// Surface laser evaluated inside the cell kernel on top faces (spot from the host per step).
+struct LaserInline {
+  int on = 0;
+  int seg = -1;
+  double sx = 0.0, sy = 0.0;     // spot position
+  double amp = 0.0;              // 2 eta / (pi r^2) (times the segment power per instance)
+  double ir2 = 0.0;              // 2 / r^2
+  double cut2 = 0.0;             // faces farther than sqrt(cut2) from the spot are skipped
+  const double* power = nullptr; // [batch][kMaxSeg]
+  const float* powerf = nullptr; // the same in FP32
 };
 
 // Material constants precomputed on the host in the kernel's precision.
@@ -155,7 +171,13 @@ struct CellLaunch {
   const float* mufh = nullptr;
   int degree = 1;
   int f32 = 0;
+  int variant = 0;  // launch shape of the FP32 residual kernel (see kCellVariants)
+  LaserInline las;
 };
+
+// Launch shapes the autotuner chooses from for the FP32 residual cell kernel:
+// {threads per block, minimum resident blocks per SM} (the second bounds registers per thread)
+constexpr int kCellVariants = 4;
 
 template <typename R>
 __host__ __device__ inline const GeoR<R>& geo_of(const CellLaunch& L);

@@ -10,6 +10,7 @@
 // values are scattered with atomics onto dofs and, through the constraint rows, onto the
 // masters of hanging nodes (G_e^T P^T).
 #include <cstdio>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -137,10 +138,44 @@ __device__ __forceinline__ constexpr double wq3(int q) {
   return Basis<P>::W(q % (P + 1)) * Basis<P>::W((q / (P + 1)) % (P + 1)) * Basis<P>::W(q / ((P + 1) * (P + 1)));
 }
 
+// Surface Gaussian 2 eta P/(pi r^2) exp(-2 d^2/r^2) on the cell's top face, (P+1)^2 Gauss
+// points, added to the top-face nodes of fe; skipped when the face lies farther than 6 r from
+// the spot (the integrand is below e^-72 there). Offsets from the spot in FP64, the rest in R.
+template <int P, typename R>
+__device__ __forceinline__ void add_laser(const CellLaunch& L, int cell, int inst, int lev, R* fe) {
+  constexpr int N = P + 1;
+  const GeoR<R>& geo = geo_of<R>(L);
+  R ox, oy, amp;
+  if (sizeof(R) == 4) {  // FP32 operator: positions and powers in FP32 too
+    ox = R(L.mesh.cell_lof[3 * cell] - float(L.las.sx));
+    oy = R(L.mesh.cell_lof[3 * cell + 1] - float(L.las.sy));
+    amp = R(float(L.las.amp) * L.las.powerf[inst * kMaxSeg + L.las.seg]);
+  } else {
+    ox = R(L.mesh.cell_lo[3 * cell] - L.las.sx);
+    oy = R(L.mesh.cell_lo[3 * cell + 1] - L.las.sy);
+    amp = R(L.las.amp * L.las.power[inst * kMaxSeg + L.las.seg]);
+  }
+  const R hx = geo.h[lev][0], hy = geo.h[lev][1];
+  const R gx = max(R(0), max(ox, -(ox + hx))), gy = max(R(0), max(oy, -(oy + hy)));
+  if (gx * gx + gy * gy > R(L.las.cut2)) return;
+  const R ir2 = R(L.las.ir2);
+#pragma unroll
+  for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+    for (int qx = 0; qx < N; ++qx) {
+      const R x = ox + R(Basis<P>::X(qx)) * hx, y = oy + R(Basis<P>::X(qy)) * hy;
+      const R q = amp * expo(-(x * x + y * y) * ir2) * R(Basis<P>::W(qx) * Basis<P>::W(qy)) * hx * hy;
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int k = 0; k < N; ++k) fe[k + N * (j + N * P)] += q * R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
+    }
+}
+
 // One kernel for the residual / capacity / stiffness / implicit-operator modes.
-template <int P, typename R, int MODE, bool NLK, bool LAT>
-__global__ void __launch_bounds__(128) k_cell(const CellLaunch L, R* __restrict__ f, R* __restrict__ fh,
-                                              R* __restrict__ C, R* __restrict__ Ch) {
+template <int P, typename R, int MODE, bool NLK, bool LAT, int BS = 128, int MINB = 1>
+__global__ void __launch_bounds__(BS, MINB) k_cell(const CellLaunch L, R* __restrict__ f, R* __restrict__ fh,
+                                                   R* __restrict__ C, R* __restrict__ Ch) {
   constexpr int N = P + 1, NP = N * N * N;
   (void)N;
   const DevMesh& M = L.mesh;
@@ -219,6 +254,7 @@ __global__ void __launch_bounds__(128) k_cell(const CellLaunch L, R* __restrict_
   }
   R fe[NP];
   integrate_values<P, R>(r, fe);
+  if (MODE == MODE_RESIDUAL && L.las.on && M.cell_top[cell]) add_laser<P, R>(L, cell, inst, lev, fe);
   scatter<P, R>(M, f, fh, cell, inst, fe);
 }
 
@@ -380,14 +416,28 @@ cudaError_t dispatch_adj(const CellLaunch& L, bool qpc, void* g, void* gh, cudaS
   return go_adj<P, R, false, false>(L, g, gh, s);
 }
 
-template <int P, typename R, int MODE, bool NLK, bool LAT>
-cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
+template <int P, typename R, int MODE, bool NLK, bool LAT, int BS = 128, int MINB = 1>
+cudaError_t go_shape(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
   const int64_t n = (int64_t)L.mesh.n_cells * L.mesh.batch;
   if (n == 0) return cudaSuccess;
-  const int bs = 128;
-  const int64_t grid = (n + bs - 1) / bs;
-  k_cell<P, R, MODE, NLK, LAT><<<(unsigned)grid, bs, 0, s>>>(L, (R*)f, (R*)fh, (R*)C, (R*)Ch);
+  const int64_t grid = (n + BS - 1) / BS;
+  k_cell<P, R, MODE, NLK, LAT, BS, MINB><<<(unsigned)grid, BS, 0, s>>>(L, (R*)f, (R*)fh, (R*)C, (R*)Ch);
   return cudaGetLastError();
+}
+
+// The FP32 residual kernel without quadrature-point capacity comes in the autotuner's launch
+// shapes; every other combination uses 128 threads with no register cap.
+template <int P, typename R, int MODE, bool NLK, bool LAT>
+cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
+  if (std::is_same<R, float>::value && MODE == MODE_RESIDUAL && !LAT) {
+    switch (L.variant) {
+      case 1: return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
+      case 2: return go_shape<P, R, MODE, NLK, LAT, 128, 6>(L, f, fh, C, Ch, s);
+      case 3: return go_shape<P, R, MODE, NLK, LAT, 64, 10>(L, f, fh, C, Ch, s);
+      default: break;
+    }
+  }
+  return go_shape<P, R, MODE, NLK, LAT>(L, f, fh, C, Ch, s);
 }
 
 template <int P, typename R>

@@ -40,11 +40,15 @@ struct CtxBase {
   double* top_geo = nullptr;
   double* cell_lo = nullptr;
   double* level_h = nullptr;
+  uint8_t* cell_top = nullptr;
+  PullMap pull;  // transposed constraint map (accumulator pointers set per launch)
   // material / instance data
   double* k_scale_d = nullptr;
   float* k_scale_f = nullptr;
   std::vector<double> k_scale_host;
   double* power = nullptr;  // [batch][kMaxSeg]
+  float* powerf = nullptr;  // the same in FP32
+  float* cell_lof = nullptr;
   std::vector<double> power_host;
   // work space
   void* f = nullptr;     // operator accumulator (FP32 or FP64) [n_dofs][batch]

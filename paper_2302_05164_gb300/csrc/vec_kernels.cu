@@ -21,16 +21,23 @@ inline unsigned grid_for(int64_t n, int bs = kBS) { return (unsigned)((n + bs - 
 template <int CAP>
 __global__ void k_update_f64(int64_t n, int B, double* __restrict__ T, double* __restrict__ f,
                              double* __restrict__ Cacc, const double* __restrict__ invC0, const NodalCap nc,
-                             const uint8_t* __restrict__ dirichlet, double T_dir, double dt) {
+                             const uint8_t* __restrict__ dirichlet, double T_dir, double dt, const PullMap pm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int d = B == 1 ? i : i / B;
-  const double fi = f[i];
+  const int d = B == 1 ? i : i / B, inst = i - d * B;
+  double fi = f[i];
   f[i] = 0.0;
   double ci = 0.0;
   if (CAP == CAP_QUADRATURE) {
     ci = Cacc[i];
     Cacc[i] = 0.0;
+  }
+  if (pm.ptr) {  // contributions of hanging nodes whose master d is (P_h^T f_h, pulled)
+    for (int e = pm.ptr[d]; e < pm.ptr[d + 1]; ++e) {
+      const int j = pm.row[e] * B + inst;
+      fi += pm.w[e] * ((const double*)pm.fh)[j];
+      if (CAP == CAP_QUADRATURE) ci += pm.w[e] * ((const double*)pm.Ch)[j];
+    }
   }
   if (dirichlet[d]) {
     T[i] = T_dir;
@@ -53,16 +60,23 @@ template <int CAP>
 __global__ void k_update_f32(int64_t n, int B, double* __restrict__ Tw, float* __restrict__ Tf,
                              float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
                              const NodalCap nc, const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir,
-                             float dt) {
+                             float dt, const PullMap pm) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int d = B == 1 ? i : i / B;
-  const float fi = f[i];
+  const int d = B == 1 ? i : i / B, inst = i - d * B;
+  float fi = f[i];
   f[i] = 0.f;
   float ci = 0.f;
   if (CAP == CAP_QUADRATURE) {
     ci = Cacc[i];
     Cacc[i] = 0.f;
+  }
+  if (pm.ptr) {  // contributions of hanging nodes whose master d is (P_h^T f_h, pulled)
+    for (int e = pm.ptr[d]; e < pm.ptr[d + 1]; ++e) {
+      const int j = pm.row[e] * B + inst;
+      fi += pm.wf[e] * ((const float*)pm.fh)[j];
+      if (CAP == CAP_QUADRATURE) ci += pm.wf[e] * ((const float*)pm.Ch)[j];
+    }
   }
   if (dirichlet[d]) {
     Tw[i] = tw_dir;
@@ -324,6 +338,22 @@ __global__ void k_hang_values(int n_hang, int B, const int32_t* __restrict__ ptr
   out[i] = s;
 }
 
+// x_h = P_h x and f_h <- 0, C_h <- 0 (before a cell kernel whose hanging contributions the
+// update kernel pulls)
+template <typename R>
+__global__ void k_hang_values_zero(int n_hang, int B, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
+                                   const R* __restrict__ w, const R* __restrict__ x, R* __restrict__ out,
+                                   R* __restrict__ fh, R* __restrict__ Ch) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_hang * B) return;
+  const int r = B == 1 ? i : i / B, b = i - r * B;
+  R s = R(0);
+  for (int e = ptr[r]; e < ptr[r + 1]; ++e) s += w[e] * x[idx[e] * B + b];
+  out[i] = s;
+  fh[i] = R(0);
+  if (Ch) Ch[i] = R(0);
+}
+
 // f += P_h^T f_h, f_h <- 0 (after the cell kernel)
 template <typename R>
 __global__ void k_hang_distribute(int n_hang, int B, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
@@ -574,23 +604,32 @@ Spot spot_at(const LaserK& k, double t) {
 
 cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double* f, double* Cacc,
                               const double* invC0, const NodalCap& nc, const uint8_t* dirichlet, double T_dir,
-                              double dt, cudaStream_t s) {
+                              double dt, cudaStream_t s, const PullMap& pm) {
   const int64_t n = n_dofs * B;
   if (n == 0) return cudaSuccess;
-  if (cap == CAP_QUADRATURE) k_update_f64<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt);
-  else if (cap == CAP_NODAL) k_update_f64<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt);
-  else k_update_f64<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt);
+  if (cap == CAP_QUADRATURE) k_update_f64<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt, pm);
+  else if (cap == CAP_NODAL) k_update_f64<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt, pm);
+  else k_update_f64<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt, pm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float* Tf, float* f, float* Cacc,
                               const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, double tw_dir,
-                              float tf_dir, float dt, cudaStream_t s) {
+                              float tf_dir, float dt, cudaStream_t s, const PullMap& pm) {
   const int64_t n = n_dofs * B;
   if (n == 0) return cudaSuccess;
-  if (cap == CAP_QUADRATURE) k_update_f32<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-  else if (cap == CAP_NODAL) k_update_f32<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-  else k_update_f32<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+  if (cap == CAP_QUADRATURE) k_update_f32<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
+  else if (cap == CAP_NODAL) k_update_f32<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
+  else k_update_f32<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hang_values_zero(bool f32, const DevMesh& M, const void* x, void* out, void* fh, void* Ch,
+                                    cudaStream_t s) {
+  const int64_t n = (int64_t)M.n_hang * M.batch;
+  if (n == 0) return cudaSuccess;
+  if (f32) k_hang_values_zero<float><<<grid_for(n), kBS, 0, s>>>(M.n_hang, M.batch, M.con_ptr, M.con_idx, M.con_wf, (const float*)x, (float*)out, (float*)fh, (float*)Ch);
+  else k_hang_values_zero<double><<<grid_for(n), kBS, 0, s>>>(M.n_hang, M.batch, M.con_ptr, M.con_idx, M.con_w, (const double*)x, (double*)out, (double*)fh, (double*)Ch);
   return cudaGetLastError();
 }
 
@@ -634,11 +673,11 @@ cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMe
     const int64_t n = (int64_t)M.n_cells * B;
     if (n == 0) return cudaSuccess;
     if (degree == 1) {
-      if (f32) k_laser_volume<1, float><<<grid_for(n), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (float*)f);
-      else k_laser_volume<1, double><<<grid_for(n), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (double*)f);
+      if (f32) k_laser_volume<1, float><<<grid_for(n, 128), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (float*)f);
+      else k_laser_volume<1, double><<<grid_for(n, 128), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (double*)f);
     } else {
-      if (f32) k_laser_volume<2, float><<<grid_for(n), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (float*)f);
-      else k_laser_volume<2, double><<<grid_for(n), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (double*)f);
+      if (f32) k_laser_volume<2, float><<<grid_for(n, 128), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (float*)f);
+      else k_laser_volume<2, double><<<grid_for(n, 128), 128, 0, s>>>(M.n_cells, B, ls.cell_lo, M.cell_level, ls.level_h, M, ls.k, power, sp, (double*)f);
     }
     return cudaGetLastError();
   }

@@ -21,12 +21,25 @@ struct NodalCap {
   double lat_ratio = 0.0, Tm = 0.0, inv_sigma = 0.0;  // c_app/c = 1 + lat_ratio exp(-((T-Tm) inv_sigma)^2/2)
   float lat_ratio_f = 0.f, tm_off_f = 0.f, inv_sigma_f = 0.f;  // FP32 form on T - T_ref
 };
+// Transposed constraint map: for dof d the hanging rows r (weight w) that have d as a master;
+// with it the update kernel pulls f_h (and C_h) instead of a separate scatter kernel.
+struct PullMap {
+  const int32_t* ptr = nullptr;  // [n_dofs + 1]; null: nothing to pull
+  const int32_t* row = nullptr;
+  const double* w = nullptr;
+  const float* wf = nullptr;
+  const void* fh = nullptr;      // [n_hang][batch] accumulators of the operator precision
+  const void* Ch = nullptr;
+};
 cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double* f, double* Cacc,
                               const double* invC0, const NodalCap& nc, const uint8_t* dirichlet, double T_dir,
-                              double dt, cudaStream_t s);
+                              double dt, cudaStream_t s, const PullMap& pm);
 cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float* Tf, float* f, float* Cacc,
                               const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, double tw_dir,
-                              float tf_dir, float dt, cudaStream_t s);
+                              float tf_dir, float dt, cudaStream_t s, const PullMap& pm);
+// x_h = P_h x with f_h (and C_h, nullable) cleared, for the pulled form
+cudaError_t launch_hang_values_zero(bool f32, const DevMesh& M, const void* x, void* out, void* fh, void* Ch,
+                                    cudaStream_t s);
 // C_out[d][b] = C0[d] c_app(T[d][b]) / c (nodal lumping) in FP64
 cudaError_t launch_capacity_nodal(int64_t n_dofs, int B, const double* C0, const double* T, const NodalCap& nc,
                                   double* C_out, cudaStream_t s);
