@@ -223,6 +223,22 @@ pbf_status pbf_explicit_step(pbf_ctx* ctx, double* T_dev, const pbf_laser* laser
 pbf_status pbf_estimate_dt(pbf_ctx* ctx, const double* x0_dev, int max_iter, double rtol, double* lambda_out,
                            double* dt_crit_out, int* iters_out, pbf_stream stream);
 
+/* Allocation-free form of pbf_estimate_dt (the paper has no counterpart: it exists for
+ * callers that cannot allocate device memory during the call, e.g. applications that
+ * reserve nearly all device memory for their own pool allocator, or latency-bound loops
+ * where cudaMalloc / cudaFree would stall the device). Same power iteration, with the
+ * vectors passed in: x_dev [n_dofs] holds the start vector on entry and the last iterate on
+ * return; y_dev [n_dofs] is overwritten (last K x). The partial sums of its reductions live
+ * in a fixed static device array of 32,768 + 64 doubles (262,656 bytes) that every GPU
+ * loading the library keeps until the process exits; meshes with more than 134,217,728 dofs
+ * are rejected with PBF_EINVAL. The first call on a device looks up that array's device
+ * address (once per device), so make the first call before any stream capture. All calls
+ * share the array and find the last call's contents in it; calls whose work overlaps on the
+ * GPU race on it. No cudaMalloc, cudaFree or allocating library routine is called.
+ * Synchronises. */
+pbf_status pbf_estimate_dt_noalloc(pbf_ctx* ctx, double* x_dev, double* y_dev, int max_iter, double rtol,
+                                   double* lambda_out, double* dt_crit_out, int* iters_out, pbf_stream stream);
+
 /* Eigenvalue bounds of D^-1 A, A = C/dt + K (consistent capacity, linear material, Dirichlet
  * rows identity), D = diag(A), from the Lanczos tridiagonal of n_iter Jacobi-PCG steps on
  * A x = b, x0 = 0 (b_dev [n_dofs]; NULL: built-in SplitMix64 vector). out = {lmin, lmax}.

@@ -78,6 +78,8 @@ _SIGS = {
     "pbf_explicit_step": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_void_p], C.c_int),
     "pbf_estimate_dt": ([C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double),
                          C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p], C.c_int),
+    "pbf_estimate_dt_noalloc": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p], C.c_int),
     "pbf_cheb_bounds": ([C.c_void_p, C.c_double, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "pbf_implicit_solve": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
@@ -244,6 +246,15 @@ def pbf_estimate_dt(h, x0=None, max_iter=200, rtol=1e-6, stream=None):
     lam, dtc, it = C.c_double(), C.c_double(), C.c_int()
     _check(lib().pbf_estimate_dt(h, _ptr(x0), int(max_iter), float(rtol), C.byref(lam), C.byref(dtc),
                                  C.byref(it), _stream(stream)))
+    return lam.value, dtc.value, it.value
+
+
+def pbf_estimate_dt_noalloc(h, x, y, max_iter=200, rtol=1e-6, stream=None):
+    """Allocation-free power iteration: x (device, start vector in, last iterate out) and y
+    (device work vector) are supplied by the caller."""
+    lam, dtc, it = C.c_double(), C.c_double(), C.c_int()
+    _check(lib().pbf_estimate_dt_noalloc(h, _ptr(x), _ptr(y), int(max_iter), float(rtol), C.byref(lam),
+                                         C.byref(dtc), C.byref(it), _stream(stream)))
     return lam.value, dtc.value, it.value
 
 
