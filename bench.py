@@ -143,6 +143,77 @@ def time_oracle(steps, max_seconds=None):
     return m.n_dofs * done / el, m.n_dofs, done, el
 
 
+def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10):
+    """Configuration 4 forward steps: Q2 brick refined to 7.8 um along the track (278,581 dofs),
+    64 instances with their own segment powers and conductivity scales, one launch per kernel
+    for all instances. The state (143 MB per vector) exceeds the L2."""
+    desc = I.c4_mesh()
+    mat = I.TI64_NONLIN_Q2
+    mesh = pbf.Mesh(desc)
+    n = mesh.info()["n_dofs"]
+    P, s = I.c4_params(batch)
+    ls = I.c4_laser(P, n_seg=16, steps_per_seg=125, dt=2e-8)
+    ctx = pbf.Context(mesh, mat, pbf.PBF_F32OP, batch)
+    pbf.pbf_ctx_set_k_scale(ctx.h, s)
+    tab = mesh.tables()
+    xyz = np.array(desc["origin"]) + np.array(desc["tree_h"]) * tab["dof_coord"] / (2 * 2.0 ** desc["max_level"])
+    T0 = I.melt_pool_field(xyz, (0.05e-3, 0.25e-3, 0.25e-3), 2500.0, 50e-6, seed=5)
+    T = torch.tensor(np.repeat(T0[:, None], batch, axis=1), dtype=torch.float64, device="cuda")
+    dt = 2e-8
+    variant = pbf.pbf_ctx_autotune(ctx.h, T, reps=3, stream=stream)
+    for k in range(3):
+        pbf.pbf_explicit_step(ctx.h, T, ls, k * chunk * dt, dt, chunk, batch=batch, stream=stream)
+    pbf.pbf_ctx_kernel_time(ctx.h)
+    pbf.pbf_ctx_set_timing(ctx.h, True)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pbf.pbf_explicit_step(ctx.h, T, ls, (3 + k) * chunk * dt, dt, chunk, batch=batch, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    pbf.pbf_ctx_set_timing(ctx.h, False)
+    cell_ms, cell_n = pbf.pbf_ctx_kernel_time(ctx.h)
+    rate = n * batch * chunk * K / (ms * 1e-3) / 1e9
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    ctx.close()
+    mesh.close()
+    return {"workload": f"C4: Q2 1.0x0.5x0.25 mm, {n} dofs x {batch} instances (own powers and k scales)",
+            "value": rate, "unit": "GDoF/s", "explicit_steps_per_step": chunk, "steps": K,
+            "cell_kernel_avg_us": 1e3 * cell_ms / max(cell_n, 1), "cell_kernel_shape_index": variant,
+            "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / hbm, "l2": "state > L2; flushed between timed steps"}
+
+
+def bench_adjoint(pbf, I, torch, stream, batch=8, nsteps=200, ckpt=10):
+    """Adjoint sweep of configuration 4 on a reduced window: 8 instances, 200 steps, 10 stored
+    states (binomial schedule), FP32 operator, gradients for 16 segment powers and s."""
+    desc = I.c4_mesh()
+    mat = I.TI64_NONLIN_Q2
+    mesh = pbf.Mesh(desc)
+    n = mesh.info()["n_dofs"]
+    P, s = I.c4_params(batch)
+    dt = 2e-8
+    ls = I.c4_laser(P, n_seg=16, steps_per_seg=-(-nsteps // 16), dt=dt)
+    ctx = pbf.Context(mesh, mat, pbf.PBF_F32OP, batch)
+    pbf.pbf_ctx_set_k_scale(ctx.h, s)
+    tab = mesh.tables()
+    xyz = np.array(desc["origin"]) + np.array(desc["tree_h"]) * tab["dof_coord"] / (2 * 2.0 ** desc["max_level"])
+    T0 = I.melt_pool_field(xyz, (0.05e-3, 0.25e-3, 0.25e-3), 2500.0, 50e-6, seed=5)
+    T = torch.tensor(np.repeat(T0[:, None], batch, axis=1), dtype=torch.float64, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    J, g, fwd = pbf.pbf_adjoint_sweep(ctx.h, T, ls, 0.0, dt, nsteps, ckpt, batch=batch, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    ctx.close()
+    mesh.close()
+    return {"workload": f"C4 mesh ({n} dofs) x {batch} instances, {nsteps} steps, {ckpt} stored states",
+            "seconds": a.elapsed_time(b) * 1e-3, "forward_steps": fwd, "finite": bool(np.isfinite(g).all())}
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -238,6 +309,8 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
+    variant = pbf.pbf_ctx_autotune(ctx.h, T, reps=5, stream=stream)
+
     def bench_step(k):
         pbf.pbf_explicit_step(ctx.h, T, ls, k * CHUNK * dt, dt, CHUNK, stream=stream)
 
@@ -275,7 +348,9 @@ def main():
            "data": "synthetic",
            "config": {"workload": WORKLOAD, "n_dofs": n, "n_cells": info["n_active"], "n_hanging": info["n_hanging"],
                       "explicit_steps_per_step": CHUNK, "dt_s": dt, "l2": "flushed between timed steps (256 MB write)",
-                      "parallelism": f"replicas x{ws} (independent instances)"},
+                      "parallelism": f"replicas x{ws} (independent instances)",
+                      "cell_kernel_shape": ["128 threads", "128 threads, 5 blocks/SM", "128 threads, 6 blocks/SM",
+                                            "64 threads, 10 blocks/SM"][variant]},
            "gpu_launches": gpu_launches}
     # roofline of the dominant kernel (cell operator), timed live with events on its stream
     avg_cell_s = cell_ms * 1e-3 / max(cell_launches, 1)
@@ -339,6 +414,8 @@ def main():
             e_ms += a.elapsed_time(b)
         out["e2e"] = {"value": n * CHUNK * K * ws / (e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
                       "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
+        out["batched"] = bench_batched(pbf, I, torch, stream, flush, peaks, K)
+        out["adjoint"] = bench_adjoint(pbf, I, torch, stream)
         if rank == 0 and ws >= 1:
             rate, n_s, done, secs = time_oracle(3, max_seconds=25.0)
             out["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

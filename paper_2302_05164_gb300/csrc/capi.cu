@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <memory>
 #include <string>
@@ -320,6 +321,37 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
       }
   }
   std::vector<float> mwf(mw.begin(), mw.end());
+  // cell patches for the patch-staged kernel (one instance): sorted unique node slots per
+  // group of kPatch consecutive cells, and each cell node's index in its group's list
+  std::vector<int32_t> pptr(1, 0), pslot;
+  std::vector<uint16_t> ploc;
+  int max_nu = 0;
+  if (batch == 1 && nc > 0) {
+    ploc.resize(nc * npc);
+    std::vector<int32_t> keys;
+    for (size_t c0 = 0; c0 < nc; c0 += kPatch) {
+      const size_t c1 = std::min(nc, c0 + (size_t)kPatch);
+      keys.clear();
+      for (size_t c = c0; c < c1; ++c)
+        for (size_t a = 0; a < npc; ++a) {
+          const int32_t d = m.cell_dofs[c * npc + a];
+          keys.push_back(d >= 0 ? d : (int32_t)m.n_dofs + (-1 - d));
+        }
+      std::sort(keys.begin(), keys.end());
+      keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+      for (size_t c = c0; c < c1; ++c)
+        for (size_t a = 0; a < npc; ++a) {
+          const int32_t d = m.cell_dofs[c * npc + a];
+          const int32_t key = d >= 0 ? d : (int32_t)m.n_dofs + (-1 - d);
+          ploc[a * nc + c] = (uint16_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
+        }
+      pslot.insert(pslot.end(), keys.begin(), keys.end());
+      pptr.push_back((int32_t)pslot.size());
+      max_nu = std::max(max_nu, (int)keys.size());
+    }
+  }
+  int32_t *d_pptr = nullptr, *d_pslot = nullptr;
+  uint16_t* d_ploc = nullptr;
   int32_t *d_mptr = nullptr, *d_mrow = nullptr;
   double* d_mw = nullptr;
   float* d_mwf = nullptr;
@@ -356,6 +388,9 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   UP(c->level_h, level_h);
   UP(c->cell_top, ctop);
   UP(c->cell_lof, lof);
+  UP(d_pptr, pptr);
+  UP(d_pslot, pslot);
+  UP(d_ploc, ploc);
   UP(d_mptr, mptr);
   UP(d_mrow, mrow);
   UP(d_mw, mw);
@@ -425,6 +460,12 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   M.cell_top = c->cell_top;
   M.cell_lo = c->cell_lo;
   M.cell_lof = c->cell_lof;
+  if (batch == 1 && nc > 0) {
+    M.patch_ptr = d_pptr;
+    M.patch_slot = d_pslot;
+    M.patch_loc = d_ploc;
+    M.patch_smem = max_nu * 2 * (int)sizeof(float);
+  }
   L.degree = c->degree;
   L.f32 = c->f32;
   L.nonlin_k = c->nonlin;
@@ -773,6 +814,10 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
   CellLaunch L = ctx->base;
   cudaError_t e = launch_prepare_f32(nv, T_dev, ctx->mat.T_ref, nullptr, ctx->Tf, s);
   L.xf = ctx->Tf;
+  // the timed launches below call the cell kernel directly: it gathers hanging-node values
+  // from L.xfh, which must hold P_h Tf
+  if (e == cudaSuccess) e = launch_hang_values(true, L.mesh, ctx->Tf, ctx->xh, s);
+  L.xfh = (const float*)ctx->xh;
   cudaEvent_t a = nullptr, b = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -780,7 +825,8 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
   float best_ms = 0.f;
   for (int v = 0; v < kCellVariants && e == cudaSuccess; ++v) {
     L.variant = v;
-    e = ctx->apply_cell(L, ctx->f, ctx->latent ? ctx->Cacc : nullptr, MODE_RESIDUAL, s);  // warm-up
+    e = launch_cell(L, ctx->f, ctx->fh, ctx->latent ? ctx->Cacc : nullptr, ctx->latent ? ctx->Ch : nullptr,
+                    MODE_RESIDUAL, s);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(a, s);
     for (int r = 0; r < reps && e == cudaSuccess; ++r)
       e = launch_cell(L, ctx->f, ctx->fh, ctx->latent ? ctx->Cacc : nullptr, ctx->latent ? ctx->Ch : nullptr,

@@ -91,6 +91,11 @@ struct DevMesh {
   const float* con_wf = nullptr;
   const uint8_t* dirichlet = nullptr;
   const uint8_t* cell_top = nullptr;  // 1 when the cell has an active top face
+  // cell patches (batch 1): kPatch consecutive cells share one list of unique node slots
+  const int32_t* patch_ptr = nullptr;   // [n_patches + 1] into patch_slot
+  const int32_t* patch_slot = nullptr;  // node slots: dof d, or n_dofs + r for hanging row r
+  const uint16_t* patch_loc = nullptr;  // [npc][n_cells] index of each cell node in its patch list
+  int patch_smem = 0;                   // bytes of dynamic shared memory for the largest patch
   const double* cell_lo = nullptr;    // [n_cells][3] lower corner
   const float* cell_lof = nullptr;    // the same in FP32
 };
@@ -177,7 +182,8 @@ struct CellLaunch {
 
 // Launch shapes the autotuner chooses from for the FP32 residual cell kernel:
 // {threads per block, minimum resident blocks per SM} (the second bounds registers per thread)
-constexpr int kCellVariants = 4;
+constexpr int kCellVariants = 5;  // variant 4: patch-staged kernel (batch 1)
+constexpr int kPatch = 128;       // cells per patch (one thread block)
 
 template <typename R>
 __host__ __device__ inline const GeoR<R>& geo_of(const CellLaunch& L);

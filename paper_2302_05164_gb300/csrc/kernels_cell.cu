@@ -324,6 +324,77 @@ __global__ void __launch_bounds__(64) k_diag(const CellLaunch L, double* __restr
 //                 - int rho c_app'(T_h) mu_h N_j ]
 // i.e. the transpose of the linearised operator of Eq. matrix_free_eval (the D_e and L_e
 // parts) plus, for the quadrature-point capacity, the transposed capacity derivative.
+// Patch-staged residual for one instance (FP32 operator): the kPatch consecutive cells of a
+// block share one sorted list of unique node slots. The block loads their values once,
+// coalesced, into shared memory; every thread gathers its cell from there, accumulates with
+// shared-memory atomics, and the block adds each slot's sum to global memory once.
+template <int P, bool NLK>
+__global__ void __launch_bounds__(kPatch) k_cell_patch(const CellLaunch L, float* __restrict__ f,
+                                                       float* __restrict__ fh) {
+  constexpr int N = P + 1, NP = N * N * N;
+  (void)N;
+  extern __shared__ float smem[];
+  const DevMesh& M = L.mesh;
+  const MatR<float>& mt = L.mf;
+  const GeoR<float>& geo = L.gf;
+  const int p0 = M.patch_ptr[blockIdx.x], nu = M.patch_ptr[blockIdx.x + 1] - p0;
+  float* sv = smem;
+  float* sf = smem + nu;
+  const int nd = M.n_dofs;
+  for (int j = threadIdx.x; j < nu; j += kPatch) {
+    const int g = __ldg(&M.patch_slot[p0 + j]);
+    sv[j] = g < nd ? __ldg(&L.xf[g]) : __ldg(&L.xfh[g - nd]);
+    sf[j] = 0.f;
+  }
+  __syncthreads();
+  const int cell = blockIdx.x * kPatch + threadIdx.x;
+  if (cell < M.n_cells) {
+    int loc[NP];
+    float u[NP], v[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) loc[a] = __ldg(&M.patch_loc[a * M.n_cells + cell]);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) u[a] = sv[loc[a]];
+    values_at_qp<P, float>(u, v);
+    const int lev = M.cell_level[cell];
+    const float detJ = geo.detJ[lev];
+    const int mat = M.cell_mat[cell];
+    const float scale = (mat == 1 ? mt.powder_scale : 1.f) * (L.k_scale_f ? L.k_scale_f[0] : 1.f);
+    float kw[NP];
+    const float k0 = mt.k0 * scale, dk = mt.dk * scale;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      float k = k0;
+      if (NLK) k = k0 + dk * clamp01((v[q] + mt.tk_off) * mt.inv_dT);
+      kw[q] = -k * (float(wq3<P>(q)) * detJ);
+    }
+    float r[NP], g[NP];
+#define PATCH_DIR(DIR, ADD)                                   \
+  {                                                           \
+    const float cd = geo.ih2[lev][DIR];                       \
+    apply1d<P, 1, DIR, false, false>(v, g);                   \
+    _Pragma("unroll") for (int q = 0; q < NP; ++q) g[q] *= kw[q] * cd; \
+    apply1d<P, 1, DIR, true, ADD>(g, r);                      \
+  }
+    PATCH_DIR(0, false)
+    PATCH_DIR(1, true)
+    PATCH_DIR(2, true)
+#undef PATCH_DIR
+    float fe[NP];
+    integrate_values<P, float>(r, fe);
+    if (L.las.on && M.cell_top[cell]) add_laser<P, float>(L, cell, 0, lev, fe);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) atomicAdd(&sf[loc[a]], fe[a]);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < nu; j += kPatch) {
+    const float val = sf[j];
+    if (val == 0.f) continue;
+    const int g = __ldg(&M.patch_slot[p0 + j]);
+    atomicAdd(g < nd ? &f[g] : &fh[g - nd], val);
+  }
+}
+
 template <int P, typename R, bool NLK, bool QPC>
 __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restrict__ g, R* __restrict__ gh) {
   constexpr int NP = (P + 1) * (P + 1) * (P + 1);
@@ -430,6 +501,12 @@ cudaError_t go_shape(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, 
 template <int P, typename R, int MODE, bool NLK, bool LAT>
 cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
   if (std::is_same<R, float>::value && MODE == MODE_RESIDUAL && !LAT) {
+    if (L.variant == 4 && L.mesh.batch == 1 && L.mesh.patch_ptr) {
+      const int np = (L.mesh.n_cells + kPatch - 1) / kPatch;
+      if (np == 0) return cudaSuccess;
+      k_cell_patch<P, NLK><<<np, kPatch, L.mesh.patch_smem, s>>>(L, (float*)f, (float*)fh);
+      return cudaGetLastError();
+    }
     switch (L.variant) {
       case 1: return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
       case 2: return go_shape<P, R, MODE, NLK, LAT, 128, 6>(L, f, fh, C, Ch, s);
@@ -463,6 +540,10 @@ cudaError_t dispatch(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, 
 }  // namespace
 
 cudaError_t launch_cell(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, int mode, cudaStream_t s) {
+  // a mesh with hanging nodes needs their values and accumulators: refuse instead of faulting
+  if (L.mesh.n_hang > 0 && ((L.f32 ? (const void*)L.xfh : (const void*)L.xh) == nullptr || fh == nullptr ||
+                            (C != nullptr && Ch == nullptr)))
+    return cudaErrorInvalidValue;
   if (L.degree == 1)
     return L.f32 ? dispatch<1, float>(L, f, fh, C, Ch, mode, s) : dispatch<1, double>(L, f, fh, C, Ch, mode, s);
   if (L.degree == 2)
@@ -471,6 +552,9 @@ cudaError_t launch_cell(const CellLaunch& L, void* f, void* fh, void* C, void* C
 }
 
 cudaError_t launch_adjoint(const CellLaunch& L, bool qp_capacity, void* g, void* gh, cudaStream_t s) {
+  if (L.mesh.n_hang > 0 && (L.f32 ? (!L.xfh || !L.vfh || (qp_capacity && !L.mufh))
+                                  : (!L.xh || !L.vh || (qp_capacity && !L.muh)) || !gh))
+    return cudaErrorInvalidValue;
   if (L.degree == 1)
     return L.f32 ? dispatch_adj<1, float>(L, qp_capacity, g, gh, s) : dispatch_adj<1, double>(L, qp_capacity, g, gh, s);
   if (L.degree == 2)
