@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 METRIC = "explicit-step DoF-updates/s (GDoF/s) and % HBM roofline, FP32-op vs FP64 at stated error"
 WORKLOAD = "C2: Q2 AMR 2x2x1 mm, 5 um cells in a 150 um ball, 1.07M dofs, nonlinear k(T) + latent heat"
 CHUNK = 50                 # explicit steps per benchmark step
+SHAPES = ["128 threads", "128 threads, 5 blocks/SM", "128 threads, 6 blocks/SM", "64 threads, 10 blocks/SM",
+          "patch-staged, 128 cells per block"]
 BYTES_PER_DOF_UPDATE = 16  # read T_n and write T_{n+1} in FP64 (c_app(T) recomputed in-kernel)
 
 
@@ -309,7 +311,7 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    variant = pbf.pbf_ctx_autotune(ctx.h, T, reps=5, stream=stream)
+    variant, shape_us = pbf.pbf_ctx_autotune(ctx.h, T, reps=5, stream=stream, times=True)
 
     def bench_step(k):
         pbf.pbf_explicit_step(ctx.h, T, ls, k * CHUNK * dt, dt, CHUNK, stream=stream)
@@ -349,8 +351,8 @@ def main():
            "config": {"workload": WORKLOAD, "n_dofs": n, "n_cells": info["n_active"], "n_hanging": info["n_hanging"],
                       "explicit_steps_per_step": CHUNK, "dt_s": dt, "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": f"replicas x{ws} (independent instances)",
-                      "cell_kernel_shape": ["128 threads", "128 threads, 5 blocks/SM", "128 threads, 6 blocks/SM",
-                                            "64 threads, 10 blocks/SM"][variant]},
+                      "cell_kernel_shape": SHAPES[variant],
+                      "autotune_us_per_launch": dict(zip(SHAPES, [round(u, 2) for u in shape_us]))},
            "gpu_launches": gpu_launches}
     # roofline of the dominant kernel (cell operator), timed live with events on its stream
     avg_cell_s = cell_ms * 1e-3 / max(cell_launches, 1)

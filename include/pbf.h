@@ -272,11 +272,16 @@ pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, const pbf_laser
  * for nsteps steps and n_snaps stored states; host only. */
 pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_out);
 
-/* Autotuner of the launch shape of the FP32-operator cell kernel (threads per block and the
- * register bound that sets resident blocks per SM): times every shape on `reps` residual
- * evaluations at the state T_dev (not modified), keeps the fastest in the context and
- * returns its index (0 = default). FP64 contexts keep the default. Synchronises. */
-pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, pbf_stream stream);
+/* Autotuner of the FP32-operator cell kernel: times its launch shapes (0: 128 threads, 1: 128
+ * threads with 5 resident blocks per SM, 2: 6 blocks, 3: 64 threads with 10 blocks, 4: the
+ * patch-staged kernel, batch 1 only) on `reps` residual evaluations at the state T_dev (not
+ * modified), keeps the fastest in the context and returns its index; us_per_launch_out
+ * (nullable, 5 entries) receives each shape's time. FP64 contexts keep shape 0. Synchronises. */
+pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, float* us_per_launch_out,
+                            pbf_stream stream);
+
+/* Selects a launch shape of the FP32 cell kernel directly (0..4, see pbf_ctx_autotune). */
+pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape);
 
 /* Kernel timing of the dominant (cell operator) kernel: when enabled, CUDA events bracket
  * every cell-operator launch on its stream; pbf_ctx_kernel_time returns the summed elapsed

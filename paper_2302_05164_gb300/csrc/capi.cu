@@ -464,7 +464,7 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     M.patch_ptr = d_pptr;
     M.patch_slot = d_pslot;
     M.patch_loc = d_ploc;
-    M.patch_smem = max_nu * 2 * (int)sizeof(float);
+    M.patch_smem = max_nu * 2 * (int)sizeof(float) + (int)(npc * kPatch * sizeof(uint16_t));
   }
   L.degree = c->degree;
   L.f32 = c->f32;
@@ -689,6 +689,9 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
   PullMap pm = pull;
   pm.fh = fh;
   pm.Ch = latent ? Ch : nullptr;
+  // the patch-staged kernel resolves hanging nodes itself: no hanging pre-pass, nothing to pull
+  const bool patch = f32 && base.variant == 4 && batch == 1 && !latent && base.mesh.patch_ptr != nullptr;
+  if (patch) pm.ptr = nullptr;
   const double tw_dir = mat.T_dirichlet - mat.T_ref;
   const float tf_dir = (float)tw_dir;
   if (f32) {
@@ -717,8 +720,11 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
       L.las.power = power;
       L.las.powerf = powerf;
     }
-    e = launch_hang_values_zero(f32, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev, xh, fh, latent ? Ch : nullptr, s);
-    ++launches;
+    if (!patch) {
+      e = launch_hang_values_zero(f32, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev, xh, fh, latent ? Ch : nullptr,
+                                  s);
+      ++launches;
+    }
     std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
     if (timing && e == cudaSuccess) {
       if (free_events.empty()) {
@@ -800,7 +806,7 @@ extern "C" pbf_status pbf_widen_to_f64(const float* x_dev, double* y_dev, int64_
 }
 
 extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out,
-                                       pbf_stream stream) {
+                                       float* us_per_launch_out, pbf_stream stream) {
   if (!ctx || !T_dev || reps < 1) return fail(PBF_EINVAL, "bad arguments");
   pbf_status st = ctx->check_usable();
   if (st) return st;
@@ -835,6 +841,7 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && us_per_launch_out) us_per_launch_out[v] = 1000.f * ms / (float)reps;
     if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
       best = v;
       best_ms = ms;
@@ -853,6 +860,12 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
   if (e != cudaSuccess) return ctx->cuda(e, "autotune");
   ctx->base.variant = best;
   if (variant_out) *variant_out = best;
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape) {
+  if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, 4]");
+  ctx->base.variant = shape;
   return PBF_OK;
 }
 

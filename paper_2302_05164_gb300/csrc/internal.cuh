@@ -95,7 +95,7 @@ struct DevMesh {
   const int32_t* patch_ptr = nullptr;   // [n_patches + 1] into patch_slot
   const int32_t* patch_slot = nullptr;  // node slots: dof d, or n_dofs + r for hanging row r
   const uint16_t* patch_loc = nullptr;  // [npc][n_cells] index of each cell node in its patch list
-  int patch_smem = 0;                   // bytes of dynamic shared memory for the largest patch
+  int patch_smem = 0;                   // dynamic shared memory: 2 floats per slot + the loc table
   const double* cell_lo = nullptr;    // [n_cells][3] lower corner
   const float* cell_lof = nullptr;    // the same in FP32
 };

@@ -324,13 +324,14 @@ __global__ void __launch_bounds__(64) k_diag(const CellLaunch L, double* __restr
 //                 - int rho c_app'(T_h) mu_h N_j ]
 // i.e. the transpose of the linearised operator of Eq. matrix_free_eval (the D_e and L_e
 // parts) plus, for the quadrature-point capacity, the transposed capacity derivative.
-// Patch-staged residual for one instance (FP32 operator): the kPatch consecutive cells of a
-// block share one sorted list of unique node slots. The block loads their values once,
-// coalesced, into shared memory; every thread gathers its cell from there, accumulates with
-// shared-memory atomics, and the block adds each slot's sum to global memory once.
+// Patch-staged residual for one instance (FP32 operator): the kPatch consecutive (Z-order)
+// cells of a block share one sorted list of unique node slots. The block stages, coalesced,
+// the slot values into shared memory, resolving hanging-node slots from their masters on the
+// fly (P G_e T), and its cells' local slot indices; every thread gathers its cell from shared
+// memory, accumulates with shared-memory atomics, and the block adds each slot's sum to
+// global memory once, pushing hanging-slot sums to their masters (G_e^T P^T).
 template <int P, bool NLK>
-__global__ void __launch_bounds__(kPatch) k_cell_patch(const CellLaunch L, float* __restrict__ f,
-                                                       float* __restrict__ fh) {
+__global__ void __launch_bounds__(kPatch) k_cell_patch(const CellLaunch L, float* __restrict__ f) {
   constexpr int N = P + 1, NP = N * N * N;
   (void)N;
   extern __shared__ float smem[];
@@ -338,23 +339,35 @@ __global__ void __launch_bounds__(kPatch) k_cell_patch(const CellLaunch L, float
   const MatR<float>& mt = L.mf;
   const GeoR<float>& geo = L.gf;
   const int p0 = M.patch_ptr[blockIdx.x], nu = M.patch_ptr[blockIdx.x + 1] - p0;
+  const int c0 = blockIdx.x * kPatch, ncell = min(kPatch, M.n_cells - c0);
   float* sv = smem;
   float* sf = smem + nu;
+  uint16_t* sloc = reinterpret_cast<uint16_t*>(smem + 2 * nu);  // [NP][kPatch]
   const int nd = M.n_dofs;
   for (int j = threadIdx.x; j < nu; j += kPatch) {
     const int g = __ldg(&M.patch_slot[p0 + j]);
-    sv[j] = g < nd ? __ldg(&L.xf[g]) : __ldg(&L.xfh[g - nd]);
+    float val;
+    if (g < nd) {
+      val = __ldg(&L.xf[g]);
+    } else {
+      const int r = g - nd;
+      val = 0.f;
+      for (int e = __ldg(&M.con_ptr[r]); e < __ldg(&M.con_ptr[r + 1]); ++e)
+        val += __ldg(&M.con_wf[e]) * __ldg(&L.xf[__ldg(&M.con_idx[e])]);
+    }
+    sv[j] = val;
     sf[j] = 0.f;
   }
+  for (int k = threadIdx.x; k < NP * ncell; k += kPatch) {
+    const int a = k / ncell, t = k - a * ncell;
+    sloc[a * kPatch + t] = __ldg(&M.patch_loc[a * M.n_cells + c0 + t]);
+  }
   __syncthreads();
-  const int cell = blockIdx.x * kPatch + threadIdx.x;
-  if (cell < M.n_cells) {
-    int loc[NP];
+  const int cell = c0 + threadIdx.x;
+  if (threadIdx.x < ncell) {
     float u[NP], v[NP];
 #pragma unroll
-    for (int a = 0; a < NP; ++a) loc[a] = __ldg(&M.patch_loc[a * M.n_cells + cell]);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) u[a] = sv[loc[a]];
+    for (int a = 0; a < NP; ++a) u[a] = sv[sloc[a * kPatch + threadIdx.x]];
     values_at_qp<P, float>(u, v);
     const int lev = M.cell_level[cell];
     const float detJ = geo.detJ[lev];
@@ -369,12 +382,12 @@ __global__ void __launch_bounds__(kPatch) k_cell_patch(const CellLaunch L, float
       kw[q] = -k * (float(wq3<P>(q)) * detJ);
     }
     float r[NP], g[NP];
-#define PATCH_DIR(DIR, ADD)                                   \
-  {                                                           \
-    const float cd = geo.ih2[lev][DIR];                       \
-    apply1d<P, 1, DIR, false, false>(v, g);                   \
+#define PATCH_DIR(DIR, ADD)                                            \
+  {                                                                    \
+    const float cd = geo.ih2[lev][DIR];                                \
+    apply1d<P, 1, DIR, false, false>(v, g);                            \
     _Pragma("unroll") for (int q = 0; q < NP; ++q) g[q] *= kw[q] * cd; \
-    apply1d<P, 1, DIR, true, ADD>(g, r);                      \
+    apply1d<P, 1, DIR, true, ADD>(g, r);                               \
   }
     PATCH_DIR(0, false)
     PATCH_DIR(1, true)
@@ -384,14 +397,20 @@ __global__ void __launch_bounds__(kPatch) k_cell_patch(const CellLaunch L, float
     integrate_values<P, float>(r, fe);
     if (L.las.on && M.cell_top[cell]) add_laser<P, float>(L, cell, 0, lev, fe);
 #pragma unroll
-    for (int a = 0; a < NP; ++a) atomicAdd(&sf[loc[a]], fe[a]);
+    for (int a = 0; a < NP; ++a) atomicAdd(&sf[sloc[a * kPatch + threadIdx.x]], fe[a]);
   }
   __syncthreads();
   for (int j = threadIdx.x; j < nu; j += kPatch) {
     const float val = sf[j];
     if (val == 0.f) continue;
     const int g = __ldg(&M.patch_slot[p0 + j]);
-    atomicAdd(g < nd ? &f[g] : &fh[g - nd], val);
+    if (g < nd) {
+      atomicAdd(&f[g], val);
+    } else {
+      const int r = g - nd;
+      for (int e = __ldg(&M.con_ptr[r]); e < __ldg(&M.con_ptr[r + 1]); ++e)
+        atomicAdd(&f[__ldg(&M.con_idx[e])], __ldg(&M.con_wf[e]) * val);
+    }
   }
 }
 
@@ -504,7 +523,7 @@ cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaSt
     if (L.variant == 4 && L.mesh.batch == 1 && L.mesh.patch_ptr) {
       const int np = (L.mesh.n_cells + kPatch - 1) / kPatch;
       if (np == 0) return cudaSuccess;
-      k_cell_patch<P, NLK><<<np, kPatch, L.mesh.patch_smem, s>>>(L, (float*)f, (float*)fh);
+      k_cell_patch<P, NLK><<<np, kPatch, L.mesh.patch_smem, s>>>(L, (float*)f);
       return cudaGetLastError();
     }
     switch (L.variant) {
@@ -540,9 +559,12 @@ cudaError_t dispatch(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, 
 }  // namespace
 
 cudaError_t launch_cell(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, int mode, cudaStream_t s) {
-  // a mesh with hanging nodes needs their values and accumulators: refuse instead of faulting
-  if (L.mesh.n_hang > 0 && ((L.f32 ? (const void*)L.xfh : (const void*)L.xh) == nullptr || fh == nullptr ||
-                            (C != nullptr && Ch == nullptr)))
+  // a mesh with hanging nodes needs their values and accumulators (except the patch-staged
+  // kernel, which resolves them itself): refuse instead of faulting
+  const bool self_contained = L.variant == 4 && L.f32 && mode == MODE_RESIDUAL && C == nullptr &&
+                              L.mesh.batch == 1 && L.mesh.patch_ptr != nullptr;
+  if (!self_contained && L.mesh.n_hang > 0 &&
+      ((L.f32 ? (const void*)L.xfh : (const void*)L.xh) == nullptr || fh == nullptr || (C != nullptr && Ch == nullptr)))
     return cudaErrorInvalidValue;
   if (L.degree == 1)
     return L.f32 ? dispatch<1, float>(L, f, fh, C, Ch, mode, s) : dispatch<1, double>(L, f, fh, C, Ch, mode, s);

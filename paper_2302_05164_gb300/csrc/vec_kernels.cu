@@ -106,6 +106,72 @@ __global__ void k_capacity_nodal(int64_t n, int B, const double* __restrict__ C0
   out[i] = C0[i / B] * (1.0 + nc.lat_ratio * exp(-0.5 * z * z));
 }
 
+// The same FP32-form update for one instance without hanging contributions to pull, four
+// dofs per thread with 16-byte loads and stores (arrays from cudaMalloc are 256-byte aligned).
+template <int CAP>
+__device__ __forceinline__ void update_one(float fi, float ci, float ic, bool fixed, double& tw, float& tf,
+                                           const NodalCap& nc, double tw_dir, float tf_dir, float dt) {
+  if (fixed) {
+    tw = tw_dir;
+    tf = tf_dir;
+    return;
+  }
+  float inc;
+  if (CAP == CAP_QUADRATURE) {
+    inc = dt * fi / ci;
+  } else if (CAP == CAP_NODAL) {
+    const float z = (d2f_rn(tw) + nc.tm_off_f) * nc.inv_sigma_f;
+    inc = dt * fi * ic / (1.f + nc.lat_ratio_f * __expf(-0.5f * z * z));
+  } else {
+    inc = dt * fi * ic;
+  }
+  tw = tw + f2d(inc);
+  tf = d2f_rn(tw);
+}
+
+template <int CAP>
+__global__ void k_update_f32_x4(int n, double* __restrict__ Tw, float* __restrict__ Tf, float* __restrict__ f,
+                                float* __restrict__ Cacc, const float* __restrict__ invC0, const NodalCap nc,
+                                const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir, float dt) {
+  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 >= n) return;
+  if (i0 + 3 < n) {
+    const float4 f4 = *reinterpret_cast<const float4*>(f + i0);
+    *reinterpret_cast<float4*>(f + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (CAP == CAP_QUADRATURE) {
+      c4 = *reinterpret_cast<const float4*>(Cacc + i0);
+      *reinterpret_cast<float4*>(Cacc + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float4 ic4 = *reinterpret_cast<const float4*>(invC0 + i0);
+    const uchar4 d4 = *reinterpret_cast<const uchar4*>(dirichlet + i0);
+    double2 a = *reinterpret_cast<const double2*>(Tw + i0), b = *reinterpret_cast<const double2*>(Tw + i0 + 2);
+    float4 t4;
+    update_one<CAP>(f4.x, c4.x, ic4.x, d4.x, a.x, t4.x, nc, tw_dir, tf_dir, dt);
+    update_one<CAP>(f4.y, c4.y, ic4.y, d4.y, a.y, t4.y, nc, tw_dir, tf_dir, dt);
+    update_one<CAP>(f4.z, c4.z, ic4.z, d4.z, b.x, t4.z, nc, tw_dir, tf_dir, dt);
+    update_one<CAP>(f4.w, c4.w, ic4.w, d4.w, b.y, t4.w, nc, tw_dir, tf_dir, dt);
+    *reinterpret_cast<double2*>(Tw + i0) = a;
+    *reinterpret_cast<double2*>(Tw + i0 + 2) = b;
+    *reinterpret_cast<float4*>(Tf + i0) = t4;
+    return;
+  }
+  for (int i = i0; i < n; ++i) {  // ragged tail
+    const float fi = f[i];
+    f[i] = 0.f;
+    float ci = 0.f;
+    if (CAP == CAP_QUADRATURE) {
+      ci = Cacc[i];
+      Cacc[i] = 0.f;
+    }
+    double tw = Tw[i];
+    float tf;
+    update_one<CAP>(fi, ci, invC0[i], dirichlet[i] != 0, tw, tf, nc, tw_dir, tf_dir, dt);
+    Tw[i] = tw;
+    Tf[i] = tf;
+  }
+}
+
 // Tw = T - off (FP64), Tf = round_to_f32(Tw); Tw may be null
 __global__ void k_prepare_f32(int64_t n, const double* __restrict__ T, double off, double* __restrict__ Tw,
                               float* __restrict__ Tf) {
@@ -618,6 +684,13 @@ cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float*
                               float tf_dir, float dt, cudaStream_t s, const PullMap& pm) {
   const int64_t n = n_dofs * B;
   if (n == 0) return cudaSuccess;
+  if (B == 1 && pm.ptr == nullptr) {
+    const int64_t nt = (n + 3) / 4;
+    if (cap == CAP_QUADRATURE) k_update_f32_x4<CAP_QUADRATURE><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+    else if (cap == CAP_NODAL) k_update_f32_x4<CAP_NODAL><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+    else k_update_f32_x4<CAP_CONST><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+    return cudaGetLastError();
+  }
   if (cap == CAP_QUADRATURE) k_update_f32<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
   else if (cap == CAP_NODAL) k_update_f32<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
   else k_update_f32<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);

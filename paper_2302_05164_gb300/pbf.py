@@ -89,7 +89,8 @@ _SIGS = {
     "pbf_revolve_cost": ([C.c_int, C.c_int, C.POINTER(C.c_longlong)], C.c_int),
     "pbf_round_to_f32": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "pbf_widen_to_f64": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
-    "pbf_ctx_autotune": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p], C.c_int),
+    "pbf_ctx_autotune": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_ctx_set_kernel_shape": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_set_timing": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_kernel_time": ([C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
     "pbf_ctx_launch_count": ([C.c_void_p, C.POINTER(C.c_longlong)], C.c_int),
@@ -298,10 +299,17 @@ def pbf_widen_to_f64(x, y, n, stream=None):
     _check(lib().pbf_widen_to_f64(_ptr(x), _ptr(y), int(n), _stream(stream)))
 
 
-def pbf_ctx_autotune(h, T, reps=5, stream=None):
+def pbf_ctx_autotune(h, T, reps=5, stream=None, times=False):
+    """Picks the fastest launch shape of the FP32 cell kernel; returns its index (and the
+    per-shape microseconds per launch when times=True)."""
     v = C.c_int()
-    _check(lib().pbf_ctx_autotune(h, _ptr(T), int(reps), C.byref(v), _stream(stream)))
-    return v.value
+    us = np.zeros(5, np.float32)
+    _check(lib().pbf_ctx_autotune(h, _ptr(T), int(reps), C.byref(v), _ptr(us), _stream(stream)))
+    return (v.value, us.tolist()) if times else v.value
+
+
+def pbf_ctx_set_kernel_shape(h, shape):
+    _check(lib().pbf_ctx_set_kernel_shape(h, int(shape)))
 
 
 def pbf_ctx_set_timing(h, enable):

@@ -134,6 +134,32 @@ def test_amr_q2_nonlinear_latent_steps(P, oracle_mod, prec):
     assert rel(got, ref) < (TOL64 if prec == "f64" else TOL32_T)
 
 
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4])
+def test_every_kernel_shape_matches_oracle(P, oracle_mod, shape):
+    """Each launch shape the autotuner can pick (incl. the patch-staged kernel, which resolves
+    hanging nodes while staging) gives the oracle's explicit steps on an AMR Q2 mesh."""
+    desc = amr_q2()
+    om = oracle_mod.Mesh(desc)
+    mat = I.TI64_NONLIN_Q2
+    lam, _ = om.lambda_max(dict(mat, k0=28.0), I.start_vector(om.n_dofs), max_iter=300, rtol=1e-8)
+    dt = 0.5 * 2.0 / lam
+    T0 = I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 2600.0, 60e-6, seed=4, noise=0.01)
+    ls = laser_over(desc, power=300.0)
+    ref = om.explicit(mat, T0, ls, 1e-4, dt, 10)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F32OP)
+    P.pbf_ctx_set_kernel_shape(ctx.h, shape)
+    Td = to_dev(T0)
+    P.pbf_explicit_step(ctx.h, Td, ls, 1e-4, dt, 10)
+    torch.cuda.synchronize()
+    assert rel(Td.cpu().numpy(), ref) < TOL32_T
+    # a residual evaluation after the steps finds every accumulator cleared
+    fd, fv, Cm = om.residual(mat, Td.cpu().numpy(), ls, 1e-4)
+    out = [torch.zeros(om.n_dofs, dtype=torch.float64, device="cuda") for _ in range(3)]
+    P.pbf_eval_residual(ctx.h, Td, ls, 1e-4, *out)
+    assert rel(out[0].cpu().numpy(), fd) < TOL32_F and rel(out[1].cpu().numpy(), fv) < TOL32_F
+
+
 def test_batched_instances_match_independent_runs(P, oracle_mod):
     """Instances of a batch (layout [n_dofs][batch]) carry their own laser powers and
     conductivity scales; each equals an independent oracle run. Batch 3 is ragged."""
