@@ -35,8 +35,10 @@ sys.path.insert(0, ROOT)
 METRIC = "explicit-step DoF-updates/s (GDoF/s) and % HBM roofline, FP32-op vs FP64 at stated error"
 WORKLOAD = "C2: Q2 AMR 2x2x1 mm, 5 um cells in a 150 um ball, 1.07M dofs, nonlinear k(T) + latent heat"
 CHUNK = 50                 # explicit steps per benchmark step
-SHAPES = ["128 threads", "128 threads, 5 blocks/SM", "128 threads, 6 blocks/SM", "64 threads, 10 blocks/SM",
-          "patch-staged, 128 cells per block"]
+SHAPES = ["per-cell kernel, 128 threads", "per-cell kernel, 128 threads, 5 blocks/SM",
+          "per-cell kernel, 128 threads, 6 blocks/SM", "per-cell kernel, 64 threads, 10 blocks/SM",
+          "fused step, 64-cell patches", "fused step, 64-cell patches, programmatic dependent launch"]
+KERNELS = ["k_cell<2,float,RESIDUAL,nonlinear>"] * 4 + ["k_step<2,nonlinear,nodal> (fused step)"] * 2
 BYTES_PER_DOF_UPDATE = 16  # read T_n and write T_{n+1} in FP64 (c_app(T) recomputed in-kernel)
 
 
@@ -185,7 +187,7 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10):
     mesh.close()
     return {"workload": f"C4: Q2 1.0x0.5x0.25 mm, {n} dofs x {batch} instances (own powers and k scales)",
             "value": rate, "unit": "GDoF/s", "explicit_steps_per_step": chunk, "steps": K,
-            "cell_kernel_avg_us": 1e3 * cell_ms / max(cell_n, 1), "cell_kernel_shape_index": variant,
+            "cell_kernel_avg_us": 1e3 * cell_ms / max(cell_n, 1), "step_shape": SHAPES[variant],
             "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / hbm, "l2": "state > L2; flushed between timed steps"}
 
 
@@ -254,16 +256,27 @@ def run_reference(args):
                       "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-def traffic_for_kernel():
-    """DRAM bytes per launch of the cell kernel from the committed ncu summary, if the kernel
-    source is unchanged since that capture (else null)."""
+TRAFFIC_RECORDS = {  # dominant kernel -> (ncu traffic record, sources it was captured from)
+    "cell": ("cell_kernel_c2_traffic.json", ["kernels_cell.cu", "cell_ops.cuh"]),
+    "step": ("step_kernel_c2_traffic.json", ["kernels_step.cu", "cell_ops.cuh"]),
+}
+
+
+def sources_sha256(names):
     import hashlib
-    path = os.path.join(ROOT, "profiles", "cell_kernel_c2_traffic.json")
-    src = os.path.join(ROOT, "paper_2302_05164_gb300", "csrc", "kernels_cell.cu")
+    h = hashlib.sha256()
+    for nm in names:
+        h.update(open(os.path.join(ROOT, "paper_2302_05164_gb300", "csrc", nm), "rb").read())
+    return h.hexdigest()
+
+
+def traffic_for_kernel(kind):
+    """DRAM bytes per launch of the dominant kernel from the committed ncu record, if the
+    kernel's sources are unchanged since that capture (else null)."""
+    fname, srcs = TRAFFIC_RECORDS[kind]
     try:
-        rec = json.load(open(path))
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        return rec["dram_bytes_per_launch"] if rec.get("kernels_cell_sha256") == h else None
+        rec = json.load(open(os.path.join(ROOT, "profiles", fname)))
+        return rec["dram_bytes_per_launch"] if rec.get("sources_sha256") == sources_sha256(srcs) else None
     except (OSError, KeyError, ValueError):
         return None
 
@@ -351,8 +364,8 @@ def main():
            "config": {"workload": WORKLOAD, "n_dofs": n, "n_cells": info["n_active"], "n_hanging": info["n_hanging"],
                       "explicit_steps_per_step": CHUNK, "dt_s": dt, "l2": "flushed between timed steps (256 MB write)",
                       "parallelism": f"replicas x{ws} (independent instances)",
-                      "cell_kernel_shape": SHAPES[variant],
-                      "autotune_us_per_launch": dict(zip(SHAPES, [round(u, 2) for u in shape_us]))},
+                      "step_shape": SHAPES[variant],
+                      "autotune_us_per_step": {k: round(u, 2) for k, u in zip(SHAPES, shape_us) if u > 0}},
            "gpu_launches": gpu_launches}
     # roofline of the dominant kernel (cell operator), timed live with events on its stream
     avg_cell_s = cell_ms * 1e-3 / max(cell_launches, 1)
@@ -362,8 +375,8 @@ def main():
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
     achieved = flops_launch / avg_cell_s / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                       "frac": achieved / fp32_peak, "traffic": traffic_for_kernel(),
-                       "kernel": "k_cell<2,float,RESIDUAL,nonlinear>", "flops_per_cell": fpc,
+                       "frac": achieved / fp32_peak, "traffic": traffic_for_kernel("step" if variant >= 4 else "cell"),
+                       "kernel": KERNELS[variant], "flops_per_cell": fpc,
                        "avg_launch_us": avg_cell_s * 1e6, "peak_basis": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
     hbm = peaks.get("hbm_gbs", 6800.0)
     out["hbm_fraction"] = {"algorithmic_bytes_per_dof_update": BYTES_PER_DOF_UPDATE,

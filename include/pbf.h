@@ -272,20 +272,30 @@ pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, const pbf_laser
  * for nsteps steps and n_snaps stored states; host only. */
 pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_out);
 
-/* Autotuner of the FP32-operator cell kernel: times its launch shapes (0: 128 threads, 1: 128
- * threads with 5 resident blocks per SM, 2: 6 blocks, 3: 64 threads with 10 blocks, 4: the
- * patch-staged kernel, batch 1 only) on `reps` residual evaluations at the state T_dev (not
- * modified), keeps the fastest in the context and returns its index; us_per_launch_out
- * (nullable, 5 entries) receives each shape's time. FP64 contexts keep shape 0. Synchronises. */
-pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, float* us_per_launch_out,
+/* Explicit-step shapes of an FP32-operator context. 0-3: the per-cell residual kernel
+ * (one thread per cell and instance, gather / atomic scatter; 0: 128 threads, 1: 128 threads
+ * with 5 resident blocks per SM, 2: 6 blocks, 3: 64 threads with 10 blocks) followed by the
+ * hanging-node and update kernels; 4: the fused step, one launch per step for one instance
+ * with the constant or nodal capacity (patches of 64 Z-order cells staged in shared memory,
+ * the previous step's update applied while staging); 5: shape 4 launched with programmatic
+ * dependent launch. Where 4/5 do not apply (batch > 1, quadrature-point capacity) they run
+ * the per-cell form; residual-only evaluations of shapes 4/5 use shape 1.
+ *
+ * pbf_ctx_autotune times `reps` explicit steps of every applicable shape with dt = 0 on a
+ * scratch copy of T_dev (not modified), with the laser of the last call, keeps the fastest in
+ * the context and returns its index; us_per_step_out (nullable, 6 entries) receives each
+ * shape's microseconds per step, -1 where it does not apply. FP64 contexts keep shape 0.
+ * Allocates one scratch vector; synchronises. */
+pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, float* us_per_step_out,
                             pbf_stream stream);
 
-/* Selects a launch shape of the FP32 cell kernel directly (0..4, see pbf_ctx_autotune). */
+/* Selects an explicit-step shape directly (0..5, see pbf_ctx_autotune). */
 pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape);
 
 /* Kernel timing of the dominant (cell operator) kernel: when enabled, CUDA events bracket
- * every cell-operator launch on its stream; pbf_ctx_kernel_time returns the summed elapsed
- * milliseconds and the launch count since the last reset (synchronises). */
+ * every cell-operator launch on its stream (the fused step kernel under shapes 4/5);
+ * pbf_ctx_kernel_time returns the summed elapsed milliseconds and the launch count since the
+ * last reset (synchronises). */
 pbf_status pbf_ctx_set_timing(pbf_ctx* ctx, int enable);
 pbf_status pbf_ctx_kernel_time(pbf_ctx* ctx, double* ms_out, long long* launches_out);
 

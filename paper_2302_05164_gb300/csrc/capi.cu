@@ -321,37 +321,62 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
       }
   }
   std::vector<float> mwf(mw.begin(), mw.end());
-  // cell patches for the patch-staged kernel (one instance): sorted unique node slots per
-  // group of kPatch consecutive cells, and each cell node's index in its group's list
-  std::vector<int32_t> pptr(1, 0), pslot;
-  std::vector<uint16_t> ploc;
-  int max_nu = 0;
-  if (batch == 1 && nc > 0) {
-    ploc.resize(nc * npc);
+  // patches of kStepCells consecutive cells for the fused step kernel (one instance, FP32
+  // operator): sorted unique node slots (dofs, then hanging rows as n_dofs + r, padded to a
+  // multiple of 4), the owning patch of each dof (the first that lists it) and each cell
+  // node's index in its patch's list
+  std::vector<int32_t> sptr, scnt, sslot;
+  std::vector<uint16_t> sloc;
+  int max_nu4 = 0;
+  if (batch == 1 && prec == PBF_F32OP && nc > 0) {
+    const size_t np = (nc + kStepCells - 1) / kStepCells;
+    sloc.assign(np * npc * kStepCells, 0);
+    std::vector<uint8_t> owned((size_t)m.n_dofs, 0);
     std::vector<int32_t> keys;
-    for (size_t c0 = 0; c0 < nc; c0 += kPatch) {
-      const size_t c1 = std::min(nc, c0 + (size_t)kPatch);
+    const int32_t nd32 = (int32_t)m.n_dofs;
+    for (size_t p = 0; p < np; ++p) {
+      const size_t c0 = p * kStepCells, c1 = std::min(nc, c0 + (size_t)kStepCells);
       keys.clear();
       for (size_t c = c0; c < c1; ++c)
         for (size_t a = 0; a < npc; ++a) {
           const int32_t d = m.cell_dofs[c * npc + a];
-          keys.push_back(d >= 0 ? d : (int32_t)m.n_dofs + (-1 - d));
+          keys.push_back(d >= 0 ? d : nd32 + (-1 - d));
         }
       std::sort(keys.begin(), keys.end());
       keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+      const int32_t nfree = (int32_t)(std::lower_bound(keys.begin(), keys.end(), nd32) - keys.begin());
       for (size_t c = c0; c < c1; ++c)
         for (size_t a = 0; a < npc; ++a) {
           const int32_t d = m.cell_dofs[c * npc + a];
-          const int32_t key = d >= 0 ? d : (int32_t)m.n_dofs + (-1 - d);
-          ploc[a * nc + c] = (uint16_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
+          const int32_t key = d >= 0 ? d : nd32 + (-1 - d);
+          sloc[(p * npc + a) * kStepCells + (c - c0)] =
+              (uint16_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
         }
-      pslot.insert(pslot.end(), keys.begin(), keys.end());
-      pptr.push_back((int32_t)pslot.size());
-      max_nu = std::max(max_nu, (int)keys.size());
+      sptr.push_back((int32_t)sslot.size());
+      scnt.push_back(nfree);
+      scnt.push_back((int32_t)keys.size());
+      for (int32_t k : keys) {
+        int32_t v = k;
+        if (k < nd32 && !owned[(size_t)k]) {
+          owned[(size_t)k] = 1;
+          v = (int32_t)((uint32_t)k | 0x80000000u);
+        }
+        sslot.push_back(v);
+      }
+      while (sslot.size() % 4) sslot.push_back(0);
+      max_nu4 = std::max(max_nu4, (int)((keys.size() + 3) & ~(size_t)3));
+    }
+    // every dof must have an owner (each lies in an active cell); otherwise no fused form
+    if (std::find(owned.begin(), owned.end(), (uint8_t)0) != owned.end()) {
+      sptr.clear();
+      scnt.clear();
+      sslot.clear();
+      sloc.clear();
+      max_nu4 = 0;
     }
   }
-  int32_t *d_pptr = nullptr, *d_pslot = nullptr;
-  uint16_t* d_ploc = nullptr;
+  int32_t *d_sptr = nullptr, *d_scnt = nullptr, *d_sslot = nullptr;
+  uint16_t* d_sloc = nullptr;
   int32_t *d_mptr = nullptr, *d_mrow = nullptr;
   double* d_mw = nullptr;
   float* d_mwf = nullptr;
@@ -388,9 +413,10 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   UP(c->level_h, level_h);
   UP(c->cell_top, ctop);
   UP(c->cell_lof, lof);
-  UP(d_pptr, pptr);
-  UP(d_pslot, pslot);
-  UP(d_ploc, ploc);
+  UP(d_sptr, sptr);
+  UP(d_scnt, scnt);
+  UP(d_sslot, sslot);
+  UP(d_sloc, sloc);
   UP(d_mptr, mptr);
   UP(d_mrow, mrow);
   UP(d_mw, mw);
@@ -460,11 +486,28 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   M.cell_top = c->cell_top;
   M.cell_lo = c->cell_lo;
   M.cell_lof = c->cell_lof;
-  if (batch == 1 && nc > 0) {
-    M.patch_ptr = d_pptr;
-    M.patch_slot = d_pslot;
-    M.patch_loc = d_ploc;
-    M.patch_smem = max_nu * 2 * (int)sizeof(float) + (int)(npc * kPatch * sizeof(uint16_t));
+  if (!sptr.empty()) {
+    StepTables& st = c->step;
+    st.n_patches = (int)sptr.size();
+    st.max_nu4 = max_nu4;
+    st.smem = (int)(npc * kStepCells * sizeof(uint16_t)) + 3 * 4 * max_nu4;
+    st.ptr = d_sptr;
+    st.cnt = reinterpret_cast<const int2*>(d_scnt);
+    st.slot = d_sslot;
+    st.loc = d_sloc;
+    c->fstep[0] = (float*)c->f;
+    c->twstep[0] = c->Tw;
+    cudaError_t e2 = dalloc(c.get(), &c->fstep[1], nd);
+    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->fstep[2], nd);
+    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->twstep[1], nd);
+    if (e2 == cudaSuccess) e2 = cudaMemset(c->fstep[1], 0, nd * 4);
+    if (e2 == cudaSuccess) e2 = cudaMemset(c->fstep[2], 0, nd * 4);
+    if (e2 != cudaSuccess) {
+      cudaGetLastError();
+      c->release();
+      return fail(e2 == cudaErrorMemoryAllocation ? PBF_ENOMEM : PBF_ECUDA, "context setup: %s",
+                  cudaGetErrorString(e2));
+    }
   }
   L.degree = c->degree;
   L.f32 = c->f32;
@@ -621,23 +664,10 @@ cudaError_t CtxBase::apply_cell(CellLaunch L, void* f, void* C, int mode, cudaSt
   else L.xh = (const double*)xhb;
   ++launches;
   if (e != cudaSuccess) return e;
-  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-  if (timing) {
-    if (free_events.empty()) {
-      cudaEventCreate(&ev.first);
-      cudaEventCreate(&ev.second);
-    } else {
-      ev = free_events.back();
-      free_events.pop_back();
-    }
-    cudaEventRecord(ev.first, s);
-  }
+  const auto ev = timing ? timing_begin(s) : std::pair<cudaEvent_t, cudaEvent_t>{};
   e = launch_cell(L, f, fhb, C, C ? Chb : nullptr, mode, s);
   ++launches;
-  if (timing) {
-    cudaEventRecord(ev.second, s);
-    events.push_back(ev);
-  }
+  if (ev.first) timing_end(ev, s);
   if (e == cudaSuccess && f) e = launch_hang_distribute(lf32, L.mesh, fhb, f, s);
   if (e == cudaSuccess && C) e = launch_hang_distribute(lf32, L.mesh, Chb, C, s);
   launches += (f ? 1 : 0) + (C ? 1 : 0);
@@ -676,22 +706,40 @@ cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_d
   return e;
 }
 
-// One fused forward-Euler step sequence on T (laser already set). Per step: hanging values of
-// the state (clearing the hanging accumulators), the cell kernel with the surface laser on
-// top faces, and the update, which pulls the hanging-node contributions to their masters.
-cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
-  CellLaunch L = base;
+LaserInline CtxBase::inline_laser(double t, Spot* sp_out) const {
   const bool with_laser = lsetup.k.n_seg > 0;
-  const bool volumetric = with_laser && lsetup.k.volumetric;
+  const Spot sp = with_laser ? spot_at(lsetup.k, t) : Spot();
+  if (sp_out) *sp_out = sp;
+  LaserInline las;
+  if (with_laser && !lsetup.k.volumetric && sp.seg >= 0) {
+    const double r = lsetup.k.radius;
+    las.on = 1;
+    las.seg = sp.seg;
+    las.sx = sp.x;
+    las.sy = sp.y;
+    las.amp = 2.0 * lsetup.k.eta / (kPi * r * r);
+    las.ir2 = 2.0 / (r * r);
+    las.cut2 = 36.0 * r * r;
+    las.power = power;
+    las.powerf = powerf;
+  }
+  return las;
+}
+
+// A forward-Euler step sequence on T (laser already set). Per step: hanging values of the
+// state (clearing the hanging accumulators), the cell kernel with the surface laser on top
+// faces, and the update, which pulls the hanging-node contributions to their masters.
+cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
+  if (nsteps <= 0) return cudaSuccess;
+  if ((base.variant == 4 || base.variant == 5) && fused_ok())
+    return explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant == 5, s);
+  CellLaunch L = base;
+  const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
   const int64_t nv = n_dofs * batch;
   cudaError_t e = cudaSuccess;
-  if (nsteps <= 0) return e;
   PullMap pm = pull;
   pm.fh = fh;
   pm.Ch = latent ? Ch : nullptr;
-  // the patch-staged kernel resolves hanging nodes itself: no hanging pre-pass, nothing to pull
-  const bool patch = f32 && base.variant == 4 && batch == 1 && !latent && base.mesh.patch_ptr != nullptr;
-  if (patch) pm.ptr = nullptr;
   const double tw_dir = mat.T_dirichlet - mat.T_ref;
   const float tf_dir = (float)tw_dir;
   if (f32) {
@@ -705,43 +753,15 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
     L.xh = (const double*)xh;
   }
   for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
-    const double t = t0 + n * dt;
-    const Spot sp = with_laser ? spot_at(lsetup.k, t) : Spot();
-    L.las = LaserInline();
-    if (with_laser && !volumetric && sp.seg >= 0) {
-      const double r = lsetup.k.radius;
-      L.las.on = 1;
-      L.las.seg = sp.seg;
-      L.las.sx = sp.x;
-      L.las.sy = sp.y;
-      L.las.amp = 2.0 * lsetup.k.eta / (kPi * r * r);
-      L.las.ir2 = 2.0 / (r * r);
-      L.las.cut2 = 36.0 * r * r;
-      L.las.power = power;
-      L.las.powerf = powerf;
-    }
-    if (!patch) {
-      e = launch_hang_values_zero(f32, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev, xh, fh, latent ? Ch : nullptr,
-                                  s);
-      ++launches;
-    }
-    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
-    if (timing && e == cudaSuccess) {
-      if (free_events.empty()) {
-        cudaEventCreate(&ev.first);
-        cudaEventCreate(&ev.second);
-      } else {
-        ev = free_events.back();
-        free_events.pop_back();
-      }
-      cudaEventRecord(ev.first, s);
-    }
+    Spot sp;
+    L.las = inline_laser(t0 + n * dt, &sp);
+    e = launch_hang_values_zero(f32, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev, xh, fh, latent ? Ch : nullptr,
+                                s);
+    ++launches;
+    const auto ev = timing && e == cudaSuccess ? timing_begin(s) : std::pair<cudaEvent_t, cudaEvent_t>{};
     if (e == cudaSuccess) e = launch_cell(L, f, fh, latent ? Cacc : nullptr, latent ? Ch : nullptr, MODE_RESIDUAL, s);
     ++launches;
-    if (timing && ev.first) {
-      cudaEventRecord(ev.second, s);
-      events.push_back(ev);
-    }
+    if (ev.first) timing_end(ev, s);
     if (e == cudaSuccess && volumetric && sp.seg >= 0) {
       e = launch_laser(degree, f32, lsetup, L.mesh, power, sp, f, s);
       ++launches;
@@ -766,6 +786,69 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
   if (e == cudaSuccess && nh) e = cudaMemsetAsync(fh, 0, nh, s);
   if (e == cudaSuccess && nh && latent) e = cudaMemsetAsync(Ch, 0, nh, s);
   return e;
+}
+
+// The fused sequence: step n (one launch) completes step n-1 while staging its patches and
+// accumulates f_n; a last streaming kernel completes step N-1 and writes T. Accumulators
+// rotate through fstep[n % 3] (f_n), fstep[(n + 1) % 3] (cleared for step n+1) and
+// fstep[(n + 2) % 3] (f_{n-1}, read); the state alternates between twstep[0] and twstep[1].
+cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, int nsteps, bool pdl, cudaStream_t s) {
+  CellLaunch L = base;
+  const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
+  const double tw_dir = mat.T_dirichlet - mat.T_ref;
+  cudaError_t e = launch_prepare_f32(n_dofs, T_dev, mat.T_ref, twstep[0], Tf, s);
+  ++launches;
+  StepState st;
+  st.invC0 = invC0_f;
+  st.nc = nodal;
+  st.tw_dir = tw_dir;
+  st.dt = (float)dt;
+  for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
+    Spot sp;
+    L.las = inline_laser(t0 + n * dt, &sp);
+    st.tw_in = twstep[n % 2];
+    st.tw_out = twstep[(n + 1) % 2];
+    st.f_in = fstep[(n + 2) % 3];
+    st.f_acc = fstep[n % 3];
+    st.f_clear = fstep[(n + 1) % 3];
+    st.first = n == 0;
+    const auto ev = timing ? timing_begin(s) : std::pair<cudaEvent_t, cudaEvent_t>{};
+    e = launch_step(L, step, st, cap, pdl, s);
+    ++launches;
+    if (ev.first) timing_end(ev, s);
+    if (e == cudaSuccess && volumetric && sp.seg >= 0) {
+      e = launch_laser(degree, true, lsetup, L.mesh, power, sp, fstep[n % 3], s);
+      ++launches;
+    }
+  }
+  if (e == cudaSuccess) {
+    e = launch_step_final(cap, n_dofs, twstep[nsteps % 2], fstep[(nsteps - 1) % 3],
+                          nsteps >= 2 ? fstep[(nsteps - 2) % 3] : nullptr, invC0_f, dirichlet, nodal, tw_dir, (float)dt,
+                          mat.T_ref, T_dev, s);
+    ++launches;
+  }
+  return e;
+}
+
+std::pair<cudaEvent_t, cudaEvent_t> CtxBase::timing_begin(cudaStream_t s) {
+  std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+  if (free_events.empty()) {
+    if (cudaEventCreate(&ev.first) != cudaSuccess || cudaEventCreate(&ev.second) != cudaSuccess) {
+      if (ev.first) cudaEventDestroy(ev.first);
+      cudaGetLastError();
+      return {nullptr, nullptr};
+    }
+  } else {
+    ev = free_events.back();
+    free_events.pop_back();
+  }
+  cudaEventRecord(ev.first, s);
+  return ev;
+}
+
+void CtxBase::timing_end(const std::pair<cudaEvent_t, cudaEvent_t>& ev, cudaStream_t s) {
+  cudaEventRecord(ev.second, s);
+  events.push_back(ev);
 }
 
 extern "C" pbf_status pbf_eval_residual(pbf_ctx* ctx, const double* T_dev, const pbf_laser* laser, double t,
@@ -806,7 +889,7 @@ extern "C" pbf_status pbf_widen_to_f64(const float* x_dev, double* y_dev, int64_
 }
 
 extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out,
-                                       float* us_per_launch_out, pbf_stream stream) {
+                                       float* us_per_step_out, pbf_stream stream) {
   if (!ctx || !T_dev || reps < 1) return fail(PBF_EINVAL, "bad arguments");
   pbf_status st = ctx->check_usable();
   if (st) return st;
@@ -816,55 +899,53 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
     if (variant_out) *variant_out = 0;
     return PBF_OK;
   }
+  // explicit steps with dt = 0 (the state does not change) on a scratch copy of T, with the
+  // laser of the last call, for every shape; kernel timing is off meanwhile
   const int64_t nv = ctx->n_dofs * ctx->batch;
-  CellLaunch L = ctx->base;
-  cudaError_t e = launch_prepare_f32(nv, T_dev, ctx->mat.T_ref, nullptr, ctx->Tf, s);
-  L.xf = ctx->Tf;
-  // the timed launches below call the cell kernel directly: it gathers hanging-node values
-  // from L.xfh, which must hold P_h Tf
-  if (e == cudaSuccess) e = launch_hang_values(true, L.mesh, ctx->Tf, ctx->xh, s);
-  L.xfh = (const float*)ctx->xh;
+  const bool timing = ctx->timing;
+  const int variant = ctx->base.variant;
+  ctx->timing = false;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMalloc(&tmp, (size_t)std::max<int64_t>(1, nv) * 8);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(tmp, T_dev, (size_t)nv * 8, cudaMemcpyDeviceToDevice, s);
   cudaEvent_t a = nullptr, b = nullptr;
   if (e == cudaSuccess) e = cudaEventCreate(&a);
   if (e == cudaSuccess) e = cudaEventCreate(&b);
-  int best = 0;
+  int best = -1;
   float best_ms = 0.f;
   for (int v = 0; v < kCellVariants && e == cudaSuccess; ++v) {
-    L.variant = v;
-    e = launch_cell(L, ctx->f, ctx->fh, ctx->latent ? ctx->Cacc : nullptr, ctx->latent ? ctx->Ch : nullptr,
-                    MODE_RESIDUAL, s);  // warm-up
+    if (us_per_step_out) us_per_step_out[v] = -1.f;
+    if (v >= 4 && !ctx->fused_ok()) continue;
+    ctx->base.variant = v;
+    e = ctx->explicit_steps(tmp, 0.0, 0.0, 2, s);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(a, s);
-    for (int r = 0; r < reps && e == cudaSuccess; ++r)
-      e = launch_cell(L, ctx->f, ctx->fh, ctx->latent ? ctx->Cacc : nullptr, ctx->latent ? ctx->Ch : nullptr,
-                      MODE_RESIDUAL, s);
+    if (e == cudaSuccess) e = ctx->explicit_steps(tmp, 0.0, 0.0, reps, s);
     if (e == cudaSuccess) e = cudaEventRecord(b, s);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
     if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
-    if (e == cudaSuccess && us_per_launch_out) us_per_launch_out[v] = 1000.f * ms / (float)reps;
-    if (e == cudaSuccess && (v == 0 || ms < best_ms)) {
+    if (e == cudaSuccess && us_per_step_out) us_per_step_out[v] = 1000.f * ms / (float)reps;
+    if (e == cudaSuccess && (best < 0 || ms < best_ms)) {
       best = v;
       best_ms = ms;
     }
-    ctx->launches += reps + 3;
   }
-  const size_t rsz = 4;
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->f, 0, (size_t)nv * rsz, s);
-  const size_t nh = std::max<size_t>(1, (size_t)ctx->n_hang * ctx->batch);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->fh, 0, nh * rsz, s);
-  if (e == cudaSuccess && ctx->latent) e = cudaMemsetAsync(ctx->Cacc, 0, (size_t)nv * rsz, s);
-  if (e == cudaSuccess && ctx->latent) e = cudaMemsetAsync(ctx->Ch, 0, nh * rsz, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
-  if (e != cudaSuccess) return ctx->cuda(e, "autotune");
+  if (tmp) cudaFree(tmp);
+  ctx->timing = timing;
+  if (e != cudaSuccess) {
+    ctx->base.variant = variant;
+    return ctx->cuda(e, "autotune");
+  }
   ctx->base.variant = best;
   if (variant_out) *variant_out = best;
   return PBF_OK;
 }
 
 extern "C" pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape) {
-  if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, 4]");
+  if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, 5]");
   ctx->base.variant = shape;
   return PBF_OK;
 }

@@ -91,11 +91,6 @@ struct DevMesh {
   const float* con_wf = nullptr;
   const uint8_t* dirichlet = nullptr;
   const uint8_t* cell_top = nullptr;  // 1 when the cell has an active top face
-  // cell patches (batch 1): kPatch consecutive cells share one list of unique node slots
-  const int32_t* patch_ptr = nullptr;   // [n_patches + 1] into patch_slot
-  const int32_t* patch_slot = nullptr;  // node slots: dof d, or n_dofs + r for hanging row r
-  const uint16_t* patch_loc = nullptr;  // [npc][n_cells] index of each cell node in its patch list
-  int patch_smem = 0;                   // dynamic shared memory: 2 floats per slot + the loc table
   const double* cell_lo = nullptr;    // [n_cells][3] lower corner
   const float* cell_lof = nullptr;    // the same in FP32
 };
@@ -180,10 +175,12 @@ struct CellLaunch {
   LaserInline las;
 };
 
-// Launch shapes the autotuner chooses from for the FP32 residual cell kernel:
-// {threads per block, minimum resident blocks per SM} (the second bounds registers per thread)
-constexpr int kCellVariants = 5;  // variant 4: patch-staged kernel (batch 1)
-constexpr int kPatch = 128;       // cells per patch (one thread block)
+// Explicit-step shapes the autotuner chooses from for the FP32 operator. 0-3: the per-cell
+// residual kernel {threads per block, minimum resident blocks per SM} = {128, 1}, {128, 5},
+// {128, 6}, {64, 10} (the second bounds registers per thread), followed by the update kernel;
+// 4: the fused step kernel (one instance, constant or nodal capacity), 5: the same launched
+// with programmatic dependent launch. Residual-only launches of shapes 4 and 5 use shape 1.
+constexpr int kCellVariants = 6;
 
 template <typename R>
 __host__ __device__ inline const GeoR<R>& geo_of(const CellLaunch& L);

@@ -12,58 +12,10 @@
 #include <cstdio>
 #include <type_traits>
 
-#include "internal.cuh"
+#include "cell_ops.cuh"
 
 namespace pbf {
 namespace {
-
-template <int N>
-__device__ __forceinline__ constexpr int lin(int dir, int a, int b, int i) {
-  return dir == 0 ? i + N * (a + N * b) : (dir == 1 ? a + N * (i + N * b) : a + N * (b + N * i));
-}
-
-template <int P, int WHICH>
-__device__ __forceinline__ constexpr double coef(int q, int i) {
-  return WHICH == 0 ? Basis<P>::S(q, i) : Basis<P>::D(q, i);
-}
-
-// out[line, q] (+)= sum_i M(q, i) in[line, i]   along direction DIR; TR uses M(i, q).
-template <int P, int WHICH, int DIR, bool TR, bool ADD, typename R>
-__device__ __forceinline__ void apply1d(const R* in, R* out) {
-  constexpr int N = P + 1;
-#pragma unroll
-  for (int b = 0; b < N; ++b)
-#pragma unroll
-    for (int a = 0; a < N; ++a)
-#pragma unroll
-      for (int q = 0; q < N; ++q) {
-        R s = ADD ? out[lin<N>(DIR, a, b, q)] : R(0);
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          const double m = TR ? coef<P, WHICH>(i, q) : coef<P, WHICH>(q, i);
-          if (m != 0.0) s = s + R(m) * in[lin<N>(DIR, a, b, i)];
-        }
-        out[lin<N>(DIR, a, b, q)] = s;
-      }
-}
-
-template <int P, typename R>
-__device__ __forceinline__ void values_at_qp(const R* u, R* v) {
-  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
-  R t[NP], w[NP];
-  apply1d<P, 0, 0, false, false>(u, t);
-  apply1d<P, 0, 1, false, false>(t, w);
-  apply1d<P, 0, 2, false, false>(w, v);
-}
-
-template <int P, typename R>
-__device__ __forceinline__ void integrate_values(const R* r, R* fe) {
-  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
-  R t[NP], w[NP];
-  apply1d<P, 0, 0, true, false>(r, t);
-  apply1d<P, 0, 1, true, false>(t, w);
-  apply1d<P, 0, 2, true, false>(w, fe);
-}
 
 template <typename R>
 __device__ __forceinline__ R weight_of(const DevMesh& M, int e);
@@ -126,50 +78,6 @@ __device__ __forceinline__ void scatter(const DevMesh& M, R* __restrict__ f, R* 
     const int j = d >= 0 ? d : -1 - d;
     atomicAdd(&base[j * B + inst], fe[a]);
   }
-}
-
-__device__ __forceinline__ float clamp01(float x) { return __saturatef(x); }
-__device__ __forceinline__ double clamp01(double x) { return fmin(fmax(x, 0.0), 1.0); }
-__device__ __forceinline__ float expo(float x) { return __expf(x); }
-__device__ __forceinline__ double expo(double x) { return exp(x); }
-
-template <int P>
-__device__ __forceinline__ constexpr double wq3(int q) {
-  return Basis<P>::W(q % (P + 1)) * Basis<P>::W((q / (P + 1)) % (P + 1)) * Basis<P>::W(q / ((P + 1) * (P + 1)));
-}
-
-// Surface Gaussian 2 eta P/(pi r^2) exp(-2 d^2/r^2) on the cell's top face, (P+1)^2 Gauss
-// points, added to the top-face nodes of fe; skipped when the face lies farther than 6 r from
-// the spot (the integrand is below e^-72 there). Offsets from the spot in FP64, the rest in R.
-template <int P, typename R>
-__device__ __forceinline__ void add_laser(const CellLaunch& L, int cell, int inst, int lev, R* fe) {
-  constexpr int N = P + 1;
-  const GeoR<R>& geo = geo_of<R>(L);
-  R ox, oy, amp;
-  if (sizeof(R) == 4) {  // FP32 operator: positions and powers in FP32 too
-    ox = R(L.mesh.cell_lof[3 * cell] - float(L.las.sx));
-    oy = R(L.mesh.cell_lof[3 * cell + 1] - float(L.las.sy));
-    amp = R(float(L.las.amp) * L.las.powerf[inst * kMaxSeg + L.las.seg]);
-  } else {
-    ox = R(L.mesh.cell_lo[3 * cell] - L.las.sx);
-    oy = R(L.mesh.cell_lo[3 * cell + 1] - L.las.sy);
-    amp = R(L.las.amp * L.las.power[inst * kMaxSeg + L.las.seg]);
-  }
-  const R hx = geo.h[lev][0], hy = geo.h[lev][1];
-  const R gx = max(R(0), max(ox, -(ox + hx))), gy = max(R(0), max(oy, -(oy + hy)));
-  if (gx * gx + gy * gy > R(L.las.cut2)) return;
-  const R ir2 = R(L.las.ir2);
-#pragma unroll
-  for (int qy = 0; qy < N; ++qy)
-#pragma unroll
-    for (int qx = 0; qx < N; ++qx) {
-      const R x = ox + R(Basis<P>::X(qx)) * hx, y = oy + R(Basis<P>::X(qy)) * hy;
-      const R q = amp * expo(-(x * x + y * y) * ir2) * R(Basis<P>::W(qx) * Basis<P>::W(qy)) * hx * hy;
-#pragma unroll
-      for (int j = 0; j < N; ++j)
-#pragma unroll
-        for (int k = 0; k < N; ++k) fe[k + N * (j + N * P)] += q * R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
-    }
 }
 
 // One kernel for the residual / capacity / stiffness / implicit-operator modes.
@@ -324,96 +232,6 @@ __global__ void __launch_bounds__(64) k_diag(const CellLaunch L, double* __restr
 //                 - int rho c_app'(T_h) mu_h N_j ]
 // i.e. the transpose of the linearised operator of Eq. matrix_free_eval (the D_e and L_e
 // parts) plus, for the quadrature-point capacity, the transposed capacity derivative.
-// Patch-staged residual for one instance (FP32 operator): the kPatch consecutive (Z-order)
-// cells of a block share one sorted list of unique node slots. The block stages, coalesced,
-// the slot values into shared memory, resolving hanging-node slots from their masters on the
-// fly (P G_e T), and its cells' local slot indices; every thread gathers its cell from shared
-// memory, accumulates with shared-memory atomics, and the block adds each slot's sum to
-// global memory once, pushing hanging-slot sums to their masters (G_e^T P^T).
-template <int P, bool NLK>
-__global__ void __launch_bounds__(kPatch) k_cell_patch(const CellLaunch L, float* __restrict__ f) {
-  constexpr int N = P + 1, NP = N * N * N;
-  (void)N;
-  extern __shared__ float smem[];
-  const DevMesh& M = L.mesh;
-  const MatR<float>& mt = L.mf;
-  const GeoR<float>& geo = L.gf;
-  const int p0 = M.patch_ptr[blockIdx.x], nu = M.patch_ptr[blockIdx.x + 1] - p0;
-  const int c0 = blockIdx.x * kPatch, ncell = min(kPatch, M.n_cells - c0);
-  float* sv = smem;
-  float* sf = smem + nu;
-  uint16_t* sloc = reinterpret_cast<uint16_t*>(smem + 2 * nu);  // [NP][kPatch]
-  const int nd = M.n_dofs;
-  for (int j = threadIdx.x; j < nu; j += kPatch) {
-    const int g = __ldg(&M.patch_slot[p0 + j]);
-    float val;
-    if (g < nd) {
-      val = __ldg(&L.xf[g]);
-    } else {
-      const int r = g - nd;
-      val = 0.f;
-      for (int e = __ldg(&M.con_ptr[r]); e < __ldg(&M.con_ptr[r + 1]); ++e)
-        val += __ldg(&M.con_wf[e]) * __ldg(&L.xf[__ldg(&M.con_idx[e])]);
-    }
-    sv[j] = val;
-    sf[j] = 0.f;
-  }
-  for (int k = threadIdx.x; k < NP * ncell; k += kPatch) {
-    const int a = k / ncell, t = k - a * ncell;
-    sloc[a * kPatch + t] = __ldg(&M.patch_loc[a * M.n_cells + c0 + t]);
-  }
-  __syncthreads();
-  const int cell = c0 + threadIdx.x;
-  if (threadIdx.x < ncell) {
-    float u[NP], v[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) u[a] = sv[sloc[a * kPatch + threadIdx.x]];
-    values_at_qp<P, float>(u, v);
-    const int lev = M.cell_level[cell];
-    const float detJ = geo.detJ[lev];
-    const int mat = M.cell_mat[cell];
-    const float scale = (mat == 1 ? mt.powder_scale : 1.f) * (L.k_scale_f ? L.k_scale_f[0] : 1.f);
-    float kw[NP];
-    const float k0 = mt.k0 * scale, dk = mt.dk * scale;
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      float k = k0;
-      if (NLK) k = k0 + dk * clamp01((v[q] + mt.tk_off) * mt.inv_dT);
-      kw[q] = -k * (float(wq3<P>(q)) * detJ);
-    }
-    float r[NP], g[NP];
-#define PATCH_DIR(DIR, ADD)                                            \
-  {                                                                    \
-    const float cd = geo.ih2[lev][DIR];                                \
-    apply1d<P, 1, DIR, false, false>(v, g);                            \
-    _Pragma("unroll") for (int q = 0; q < NP; ++q) g[q] *= kw[q] * cd; \
-    apply1d<P, 1, DIR, true, ADD>(g, r);                               \
-  }
-    PATCH_DIR(0, false)
-    PATCH_DIR(1, true)
-    PATCH_DIR(2, true)
-#undef PATCH_DIR
-    float fe[NP];
-    integrate_values<P, float>(r, fe);
-    if (L.las.on && M.cell_top[cell]) add_laser<P, float>(L, cell, 0, lev, fe);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) atomicAdd(&sf[sloc[a * kPatch + threadIdx.x]], fe[a]);
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < nu; j += kPatch) {
-    const float val = sf[j];
-    if (val == 0.f) continue;
-    const int g = __ldg(&M.patch_slot[p0 + j]);
-    if (g < nd) {
-      atomicAdd(&f[g], val);
-    } else {
-      const int r = g - nd;
-      for (int e = __ldg(&M.con_ptr[r]); e < __ldg(&M.con_ptr[r + 1]); ++e)
-        atomicAdd(&f[__ldg(&M.con_idx[e])], __ldg(&M.con_wf[e]) * val);
-    }
-  }
-}
-
 template <int P, typename R, bool NLK, bool QPC>
 __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restrict__ g, R* __restrict__ gh) {
   constexpr int NP = (P + 1) * (P + 1) * (P + 1);
@@ -520,14 +338,10 @@ cudaError_t go_shape(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, 
 template <int P, typename R, int MODE, bool NLK, bool LAT>
 cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
   if (std::is_same<R, float>::value && MODE == MODE_RESIDUAL && !LAT) {
-    if (L.variant == 4 && L.mesh.batch == 1 && L.mesh.patch_ptr) {
-      const int np = (L.mesh.n_cells + kPatch - 1) / kPatch;
-      if (np == 0) return cudaSuccess;
-      k_cell_patch<P, NLK><<<np, kPatch, L.mesh.patch_smem, s>>>(L, (float*)f);
-      return cudaGetLastError();
-    }
     switch (L.variant) {
-      case 1: return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
+      case 1:
+      case 4:  // shape 4 is the fused explicit step; residual-only launches use shape 1
+      case 5: return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
       case 2: return go_shape<P, R, MODE, NLK, LAT, 128, 6>(L, f, fh, C, Ch, s);
       case 3: return go_shape<P, R, MODE, NLK, LAT, 64, 10>(L, f, fh, C, Ch, s);
       default: break;
@@ -559,11 +373,8 @@ cudaError_t dispatch(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, 
 }  // namespace
 
 cudaError_t launch_cell(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, int mode, cudaStream_t s) {
-  // a mesh with hanging nodes needs their values and accumulators (except the patch-staged
-  // kernel, which resolves them itself): refuse instead of faulting
-  const bool self_contained = L.variant == 4 && L.f32 && mode == MODE_RESIDUAL && C == nullptr &&
-                              L.mesh.batch == 1 && L.mesh.patch_ptr != nullptr;
-  if (!self_contained && L.mesh.n_hang > 0 &&
+  // a mesh with hanging nodes needs their values and accumulators: refuse instead of faulting
+  if (L.mesh.n_hang > 0 &&
       ((L.f32 ? (const void*)L.xfh : (const void*)L.xh) == nullptr || fh == nullptr || (C != nullptr && Ch == nullptr)))
     return cudaErrorInvalidValue;
   if (L.degree == 1)

@@ -9,6 +9,7 @@
 #include "internal.cuh"
 #include "mesh.hpp"
 #include "pbf.h"
+#include "step.cuh"
 #include "vec_kernels.cuh"
 
 namespace pbf {
@@ -62,6 +63,11 @@ struct CtxBase {
   void* Ch = nullptr;    // capacity accumulator at hanging nodes
   double* fh64 = nullptr;  // FP64 accumulators for FP64-operator launches of an FP32 context
   double* Ch64 = nullptr;
+  // fused explicit step (one instance, FP32 operator): patch tables, the three rotating
+  // accumulators (fstep[0] is f) and the two FP64 working states (twstep[0] is Tw)
+  StepTables step;
+  float* fstep[3] = {nullptr, nullptr, nullptr};
+  double* twstep[2] = {nullptr, nullptr};
   double* C0 = nullptr;  // lumped capacity with the plain c [n_dofs]
   double* invC0_d = nullptr;
   float* invC0_f = nullptr;
@@ -90,8 +96,16 @@ struct CtxBase {
   cudaError_t apply_cell(CellLaunch L, void* f, void* C, int mode, cudaStream_t s);
   // f_diff, f_vol and C~ at T in FP64 (laser set beforehand; any output may be null)
   cudaError_t residual_f64(const double* T, double t, double* fd, double* fv, double* C, cudaStream_t s);
-  // nsteps forward-Euler steps in place on T (laser set beforehand)
+  // nsteps forward-Euler steps in place on T (laser set beforehand); the fused form runs when
+  // the context's shape is 4 or 5 and fused_ok()
   cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
+  cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, cudaStream_t s);
+  bool fused_ok() const { return f32 && batch == 1 && cap != CAP_QUADRATURE && step.n_patches > 0; }
+  // the surface laser of the cell kernels at time t (off for the volumetric source)
+  LaserInline inline_laser(double t, Spot* sp) const;
+  // CUDA events around one timed launch (kernel timing on)
+  std::pair<cudaEvent_t, cudaEvent_t> timing_begin(cudaStream_t s);
+  void timing_end(const std::pair<cudaEvent_t, cudaEvent_t>& ev, cudaStream_t s);
   // adjoint work space
   int32_t* surf_idx = nullptr;
   double* surf_w = nullptr;

@@ -83,17 +83,7 @@ __global__ void k_update_f32(int64_t n, int B, double* __restrict__ Tw, float* _
     Tf[i] = tf_dir;
     return;
   }
-  const double tw = Tw[i];
-  float inc;
-  if (CAP == CAP_QUADRATURE) {
-    inc = dt * fi / ci;
-  } else if (CAP == CAP_NODAL) {
-    const float z = (d2f_rn(tw) + nc.tm_off_f) * nc.inv_sigma_f;
-    inc = dt * fi * invC0[d] / (1.f + nc.lat_ratio_f * __expf(-0.5f * z * z));
-  } else {
-    inc = dt * fi * invC0[d];
-  }
-  const double t = tw + f2d(inc);
+  const double t = euler_f32<CAP>(Tw[i], fi, ci, CAP == CAP_QUADRATURE ? 0.f : invC0[d], false, nc, tw_dir, dt);
   Tw[i] = t;
   Tf[i] = d2f_rn(t);
 }
@@ -111,22 +101,8 @@ __global__ void k_capacity_nodal(int64_t n, int B, const double* __restrict__ C0
 template <int CAP>
 __device__ __forceinline__ void update_one(float fi, float ci, float ic, bool fixed, double& tw, float& tf,
                                            const NodalCap& nc, double tw_dir, float tf_dir, float dt) {
-  if (fixed) {
-    tw = tw_dir;
-    tf = tf_dir;
-    return;
-  }
-  float inc;
-  if (CAP == CAP_QUADRATURE) {
-    inc = dt * fi / ci;
-  } else if (CAP == CAP_NODAL) {
-    const float z = (d2f_rn(tw) + nc.tm_off_f) * nc.inv_sigma_f;
-    inc = dt * fi * ic / (1.f + nc.lat_ratio_f * __expf(-0.5f * z * z));
-  } else {
-    inc = dt * fi * ic;
-  }
-  tw = tw + f2d(inc);
-  tf = d2f_rn(tw);
+  tw = euler_f32<CAP>(tw, fi, ci, ic, fixed, nc, tw_dir, dt);
+  tf = fixed ? tf_dir : d2f_rn(tw);
 }
 
 template <int CAP>

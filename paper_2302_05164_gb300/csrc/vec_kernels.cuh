@@ -21,6 +21,26 @@ struct NodalCap {
   double lat_ratio = 0.0, Tm = 0.0, inv_sigma = 0.0;  // c_app/c = 1 + lat_ratio exp(-((T-Tm) inv_sigma)^2/2)
   float lat_ratio_f = 0.f, tm_off_f = 0.f, inv_sigma_f = 0.f;  // FP32 form on T - T_ref
 };
+// The FP32-operator forward-Euler update of one dof (Eq. forward_euler): the increment
+// dt f / C~ formed in FP32 (C~: the accumulated quadrature row sum ci, or the inverse lumped
+// capacity ic of the constant c, scaled for the nodal apparent capacity by
+// 1 / (1 + lat_ratio exp(-z^2/2)) at the old state) and added to the FP64 working state tw;
+// Dirichlet dofs take tw_dir. Every kernel that advances the FP32-operator state uses it.
+template <int CAP>
+__device__ __forceinline__ double euler_f32(double tw, float fi, float ci, float ic, bool fixed, const NodalCap& nc,
+                                            double tw_dir, float dt) {
+  if (fixed) return tw_dir;
+  float inc;
+  if (CAP == CAP_QUADRATURE) {
+    inc = dt * fi / ci;
+  } else if (CAP == CAP_NODAL) {
+    const float z = (d2f_rn(tw) + nc.tm_off_f) * nc.inv_sigma_f;
+    inc = dt * fi * ic / (1.f + nc.lat_ratio_f * __expf(-0.5f * z * z));
+  } else {
+    inc = dt * fi * ic;
+  }
+  return tw + f2d(inc);
+}
 // Transposed constraint map: for dof d the hanging rows r (weight w) that have d as a master;
 // with it the update kernel pulls f_h (and C_h) instead of a separate scatter kernel.
 struct PullMap {

@@ -299,11 +299,15 @@ def pbf_widen_to_f64(x, y, n, stream=None):
     _check(lib().pbf_widen_to_f64(_ptr(x), _ptr(y), int(n), _stream(stream)))
 
 
+N_SHAPES = 6
+
+
 def pbf_ctx_autotune(h, T, reps=5, stream=None, times=False):
-    """Picks the fastest launch shape of the FP32 cell kernel; returns its index (and the
-    per-shape microseconds per launch when times=True)."""
+    """Picks the fastest explicit-step shape of an FP32-operator context; returns its index
+    (and the microseconds per step of every shape, -1 where a shape does not apply, when
+    times=True)."""
     v = C.c_int()
-    us = np.zeros(5, np.float32)
+    us = np.zeros(N_SHAPES, np.float32)
     _check(lib().pbf_ctx_autotune(h, _ptr(T), int(reps), C.byref(v), _ptr(us), _stream(stream)))
     return (v.value, us.tolist()) if times else v.value
 

@@ -1,0 +1,175 @@
+"""GPU parity of the fused explicit step (one launch per forward-Euler step: the patch-staged
+cell operator that completes the previous step while staging) against the oracle, through
+the C ABI: degrees 1 and 2 on adaptive meshes with hanging nodes, constant / nonlinear
+conductivity, nodal apparent capacity, surface and volumetric lasers, Dirichlet dofs that
+start away from T_D, short sequences that exercise the accumulator rotation (1, 2, 3 steps)
+and consecutive calls mixing the fused and per-cell forms.
+
+Tolerance: FP32 operator, 2e-4 relative max-norm on temperatures (as for the per-cell form)."""
+import numpy as np
+import pytest
+
+from paper_2302_05164_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL32_T = 2e-4
+FUSED, FUSED_PDL, PER_CELL = 4, 5, 1
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_05164_gb300 import pbf
+    return pbf
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def amr(degree):
+    regions = [(I.BALL, (0.3e-3, 0.25e-3, 0.25e-3), (0, 0, 0), 120e-6, 3),
+               (I.BOX, (0.6e-3, 0.1e-3, 0.1e-3), (0.7e-3, 0.2e-3, 0.2e-3), 20e-6, 2)]
+    return I.mesh_desc((8, 4, 2), (125e-6,) * 3, degree, 3, regions, powder_z0=0.15e-3, powder_z1=0.2e-3)
+
+
+def track_laser(desc, power=300.0, volumetric=False):
+    y = desc["ntree"][1] * desc["tree_h"][1] / 2
+    return I.laser([(0.1e-3, y, 0.9e-3, y, 0.0, 1e-3)], [power], eta=0.35, radius=40e-6, volumetric=volumetric,
+                   h_powder=40e-6)
+
+
+def to_dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def stable_dt(om, mat):
+    lam, _ = om.lambda_max(dict(mat, k0=max(mat["k0"], mat["k1"])), I.start_vector(om.n_dofs), max_iter=300,
+                           rtol=1e-8)
+    return 0.5 * 2.0 / lam
+
+
+def fused_run(P, desc, mat, T0, ls, t0, dt, calls, shape=FUSED):
+    """calls: list of (shape, nsteps) run back to back on one context."""
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F32OP)
+    Td = to_dev(T0)
+    t = t0
+    for sh, n in calls:
+        P.pbf_ctx_set_kernel_shape(ctx.h, sh)
+        P.pbf_explicit_step(ctx.h, Td, ls, t, dt, n)
+        t += n * dt
+    torch.cuda.synchronize()
+    return Td.cpu().numpy(), ctx, m
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+@pytest.mark.parametrize("mat", ["const", "nonlin_nodal"])
+@pytest.mark.parametrize("shape", [FUSED, FUSED_PDL])
+def test_fused_steps_match_oracle(P, oracle_mod, degree, mat, shape):
+    desc = amr(degree)
+    material = I.TI64_CONST if mat == "const" else I.TI64_NONLIN_Q2
+    om = oracle_mod.Mesh(desc)
+    dt = stable_dt(om, material)
+    T0 = I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 2600.0, 60e-6, seed=11, noise=0.01)
+    ls = track_laser(desc)
+    ref = om.explicit(material, T0, ls, 1e-4, dt, 12)
+    got, _, _ = fused_run(P, desc, material, T0, ls, 1e-4, dt, [(shape, 12)])
+    assert rel(got, ref) < TOL32_T
+    assert np.abs(ref - T0).max() > 1.0  # the steps changed the field
+
+
+@pytest.mark.parametrize("nsteps", [1, 2, 3])
+def test_short_sequences_rotate_accumulators(P, oracle_mod, nsteps):
+    """1, 2 and 3 steps (every position of the three-buffer rotation at the final update),
+    each followed by a residual that must find all accumulators cleared."""
+    desc = amr(2)
+    om = oracle_mod.Mesh(desc)
+    mat = I.TI64_NONLIN_Q2
+    dt = stable_dt(om, mat)
+    T0 = I.smooth_field(om.dof_xyz(), seed=12, lo=353.0, hi=2400.0)
+    ls = track_laser(desc)
+    ref = om.explicit(mat, T0, ls, 2e-4, dt, nsteps)
+    got, ctx, m = fused_run(P, desc, mat, T0, ls, 2e-4, dt, [(FUSED, nsteps)])
+    assert rel(got, ref) < TOL32_T
+    fd, fv, _ = om.residual(mat, got, ls, 3e-4)
+    out = [torch.zeros(om.n_dofs, dtype=torch.float64, device="cuda") for _ in range(3)]
+    P.pbf_eval_residual(ctx.h, to_dev(got), ls, 3e-4, *out)
+    assert rel(out[0].cpu().numpy(), fd) < 2e-5 and rel(out[1].cpu().numpy(), fv) < 2e-5
+
+
+def test_dirichlet_dofs_start_away_from_td(P, oracle_mod):
+    """The first step evaluates the operator at the state as given, Dirichlet dofs included;
+    from then on they hold T_D (the oracle's order)."""
+    desc = amr(2)
+    om = oracle_mod.Mesh(desc)
+    mat = I.TI64_CONST
+    dt = stable_dt(om, mat)
+    T0 = I.smooth_field(om.dof_xyz(), seed=13, lo=400.0, hi=2000.0)
+    tab = om.tables()
+    assert T0[tab["dirichlet"] != 0].min() > mat["T_dirichlet"]
+    ls = track_laser(desc, power=0.0)
+    for n in (1, 4):
+        ref = om.explicit(mat, T0, ls, 0.0, dt, n)
+        got, _, _ = fused_run(P, desc, mat, T0, ls, 0.0, dt, [(FUSED, n)])
+        assert rel(got, ref) < TOL32_T
+        assert np.all(got[tab["dirichlet"] != 0] == mat["T_dirichlet"])
+
+
+def test_volumetric_source_in_fused_steps(P, oracle_mod):
+    desc = amr(2)
+    desc = dict(desc, active_top_z=0.25e-3)
+    om = oracle_mod.Mesh(desc)
+    mat = I.TI64_NONLIN_Q2
+    dt = stable_dt(om, mat)
+    T0 = np.full(om.n_dofs, I.T0)
+    ls = track_laser(desc, power=250.0, volumetric=True)
+    ref = om.explicit(mat, T0, ls, 1e-4, dt, 8)
+    got, _, _ = fused_run(P, desc, mat, T0, ls, 1e-4, dt, [(FUSED_PDL, 8)])
+    assert ref.max() > I.T0 + 1.0
+    assert rel(got, ref) < TOL32_T
+
+
+def test_consecutive_calls_mix_forms(P, oracle_mod):
+    """Fused, per-cell and fused calls back to back on one context equal one oracle run."""
+    desc = amr(2)
+    om = oracle_mod.Mesh(desc)
+    mat = I.TI64_NONLIN_Q2
+    dt = stable_dt(om, mat)
+    T0 = I.melt_pool_field(om.dof_xyz(), (0.5e-3, 0.25e-3, 0.25e-3), 2400.0, 80e-6, seed=14, noise=0.01)
+    ls = track_laser(desc)
+    ref = om.explicit(mat, T0, ls, 0.0, dt, 17)
+    got, _, _ = fused_run(P, desc, mat, T0, ls, 0.0, dt, [(FUSED, 5), (PER_CELL, 4), (FUSED_PDL, 8)])
+    assert rel(got, ref) < TOL32_T
+
+
+def test_quadrature_capacity_falls_back(P, oracle_mod):
+    """The fused form covers the constant and nodal capacities; with the quadrature-point
+    capacity shapes 4/5 run the per-cell form and still match the oracle."""
+    desc = amr(1)
+    om = oracle_mod.Mesh(desc)
+    mat = I.TI64_NONLIN
+    dt = stable_dt(om, mat)
+    T0 = I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 2600.0, 60e-6, seed=15, noise=0.01)
+    ls = track_laser(desc)
+    ref = om.explicit(mat, T0, ls, 1e-4, dt, 6)
+    got, _, _ = fused_run(P, desc, mat, T0, ls, 1e-4, dt, [(FUSED, 6)])
+    assert rel(got, ref) < TOL32_T
+
+
+def test_autotune_times_every_step_form(P):
+    desc = amr(2)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, I.TI64_NONLIN_Q2, P.PBF_F32OP)
+    T = torch.full((m.info()["n_dofs"],), 900.0, dtype=torch.float64, device="cuda")
+    T0 = T.clone()
+    v, us = P.pbf_ctx_autotune(ctx.h, T, reps=3, times=True)
+    assert len(us) == 6 and all(u > 0 for u in us) and us[v] == min(us)
+    assert torch.equal(T, T0)  # the state is not modified
+    bctx = P.Context(m, I.TI64_NONLIN_Q2, P.PBF_F32OP, 2)  # batches have no fused form
+    Tb = torch.full((2 * m.info()["n_dofs"],), 900.0, dtype=torch.float64, device="cuda")
+    v, us = P.pbf_ctx_autotune(bctx.h, Tb, reps=2, times=True)
+    assert us[4] < 0 and us[5] < 0 and v < 4
