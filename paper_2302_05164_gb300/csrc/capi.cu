@@ -322,61 +322,93 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   }
   std::vector<float> mwf(mw.begin(), mw.end());
   // patches of kStepCells consecutive cells for the fused step kernel (one instance, FP32
-  // operator): sorted unique node slots (dofs, then hanging rows as n_dofs + r, padded to a
-  // multiple of 4), the owning patch of each dof (the first that lists it) and each cell
-  // node's index in its patch's list
+  // operator): each patch lists its unique node slots (the dofs of its cells and the masters
+  // of its hanging nodes, ascending, then its hanging nodes), the owning patch of each dof
+  // (the first that lists it), each cell node's shared-memory position and, per hanging
+  // slot, its constraint row with the masters' positions
   std::vector<int32_t> sptr, scnt, sslot;
-  std::vector<uint16_t> sloc;
-  int max_nu4 = 0;
-  if (batch == 1 && prec == PBF_F32OP && nc > 0) {
+  std::vector<uint16_t> sloc, shloc;
+  std::vector<float> shw;
+  int max_nu = 0, max_hent = 0;
+  bool step_ok = batch == 1 && prec == PBF_F32OP && nc > 0;
+  if (step_ok) {
     const size_t np = (nc + kStepCells - 1) / kStepCells;
     sloc.assign(np * npc * kStepCells, 0);
     std::vector<uint8_t> owned((size_t)m.n_dofs, 0);
     std::vector<int32_t> keys;
     const int32_t nd32 = (int32_t)m.n_dofs;
-    for (size_t p = 0; p < np; ++p) {
+    for (size_t p = 0; p < np && step_ok; ++p) {
       const size_t c0 = p * kStepCells, c1 = std::min(nc, c0 + (size_t)kStepCells);
       keys.clear();
       for (size_t c = c0; c < c1; ++c)
         for (size_t a = 0; a < npc; ++a) {
           const int32_t d = m.cell_dofs[c * npc + a];
-          keys.push_back(d >= 0 ? d : nd32 + (-1 - d));
+          if (d >= 0) {
+            keys.push_back(d);
+          } else {
+            const int32_t r = -1 - d;
+            keys.push_back(nd32 + r);
+            for (int32_t e = m.con_ptr[(size_t)r]; e < m.con_ptr[(size_t)r + 1]; ++e) keys.push_back(m.con_idx[(size_t)e]);
+          }
         }
       std::sort(keys.begin(), keys.end());
       keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+      const int32_t nu = (int32_t)keys.size();
       const int32_t nfree = (int32_t)(std::lower_bound(keys.begin(), keys.end(), nd32) - keys.begin());
+      auto pos = [&](int32_t key) {
+        return step_swizzle((int)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin()));
+      };
       for (size_t c = c0; c < c1; ++c)
         for (size_t a = 0; a < npc; ++a) {
           const int32_t d = m.cell_dofs[c * npc + a];
-          const int32_t key = d >= 0 ? d : nd32 + (-1 - d);
-          sloc[(p * npc + a) * kStepCells + (c - c0)] =
-              (uint16_t)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin());
+          sloc[(p * npc + a) * kStepCells + (c - c0)] = (uint16_t)pos(d >= 0 ? d : nd32 + (-1 - d));
         }
+      const int32_t hbegin = (int32_t)shloc.size();
       sptr.push_back((int32_t)sslot.size());
-      scnt.push_back(nfree);
-      scnt.push_back((int32_t)keys.size());
-      for (int32_t k : keys) {
-        int32_t v = k;
-        if (k < nd32 && !owned[(size_t)k]) {
-          owned[(size_t)k] = 1;
-          v = (int32_t)((uint32_t)k | 0x80000000u);
+      for (int32_t j = 0; j < nu; ++j) {
+        const int32_t k = keys[(size_t)j];
+        if (k < nd32) {
+          int32_t v = k;
+          if (!owned[(size_t)k]) {
+            owned[(size_t)k] = 1;
+            v = (int32_t)((uint32_t)k | 0x80000000u);
+          }
+          sslot.push_back(v);
+        } else {
+          const int32_t r = k - nd32, e0 = m.con_ptr[(size_t)r], e1 = m.con_ptr[(size_t)r + 1];
+          const int32_t start = (int32_t)shloc.size() - hbegin;
+          if (e1 - e0 > 31 || start >= (1 << 26)) step_ok = false;
+          for (int32_t e = e0; e < e1; ++e) {
+            shloc.push_back((uint16_t)pos(m.con_idx[(size_t)e]));
+            shw.push_back((float)m.con_w[(size_t)e]);
+          }
+          sslot.push_back((start << 5) | (e1 - e0));
         }
-        sslot.push_back(v);
       }
       while (sslot.size() % 4) sslot.push_back(0);
-      max_nu4 = std::max(max_nu4, (int)((keys.size() + 3) & ~(size_t)3));
+      scnt.push_back(nfree);
+      scnt.push_back(nu);
+      scnt.push_back(hbegin);
+      scnt.push_back((int32_t)shloc.size());
+      max_nu = std::max(max_nu, (int)nu);
+      max_hent = std::max(max_hent, (int)shloc.size() - hbegin);
     }
-    // every dof must have an owner (each lies in an active cell); otherwise no fused form
-    if (std::find(owned.begin(), owned.end(), (uint8_t)0) != owned.end()) {
+    // every dof needs an owner (each lies in an active cell), and shared-memory positions
+    // are 16-bit; otherwise the context has no fused form
+    if (step_ok && std::find(owned.begin(), owned.end(), (uint8_t)0) != owned.end()) step_ok = false;
+    if (step_ok && ((max_nu + 31) & ~31) > 65536) step_ok = false;
+    if (!step_ok) {
       sptr.clear();
       scnt.clear();
       sslot.clear();
       sloc.clear();
-      max_nu4 = 0;
+      shloc.clear();
+      shw.clear();
     }
   }
   int32_t *d_sptr = nullptr, *d_scnt = nullptr, *d_sslot = nullptr;
-  uint16_t* d_sloc = nullptr;
+  uint16_t *d_sloc = nullptr, *d_shloc = nullptr;
+  float* d_shw = nullptr;
   int32_t *d_mptr = nullptr, *d_mrow = nullptr;
   double* d_mw = nullptr;
   float* d_mwf = nullptr;
@@ -417,6 +449,8 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   UP(d_scnt, scnt);
   UP(d_sslot, sslot);
   UP(d_sloc, sloc);
+  UP(d_shloc, shloc);
+  UP(d_shw, shw);
   UP(d_mptr, mptr);
   UP(d_mrow, mrow);
   UP(d_mw, mw);
@@ -489,17 +523,21 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   if (!sptr.empty()) {
     StepTables& st = c->step;
     st.n_patches = (int)sptr.size();
-    st.max_nu4 = max_nu4;
-    st.smem = (int)(npc * kStepCells * sizeof(uint16_t)) + 3 * 4 * max_nu4;
+    st.max_nu32 = (max_nu + 31) & ~31;
+    st.max_hent8 = (max_hent + 7) & ~7;
+    st.smem = step_smem_bytes((int)npc, st.max_nu32, st.max_hent8);
     st.ptr = d_sptr;
-    st.cnt = reinterpret_cast<const int2*>(d_scnt);
+    st.cnt = reinterpret_cast<const int4*>(d_scnt);
     st.slot = d_sslot;
     st.loc = d_sloc;
+    st.hloc = d_shloc;
+    st.hw = d_shw;
     c->fstep[0] = (float*)c->f;
-    c->twstep[0] = c->Tw;
     cudaError_t e2 = dalloc(c.get(), &c->fstep[1], nd);
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->fstep[2], nd);
-    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->twstep[1], nd);
+    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->xstep[0], nd);
+    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->xstep[1], nd);
+    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->invC0_fx, nd);
     if (e2 == cudaSuccess) e2 = cudaMemset(c->fstep[1], 0, nd * 4);
     if (e2 == cudaSuccess) e2 = cudaMemset(c->fstep[2], 0, nd * 4);
     if (e2 != cudaSuccess) {
@@ -534,7 +572,7 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     if (e == cudaSuccess) e = cudaMemcpy(Tz, zero.data(), nd * 8, cudaMemcpyHostToDevice);
     Lc.x = Tz;
     if (e == cudaSuccess) e = c->apply_cell(Lc, nullptr, c->C0, MODE_CAPACITY, 0);
-    if (e == cudaSuccess) e = launch_reciprocal((int64_t)nd, c->C0, c->invC0_d, c->invC0_f, 0);
+    if (e == cudaSuccess) e = launch_reciprocal((int64_t)nd, c->C0, c->invC0_d, c->invC0_f, c->invC0_fx, c->dirichlet, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(Tz);
     c->launches += 2;
@@ -791,23 +829,26 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
 // The fused sequence: step n (one launch) completes step n-1 while staging its patches and
 // accumulates f_n; a last streaming kernel completes step N-1 and writes T. Accumulators
 // rotate through fstep[n % 3] (f_n), fstep[(n + 1) % 3] (cleared for step n+1) and
-// fstep[(n + 2) % 3] (f_{n-1}, read); the state alternates between twstep[0] and twstep[1].
+// fstep[(n + 2) % 3] (f_{n-1}, read); the state, T - T_ref as an FP32 pair hi + lo, alternates
+// between xstep[0] and xstep[1].
 cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, int nsteps, bool pdl, cudaStream_t s) {
   CellLaunch L = base;
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
-  const double tw_dir = mat.T_dirichlet - mat.T_ref;
-  cudaError_t e = launch_prepare_f32(n_dofs, T_dev, mat.T_ref, twstep[0], Tf, s);
+  const double xd = mat.T_dirichlet - mat.T_ref;
+  const float xd_hi = (float)xd;
+  const float2 x_dir = make_float2(xd_hi, (float)(xd - (double)xd_hi));
+  cudaError_t e = launch_step_prepare(n_dofs, T_dev, mat.T_ref, xstep[0], s);
   ++launches;
   StepState st;
-  st.invC0 = invC0_f;
+  st.invC0x = invC0_fx;
   st.nc = nodal;
-  st.tw_dir = tw_dir;
+  st.x_dir = x_dir;
   st.dt = (float)dt;
   for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
     Spot sp;
     L.las = inline_laser(t0 + n * dt, &sp);
-    st.tw_in = twstep[n % 2];
-    st.tw_out = twstep[(n + 1) % 2];
+    st.x_in = xstep[n % 2];
+    st.x_out = xstep[(n + 1) % 2];
     st.f_in = fstep[(n + 2) % 3];
     st.f_acc = fstep[n % 3];
     st.f_clear = fstep[(n + 1) % 3];
@@ -822,8 +863,8 @@ cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, i
     }
   }
   if (e == cudaSuccess) {
-    e = launch_step_final(cap, n_dofs, twstep[nsteps % 2], fstep[(nsteps - 1) % 3],
-                          nsteps >= 2 ? fstep[(nsteps - 2) % 3] : nullptr, invC0_f, dirichlet, nodal, tw_dir, (float)dt,
+    e = launch_step_final(cap, n_dofs, xstep[nsteps % 2], fstep[(nsteps - 1) % 3],
+                          nsteps >= 2 ? fstep[(nsteps - 2) % 3] : nullptr, invC0_fx, nodal, x_dir, (float)dt,
                           mat.T_ref, T_dev, s);
     ++launches;
   }

@@ -6,11 +6,12 @@
 //     dependent launch this overlaps the previous kernel's tail);
 //  2. stages the patch's unique node values in shared memory, completing the previous step
 //     on the fly, T_n = T_{n-1} + dt f_{n-1} / C~, at every dof slot (the patch that owns
-//     the dof stores T_n) and interpolating hanging nodes from their masters (T_e = P G_e T);
+//     the dof stores T_n), then interpolates its hanging nodes from their masters, which the
+//     patch lists too (T_e = P G_e T);
 //  3. evaluates the sum-factorised diffusion operator and the surface laser of its cells,
 //     one thread per cell, gathering from and accumulating into shared memory;
-//  4. adds each slot's sum to global memory once, in ascending dof order, and pushes hanging
-//     slots to their masters (G_e^T P^T).
+//  4. pushes hanging-node sums to their masters in shared memory (G_e^T P^T) and adds each
+//     dof slot's sum to global memory once, in ascending dof order.
 // Compared with a per-cell gather / atomic scatter plus a separate update kernel, a dof's
 // value is read about 1.4 times instead of once per adjacent cell (up to 8 for Q2 vertices),
 // its contributions are added with one global atomic per patch instead of one per cell, and
@@ -36,14 +37,16 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
   (void)N;
   extern __shared__ __align__(16) unsigned char smem[];
   uint16_t* sloc = reinterpret_cast<uint16_t*>(smem);                // [NP][KP]
-  int32_t* sslot = reinterpret_cast<int32_t*>(smem + NP * KP * 2);   // [max_nu4]
-  float* sv = reinterpret_cast<float*>(sslot + T.max_nu4);           // staged values
-  float* sf = sv + T.max_nu4;                                        // accumulated contributions
+  int32_t* sslot = reinterpret_cast<int32_t*>(smem + NP * KP * 2);   // [max_nu32]
+  float* sv = reinterpret_cast<float*>(sslot + T.max_nu32);          // staged values (swizzled)
+  float* sf = sv + T.max_nu32;                                       // contributions (swizzled)
+  float* shw = sf + T.max_nu32;                                      // [max_hent8] weights
+  uint16_t* shl = reinterpret_cast<uint16_t*>(shw + T.max_hent8);    // [max_hent8] master positions
   const DevMesh& M = L.mesh;
   const int p = blockIdx.x, tid = threadIdx.x;
   const int p0 = __ldg(&T.ptr[p]);
-  const int2 cn = __ldg(&T.cnt[p]);
-  const int nfree = cn.x, nu = cn.y;
+  const int4 cn = __ldg(&T.cnt[p]);
+  const int nfree = cn.x, nu = cn.y, hb = cn.z, nh = cn.w - cn.z;
 
   // 1. tables (16-byte loads; the loc table of a patch is NP * KP * 2 bytes, a multiple of 16)
   {
@@ -55,6 +58,10 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     int4* d4 = reinterpret_cast<int4*>(sslot);
     const int n4 = (nu + 3) >> 2;
     for (int i = tid; i < n4; i += KP) d4[i] = __ldg(&s4[i]);
+    for (int i = tid; i < nh; i += KP) {
+      shl[i] = __ldg(&T.hloc[hb + i]);
+      shw[i] = __ldg(&T.hw[hb + i]);
+    }
   }
   const int c0 = p * KP, ncell = min(KP, M.n_cells - c0);
   const int cell = c0 + tid;
@@ -71,9 +78,8 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
   // 2a. dof slots: U independent slots in flight per thread
   for (int j0 = 0; j0 < nfree; j0 += KP * U) {
     int g[U];
-    double tw[U];
+    float2 x[U];
     float fi[U], ic[U];
-    bool fx[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * KP + tid;
@@ -82,40 +88,34 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int d = g[u] < 0 ? 0 : g[u];
-      tw[u] = __ldg(&S.tw_in[d]);
+      x[u] = __ldg(&S.x_in[d]);
       fi[u] = __ldg(&S.f_in[d]);
-      ic[u] = __ldg(&S.invC0[d]);
-      fx[u] = __ldg(&M.dirichlet[d]) != 0;
+      ic[u] = __ldg(&S.invC0x[d]);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * KP + tid;
       if (g[u] >= 0) {
-        const double t = S.first ? tw[u] : euler_f32<CAP>(tw[u], fi[u], 0.f, ic[u], fx[u], S.nc, S.tw_dir, S.dt);
-        sv[j] = d2f_rn(t);
-        sf[j] = 0.f;
+        const float2 t = S.first ? x[u] : euler_ff<CAP>(x[u], fi[u], ic[u], S.nc, S.x_dir, S.dt);
+        const int q = step_swizzle(j);
+        sv[q] = t.x;
+        sf[q] = 0.f;
         if (sslot[j] < 0) {
-          S.tw_out[g[u]] = t;
+          S.x_out[g[u]] = t;
           S.f_clear[g[u]] = 0.f;
         }
       }
     }
   }
-  // 2b. hanging slots: x_h = sum_m w_m round(T_n[m]) over the constraint row's masters
+  __syncthreads();
+  // 2b. hanging slots from their masters in shared memory: x_h = sum_m w_m x_m
   for (int j = nfree + tid; j < nu; j += KP) {
-    const int r = sslot[j] - M.n_dofs;
-    const int e0 = __ldg(&M.con_ptr[r]), e1 = __ldg(&M.con_ptr[r + 1]);
+    const int h = sslot[j], e0 = h >> 5, ne = h & 31;
     float val = 0.f;
-    for (int e = e0; e < e1; ++e) {
-      const int m = __ldg(&M.con_idx[e]);
-      double t = __ldg(&S.tw_in[m]);
-      if (!S.first)
-        t = euler_f32<CAP>(t, __ldg(&S.f_in[m]), 0.f, __ldg(&S.invC0[m]), __ldg(&M.dirichlet[m]) != 0, S.nc, S.tw_dir,
-                           S.dt);
-      val += __ldg(&M.con_wf[e]) * d2f_rn(t);
-    }
-    sv[j] = val;
-    sf[j] = 0.f;
+    for (int e = e0; e < e0 + ne; ++e) val += shw[e] * sv[shl[e]];
+    const int q = step_swizzle(j);
+    sv[q] = val;
+    sf[q] = 0.f;
   }
   __syncthreads();
 
@@ -167,32 +167,41 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
   }
   __syncthreads();
   grid_dependency_trigger();  // the next step may start loading its tables
-
-  // 4. one global addition per slot
-  for (int j = tid; j < nfree; j += KP) {
-    const float val = sf[j];
-    if (val != 0.f) atomicAdd(&S.f_acc[sslot[j] & 0x7fffffff], val);
-  }
+  // 4a. hanging contributions to their masters (P_h^T f_h), in shared memory
   for (int j = nfree + tid; j < nu; j += KP) {
-    const float val = sf[j];
-    if (val == 0.f) continue;
-    const int r = sslot[j] - M.n_dofs;
-    for (int e = __ldg(&M.con_ptr[r]); e < __ldg(&M.con_ptr[r + 1]); ++e)
-      atomicAdd(&S.f_acc[__ldg(&M.con_idx[e])], __ldg(&M.con_wf[e]) * val);
+    const int h = sslot[j], e0 = h >> 5, ne = h & 31;
+    const float val = sf[step_swizzle(j)];
+    if (val != 0.f)
+      for (int e = e0; e < e0 + ne; ++e) atomicAdd(&sf[shl[e]], shw[e] * val);
+  }
+  __syncthreads();
+  // 4b. one global addition per dof slot
+  for (int j = tid; j < nfree; j += KP) {
+    const float val = sf[step_swizzle(j)];
+    if (val != 0.f) atomicAdd(&S.f_acc[sslot[j] & 0x7fffffff], val);
   }
 }
 
 template <int CAP>
-__global__ void k_step_final(int n, const double* __restrict__ tw_in, float* __restrict__ f_in,
-                             float* __restrict__ f_other, const float* __restrict__ invC0,
-                             const uint8_t* __restrict__ dirichlet, const NodalCap nc, double tw_dir, float dt,
-                             double off, double* __restrict__ T) {
+__global__ void k_step_final(int n, const float2* __restrict__ x_in, float* __restrict__ f_in,
+                             float* __restrict__ f_other, const float* __restrict__ invC0x, const NodalCap nc,
+                             float2 x_dir, float dt, double off, double* __restrict__ T) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double t = euler_f32<CAP>(tw_in[i], f_in[i], 0.f, invC0[i], dirichlet[i] != 0, nc, tw_dir, dt);
-  T[i] = t + off;
+  const float2 t = euler_ff<CAP>(x_in[i], f_in[i], invC0x[i], nc, x_dir, dt);
+  T[i] = off + (f2d(t.x) + f2d(t.y));
   f_in[i] = 0.f;
   if (f_other) f_other[i] = 0.f;
+}
+
+// x = T - off as hi + lo: the FP64 difference is exact to 53 bits, hi its FP32 rounding and
+// lo = (T - off - hi) rounded (the FP64 subtraction is exact)
+__global__ void k_step_prepare(int n, const double* __restrict__ T, double off, float2* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = T[i] - off;
+  const float hi = d2f_rn(v);
+  x[i] = make_float2(hi, d2f_rn(v - f2d(hi)));
 }
 
 template <typename... KArgs, typename... Args>
@@ -234,9 +243,9 @@ cudaError_t dispatch_step(const CellLaunch& L, const StepTables& t, const StepSt
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                         cudaStream_t s) {
   // the fused form covers one instance of the FP32 operator with the constant or nodal capacity
-  if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
-      !t.loc || !st.tw_in || !st.tw_out || !st.f_in || !st.f_acc || !st.f_clear || !st.invC0 ||
-      st.tw_in == st.tw_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear)
+  if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot || !t.hloc || !t.hw ||
+      !t.loc || !st.x_in || !st.x_out || !st.f_in || !st.f_acc || !st.f_clear || !st.invC0x ||
+      st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear)
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
   if (L.degree == 1) return dispatch_step<1>(L, t, st, cap, pdl, s);
@@ -244,18 +253,23 @@ cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepStat
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_step_final(int cap, int64_t n_dofs, const double* tw_in, float* f_in, float* f_other,
-                              const float* invC0, const uint8_t* dirichlet, const NodalCap& nc, double tw_dir, float dt,
-                              double off, double* T, cudaStream_t s) {
+cudaError_t launch_step_prepare(int64_t n_dofs, const double* T, double off, float2* x, cudaStream_t s) {
+  if (n_dofs == 0) return cudaSuccess;
+  const int bs = 256;
+  k_step_prepare<<<(unsigned)((n_dofs + bs - 1) / bs), bs, 0, s>>>((int)n_dofs, T, off, x);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_final(int cap, int64_t n_dofs, const float2* x_in, float* f_in, float* f_other,
+                              const float* invC0x, const NodalCap& nc, float2 x_dir, float dt, double off, double* T,
+                              cudaStream_t s) {
   if (n_dofs == 0) return cudaSuccess;
   const int bs = 256;
   const unsigned grid = (unsigned)((n_dofs + bs - 1) / bs);
   if (cap == CAP_NODAL)
-    k_step_final<CAP_NODAL><<<grid, bs, 0, s>>>((int)n_dofs, tw_in, f_in, f_other, invC0, dirichlet, nc, tw_dir, dt,
-                                                off, T);
+    k_step_final<CAP_NODAL><<<grid, bs, 0, s>>>((int)n_dofs, x_in, f_in, f_other, invC0x, nc, x_dir, dt, off, T);
   else if (cap == CAP_CONST)
-    k_step_final<CAP_CONST><<<grid, bs, 0, s>>>((int)n_dofs, tw_in, f_in, f_other, invC0, dirichlet, nc, tw_dir, dt,
-                                                off, T);
+    k_step_final<CAP_CONST><<<grid, bs, 0, s>>>((int)n_dofs, x_in, f_in, f_other, invC0x, nc, x_dir, dt, off, T);
   else
     return cudaErrorInvalidValue;
   return cudaGetLastError();

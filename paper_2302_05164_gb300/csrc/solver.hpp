@@ -64,10 +64,12 @@ struct CtxBase {
   double* fh64 = nullptr;  // FP64 accumulators for FP64-operator launches of an FP32 context
   double* Ch64 = nullptr;
   // fused explicit step (one instance, FP32 operator): patch tables, the three rotating
-  // accumulators (fstep[0] is f) and the two FP64 working states (twstep[0] is Tw)
+  // accumulators (fstep[0] is f), the two working states as FP32 pairs hi + lo, and the
+  // inverse constant-c capacity with -1 at Dirichlet dofs
   StepTables step;
   float* fstep[3] = {nullptr, nullptr, nullptr};
-  double* twstep[2] = {nullptr, nullptr};
+  float2* xstep[2] = {nullptr, nullptr};
+  float* invC0_fx = nullptr;
   double* C0 = nullptr;  // lumped capacity with the plain c [n_dofs]
   double* invC0_d = nullptr;
   float* invC0_f = nullptr;

@@ -8,46 +8,88 @@ namespace pbf {
 constexpr int kStepCells = 64;  // cells per patch = threads per block of the fused step kernel
 
 // Patches of kStepCells consecutive (Z-order) cells, built once per context on the host. Each
-// patch lists its unique node slots: first the dofs in ascending order, then the hanging
-// nodes (as n_dofs + constraint row), padded to a multiple of 4 entries so that a block can
-// load its list with 16-byte loads. Every dof is owned by exactly one patch, the first that
-// lists it; the owner writes the dof's new state.
+// patch lists its unique node slots: first the dofs of its cells and the masters of its
+// hanging nodes, in ascending order, then its hanging nodes, padded to a multiple of 4
+// entries so that a block can load its list with 16-byte loads. Every dof is owned by exactly
+// one patch, the first that lists it; the owner writes the dof's new state. A hanging slot
+// stores (start << 5) | count of its constraint row in the patch's hanging table, whose
+// entries give each master's shared-memory position and weight: hanging values and
+// contributions never leave the block.
 struct StepTables {
   int n_patches = 0;
-  int max_nu4 = 0;                // longest list, rounded up to a multiple of 4
+  int max_nu32 = 0;               // longest slot list, rounded up to a multiple of 32
+  int max_hent8 = 0;              // longest hanging table, rounded up to a multiple of 8
   int smem = 0;                   // dynamic shared memory per block (bytes)
   const int32_t* ptr = nullptr;   // [n_patches] start of each list in slot (a multiple of 4)
-  const int2* cnt = nullptr;      // [n_patches] {dof slots, all slots}
-  const int32_t* slot = nullptr;  // dof d or n_dofs + r; bit 31 set where this patch owns dof d
-  const uint16_t* loc = nullptr;  // [n_patches][npc][kStepCells] list index of each cell node
+  const int4* cnt = nullptr;      // [n_patches] {dof slots, all slots, hanging table begin, end}
+  const int32_t* slot = nullptr;  // dof d (bit 31: owned here) or a hanging row reference
+  const uint16_t* loc = nullptr;  // [n_patches][npc][kStepCells] shared position of each cell node
+  const uint16_t* hloc = nullptr; // hanging tables: master positions ...
+  const float* hw = nullptr;      // ... and constraint weights
 };
+
+// Shared-memory position of slot j of a patch: an XOR swizzle within each 32-slot block.
+// Slots of consecutive Z-order cells are about 8 apart (the new nodes per Q2 cell), so the
+// same local node of the 32 cells of a warp would fall into 4 banks; the swizzle spreads them
+// over all 32, and keeps a warp's 32 consecutive slots conflict-free.
+__host__ __device__ inline int step_swizzle(int j) { return j ^ ((j >> 5) & 31); }
+
+// loc table, slot list, staged values and contributions, hanging tables
+inline int step_smem_bytes(int npc, int max_nu32, int max_hent8) {
+  return npc * kStepCells * 2 + max_nu32 * 3 * 4 + max_hent8 * (2 + 4);
+}
+
+// The fused sequence keeps the working state T - T_ref as an unevaluated sum hi + lo of two
+// FP32 numbers (about 48 significant bits; |lo| <= ulp(hi) / 2, so hi is the state rounded to
+// FP32, the value the FP32 operator reads). The FP32 increment dt f / C~ is added exactly with
+// an error-free transformation (TwoSum) and renormalised (Fast2Sum), so that no FP64
+// operation or conversion is left in the step: on this GPU both run at about 1/60 of the
+// FP32 rate.
+__device__ __forceinline__ float2 ff_add(float2 x, float b) {
+  const float s = x.x + b;
+  const float bb = s - x.x;
+  const float err = (x.x - (s - bb)) + (b - bb);  // s + err == x.x + b exactly
+  const float t = x.y + err;
+  const float hi = s + t;
+  return make_float2(hi, t - (hi - s));
+}
 
 // One step n of the fused sequence. The kernel first completes step n-1 on the fly:
 // T_n = T_{n-1} + dt f_{n-1} / C~ for every slot it stages (the owner stores T_n), then
 // accumulates f_n = f(T_n) (diffusion and surface laser) and clears the accumulator of step
 // n+1. Three accumulators rotate so that no launch reads a buffer that it also writes.
 struct StepState {
-  const double* tw_in = nullptr;  // T_{n-1} - T_ref (n = 0: T_0 - T_ref)
-  double* tw_out = nullptr;       // T_n - T_ref (owned dofs written)
+  const float2* x_in = nullptr;   // T_{n-1} - T_ref as hi + lo (n = 0: T_0 - T_ref)
+  float2* x_out = nullptr;        // T_n - T_ref (owned dofs written)
   const float* f_in = nullptr;    // f_{n-1} (unused when first)
   float* f_acc = nullptr;         // f_n, zero on entry
   float* f_clear = nullptr;       // set to zero on owned dofs (the accumulator of step n+1)
-  const float* invC0 = nullptr;   // 1 / lumped capacity with the plain c
+  const float* invC0x = nullptr;  // 1 / lumped capacity with the plain c; -1 at Dirichlet dofs
   NodalCap nc;
-  double tw_dir = 0.0;            // T_D - T_ref
+  float2 x_dir = {0.f, 0.f};      // T_D - T_ref as hi + lo
   float dt = 0.f;
   int first = 0;                  // step 0: T_0 is the state as given (no update)
 };
+
+// The update of one dof of the fused sequence (Dirichlet dofs, ic < 0, take x_dir).
+template <int CAP>
+__device__ __forceinline__ float2 euler_ff(float2 x, float fi, float ic, const NodalCap& nc, float2 x_dir, float dt) {
+  if (ic < 0.f) return x_dir;
+  return ff_add(x, increment_f32<CAP>(x.x, fi, 0.f, ic, nc, dt));
+}
 
 // cap: CAP_CONST or CAP_NODAL. pdl: launch with programmatic stream serialisation, so that
 // the block prologue (table loads) overlaps the tail of the previous kernel in the stream.
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                         cudaStream_t s);
 
-// The last update of a sequence, T = T_ref + T_{N-1} + dt f_{N-1} / C~ (FP64 out), clearing
-// f_in and f_other (nullable): afterwards all three accumulators are zero again.
-cudaError_t launch_step_final(int cap, int64_t n_dofs, const double* tw_in, float* f_in, float* f_other,
-                              const float* invC0, const uint8_t* dirichlet, const NodalCap& nc, double tw_dir, float dt,
-                              double off, double* T, cudaStream_t s);
+// x = T - off split into hi + lo (hi = T - off rounded to FP32, lo = the rest rounded)
+cudaError_t launch_step_prepare(int64_t n_dofs, const double* T, double off, float2* x, cudaStream_t s);
+
+// The last update of a sequence, T = off + T_{N-1} + dt f_{N-1} / C~ (FP64 out), clearing f_in
+// and f_other (nullable): afterwards all three accumulators are zero again.
+cudaError_t launch_step_final(int cap, int64_t n_dofs, const float2* x_in, float* f_in, float* f_other,
+                              const float* invC0x, const NodalCap& nc, float2 x_dir, float dt, double off, double* T,
+                              cudaStream_t s);
 
 }  // namespace pbf

@@ -293,12 +293,14 @@ __global__ void k_broadcast_dofs(int64_t n, int B, const double* __restrict__ a,
 }
 
 __global__ void k_reciprocal(int64_t n, const double* __restrict__ c, double* __restrict__ inv_d,
-                             float* __restrict__ inv_f) {
+                             float* __restrict__ inv_f, float* __restrict__ inv_fx,
+                             const uint8_t* __restrict__ dirichlet) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) {
     const double v = 1.0 / c[i];
     inv_d[i] = v;
     inv_f[i] = (float)v;
+    if (inv_fx) inv_fx[i] = dirichlet[i] ? -1.f : (float)v;
   }
 }
 
@@ -756,9 +758,11 @@ cudaError_t launch_broadcast_dofs(int64_t n_dofs, int B, const double* a, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_reciprocal(int64_t n, const double* c, double* inv_d, float* inv_f, cudaStream_t s) {
+cudaError_t launch_reciprocal(int64_t n, const double* c, double* inv_d, float* inv_f, float* inv_fx,
+                              const uint8_t* dirichlet, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_reciprocal<<<grid_for(n), kBS, 0, s>>>(n, c, inv_d, inv_f);
+  if (inv_fx && !dirichlet) return cudaErrorInvalidValue;
+  k_reciprocal<<<grid_for(n), kBS, 0, s>>>(n, c, inv_d, inv_f, inv_fx, dirichlet);
   return cudaGetLastError();
 }
 

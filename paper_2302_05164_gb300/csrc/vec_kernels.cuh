@@ -21,26 +21,30 @@ struct NodalCap {
   double lat_ratio = 0.0, Tm = 0.0, inv_sigma = 0.0;  // c_app/c = 1 + lat_ratio exp(-((T-Tm) inv_sigma)^2/2)
   float lat_ratio_f = 0.f, tm_off_f = 0.f, inv_sigma_f = 0.f;  // FP32 form on T - T_ref
 };
-// The FP32-operator forward-Euler update of one dof (Eq. forward_euler): the increment
-// dt f / C~ formed in FP32 (C~: the accumulated quadrature row sum ci, or the inverse lumped
-// capacity ic of the constant c, scaled for the nodal apparent capacity by
-// 1 / (1 + lat_ratio exp(-z^2/2)) at the old state) and added to the FP64 working state tw;
-// Dirichlet dofs take tw_dir. Every kernel that advances the FP32-operator state uses it.
+// The FP32-operator increment dt f / C~ of one dof (Eq. forward_euler), formed in FP32. C~ is
+// the accumulated quadrature row sum ci, or comes from the inverse lumped capacity ic of the
+// constant c, scaled for the nodal apparent capacity by 1 / (1 + lat_ratio exp(-z^2/2)) with z
+// from the dof's FP32 value T - T_ref (value: only read for the nodal capacity).
+template <int CAP>
+__device__ __forceinline__ float increment_f32(float value, float fi, float ci, float ic, const NodalCap& nc,
+                                               float dt) {
+  if (CAP == CAP_QUADRATURE) return dt * fi / ci;
+  if (CAP == CAP_NODAL) {
+    const float z = (value + nc.tm_off_f) * nc.inv_sigma_f;
+    return __fdividef(dt * fi * ic, 1.f + nc.lat_ratio_f * __expf(-0.5f * z * z));
+  }
+  return dt * fi * ic;
+}
+
+// The FP32-operator update of the FP64 working state tw (one FP64 add); Dirichlet dofs take
+// tw_dir.
 template <int CAP>
 __device__ __forceinline__ double euler_f32(double tw, float fi, float ci, float ic, bool fixed, const NodalCap& nc,
                                             double tw_dir, float dt) {
   if (fixed) return tw_dir;
-  float inc;
-  if (CAP == CAP_QUADRATURE) {
-    inc = dt * fi / ci;
-  } else if (CAP == CAP_NODAL) {
-    const float z = (d2f_rn(tw) + nc.tm_off_f) * nc.inv_sigma_f;
-    inc = dt * fi * ic / (1.f + nc.lat_ratio_f * __expf(-0.5f * z * z));
-  } else {
-    inc = dt * fi * ic;
-  }
-  return tw + f2d(inc);
+  return tw + f2d(increment_f32<CAP>(CAP == CAP_NODAL ? d2f_rn(tw) : 0.f, fi, ci, ic, nc, dt));
 }
+
 // Transposed constraint map: for dof d the hanging rows r (weight w) that have d as a master;
 // with it the update kernel pulls f_h (and C_h) instead of a separate scatter kernel.
 struct PullMap {
@@ -73,7 +77,9 @@ cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMe
 Spot spot_at(const LaserK& k, double t);
 cudaError_t launch_to_f64(bool f32, int64_t n, const void* a, double* out, cudaStream_t s);
 cudaError_t launch_broadcast_dofs(int64_t n_dofs, int B, const double* a, double* out, cudaStream_t s);
-cudaError_t launch_reciprocal(int64_t n, const double* c, double* inv_d, float* inv_f, cudaStream_t s);
+// inv_d = 1 / c, inv_f = its FP32 rounding; inv_fx (nullable) the same with -1 at Dirichlet dofs
+cudaError_t launch_reciprocal(int64_t n, const double* c, double* inv_d, float* inv_f, float* inv_fx,
+                              const uint8_t* dirichlet, cudaStream_t s);
 // x_h = P_h x (values at hanging nodes) and f += P_h^T f_h (f_h cleared); FP32 or FP64 arrays
 cudaError_t launch_hang_values(bool f32, const DevMesh& M, const void* x, void* out, cudaStream_t s);
 cudaError_t launch_hang_distribute(bool f32, const DevMesh& M, void* fh, void* f, cudaStream_t s);
