@@ -37,8 +37,10 @@ WORKLOAD = "C2: Q2 AMR 2x2x1 mm, 5 um cells in a 150 um ball, 1.07M dofs, nonlin
 CHUNK = 50                 # explicit steps per benchmark step
 SHAPES = ["per-cell kernel, 128 threads", "per-cell kernel, 128 threads, 5 blocks/SM",
           "per-cell kernel, 128 threads, 6 blocks/SM", "per-cell kernel, 64 threads, 10 blocks/SM",
-          "fused step, 64-cell patches", "fused step, 64-cell patches, programmatic dependent launch"]
-KERNELS = ["k_cell<2,float,RESIDUAL,nonlinear>"] * 4 + ["k_step<2,nonlinear,nodal> (fused step)"] * 2
+          "fused step, 64-cell patches", "fused step, 64-cell patches, programmatic dependent launch",
+          "fused steps, one persistent cooperative launch per call"]
+KERNELS = ["k_cell<2,float,RESIDUAL,nonlinear>"] * 4 + ["k_step<2,nonlinear,nodal> (fused step)"] * 2 + \
+    ["k_steps<2,nonlinear,nodal> (persistent fused steps)"]
 BYTES_PER_DOF_UPDATE = 16  # read T_n and write T_{n+1} in FP64 (c_app(T) recomputed in-kernel)
 
 
@@ -370,13 +372,14 @@ def main():
     # roofline of the dominant kernel (cell operator), timed live with events on its stream
     avg_cell_s = cell_ms * 1e-3 / max(cell_launches, 1)
     fpc = flops_per_cell_q2_nonlinear()
-    flops_launch = fpc * info["n_active"]
+    steps_per_launch = CHUNK if variant == 6 else 1  # the persistent form runs a whole call per launch
+    flops_launch = fpc * info["n_active"] * steps_per_launch
     sm_mhz = peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
     achieved = flops_launch / avg_cell_s / 1e12
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                        "frac": achieved / fp32_peak, "traffic": traffic_for_kernel("step" if variant >= 4 else "cell"),
-                       "kernel": KERNELS[variant], "flops_per_cell": fpc,
+                       "kernel": KERNELS[variant], "flops_per_cell": fpc, "steps_per_launch": steps_per_launch,
                        "avg_launch_us": avg_cell_s * 1e6, "peak_basis": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
     hbm = peaks.get("hbm_gbs", 6800.0)
     out["hbm_fraction"] = {"algorithmic_bytes_per_dof_update": BYTES_PER_DOF_UPDATE,

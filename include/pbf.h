@@ -277,20 +277,30 @@ pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_ou
  * with 5 resident blocks per SM, 2: 6 blocks, 3: 64 threads with 10 blocks) followed by the
  * hanging-node and update kernels; 4: the fused step, one launch per step for one instance
  * with the constant or nodal capacity (patches of 64 Z-order cells staged in shared memory,
- * the previous step's update applied while staging); 5: shape 4 launched with programmatic
- * dependent launch. Where 4/5 do not apply (batch > 1, quadrature-point capacity) they run
- * the per-cell form; residual-only evaluations of shapes 4/5 use shape 1.
+ * the previous step's update applied while staging, the state kept as an FP32 pair); 5:
+ * shape 4 launched with programmatic dependent launch; 6: the fused step for all steps of a
+ * call in one persistent cooperative launch, with a grid barrier between steps whose waits
+ * end after one second with PBF_ETIMEOUT (state undefined, context still usable); shape 6
+ * synchronises the stream. Where 4-6 do not apply (batch > 1, quadrature-point capacity)
+ * they run the per-cell form; with a volumetric source shape 6 runs shape 5; residual-only
+ * evaluations of shapes 4-6 use shape 1.
  *
  * pbf_ctx_autotune times `reps` explicit steps of every applicable shape with dt = 0 on a
  * scratch copy of T_dev (not modified), with the laser of the last call, keeps the fastest in
- * the context and returns its index; us_per_step_out (nullable, 6 entries) receives each
+ * the context and returns its index; us_per_step_out (nullable, 7 entries) receives each
  * shape's microseconds per step, -1 where it does not apply. FP64 contexts keep shape 0.
  * Allocates one scratch vector; synchronises. */
 pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, float* us_per_step_out,
                             pbf_stream stream);
 
-/* Selects an explicit-step shape directly (0..5, see pbf_ctx_autotune). */
+/* Selects an explicit-step shape directly (0..6, see pbf_ctx_autotune). */
 pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape);
+
+/* Test hook for the time-out path of shape 6 (no counterpart in the paper): while
+ * extra_blocks > 0 the persistent form's grid barrier waits for that many blocks more than
+ * were launched, so its first wait runs out (after one second) and the call returns
+ * PBF_ETIMEOUT. 0 restores normal operation. */
+pbf_status pbf_ctx_set_barrier_test(pbf_ctx* ctx, int extra_blocks);
 
 /* Kernel timing of the dominant (cell operator) kernel: when enabled, CUDA events bracket
  * every cell-operator launch on its stream (the fused step kernel under shapes 4/5);

@@ -538,6 +538,8 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->xstep[0], nd);
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->xstep[1], nd);
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->invC0_fx, nd);
+    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->bar, 1);
+    if (e2 == cudaSuccess) e2 = cudaMemset(c->bar, 0, sizeof(GridBarrier));
     if (e2 == cudaSuccess) e2 = cudaMemset(c->fstep[1], 0, nd * 4);
     if (e2 == cudaSuccess) e2 = cudaMemset(c->fstep[2], 0, nd * 4);
     if (e2 != cudaSuccess) {
@@ -641,6 +643,10 @@ pbf_status CtxBase::check_usable() {
 
 pbf_status CtxBase::cuda(cudaError_t e, const char* what) {
   if (e == cudaSuccess) return PBF_OK;
+  if (barrier_timed_out) {  // a bounded device wait expired: no CUDA error, the context stays usable
+    barrier_timed_out = false;
+    return fail(PBF_ETIMEOUT, "%s: a grid barrier wait ran out of time (state left undefined)", what);
+  }
   cudaGetLastError();
   poisoned = true;
   return fail(PBF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
@@ -769,8 +775,10 @@ LaserInline CtxBase::inline_laser(double t, Spot* sp_out) const {
 // faces, and the update, which pulls the hanging-node contributions to their masters.
 cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
   if (nsteps <= 0) return cudaSuccess;
-  if ((base.variant == 4 || base.variant == 5) && fused_ok())
-    return explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant == 5, s);
+  if (base.variant >= 4 && fused_ok())
+    return base.variant == 6 && !(lsetup.k.n_seg > 0 && lsetup.k.volumetric)
+               ? explicit_steps_persistent(T_dev, t0, dt, nsteps, s)
+               : explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant == 5, s);
   CellLaunch L = base;
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
   const int64_t nv = n_dofs * batch;
@@ -837,9 +845,10 @@ cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, i
   const double xd = mat.T_dirichlet - mat.T_ref;
   const float xd_hi = (float)xd;
   const float2 x_dir = make_float2(xd_hi, (float)(xd - (double)xd_hi));
-  cudaError_t e = launch_step_prepare(n_dofs, T_dev, mat.T_ref, xstep[0], s);
-  ++launches;
+  cudaError_t e = cudaSuccess;
   StepState st;
+  st.T0 = T_dev;
+  st.off = mat.T_ref;
   st.invC0x = invC0_fx;
   st.nc = nodal;
   st.x_dir = x_dir;
@@ -867,6 +876,60 @@ cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, i
                           nsteps >= 2 ? fstep[(nsteps - 2) % 3] : nullptr, invC0_fx, nodal, x_dir, (float)dt,
                           mat.T_ref, T_dev, s);
     ++launches;
+  }
+  return e;
+}
+
+// The persistent form: one cooperative launch runs the whole sequence (grid barrier between
+// steps). It synchronises to read the barrier's time-out flag.
+cudaError_t CtxBase::explicit_steps_persistent(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
+  PersistState ps;
+  const double xd = mat.T_dirichlet - mat.T_ref;
+  const float xd_hi = (float)xd;
+  ps.st.T0 = T_dev;
+  ps.st.off = mat.T_ref;
+  ps.st.invC0x = invC0_fx;
+  ps.st.nc = nodal;
+  ps.st.x_dir = make_float2(xd_hi, (float)(xd - (double)xd_hi));
+  ps.st.dt = (float)dt;
+  ps.x[0] = xstep[0];
+  ps.x[1] = xstep[1];
+  for (int i = 0; i < 3; ++i) ps.f[i] = fstep[i];
+  ps.T = T_dev;
+  ps.nsteps = nsteps;
+  ps.t0 = t0;
+  ps.dt64 = dt;
+  ps.laser = lsetup.k;
+  ps.las = inline_laser(t0, nullptr);
+  if (lsetup.k.n_seg > 0) {  // constants of the surface laser; the spot follows per step
+    const double r = lsetup.k.radius;
+    ps.las.on = 1;
+    ps.las.amp = 2.0 * lsetup.k.eta / (kPi * r * r);
+    ps.las.ir2 = 2.0 / (r * r);
+    ps.las.cut2 = 36.0 * r * r;
+    ps.las.power = power;
+    ps.las.powerf = powerf;
+  }
+  ps.bar = bar;
+  ps.extra_arrivals = barrier_test_extra;
+  barrier_timed_out = false;
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(GridBarrier), s);
+  const auto ev = timing && e == cudaSuccess ? timing_begin(s) : std::pair<cudaEvent_t, cudaEvent_t>{};
+  if (e == cudaSuccess) e = launch_steps_persistent(base, step, ps, cap, nullptr, s);
+  ++launches;
+  if (ev.first) timing_end(ev, s);
+  unsigned flag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, &bar->err, sizeof(flag), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && flag) {
+    // the sequence stopped part-way: clear the accumulators so that the next call starts
+    // from the usual all-zero state
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaMemsetAsync(fstep[i], 0, (size_t)n_dofs * 4, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) {
+      barrier_timed_out = true;
+      e = cudaErrorTimeout;
+    }
   }
   return e;
 }
@@ -986,8 +1049,14 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
 }
 
 extern "C" pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape) {
-  if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, 5]");
+  if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, 6]");
   ctx->base.variant = shape;
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_ctx_set_barrier_test(pbf_ctx* ctx, int extra_blocks) {
+  if (!ctx || extra_blocks < 0) return fail(PBF_EINVAL, "bad arguments");
+  ctx->barrier_test_extra = (unsigned)extra_blocks;
   return PBF_OK;
 }
 

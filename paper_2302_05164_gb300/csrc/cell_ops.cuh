@@ -70,23 +70,24 @@ __device__ __forceinline__ constexpr double wq3(int q) {
 // points, added to the top-face nodes of fe; skipped when the face lies farther than 6 r from
 // the spot (the integrand is below e^-72 there). Offsets from the spot in FP64, the rest in R.
 template <int P, typename R>
-__device__ __forceinline__ void add_laser(const CellLaunch& L, int cell, int inst, int lev, R* fe) {
+__device__ __forceinline__ void add_laser(const CellLaunch& L, const LaserInline& las, int cell, int inst, int lev,
+                                          R* fe) {
   constexpr int N = P + 1;
   const GeoR<R>& geo = geo_of<R>(L);
   R ox, oy, amp;
   if (sizeof(R) == 4) {  // FP32 operator: positions and powers in FP32 too
-    ox = R(L.mesh.cell_lof[3 * cell] - float(L.las.sx));
-    oy = R(L.mesh.cell_lof[3 * cell + 1] - float(L.las.sy));
-    amp = R(float(L.las.amp) * L.las.powerf[inst * kMaxSeg + L.las.seg]);
+    ox = R(L.mesh.cell_lof[3 * cell] - float(las.sx));
+    oy = R(L.mesh.cell_lof[3 * cell + 1] - float(las.sy));
+    amp = R(float(las.amp) * las.powerf[inst * kMaxSeg + las.seg]);
   } else {
-    ox = R(L.mesh.cell_lo[3 * cell] - L.las.sx);
-    oy = R(L.mesh.cell_lo[3 * cell + 1] - L.las.sy);
-    amp = R(L.las.amp * L.las.power[inst * kMaxSeg + L.las.seg]);
+    ox = R(L.mesh.cell_lo[3 * cell] - las.sx);
+    oy = R(L.mesh.cell_lo[3 * cell + 1] - las.sy);
+    amp = R(las.amp * las.power[inst * kMaxSeg + las.seg]);
   }
   const R hx = geo.h[lev][0], hy = geo.h[lev][1];
   const R gx = max(R(0), max(ox, -(ox + hx))), gy = max(R(0), max(oy, -(oy + hy)));
-  if (gx * gx + gy * gy > R(L.las.cut2)) return;
-  const R ir2 = R(L.las.ir2);
+  if (gx * gx + gy * gy > R(las.cut2)) return;
+  const R ir2 = R(las.ir2);
 #pragma unroll
   for (int qy = 0; qy < N; ++qy)
 #pragma unroll

@@ -138,6 +138,29 @@ struct Spot {
   int seg = -1;
 };
 
+// The spot at time t: the first segment with t0 <= t < t1, moving linearly from (x0, y0) to
+// (x1, y1). Host and device evaluate it with the same correctly rounded FP64 operations.
+__host__ __device__ inline Spot spot_at(const LaserK& k, double t) {
+  Spot sp;
+  for (int i = 0; i < k.n_seg; ++i) {
+    const double* g = k.seg[i];
+    if (t >= g[4] && t < g[5]) {
+#ifdef __CUDA_ARCH__
+      const double a = __ddiv_rn(__dsub_rn(t, g[4]), __dsub_rn(g[5], g[4]));
+      sp.x = __dadd_rn(g[0], __dmul_rn(__dsub_rn(g[2], g[0]), a));
+      sp.y = __dadd_rn(g[1], __dmul_rn(__dsub_rn(g[3], g[1]), a));
+#else
+      const double a = (t - g[4]) / (g[5] - g[4]);
+      sp.x = g[0] + (g[2] - g[0]) * a;
+      sp.y = g[1] + (g[3] - g[1]) * a;
+#endif
+      sp.seg = i;
+      return sp;
+    }
+  }
+  return sp;
+}
+
 // ---- launchers (kernels_cell.cu) --------------------------------------------------------
 enum CellMode {
   MODE_RESIDUAL = 0,  // f += f_diff(T), C += lumped capacity (when C != null)
@@ -179,8 +202,9 @@ struct CellLaunch {
 // residual kernel {threads per block, minimum resident blocks per SM} = {128, 1}, {128, 5},
 // {128, 6}, {64, 10} (the second bounds registers per thread), followed by the update kernel;
 // 4: the fused step kernel (one instance, constant or nodal capacity), 5: the same launched
-// with programmatic dependent launch. Residual-only launches of shapes 4 and 5 use shape 1.
-constexpr int kCellVariants = 6;
+// with programmatic dependent launch, 6: all steps in one persistent cooperative launch.
+// Residual-only launches of shapes 4-6 use shape 1.
+constexpr int kCellVariants = 7;
 
 template <typename R>
 __host__ __device__ inline const GeoR<R>& geo_of(const CellLaunch& L);

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(BS, MINB) k_cell(const CellLaunch L, R* __rest
   }
   R fe[NP];
   integrate_values<P, R>(r, fe);
-  if (MODE == MODE_RESIDUAL && L.las.on && M.cell_top[cell]) add_laser<P, R>(L, cell, inst, lev, fe);
+  if (MODE == MODE_RESIDUAL && L.las.on && M.cell_top[cell]) add_laser<P, R>(L, L.las, cell, inst, lev, fe);
   scatter<P, R>(M, f, fh, cell, inst, fe);
 }
 
@@ -340,8 +340,9 @@ cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaSt
   if (std::is_same<R, float>::value && MODE == MODE_RESIDUAL && !LAT) {
     switch (L.variant) {
       case 1:
-      case 4:  // shape 4 is the fused explicit step; residual-only launches use shape 1
-      case 5: return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
+      case 4:  // shapes 4-6 are forms of the fused explicit step; residual-only launches use shape 1
+      case 5:
+      case 6: return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
       case 2: return go_shape<P, R, MODE, NLK, LAT, 128, 6>(L, f, fh, C, Ch, s);
       case 3: return go_shape<P, R, MODE, NLK, LAT, 64, 10>(L, f, fh, C, Ch, s);
       default: break;

@@ -16,6 +16,7 @@
 // value is read about 1.4 times instead of once per adjacent cell (up to 8 for Q2 vertices),
 // its contributions are added with one global atomic per patch instead of one per cell, and
 // the update costs no launch of its own.
+#include <algorithm>
 #include <utility>
 
 #include "cell_ops.cuh"
@@ -30,39 +31,66 @@ __device__ __forceinline__ void grid_dependency_trigger() { asm volatile("gridde
 constexpr int kStepMinBlocks = 10;  // 64-thread blocks: at most 102 registers per thread
 constexpr int kStageUnroll = 8;     // dof slots each thread has in flight while staging
 
-template <int P, bool NLK, int CAP>
-__global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
-    k_step(const CellLaunch L, const StepTables T, const StepState S) {
+// Loads of data that changes between steps: through the read-only path when each step is its
+// own launch, through L2 only (coherent with other blocks' stores) inside a persistent launch.
+template <bool COHERENT, typename V>
+__device__ __forceinline__ V ld_step(const V* p) {
+  if (COHERENT) return __ldcg(p);
+  return __ldg(p);
+}
+
+// Shared-memory layout of one block (dynamic shared memory, sized by step_smem_bytes).
+template <int NP>
+struct StepSmem {
+  uint16_t* loc;   // [NP][kStepCells] shared position of each cell node
+  int32_t* slot;   // [max_nu32] the patch's slot list
+  float* v;        // [max_nu32] staged values, swizzled
+  float* f;        // [max_nu32] accumulated contributions, swizzled
+  float* hw;       // [max_hent8] hanging-table weights
+  uint16_t* hl;    // [max_hent8] hanging-table master positions
+  __device__ StepSmem(unsigned char* base, const StepTables& T) {
+    loc = reinterpret_cast<uint16_t*>(base);
+    slot = reinterpret_cast<int32_t*>(base + NP * kStepCells * 2);
+    v = reinterpret_cast<float*>(slot + T.max_nu32);
+    f = v + T.max_nu32;
+    hw = f + T.max_nu32;
+    hl = reinterpret_cast<uint16_t*>(hw + T.max_hent8);
+  }
+};
+
+// Patch tables into shared memory (they never change: read-only path).
+template <int NP>
+__device__ __forceinline__ void load_patch_tables(const StepTables& T, const StepSmem<NP>& sm, int p, int4& cn) {
+  constexpr int KP = kStepCells;
+  const int tid = threadIdx.x;
+  const int p0 = __ldg(&T.ptr[p]);
+  cn = __ldg(&T.cnt[p]);
+  const uint4* src = reinterpret_cast<const uint4*>(T.loc + (size_t)p * NP * KP);
+  uint4* dst = reinterpret_cast<uint4*>(sm.loc);
+#pragma unroll 4
+  for (int i = tid; i < NP * KP / 8; i += KP) dst[i] = __ldg(&src[i]);
+  const int4* s4 = reinterpret_cast<const int4*>(T.slot + p0);
+  int4* d4 = reinterpret_cast<int4*>(sm.slot);
+  const int n4 = (cn.y + 3) >> 2;
+  for (int i = tid; i < n4; i += KP) d4[i] = __ldg(&s4[i]);
+  const int hb = cn.z, nh = cn.w - cn.z;
+  for (int i = tid; i < nh; i += KP) {
+    sm.hl[i] = __ldg(&T.hloc[hb + i]);
+    sm.hw[i] = __ldg(&T.hw[hb + i]);
+  }
+}
+
+// Steps 2-4 of one patch (tables already in shared memory, a barrier after loading them):
+// staging with the previous step's update, hanging values, the cells, the push of hanging
+// sums and the scatter of the dof sums into S.f_acc.
+template <int P, bool NLK, int CAP, bool COHERENT>
+__device__ __forceinline__ void step_patch(const CellLaunch& L, const LaserInline& las, const StepState& S,
+                                           const StepSmem<(P + 1) * (P + 1) * (P + 1)>& sm, int p, int4 cn) {
   constexpr int N = P + 1, NP = N * N * N, KP = kStepCells, U = kStageUnroll;
   (void)N;
-  extern __shared__ __align__(16) unsigned char smem[];
-  uint16_t* sloc = reinterpret_cast<uint16_t*>(smem);                // [NP][KP]
-  int32_t* sslot = reinterpret_cast<int32_t*>(smem + NP * KP * 2);   // [max_nu32]
-  float* sv = reinterpret_cast<float*>(sslot + T.max_nu32);          // staged values (swizzled)
-  float* sf = sv + T.max_nu32;                                       // contributions (swizzled)
-  float* shw = sf + T.max_nu32;                                      // [max_hent8] weights
-  uint16_t* shl = reinterpret_cast<uint16_t*>(shw + T.max_hent8);    // [max_hent8] master positions
   const DevMesh& M = L.mesh;
-  const int p = blockIdx.x, tid = threadIdx.x;
-  const int p0 = __ldg(&T.ptr[p]);
-  const int4 cn = __ldg(&T.cnt[p]);
-  const int nfree = cn.x, nu = cn.y, hb = cn.z, nh = cn.w - cn.z;
-
-  // 1. tables (16-byte loads; the loc table of a patch is NP * KP * 2 bytes, a multiple of 16)
-  {
-    const uint4* src = reinterpret_cast<const uint4*>(T.loc + (size_t)p * NP * KP);
-    uint4* dst = reinterpret_cast<uint4*>(sloc);
-#pragma unroll 4
-    for (int i = tid; i < NP * KP / 8; i += KP) dst[i] = __ldg(&src[i]);
-    const int4* s4 = reinterpret_cast<const int4*>(T.slot + p0);
-    int4* d4 = reinterpret_cast<int4*>(sslot);
-    const int n4 = (nu + 3) >> 2;
-    for (int i = tid; i < n4; i += KP) d4[i] = __ldg(&s4[i]);
-    for (int i = tid; i < nh; i += KP) {
-      shl[i] = __ldg(&T.hloc[hb + i]);
-      shw[i] = __ldg(&T.hw[hb + i]);
-    }
-  }
+  const int tid = threadIdx.x;
+  const int nfree = cn.x, nu = cn.y;
   const int c0 = p * KP, ncell = min(KP, M.n_cells - c0);
   const int cell = c0 + tid;
   const bool active = tid < ncell;
@@ -72,10 +100,8 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     mat = __ldg(&M.cell_mat[cell]);
     top = __ldg(&M.cell_top[cell]);
   }
-  grid_dependency_wait();  // the previous step's state and accumulators are complete
-  __syncthreads();
-
-  // 2a. dof slots: U independent slots in flight per thread
+  // 2a. dof slots, U independent slots in flight per thread. Step 0 takes the state as given
+  // (T - T_ref split into hi + lo); later steps complete the previous step first.
   for (int j0 = 0; j0 < nfree; j0 += KP * U) {
     int g[U];
     float2 x[U];
@@ -83,25 +109,35 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * KP + tid;
-      g[u] = j < nfree ? (sslot[j] & 0x7fffffff) : -1;
+      g[u] = j < nfree ? (sm.slot[j] & 0x7fffffff) : -1;
     }
+    if (S.first) {
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int d = g[u] < 0 ? 0 : g[u];
-      x[u] = __ldg(&S.x_in[d]);
-      fi[u] = __ldg(&S.f_in[d]);
-      ic[u] = __ldg(&S.invC0x[d]);
+      for (int u = 0; u < U; ++u) {
+        const double v = __ldg(&S.T0[g[u] < 0 ? 0 : g[u]]) - S.off;
+        const float hi = d2f_rn(v);
+        x[u] = make_float2(hi, d2f_rn(v - f2d(hi)));
+      }
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int d = g[u] < 0 ? 0 : g[u];
+        x[u] = ld_step<COHERENT>(&S.x_in[d]);
+        fi[u] = ld_step<COHERENT>(&S.f_in[d]);
+        ic[u] = __ldg(&S.invC0x[d]);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) x[u] = euler_ff<CAP>(x[u], fi[u], ic[u], S.nc, S.x_dir, S.dt);
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int j = j0 + u * KP + tid;
       if (g[u] >= 0) {
-        const float2 t = S.first ? x[u] : euler_ff<CAP>(x[u], fi[u], ic[u], S.nc, S.x_dir, S.dt);
         const int q = step_swizzle(j);
-        sv[q] = t.x;
-        sf[q] = 0.f;
-        if (sslot[j] < 0) {
-          S.x_out[g[u]] = t;
+        sm.v[q] = x[u].x;
+        sm.f[q] = 0.f;
+        if (sm.slot[j] < 0) {
+          S.x_out[g[u]] = x[u];
           S.f_clear[g[u]] = 0.f;
         }
       }
@@ -110,12 +146,12 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
   __syncthreads();
   // 2b. hanging slots from their masters in shared memory: x_h = sum_m w_m x_m
   for (int j = nfree + tid; j < nu; j += KP) {
-    const int h = sslot[j], e0 = h >> 5, ne = h & 31;
+    const int h = sm.slot[j], e0 = h >> 5, ne = h & 31;
     float val = 0.f;
-    for (int e = e0; e < e0 + ne; ++e) val += shw[e] * sv[shl[e]];
+    for (int e = e0; e < e0 + ne; ++e) val += sm.hw[e] * sm.v[sm.hl[e]];
     const int q = step_swizzle(j);
-    sv[q] = val;
-    sf[q] = 0.f;
+    sm.v[q] = val;
+    sm.f[q] = 0.f;
   }
   __syncthreads();
 
@@ -125,7 +161,7 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     const GeoR<float>& geo = L.gf;
     float u[NP], v[NP];
 #pragma unroll
-    for (int a = 0; a < NP; ++a) u[a] = sv[sloc[a * KP + tid]];
+    for (int a = 0; a < NP; ++a) u[a] = sm.v[sm.loc[a * KP + tid]];
     values_at_qp<P, float>(u, v);
     const float detJ = geo.detJ[lev];
     const float scale = (mat == 1 ? mt.powder_scale : 1.f) * (L.k_scale_f ? L.k_scale_f[0] : 1.f);
@@ -161,24 +197,147 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     }
     float fe[NP];
     integrate_values<P, float>(r, fe);
-    if (L.las.on && top) add_laser<P, float>(L, cell, 0, lev, fe);
+    if (las.on && top) add_laser<P, float>(L, las, cell, 0, lev, fe);
 #pragma unroll
-    for (int a = 0; a < NP; ++a) atomicAdd(&sf[sloc[a * KP + tid]], fe[a]);
+    for (int a = 0; a < NP; ++a) atomicAdd(&sm.f[sm.loc[a * KP + tid]], fe[a]);
   }
   __syncthreads();
-  grid_dependency_trigger();  // the next step may start loading its tables
+  if (!COHERENT) grid_dependency_trigger();  // the next step may start loading its tables
   // 4a. hanging contributions to their masters (P_h^T f_h), in shared memory
   for (int j = nfree + tid; j < nu; j += KP) {
-    const int h = sslot[j], e0 = h >> 5, ne = h & 31;
-    const float val = sf[step_swizzle(j)];
+    const int h = sm.slot[j], e0 = h >> 5, ne = h & 31;
+    const float val = sm.f[step_swizzle(j)];
     if (val != 0.f)
-      for (int e = e0; e < e0 + ne; ++e) atomicAdd(&sf[shl[e]], shw[e] * val);
+      for (int e = e0; e < e0 + ne; ++e) atomicAdd(&sm.f[sm.hl[e]], sm.hw[e] * val);
   }
   __syncthreads();
   // 4b. one global addition per dof slot
   for (int j = tid; j < nfree; j += KP) {
-    const float val = sf[step_swizzle(j)];
-    if (val != 0.f) atomicAdd(&S.f_acc[sslot[j] & 0x7fffffff], val);
+    const float val = sm.f[step_swizzle(j)];
+    if (val != 0.f) atomicAdd(&S.f_acc[sm.slot[j] & 0x7fffffff], val);
+  }
+}
+
+// One launch per step: block p takes patch p.
+template <int P, bool NLK, int CAP>
+__global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
+    k_step(const CellLaunch L, const StepTables T, const StepState S) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const StepSmem<NP> sm(smem, T);
+  int4 cn;
+  load_patch_tables<NP>(T, sm, blockIdx.x, cn);
+  grid_dependency_wait();  // the previous step's state and accumulators are complete
+  __syncthreads();
+  step_patch<P, NLK, CAP, false>(L, L.las, S, sm, blockIdx.x, cn);
+}
+
+// ---- persistent form: all steps of a sequence in one cooperative launch -----------------
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Grid-wide barrier of a cooperative launch (all blocks resident). Sense by generation: the
+// last block to arrive resets the count and advances the generation. A wait longer than
+// kBarrierTimeoutNs, or an error flagged by another block, makes every block return false;
+// the caller then leaves the kernel, so no block waits twice.
+constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
+__device__ bool grid_sync(GridBarrier* gb, unsigned nblocks, unsigned& gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicAdd(&gb->gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      while (ld_acquire_gpu(&gb->gen) == gen) {
+        if (ld_acquire_gpu(&gb->err) != 0u) {
+          ok = 0;
+          break;
+        }
+        if (global_ns() - t0 > kBarrierTimeoutNs) {
+          atomicExch(&gb->err, 1u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    gen += 1;
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int P, bool NLK, int CAP>
+__global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
+    k_steps(const CellLaunch L, const StepTables T, const PersistState A) {
+  constexpr int NP = (P + 1) * (P + 1) * (P + 1);
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ LaserInline s_las;
+  __shared__ unsigned s_gen0;
+  const StepSmem<NP> sm(smem, T);
+  if (threadIdx.x == 0) s_gen0 = ld_acquire_gpu(&A.bar->gen);  // no barrier completes before all blocks arrive
+  unsigned gen = 0;
+  __syncthreads();
+  gen = s_gen0;
+  StepState S = A.st;
+  for (int n = 0; n < A.nsteps; ++n) {
+    S.x_in = A.x[n & 1];
+    S.x_out = A.x[(n + 1) & 1];
+    S.f_in = A.f[(n + 2) % 3];
+    S.f_acc = A.f[n % 3];
+    S.f_clear = A.f[(n + 1) % 3];
+    S.first = n == 0;
+    if (threadIdx.x == 0) {
+      LaserInline las = A.las;
+      const Spot sp = spot_at(A.laser, A.t0 + n * A.dt64);
+      las.on = A.las.on && sp.seg >= 0;
+      las.seg = sp.seg;
+      las.sx = sp.x;
+      las.sy = sp.y;
+      s_las = las;
+    }
+    for (int p = blockIdx.x; p < T.n_patches; p += gridDim.x) {
+      __syncthreads();  // the previous patch is done with shared memory; s_las is set
+      int4 cn;
+      load_patch_tables<NP>(T, sm, p, cn);
+      __syncthreads();
+      step_patch<P, NLK, CAP, true>(L, s_las, S, sm, p, cn);
+    }
+    if (!grid_sync(A.bar, gridDim.x + A.extra_arrivals, gen)) return;
+  }
+  // the last update: T = T_ref + x_{N-1} + dt f_{N-1} / C~ on owned dofs; clear f_{N-1}, f_{N-2}
+  const float2* x_last = A.x[A.nsteps & 1];
+  float* f_last = A.f[(A.nsteps - 1) % 3];
+  float* f_prev = A.nsteps >= 2 ? A.f[(A.nsteps - 2) % 3] : nullptr;
+  for (int p = blockIdx.x; p < T.n_patches; p += gridDim.x) {
+    const int p0 = __ldg(&T.ptr[p]);
+    const int nfree = __ldg(&T.cnt[p]).x;
+    for (int j = threadIdx.x; j < nfree; j += kStepCells) {
+      const int s = __ldg(&T.slot[p0 + j]);
+      if (s >= 0) continue;
+      const int d = s & 0x7fffffff;
+      const float2 t = euler_ff<CAP>(__ldcg(&x_last[d]), __ldcg(&f_last[d]), __ldg(&A.st.invC0x[d]), A.st.nc,
+                                     A.st.x_dir, A.st.dt);
+      A.T[d] = A.st.off + (f2d(t.x) + f2d(t.y));
+      f_last[d] = 0.f;
+      if (f_prev) f_prev[d] = 0.f;
+    }
   }
 }
 
@@ -194,29 +353,25 @@ __global__ void k_step_final(int n, const float2* __restrict__ x_in, float* __re
   if (f_other) f_other[i] = 0.f;
 }
 
-// x = T - off as hi + lo: the FP64 difference is exact to 53 bits, hi its FP32 rounding and
-// lo = (T - off - hi) rounded (the FP64 subtraction is exact)
-__global__ void k_step_prepare(int n, const double* __restrict__ T, double off, float2* __restrict__ x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const double v = T[i] - off;
-  const float hi = d2f_rn(v);
-  x[i] = make_float2(hi, d2f_rn(v - f2d(hi)));
-}
-
+// attr: 0 plain, 1 programmatic stream serialisation, 2 cooperative
 template <typename... KArgs, typename... Args>
-cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, bool pdl, cudaStream_t s,
-                      Args&&... args) {
+cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, int attr_kind,
+                      cudaStream_t s, Args&&... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = pdl ? attr : nullptr;
-  cfg.numAttrs = pdl ? 1 : 0;
+  if (attr_kind == 1) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+  } else {
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+  }
+  cfg.attrs = attr_kind ? attr : nullptr;
+  cfg.numAttrs = attr_kind ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
@@ -227,7 +382,7 @@ cudaError_t go_step(const CellLaunch& L, const StepTables& t, const StepState& s
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
     if (e != cudaSuccess) return e;
   }
-  return launch_ex(kern, (unsigned)t.n_patches, kStepCells, (size_t)t.smem, pdl, s, L, t, st);
+  return launch_ex(kern, (unsigned)t.n_patches, kStepCells, (size_t)t.smem, pdl ? 1 : 0, s, L, t, st);
 }
 
 template <int P>
@@ -238,7 +393,45 @@ cudaError_t dispatch_step(const CellLaunch& L, const StepTables& t, const StepSt
   return nl ? go_step<P, true, CAP_CONST>(L, t, st, pdl, s) : go_step<P, false, CAP_CONST>(L, t, st, pdl, s);
 }
 
+template <int P, bool NLK, int CAP>
+cudaError_t go_steps(const CellLaunch& L, const StepTables& t, const PersistState& ps, int* blocks, cudaStream_t s) {
+  auto kern = k_steps<P, NLK, CAP>;
+  cudaError_t e = cudaSuccess;
+  if (t.smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kStepCells, (size_t)t.smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = std::min(t.n_patches, nsm * per_sm);
+  if (blocks) *blocks = grid;
+  return launch_ex(kern, (unsigned)grid, kStepCells, (size_t)t.smem, 2, s, L, t, ps);
+}
+
+template <int P>
+cudaError_t dispatch_steps(const CellLaunch& L, const StepTables& t, const PersistState& ps, int cap, int* blocks,
+                           cudaStream_t s) {
+  const bool nl = L.nonlin_k != 0;
+  if (cap == CAP_NODAL)
+    return nl ? go_steps<P, true, CAP_NODAL>(L, t, ps, blocks, s) : go_steps<P, false, CAP_NODAL>(L, t, ps, blocks, s);
+  return nl ? go_steps<P, true, CAP_CONST>(L, t, ps, blocks, s) : go_steps<P, false, CAP_CONST>(L, t, ps, blocks, s);
+}
+
 }  // namespace
+
+cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, const PersistState& ps, int cap,
+                                    int* blocks, cudaStream_t s) {
+  const StepState& st = ps.st;
+  if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
+      !t.hloc || !t.hw || !ps.x[0] || !ps.x[1] || !ps.f[0] || !ps.f[1] || !ps.f[2] || !ps.T || !st.T0 ||
+      !st.invC0x || !ps.bar || ps.nsteps < 1 || ps.laser.volumetric)
+    return cudaErrorInvalidValue;
+  if (t.n_patches == 0) return cudaSuccess;
+  if (L.degree == 1) return dispatch_steps<1>(L, t, ps, cap, blocks, s);
+  if (L.degree == 2) return dispatch_steps<2>(L, t, ps, cap, blocks, s);
+  return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                         cudaStream_t s) {
@@ -251,13 +444,6 @@ cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepStat
   if (L.degree == 1) return dispatch_step<1>(L, t, st, cap, pdl, s);
   if (L.degree == 2) return dispatch_step<2>(L, t, st, cap, pdl, s);
   return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_step_prepare(int64_t n_dofs, const double* T, double off, float2* x, cudaStream_t s) {
-  if (n_dofs == 0) return cudaSuccess;
-  const int bs = 256;
-  k_step_prepare<<<(unsigned)((n_dofs + bs - 1) / bs), bs, 0, s>>>((int)n_dofs, T, off, x);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_step_final(int cap, int64_t n_dofs, const float2* x_in, float* f_in, float* f_other,

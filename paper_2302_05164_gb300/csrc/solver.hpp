@@ -70,6 +70,9 @@ struct CtxBase {
   float* fstep[3] = {nullptr, nullptr, nullptr};
   float2* xstep[2] = {nullptr, nullptr};
   float* invC0_fx = nullptr;
+  GridBarrier* bar = nullptr;  // grid barrier of the persistent form
+  unsigned barrier_test_extra = 0;  // test hook (pbf_ctx_set_barrier_test)
+  bool barrier_timed_out = false;   // the last persistent launch's barrier ran out of time
   double* C0 = nullptr;  // lumped capacity with the plain c [n_dofs]
   double* invC0_d = nullptr;
   float* invC0_f = nullptr;
@@ -99,9 +102,10 @@ struct CtxBase {
   // f_diff, f_vol and C~ at T in FP64 (laser set beforehand; any output may be null)
   cudaError_t residual_f64(const double* T, double t, double* fd, double* fv, double* C, cudaStream_t s);
   // nsteps forward-Euler steps in place on T (laser set beforehand); the fused form runs when
-  // the context's shape is 4 or 5 and fused_ok()
+  // the context's shape is 4, 5 or 6 (persistent; not with a volumetric source) and fused_ok()
   cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
   cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, cudaStream_t s);
+  cudaError_t explicit_steps_persistent(double* T, double t0, double dt, int nsteps, cudaStream_t s);
   bool fused_ok() const { return f32 && batch == 1 && cap != CAP_QUADRATURE && step.n_patches > 0; }
   // the surface laser of the cell kernels at time t (off for the volumetric source)
   LaserInline inline_laser(double t, Spot* sp) const;

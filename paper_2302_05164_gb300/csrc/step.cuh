@@ -59,7 +59,9 @@ __device__ __forceinline__ float2 ff_add(float2 x, float b) {
 // accumulates f_n = f(T_n) (diffusion and surface laser) and clears the accumulator of step
 // n+1. Three accumulators rotate so that no launch reads a buffer that it also writes.
 struct StepState {
-  const float2* x_in = nullptr;   // T_{n-1} - T_ref as hi + lo (n = 0: T_0 - T_ref)
+  const double* T0 = nullptr;     // step 0: the state T_0 as given (FP64)
+  double off = 0.0;               // T_ref
+  const float2* x_in = nullptr;   // T_{n-1} - T_ref as hi + lo (unused when first)
   float2* x_out = nullptr;        // T_n - T_ref (owned dofs written)
   const float* f_in = nullptr;    // f_{n-1} (unused when first)
   float* f_acc = nullptr;         // f_n, zero on entry
@@ -83,8 +85,27 @@ __device__ __forceinline__ float2 euler_ff(float2 x, float fi, float ic, const N
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                         cudaStream_t s);
 
-// x = T - off split into hi + lo (hi = T - off rounded to FP32, lo = the rest rounded)
-cudaError_t launch_step_prepare(int64_t n_dofs, const double* T, double off, float2* x, cudaStream_t s);
+// Persistent form: every step of a sequence in one cooperative launch, a grid-wide barrier
+// between steps, the spot of each step computed on the device, and the last update applied
+// by the owners after the last barrier (T written in FP64, f_{N-1} and f_{N-2} cleared).
+struct GridBarrier {
+  unsigned count = 0, gen = 0, err = 0, pad = 0;  // err: a wait ran out of time (set once)
+};
+struct PersistState {
+  StepState st;             // constants; the per-step pointers rotate inside the kernel
+  float2* x[2] = {nullptr, nullptr};
+  float* f[3] = {nullptr, nullptr, nullptr};
+  double* T = nullptr;      // state in (step 0, through st.T0) and out (after the last step)
+  int nsteps = 0;
+  double t0 = 0.0, dt64 = 0.0;
+  LaserInline las;          // surface laser constants (spot and segment filled per step)
+  LaserK laser;             // segments (n_seg = 0: no laser)
+  GridBarrier* bar = nullptr;  // zeroed before the launch
+  unsigned extra_arrivals = 0; // test hook: barriers wait for this many blocks more than launched
+};
+// blocks: set to the grid size used (all blocks resident). Volumetric lasers are not covered.
+cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, const PersistState& ps, int cap,
+                                    int* blocks, cudaStream_t s);
 
 // The last update of a sequence, T = off + T_{N-1} + dt f_{N-1} / C~ (FP64 out), clearing f_in
 // and f_other (nullable): afterwards all three accumulators are zero again.

@@ -631,21 +631,6 @@ __global__ void k_transfer(int64_t n_new, int B, const int32_t* __restrict__ ptr
 
 // ---- host launchers -------------------------------------------------------------------------
 
-Spot spot_at(const LaserK& k, double t) {
-  Spot sp;
-  for (int i = 0; i < k.n_seg; ++i) {
-    const double* g = k.seg[i];
-    if (t >= g[4] && t < g[5]) {
-      const double a = (t - g[4]) / (g[5] - g[4]);
-      sp.x = g[0] + (g[2] - g[0]) * a;
-      sp.y = g[1] + (g[3] - g[1]) * a;
-      sp.seg = i;
-      return sp;
-    }
-  }
-  return sp;
-}
-
 cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double* f, double* Cacc,
                               const double* invC0, const NodalCap& nc, const uint8_t* dirichlet, double T_dir,
                               double dt, cudaStream_t s, const PullMap& pm) {

@@ -73,8 +73,6 @@ cudaError_t launch_round_f32(int64_t n, const double* x, float* y, cudaStream_t 
 cudaError_t launch_f32_to_f64(int64_t n, const float* x, double* y, cudaStream_t s);
 cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const double* power,
                          const Spot& sp, void* f, cudaStream_t s);
-// Host evaluation of the spot at time t (first segment with t0 <= t < t1, linear motion).
-Spot spot_at(const LaserK& k, double t);
 cudaError_t launch_to_f64(bool f32, int64_t n, const void* a, double* out, cudaStream_t s);
 cudaError_t launch_broadcast_dofs(int64_t n_dofs, int B, const double* a, double* out, cudaStream_t s);
 // inv_d = 1 / c, inv_f = its FP32 rounding; inv_fx (nullable) the same with -1 at Dirichlet dofs

@@ -91,6 +91,7 @@ _SIGS = {
     "pbf_widen_to_f64": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p], C.c_int),
     "pbf_ctx_autotune": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p], C.c_int),
     "pbf_ctx_set_kernel_shape": ([C.c_void_p, C.c_int], C.c_int),
+    "pbf_ctx_set_barrier_test": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_set_timing": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_kernel_time": ([C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
     "pbf_ctx_launch_count": ([C.c_void_p, C.POINTER(C.c_longlong)], C.c_int),
@@ -299,7 +300,7 @@ def pbf_widen_to_f64(x, y, n, stream=None):
     _check(lib().pbf_widen_to_f64(_ptr(x), _ptr(y), int(n), _stream(stream)))
 
 
-N_SHAPES = 6
+N_SHAPES = 7
 
 
 def pbf_ctx_autotune(h, T, reps=5, stream=None, times=False):
@@ -314,6 +315,10 @@ def pbf_ctx_autotune(h, T, reps=5, stream=None, times=False):
 
 def pbf_ctx_set_kernel_shape(h, shape):
     _check(lib().pbf_ctx_set_kernel_shape(h, int(shape)))
+
+
+def pbf_ctx_set_barrier_test(h, extra_blocks):
+    _check(lib().pbf_ctx_set_barrier_test(h, int(extra_blocks)))
 
 
 def pbf_ctx_set_timing(h, enable):

@@ -134,7 +134,7 @@ def test_amr_q2_nonlinear_latent_steps(P, oracle_mod, prec):
     assert rel(got, ref) < (TOL64 if prec == "f64" else TOL32_T)
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
 def test_every_kernel_shape_matches_oracle(P, oracle_mod, shape):
     """Each explicit-step shape the autotuner can pick (the per-cell kernel's launch shapes,
     and the fused patch step kernel with and without programmatic dependent launch) gives the

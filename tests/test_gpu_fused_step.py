@@ -15,7 +15,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL32_T = 2e-4
-FUSED, FUSED_PDL, PER_CELL = 4, 5, 1
+FUSED, FUSED_PDL, PERSISTENT, PER_CELL = 4, 5, 6, 1
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +68,7 @@ def fused_run(P, desc, mat, T0, ls, t0, dt, calls, shape=FUSED):
 
 @pytest.mark.parametrize("degree", [1, 2])
 @pytest.mark.parametrize("mat", ["const", "nonlin_nodal"])
-@pytest.mark.parametrize("shape", [FUSED, FUSED_PDL])
+@pytest.mark.parametrize("shape", [FUSED, FUSED_PDL, PERSISTENT])
 def test_fused_steps_match_oracle(P, oracle_mod, degree, mat, shape):
     desc = amr(degree)
     material = I.TI64_CONST if mat == "const" else I.TI64_NONLIN_Q2
@@ -82,8 +82,9 @@ def test_fused_steps_match_oracle(P, oracle_mod, degree, mat, shape):
     assert np.abs(ref - T0).max() > 1.0  # the steps changed the field
 
 
+@pytest.mark.parametrize("shape", [FUSED, PERSISTENT])
 @pytest.mark.parametrize("nsteps", [1, 2, 3])
-def test_short_sequences_rotate_accumulators(P, oracle_mod, nsteps):
+def test_short_sequences_rotate_accumulators(P, oracle_mod, nsteps, shape):
     """1, 2 and 3 steps (every position of the three-buffer rotation at the final update),
     each followed by a residual that must find all accumulators cleared."""
     desc = amr(2)
@@ -93,7 +94,7 @@ def test_short_sequences_rotate_accumulators(P, oracle_mod, nsteps):
     T0 = I.smooth_field(om.dof_xyz(), seed=12, lo=353.0, hi=2400.0)
     ls = track_laser(desc)
     ref = om.explicit(mat, T0, ls, 2e-4, dt, nsteps)
-    got, ctx, m = fused_run(P, desc, mat, T0, ls, 2e-4, dt, [(FUSED, nsteps)])
+    got, ctx, m = fused_run(P, desc, mat, T0, ls, 2e-4, dt, [(shape, nsteps)])
     assert rel(got, ref) < TOL32_T
     fd, fv, _ = om.residual(mat, got, ls, 3e-4)
     out = [torch.zeros(om.n_dofs, dtype=torch.float64, device="cuda") for _ in range(3)]
@@ -112,9 +113,9 @@ def test_dirichlet_dofs_start_away_from_td(P, oracle_mod):
     tab = om.tables()
     assert T0[tab["dirichlet"] != 0].min() > mat["T_dirichlet"]
     ls = track_laser(desc, power=0.0)
-    for n in (1, 4):
+    for n, shape in ((1, FUSED), (4, FUSED), (1, PERSISTENT), (4, PERSISTENT)):
         ref = om.explicit(mat, T0, ls, 0.0, dt, n)
-        got, _, _ = fused_run(P, desc, mat, T0, ls, 0.0, dt, [(FUSED, n)])
+        got, _, _ = fused_run(P, desc, mat, T0, ls, 0.0, dt, [(shape, n)])
         assert rel(got, ref) < TOL32_T
         assert np.all(got[tab["dirichlet"] != 0] == mat["T_dirichlet"])
 
@@ -128,7 +129,7 @@ def test_volumetric_source_in_fused_steps(P, oracle_mod):
     T0 = np.full(om.n_dofs, I.T0)
     ls = track_laser(desc, power=250.0, volumetric=True)
     ref = om.explicit(mat, T0, ls, 1e-4, dt, 8)
-    got, _, _ = fused_run(P, desc, mat, T0, ls, 1e-4, dt, [(FUSED_PDL, 8)])
+    got, _, _ = fused_run(P, desc, mat, T0, ls, 1e-4, dt, [(FUSED_PDL, 4), (PERSISTENT, 4)])
     assert ref.max() > I.T0 + 1.0
     assert rel(got, ref) < TOL32_T
 
@@ -141,8 +142,9 @@ def test_consecutive_calls_mix_forms(P, oracle_mod):
     dt = stable_dt(om, mat)
     T0 = I.melt_pool_field(om.dof_xyz(), (0.5e-3, 0.25e-3, 0.25e-3), 2400.0, 80e-6, seed=14, noise=0.01)
     ls = track_laser(desc)
-    ref = om.explicit(mat, T0, ls, 0.0, dt, 17)
-    got, _, _ = fused_run(P, desc, mat, T0, ls, 0.0, dt, [(FUSED, 5), (PER_CELL, 4), (FUSED_PDL, 8)])
+    ref = om.explicit(mat, T0, ls, 0.0, dt, 22)
+    got, _, _ = fused_run(P, desc, mat, T0, ls, 0.0, dt,
+                          [(FUSED, 5), (PER_CELL, 4), (PERSISTENT, 3), (FUSED_PDL, 8), (PERSISTENT, 2)])
     assert rel(got, ref) < TOL32_T
 
 
@@ -167,9 +169,37 @@ def test_autotune_times_every_step_form(P):
     T = torch.full((m.info()["n_dofs"],), 900.0, dtype=torch.float64, device="cuda")
     T0 = T.clone()
     v, us = P.pbf_ctx_autotune(ctx.h, T, reps=3, times=True)
-    assert len(us) == 6 and all(u > 0 for u in us) and us[v] == min(us)
+    assert len(us) == 7 and all(u > 0 for u in us) and us[v] == min(us)
     assert torch.equal(T, T0)  # the state is not modified
     bctx = P.Context(m, I.TI64_NONLIN_Q2, P.PBF_F32OP, 2)  # batches have no fused form
     Tb = torch.full((2 * m.info()["n_dofs"],), 900.0, dtype=torch.float64, device="cuda")
     v, us = P.pbf_ctx_autotune(bctx.h, Tb, reps=2, times=True)
-    assert us[4] < 0 and us[5] < 0 and v < 4
+    assert us[4] < 0 and us[5] < 0 and us[6] < 0 and v < 4
+
+
+def test_persistent_barrier_time_out_is_reported(P, oracle_mod):
+    """The persistent form's grid barrier ends its waits after one second: with the test hook
+    the barrier waits for blocks that do not exist, the call returns PBF_ETIMEOUT, and the
+    context stays usable (the next call matches the oracle)."""
+    import time
+    desc = amr(1)
+    om = oracle_mod.Mesh(desc)
+    mat = I.TI64_CONST
+    dt = stable_dt(om, mat)
+    T0 = I.smooth_field(om.dof_xyz(), seed=16, lo=353.0, hi=1500.0)
+    ls = track_laser(desc)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F32OP)
+    P.pbf_ctx_set_kernel_shape(ctx.h, PERSISTENT)
+    P.pbf_ctx_set_barrier_test(ctx.h, 1)
+    Td = to_dev(T0)
+    t0 = time.perf_counter()
+    with pytest.raises(P.PbfError) as err:
+        P.pbf_explicit_step(ctx.h, Td, ls, 0.0, dt, 3)
+    assert err.value.status == 6  # PBF_ETIMEOUT
+    assert time.perf_counter() - t0 < 10.0
+    P.pbf_ctx_set_barrier_test(ctx.h, 0)
+    Td = to_dev(T0)
+    P.pbf_explicit_step(ctx.h, Td, ls, 0.0, dt, 3)
+    torch.cuda.synchronize()
+    assert rel(Td.cpu().numpy(), om.explicit(mat, T0, ls, 0.0, dt, 3)) < TOL32_T
