@@ -149,7 +149,7 @@ def time_oracle(steps, max_seconds=None):
     return m.n_dofs * done / el, m.n_dofs, done, el
 
 
-def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10):
+def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10, shape=-1):
     """Configuration 4 forward steps: Q2 brick refined to 7.8 um along the track (278,581 dofs),
     64 instances with their own segment powers and conductivity scales, one launch per kernel
     for all instances. The state (143 MB per vector) exceeds the L2."""
@@ -166,7 +166,11 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10):
     T0 = I.melt_pool_field(xyz, (0.05e-3, 0.25e-3, 0.25e-3), 2500.0, 50e-6, seed=5)
     T = torch.tensor(np.repeat(T0[:, None], batch, axis=1), dtype=torch.float64, device="cuda")
     dt = 2e-8
-    variant = pbf.pbf_ctx_autotune(ctx.h, T, reps=3, stream=stream)
+    if shape >= 0:
+        variant = shape
+        pbf.pbf_ctx_set_kernel_shape(ctx.h, shape)
+    else:
+        variant = pbf.pbf_ctx_autotune(ctx.h, T, reps=3, stream=stream)
     for k in range(3):
         pbf.pbf_explicit_step(ctx.h, T, ls, k * chunk * dt, dt, chunk, batch=batch, stream=stream)
     pbf.pbf_ctx_kernel_time(ctx.h)
@@ -259,8 +263,9 @@ def run_reference(args):
 
 
 TRAFFIC_RECORDS = {  # dominant kernel -> (ncu traffic record, sources it was captured from)
-    "cell": ("cell_kernel_c2_traffic.json", ["kernels_cell.cu", "cell_ops.cuh"]),
-    "step": ("step_kernel_c2_traffic.json", ["kernels_step.cu", "cell_ops.cuh"]),
+    "cell": ("cell_kernel_c2_traffic.txt", ["kernels_cell.cu", "cell_ops.cuh", "internal.cuh"]),
+    "step": ("step_kernel_c2_traffic.txt", ["kernels_step.cu", "cell_ops.cuh", "step.cuh", "vec_kernels.cuh",
+                                             "internal.cuh"]),
 }
 
 
@@ -290,6 +295,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="timed loop only (for profiler launch lists)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+                    help="c4: only the batched forward steps of configuration 4 (for profiler runs)")
+    ap.add_argument("--shape", type=int, default=-1,
+                    help="explicit-step kernel shape to use instead of the autotuner's pick (0-6)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -303,6 +312,12 @@ def main():
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     W, K = max(3, args.warmup), args.steps
+    if args.workload == "c4":
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+        out = bench_batched(pbf, I, torch, torch.cuda.current_stream(), flush, load_peaks()[0], K, shape=args.shape)
+        if rank == 0:
+            print(json.dumps(out))
+        return
 
     desc = I.c2_mesh()
     mat = I.TI64_NONLIN_Q2
@@ -326,7 +341,11 @@ def main():
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    variant, shape_us = pbf.pbf_ctx_autotune(ctx.h, T, reps=5, stream=stream, times=True)
+    if args.shape >= 0:
+        variant, shape_us = args.shape, [-1.0] * len(SHAPES)
+        pbf.pbf_ctx_set_kernel_shape(ctx.h, variant)
+    else:
+        variant, shape_us = pbf.pbf_ctx_autotune(ctx.h, T, reps=5, stream=stream, times=True)
 
     def bench_step(k):
         pbf.pbf_explicit_step(ctx.h, T, ls, k * CHUNK * dt, dt, CHUNK, stream=stream)
@@ -338,8 +357,6 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     launches0 = pbf.pbf_ctx_launch_count(ctx.h)
-    pbf.pbf_ctx_kernel_time(ctx.h)
-    pbf.pbf_ctx_set_timing(ctx.h, True)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     with ClockSampler(dev) as clocks:
         for k in range(K):
@@ -348,10 +365,19 @@ def main():
             bench_step(W + k)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
-    pbf.pbf_ctx_set_timing(ctx.h, False)
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    cell_ms, cell_launches = pbf.pbf_ctx_kernel_time(ctx.h)
     gpu_launches = pbf.pbf_ctx_launch_count(ctx.h) - launches0
+    # the dominant kernel's launch duration: the same K benchmark steps again, with an event
+    # pair around every launch of it on the library's stream (kept out of the timed loop
+    # above: an event between two launches stops their programmatic overlap)
+    pbf.pbf_ctx_kernel_time(ctx.h)
+    pbf.pbf_ctx_set_timing(ctx.h, True)
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        bench_step(W + K + k)
+    torch.cuda.synchronize()
+    pbf.pbf_ctx_set_timing(ctx.h, False)
+    cell_ms, cell_launches = pbf.pbf_ctx_kernel_time(ctx.h)
     if ws > 1:
         t = torch.tensor([ms], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -380,7 +406,9 @@ def main():
     out["roofline"] = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                        "frac": achieved / fp32_peak, "traffic": traffic_for_kernel("step" if variant >= 4 else "cell"),
                        "kernel": KERNELS[variant], "flops_per_cell": fpc, "steps_per_launch": steps_per_launch,
-                       "avg_launch_us": avg_cell_s * 1e6, "peak_basis": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
+                       "avg_launch_us": avg_cell_s * 1e6, "launches_timed": cell_launches,
+                       "duration_source": "CUDA events around each launch, second pass of the K timed steps",
+                       "peak_basis": f"152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"}
     hbm = peaks.get("hbm_gbs", 6800.0)
     out["hbm_fraction"] = {"algorithmic_bytes_per_dof_update": BYTES_PER_DOF_UPDATE,
                            "achieved_gbs": value * BYTES_PER_DOF_UPDATE,

@@ -276,14 +276,16 @@ pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_ou
  * (one thread per cell and instance, gather / atomic scatter; 0: 128 threads, 1: 128 threads
  * with 5 resident blocks per SM, 2: 6 blocks, 3: 64 threads with 10 blocks) followed by the
  * hanging-node and update kernels; 4: the fused step, one launch per step for one instance
- * with the constant or nodal capacity (patches of 64 Z-order cells staged in shared memory,
- * the previous step's update applied while staging, the state kept as an FP32 pair); 5:
- * shape 4 launched with programmatic dependent launch; 6: the fused step for all steps of a
- * call in one persistent cooperative launch, with a grid barrier between steps whose waits
- * end after one second with PBF_ETIMEOUT (state undefined, context still usable); shape 6
- * synchronises the stream. Where 4-6 do not apply (batch > 1, quadrature-point capacity)
- * they run the per-cell form; with a volumetric source shape 6 runs shape 5; residual-only
- * evaluations of shapes 4-6 use shape 1.
+ * with the constant or nodal capacity (patches of 64 cells, consecutive in the global Morton
+ * order, staged in shared memory, the previous step's update applied while staging, the
+ * state kept as an FP32 pair); 5: shape 4 launched with programmatic dependent launch; 6: the
+ * fused step for all steps of a call in one persistent cooperative launch, with a grid
+ * barrier between steps whose waits end after one second with PBF_ETIMEOUT (state undefined,
+ * context still usable; when the resident blocks cover every patch, each keeps its patch
+ * tables in shared memory for the whole call); shape 6 synchronises the stream. Where 4-6 do
+ * not apply (batch > 1, quadrature-point capacity) they run the per-cell form; with a
+ * volumetric source shape 6 runs shape 5; residual-only evaluations of shapes 4-6 use
+ * shape 1.
  *
  * pbf_ctx_autotune times `reps` explicit steps of every applicable shape with dt = 0 on a
  * scratch copy of T_dev (not modified), with the laser of the last call, keeps the fastest in

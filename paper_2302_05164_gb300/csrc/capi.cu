@@ -206,6 +206,125 @@ extern "C" pbf_status pbf_mesh_transfer(pbf_mesh* mesh, const double* T_old_dev,
 // context
 // ======================================================================================
 
+// Patch tables of the fused step kernel. A patch is kStepCells cells that are consecutive in
+// the global Morton order of their anchors (over the whole brick, not tree by tree), so that
+// coarse regions give compact 4 x 4 x 4 blocks instead of rows of trees and a patch shares
+// as few nodes as possible with its neighbours. Each patch lists its unique node slots: the
+// dofs of its cells and the masters of its hanging nodes, ascending, then its hanging nodes.
+// Patches are numbered by decreasing work (slots plus twice the hanging-table entries), so
+// the blocks of the expensive patches at refinement interfaces start first instead of
+// forming the tail of a launch. Every dof is owned by the first patch in that numbering
+// that lists it. Leaves `out` empty when the fused form does not apply.
+struct StepHost {
+  std::vector<int32_t> ptr, cnt, slot, cell;
+  std::vector<uint16_t> loc, hloc;
+  std::vector<float> hw;
+  int max_nu = 0, max_hent = 0;
+};
+
+static uint64_t spread_bits3(uint64_t v) {
+  uint64_t r = 0;
+  for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1u) << (3 * b);
+  return r;
+}
+
+static void build_step_tables(const HostMesh& m, StepHost& out) {
+  const size_t nc = m.leaf_of_active.size(), npc = (size_t)m.npc;
+  const int32_t nd32 = (int32_t)m.n_dofs;
+  const size_t np = (nc + kStepCells - 1) / kStepCells;
+  std::vector<std::pair<uint64_t, int32_t>> order(nc);
+  for (size_t c = 0; c < nc; ++c) {
+    const Octant& o = m.oct[(size_t)m.leaf_of_active[c]];
+    const uint64_t k = spread_bits3((uint64_t)o.a[0]) | (spread_bits3((uint64_t)o.a[1]) << 1) |
+                       (spread_bits3((uint64_t)o.a[2]) << 2);
+    order[c] = {k, (int32_t)c};
+  }
+  std::sort(order.begin(), order.end());
+  // unique slot keys of every patch (dof d, or n_dofs + r for hanging row r), and its work
+  std::vector<size_t> kptr(np + 1, 0);
+  std::vector<int32_t> keys, tmp;
+  std::vector<int64_t> work(np, 0);
+  for (size_t p = 0; p < np; ++p) {
+    tmp.clear();
+    int64_t hent = 0;
+    for (size_t c = p * kStepCells; c < std::min(nc, (p + 1) * kStepCells); ++c)
+      for (size_t a = 0; a < npc; ++a) {
+        const int32_t d = m.cell_dofs[(size_t)order[c].second * npc + a];
+        if (d >= 0) {
+          tmp.push_back(d);
+        } else {
+          const int32_t r = -1 - d;
+          tmp.push_back(nd32 + r);
+          for (int32_t e = m.con_ptr[(size_t)r]; e < m.con_ptr[(size_t)r + 1]; ++e) tmp.push_back(m.con_idx[(size_t)e]);
+        }
+      }
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    for (int32_t k : tmp)
+      if (k >= nd32) hent += m.con_ptr[(size_t)(k - nd32) + 1] - m.con_ptr[(size_t)(k - nd32)];
+    keys.insert(keys.end(), tmp.begin(), tmp.end());
+    kptr[p + 1] = keys.size();
+    work[p] = (int64_t)tmp.size() + 2 * hent;
+  }
+  std::vector<int32_t> porder(np);
+  for (size_t p = 0; p < np; ++p) porder[p] = (int32_t)p;
+  std::stable_sort(porder.begin(), porder.end(), [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
+  StepHost& o = out;
+  o.loc.assign(np * npc * kStepCells, 0);
+  o.cell.assign(np * kStepCells, -1);
+  std::vector<uint8_t> owned((size_t)m.n_dofs, 0);
+  bool ok = true;
+  for (size_t q = 0; q < np && ok; ++q) {
+    const size_t p = (size_t)porder[q];
+    const int32_t* kb = keys.data() + kptr[p];
+    const int32_t nu = (int32_t)(kptr[p + 1] - kptr[p]);
+    const int32_t nfree = (int32_t)(std::lower_bound(kb, kb + nu, nd32) - kb);
+    auto pos = [&](int32_t key) { return step_swizzle((int)(std::lower_bound(kb, kb + nu, key) - kb)); };
+    for (size_t c = p * kStepCells; c < std::min(nc, (p + 1) * kStepCells); ++c) {
+      const size_t lane = c - p * kStepCells, cell = (size_t)order[c].second;
+      o.cell[q * kStepCells + lane] = (int32_t)cell;
+      for (size_t a = 0; a < npc; ++a) {
+        const int32_t d = m.cell_dofs[cell * npc + a];
+        o.loc[(q * npc + a) * kStepCells + lane] = (uint16_t)pos(d >= 0 ? d : nd32 + (-1 - d));
+      }
+    }
+    const int32_t hbegin = (int32_t)o.hloc.size();
+    o.ptr.push_back((int32_t)o.slot.size());
+    for (int32_t j = 0; j < nu; ++j) {
+      const int32_t k = kb[j];
+      if (k < nd32) {
+        int32_t v = k;
+        if (!owned[(size_t)k]) {
+          owned[(size_t)k] = 1;
+          v = (int32_t)((uint32_t)k | 0x80000000u);
+        }
+        o.slot.push_back(v);
+      } else {
+        const int32_t r = k - nd32, e0 = m.con_ptr[(size_t)r], e1 = m.con_ptr[(size_t)r + 1];
+        const int32_t start = (int32_t)o.hloc.size() - hbegin;
+        if (e1 - e0 > 31 || start >= (1 << 26)) ok = false;
+        for (int32_t e = e0; e < e1; ++e) {
+          o.hloc.push_back((uint16_t)pos(m.con_idx[(size_t)e]));
+          o.hw.push_back((float)m.con_w[(size_t)e]);
+        }
+        o.slot.push_back((start << 5) | (e1 - e0));
+      }
+    }
+    while (o.slot.size() % 4) o.slot.push_back(0);
+    o.cnt.push_back(nfree);
+    o.cnt.push_back(nu);
+    o.cnt.push_back(hbegin);
+    o.cnt.push_back((int32_t)o.hloc.size());
+    o.max_nu = std::max(o.max_nu, (int)nu);
+    o.max_hent = std::max(o.max_hent, (int)o.hloc.size() - hbegin);
+  }
+  // every dof needs an owner (each lies in an active cell), and shared-memory positions
+  // are 16-bit; otherwise the context has no fused form
+  if (ok && std::find(owned.begin(), owned.end(), (uint8_t)0) != owned.end()) ok = false;
+  if (ok && ((o.max_nu + 31) & ~31) > 65536) ok = false;
+  if (!ok) out = StepHost();
+}
+
 pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pbf_precision prec, int batch,
                                pbf_ctx** out);
 
@@ -270,6 +389,11 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     c->nodal.lat_ratio_f = (float)c->nodal.lat_ratio;
     c->nodal.tm_off_f = (float)(mat->T_ref - mat->Tm);
     c->nodal.inv_sigma_f = (float)c->nodal.inv_sigma;
+    // lat_ratio exp(-z^2/2) < 2^-26 for z^2 > 2 (ln lat_ratio + 26 ln 2); one more unit of
+    // margin for the approximate exponential
+    c->nodal.z2_cut_f = c->nodal.lat_ratio > 0.0
+                            ? (float)(2.0 * (std::log(c->nodal.lat_ratio) + 26.0 * std::log(2.0)) + 1.0)
+                            : 0.f;
   }
   c->nonlin = mat->Tk1 > mat->Tk0 && mat->k1 != mat->k0;
   // kernels index with 32-bit integers: every (entity x instance) count stays below 2^31
@@ -304,114 +428,20 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   std::vector<float> lof(lo.size());
   for (size_t e = 0; e < nc; ++e)
     for (int a = 0; a < 3; ++a) lof[e * 3 + a] = (float)lo[e * 3 + a];
-  // transposed constraint map: for each dof the hanging rows it is a master of
-  std::vector<int32_t> mptr((size_t)m.n_dofs + 1, 0), mrow;
-  std::vector<double> mw;
-  for (size_t e = 0; e < m.con_idx.size(); ++e) ++mptr[(size_t)m.con_idx[e] + 1];
-  for (size_t d = 0; d < (size_t)m.n_dofs; ++d) mptr[d + 1] += mptr[d];
-  mrow.resize(m.con_idx.size());
-  mw.resize(m.con_idx.size());
-  {
-    std::vector<int32_t> fill(mptr.begin(), mptr.end() - 1);
-    for (size_t r = 0; r + 1 < m.con_ptr.size(); ++r)
-      for (int32_t e = m.con_ptr[r]; e < m.con_ptr[r + 1]; ++e) {
-        const int32_t slot = fill[(size_t)m.con_idx[(size_t)e]]++;
-        mrow[(size_t)slot] = (int32_t)r;
-        mw[(size_t)slot] = m.con_w[(size_t)e];
-      }
-  }
-  std::vector<float> mwf(mw.begin(), mw.end());
-  // patches of kStepCells consecutive cells for the fused step kernel (one instance, FP32
-  // operator): each patch lists its unique node slots (the dofs of its cells and the masters
-  // of its hanging nodes, ascending, then its hanging nodes), the owning patch of each dof
-  // (the first that lists it), each cell node's shared-memory position and, per hanging
-  // slot, its constraint row with the masters' positions
-  std::vector<int32_t> sptr, scnt, sslot;
-  std::vector<uint16_t> sloc, shloc;
-  std::vector<float> shw;
-  int max_nu = 0, max_hent = 0;
-  bool step_ok = batch == 1 && prec == PBF_F32OP && nc > 0;
-  if (step_ok) {
-    const size_t np = (nc + kStepCells - 1) / kStepCells;
-    sloc.assign(np * npc * kStepCells, 0);
-    std::vector<uint8_t> owned((size_t)m.n_dofs, 0);
-    std::vector<int32_t> keys;
-    const int32_t nd32 = (int32_t)m.n_dofs;
-    for (size_t p = 0; p < np && step_ok; ++p) {
-      const size_t c0 = p * kStepCells, c1 = std::min(nc, c0 + (size_t)kStepCells);
-      keys.clear();
-      for (size_t c = c0; c < c1; ++c)
-        for (size_t a = 0; a < npc; ++a) {
-          const int32_t d = m.cell_dofs[c * npc + a];
-          if (d >= 0) {
-            keys.push_back(d);
-          } else {
-            const int32_t r = -1 - d;
-            keys.push_back(nd32 + r);
-            for (int32_t e = m.con_ptr[(size_t)r]; e < m.con_ptr[(size_t)r + 1]; ++e) keys.push_back(m.con_idx[(size_t)e]);
-          }
-        }
-      std::sort(keys.begin(), keys.end());
-      keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-      const int32_t nu = (int32_t)keys.size();
-      const int32_t nfree = (int32_t)(std::lower_bound(keys.begin(), keys.end(), nd32) - keys.begin());
-      auto pos = [&](int32_t key) {
-        return step_swizzle((int)(std::lower_bound(keys.begin(), keys.end(), key) - keys.begin()));
-      };
-      for (size_t c = c0; c < c1; ++c)
-        for (size_t a = 0; a < npc; ++a) {
-          const int32_t d = m.cell_dofs[c * npc + a];
-          sloc[(p * npc + a) * kStepCells + (c - c0)] = (uint16_t)pos(d >= 0 ? d : nd32 + (-1 - d));
-        }
-      const int32_t hbegin = (int32_t)shloc.size();
-      sptr.push_back((int32_t)sslot.size());
-      for (int32_t j = 0; j < nu; ++j) {
-        const int32_t k = keys[(size_t)j];
-        if (k < nd32) {
-          int32_t v = k;
-          if (!owned[(size_t)k]) {
-            owned[(size_t)k] = 1;
-            v = (int32_t)((uint32_t)k | 0x80000000u);
-          }
-          sslot.push_back(v);
-        } else {
-          const int32_t r = k - nd32, e0 = m.con_ptr[(size_t)r], e1 = m.con_ptr[(size_t)r + 1];
-          const int32_t start = (int32_t)shloc.size() - hbegin;
-          if (e1 - e0 > 31 || start >= (1 << 26)) step_ok = false;
-          for (int32_t e = e0; e < e1; ++e) {
-            shloc.push_back((uint16_t)pos(m.con_idx[(size_t)e]));
-            shw.push_back((float)m.con_w[(size_t)e]);
-          }
-          sslot.push_back((start << 5) | (e1 - e0));
-        }
-      }
-      while (sslot.size() % 4) sslot.push_back(0);
-      scnt.push_back(nfree);
-      scnt.push_back(nu);
-      scnt.push_back(hbegin);
-      scnt.push_back((int32_t)shloc.size());
-      max_nu = std::max(max_nu, (int)nu);
-      max_hent = std::max(max_hent, (int)shloc.size() - hbegin);
-    }
-    // every dof needs an owner (each lies in an active cell), and shared-memory positions
-    // are 16-bit; otherwise the context has no fused form
-    if (step_ok && std::find(owned.begin(), owned.end(), (uint8_t)0) != owned.end()) step_ok = false;
-    if (step_ok && ((max_nu + 31) & ~31) > 65536) step_ok = false;
-    if (!step_ok) {
-      sptr.clear();
-      scnt.clear();
-      sslot.clear();
-      sloc.clear();
-      shloc.clear();
-      shw.clear();
-    }
-  }
-  int32_t *d_sptr = nullptr, *d_scnt = nullptr, *d_sslot = nullptr;
+  // patch tables of the fused step kernel (one instance, FP32 operator)
+  StepHost sh;
+  if (batch == 1 && prec == PBF_F32OP && nc > 0) build_step_tables(m, sh);
+  std::vector<int32_t>& sptr = sh.ptr;
+  std::vector<int32_t>& scnt = sh.cnt;
+  std::vector<int32_t>& sslot = sh.slot;
+  std::vector<int32_t>& scell = sh.cell;
+  std::vector<uint16_t>& sloc = sh.loc;
+  std::vector<uint16_t>& shloc = sh.hloc;
+  std::vector<float>& shw = sh.hw;
+  const int max_nu = sh.max_nu;
+  int32_t *d_sptr = nullptr, *d_scnt = nullptr, *d_sslot = nullptr, *d_scell = nullptr;
   uint16_t *d_sloc = nullptr, *d_shloc = nullptr;
   float* d_shw = nullptr;
-  int32_t *d_mptr = nullptr, *d_mrow = nullptr;
-  double* d_mw = nullptr;
-  float* d_mwf = nullptr;
   std::vector<double> level_h((size_t)kMaxLevels * 3, 0.0);
   CellLaunch& L = c->base;
   for (int l = 0; l <= m.L && l < kMaxLevels; ++l) {
@@ -448,20 +478,11 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   UP(d_sptr, sptr);
   UP(d_scnt, scnt);
   UP(d_sslot, sslot);
+  UP(d_scell, scell);
   UP(d_sloc, sloc);
   UP(d_shloc, shloc);
   UP(d_shw, shw);
-  UP(d_mptr, mptr);
-  UP(d_mrow, mrow);
-  UP(d_mw, mw);
-  UP(d_mwf, mwf);
 #undef UP
-  if (c->n_hang > 0) {
-    c->pull.ptr = d_mptr;
-    c->pull.row = d_mrow;
-    c->pull.w = d_mw;
-    c->pull.wf = d_mwf;
-  }
   c->n_top = (int64_t)top_cell.size();
   const size_t rsz = c->f32 ? 4 : 8;
   const size_t nv = nd * (size_t)batch;
@@ -524,11 +545,12 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     StepTables& st = c->step;
     st.n_patches = (int)sptr.size();
     st.max_nu32 = (max_nu + 31) & ~31;
-    st.max_hent8 = (max_hent + 7) & ~7;
+    st.max_hent8 = (sh.max_hent + 7) & ~7;
     st.smem = step_smem_bytes((int)npc, st.max_nu32, st.max_hent8);
     st.ptr = d_sptr;
     st.cnt = reinterpret_cast<const int4*>(d_scnt);
     st.slot = d_sslot;
+    st.cell = d_scell;
     st.loc = d_sloc;
     st.hloc = d_shloc;
     st.hw = d_shw;
@@ -772,7 +794,8 @@ LaserInline CtxBase::inline_laser(double t, Spot* sp_out) const {
 
 // A forward-Euler step sequence on T (laser already set). Per step: hanging values of the
 // state (clearing the hanging accumulators), the cell kernel with the surface laser on top
-// faces, and the update, which pulls the hanging-node contributions to their masters.
+// faces, the distribution of the hanging-node contributions to their masters, and the
+// update.
 cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
   if (nsteps <= 0) return cudaSuccess;
   if (base.variant >= 4 && fused_ok())
@@ -783,9 +806,6 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
   const int64_t nv = n_dofs * batch;
   cudaError_t e = cudaSuccess;
-  PullMap pm = pull;
-  pm.fh = fh;
-  pm.Ch = latent ? Ch : nullptr;
   const double tw_dir = mat.T_dirichlet - mat.T_ref;
   const float tf_dir = (float)tw_dir;
   if (f32) {
@@ -812,13 +832,24 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
       e = launch_laser(degree, f32, lsetup, L.mesh, power, sp, f, s);
       ++launches;
     }
+    // hanging-node contributions to their masters (P_h^T f_h), one thread per row and
+    // instance with atomic additions that are contiguous over the instances; the update is
+    // then a plain streaming kernel
+    if (e == cudaSuccess && n_hang > 0) {
+      e = launch_hang_distribute(f32, L.mesh, fh, f, s);
+      ++launches;
+      if (e == cudaSuccess && latent) {
+        e = launch_hang_distribute(f32, L.mesh, Ch, Cacc, s);
+        ++launches;
+      }
+    }
     if (e == cudaSuccess) {
       if (f32)
         e = launch_update_f32(cap, n_dofs, batch, Tw, Tf, (float*)f, (float*)Cacc, invC0_f, nodal, dirichlet, tw_dir,
-                              tf_dir, (float)dt, s, pm);
+                              tf_dir, (float)dt, s);
       else
         e = launch_update_f64(cap, n_dofs, batch, T_dev, (double*)f, (double*)Cacc, invC0_d, nodal, dirichlet,
-                              mat.T_dirichlet, dt, s, pm);
+                              mat.T_dirichlet, dt, s);
     }
     ++launches;
   }
@@ -826,11 +857,7 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
     e = launch_finish_f32(nv, Tw, mat.T_ref, T_dev, s);
     ++launches;
   }
-  // the update pulls f_h without clearing it: clear it (and C_h) so that every accumulator is
-  // zero between calls, as the other operator paths expect
-  const size_t nh = (size_t)n_hang * (size_t)batch * (f32 ? 4 : 8);
-  if (e == cudaSuccess && nh) e = cudaMemsetAsync(fh, 0, nh, s);
-  if (e == cudaSuccess && nh && latent) e = cudaMemsetAsync(Ch, 0, nh, s);
+  // every accumulator is zero between calls: the distribution cleared f_h and C_h
   return e;
 }
 

@@ -1,7 +1,7 @@
 // Fused explicit step (FP32 operator, one instance): one launch per forward-Euler step of
 // Eq. forward_euler with the matrix-free operator of Sec. 4.2.
 //
-// Each block takes a patch of kStepCells consecutive Z-order cells and
+// Each block takes a patch of kStepCells cells (consecutive in the global Morton order) and
 //  1. loads its patch tables (independent of the previous step, so under programmatic
 //     dependent launch this overlaps the previous kernel's tail);
 //  2. stages the patch's unique node values in shared memory, completing the previous step
@@ -85,15 +85,15 @@ __device__ __forceinline__ void load_patch_tables(const StepTables& T, const Ste
 // sums and the scatter of the dof sums into S.f_acc.
 template <int P, bool NLK, int CAP, bool COHERENT>
 __device__ __forceinline__ void step_patch(const CellLaunch& L, const LaserInline& las, const StepState& S,
-                                           const StepSmem<(P + 1) * (P + 1) * (P + 1)>& sm, int p, int4 cn) {
+                                           const StepTables& T, const StepSmem<(P + 1) * (P + 1) * (P + 1)>& sm,
+                                           int p, int4 cn) {
   constexpr int N = P + 1, NP = N * N * N, KP = kStepCells, U = kStageUnroll;
   (void)N;
   const DevMesh& M = L.mesh;
   const int tid = threadIdx.x;
   const int nfree = cn.x, nu = cn.y;
-  const int c0 = p * KP, ncell = min(KP, M.n_cells - c0);
-  const int cell = c0 + tid;
-  const bool active = tid < ncell;
+  const int cell = __ldg(&T.cell[p * KP + tid]);
+  const bool active = cell >= 0;
   int lev = 0, mat = 0, top = 0;
   if (active) {
     lev = __ldg(&M.cell_level[cell]);
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
   load_patch_tables<NP>(T, sm, blockIdx.x, cn);
   grid_dependency_wait();  // the previous step's state and accumulators are complete
   __syncthreads();
-  step_patch<P, NLK, CAP, false>(L, L.las, S, sm, blockIdx.x, cn);
+  step_patch<P, NLK, CAP, false>(L, L.las, S, T, sm, blockIdx.x, cn);
 }
 
 // ---- persistent form: all steps of a sequence in one cooperative launch -----------------
@@ -245,22 +245,34 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Grid-wide barrier of a cooperative launch (all blocks resident). Sense by generation: the
-// last block to arrive resets the count and advances the generation. A wait longer than
-// kBarrierTimeoutNs, or an error flagged by another block, makes every block return false;
-// the caller then leaves the kernel, so no block waits twice.
+// Grid-wide barrier of a cooperative launch (all blocks resident), in two levels so that no
+// counter takes more than a few dozen atomics: block b arrives at the counter of its group
+// b % kBarrierGroups; the last block of a group resets that counter and arrives at the top
+// counter; the last group resets it and advances the generation, which every block waits
+// for. A wait longer than kBarrierTimeoutNs, or an error flagged by another block, makes
+// every block return false; the caller then leaves the kernel, so no block waits twice.
 constexpr unsigned long long kBarrierTimeoutNs = 1000000000ull;
 __device__ bool grid_sync(GridBarrier* gb, unsigned nblocks, unsigned& gen) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
+    const unsigned G = nblocks < kBarrierGroups ? nblocks : kBarrierGroups;
+    const unsigned g = blockIdx.x % G;
+    const unsigned in_group = nblocks / G + (g < nblocks % G ? 1u : 0u);
     __threadfence();
-    if (atomicAdd(&gb->count, 1u) == nblocks - 1) {
-      atomicExch(&gb->count, 0u);
+    bool last = false;
+    if (atomicAdd(&gb->group[g].count, 1u) == in_group - 1) {
+      atomicExch(&gb->group[g].count, 0u);
       __threadfence();
-      atomicAdd(&gb->gen, 1u);
-    } else {
+      if (atomicAdd(&gb->count, 1u) == G - 1) {
+        atomicExch(&gb->count, 0u);
+        __threadfence();
+        atomicAdd(&gb->gen, 1u);
+        last = true;
+      }
+    }
+    if (!last) {
       const unsigned long long t0 = global_ns();
       while (ld_acquire_gpu(&gb->gen) == gen) {
         if (ld_acquire_gpu(&gb->err) != 0u) {
@@ -272,7 +284,7 @@ __device__ bool grid_sync(GridBarrier* gb, unsigned nblocks, unsigned& gen) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        __nanosleep(32);
       }
     }
     __threadfence();
@@ -289,6 +301,7 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
   constexpr int NP = (P + 1) * (P + 1) * (P + 1);
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ LaserInline s_las;
+  __shared__ Spot s_spot[32];  // spots of steps 32 k .. 32 k + 31, computed by warp 0 in parallel
   __shared__ unsigned s_gen0;
   const StepSmem<NP> sm(smem, T);
   if (threadIdx.x == 0) s_gen0 = ld_acquire_gpu(&A.bar->gen);  // no barrier completes before all blocks arrive
@@ -296,6 +309,10 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
   __syncthreads();
   gen = s_gen0;
   StepState S = A.st;
+  // with a block for every patch the patch tables stay in shared memory for all steps
+  const bool resident = (int)gridDim.x >= T.n_patches;
+  int4 cn0 = make_int4(0, 0, 0, 0);
+  if (resident) load_patch_tables<NP>(T, sm, blockIdx.x, cn0);
   for (int n = 0; n < A.nsteps; ++n) {
     S.x_in = A.x[n & 1];
     S.x_out = A.x[(n + 1) & 1];
@@ -303,9 +320,14 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     S.f_acc = A.f[n % 3];
     S.f_clear = A.f[(n + 1) % 3];
     S.first = n == 0;
+    if ((n & 31) == 0 && threadIdx.x < 32) {
+      // the time as the host forms it for the per-launch form: t0 + n dt, each rounded
+      s_spot[threadIdx.x] = spot_at(A.laser, __dadd_rn(A.t0, __dmul_rn((double)(n + (int)threadIdx.x), A.dt64)));
+      __syncwarp();
+    }
     if (threadIdx.x == 0) {
       LaserInline las = A.las;
-      const Spot sp = spot_at(A.laser, A.t0 + n * A.dt64);
+      const Spot sp = s_spot[n & 31];
       las.on = A.las.on && sp.seg >= 0;
       las.seg = sp.seg;
       las.sx = sp.x;
@@ -314,10 +336,12 @@ __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     }
     for (int p = blockIdx.x; p < T.n_patches; p += gridDim.x) {
       __syncthreads();  // the previous patch is done with shared memory; s_las is set
-      int4 cn;
-      load_patch_tables<NP>(T, sm, p, cn);
-      __syncthreads();
-      step_patch<P, NLK, CAP, true>(L, s_las, S, sm, p, cn);
+      int4 cn = cn0;
+      if (!resident) {
+        load_patch_tables<NP>(T, sm, p, cn);
+        __syncthreads();
+      }
+      step_patch<P, NLK, CAP, true>(L, s_las, S, T, sm, p, cn);
     }
     if (!grid_sync(A.bar, gridDim.x + A.extra_arrivals, gen)) return;
   }
@@ -424,8 +448,8 @@ cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, co
                                     int* blocks, cudaStream_t s) {
   const StepState& st = ps.st;
   if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
-      !t.hloc || !t.hw || !ps.x[0] || !ps.x[1] || !ps.f[0] || !ps.f[1] || !ps.f[2] || !ps.T || !st.T0 ||
-      !st.invC0x || !ps.bar || ps.nsteps < 1 || ps.laser.volumetric)
+      !t.cell || !t.loc || !t.hloc || !t.hw || !ps.x[0] || !ps.x[1] || !ps.f[0] || !ps.f[1] || !ps.f[2] || !ps.T ||
+      !st.T0 || !st.invC0x || !ps.bar || ps.nsteps < 1 || ps.laser.volumetric)
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
   if (L.degree == 1) return dispatch_steps<1>(L, t, ps, cap, blocks, s);
@@ -436,9 +460,9 @@ cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, co
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                         cudaStream_t s) {
   // the fused form covers one instance of the FP32 operator with the constant or nodal capacity
-  if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot || !t.hloc || !t.hw ||
-      !t.loc || !st.x_in || !st.x_out || !st.f_in || !st.f_acc || !st.f_clear || !st.invC0x ||
-      st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear)
+  if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
+      !t.cell || !t.hloc || !t.hw || !t.loc || !st.x_in || !st.x_out || !st.f_in || !st.f_acc || !st.f_clear ||
+      !st.invC0x || st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear)
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
   if (L.degree == 1) return dispatch_step<1>(L, t, st, cap, pdl, s);

@@ -42,7 +42,6 @@ struct CtxBase {
   double* cell_lo = nullptr;
   double* level_h = nullptr;
   uint8_t* cell_top = nullptr;
-  PullMap pull;  // transposed constraint map (accumulator pointers set per launch)
   // material / instance data
   double* k_scale_d = nullptr;
   float* k_scale_f = nullptr;

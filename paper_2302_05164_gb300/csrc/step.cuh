@@ -7,14 +7,14 @@ namespace pbf {
 
 constexpr int kStepCells = 64;  // cells per patch = threads per block of the fused step kernel
 
-// Patches of kStepCells consecutive (Z-order) cells, built once per context on the host. Each
-// patch lists its unique node slots: first the dofs of its cells and the masters of its
-// hanging nodes, in ascending order, then its hanging nodes, padded to a multiple of 4
-// entries so that a block can load its list with 16-byte loads. Every dof is owned by exactly
-// one patch, the first that lists it; the owner writes the dof's new state. A hanging slot
-// stores (start << 5) | count of its constraint row in the patch's hanging table, whose
-// entries give each master's shared-memory position and weight: hanging values and
-// contributions never leave the block.
+// Patches of kStepCells cells, built once per context on the host (cells consecutive in the
+// global Morton order, patches numbered by decreasing work). Each patch lists its unique node
+// slots: first the dofs of its cells and the masters of its hanging nodes, in ascending
+// order, then its hanging nodes, padded to a multiple of 4 entries so that a block can load
+// its list with 16-byte loads. Every dof is owned by exactly one patch, the first that lists
+// it; the owner writes the dof's new state. A hanging slot stores (start << 5) | count of its
+// constraint row in the patch's hanging table, whose entries give each master's shared-memory
+// position and weight: hanging values and contributions never leave the block.
 struct StepTables {
   int n_patches = 0;
   int max_nu32 = 0;               // longest slot list, rounded up to a multiple of 32
@@ -23,6 +23,7 @@ struct StepTables {
   const int32_t* ptr = nullptr;   // [n_patches] start of each list in slot (a multiple of 4)
   const int4* cnt = nullptr;      // [n_patches] {dof slots, all slots, hanging table begin, end}
   const int32_t* slot = nullptr;  // dof d (bit 31: owned here) or a hanging row reference
+  const int32_t* cell = nullptr;  // [n_patches][kStepCells] the cell of each lane, -1 if none
   const uint16_t* loc = nullptr;  // [n_patches][npc][kStepCells] shared position of each cell node
   const uint16_t* hloc = nullptr; // hanging tables: master positions ...
   const float* hw = nullptr;      // ... and constraint weights
@@ -88,8 +89,12 @@ cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepStat
 // Persistent form: every step of a sequence in one cooperative launch, a grid-wide barrier
 // between steps, the spot of each step computed on the device, and the last update applied
 // by the owners after the last barrier (T written in FP64, f_{N-1} and f_{N-2} cleared).
+constexpr unsigned kBarrierGroups = 64;
 struct GridBarrier {
   unsigned count = 0, gen = 0, err = 0, pad = 0;  // err: a wait ran out of time (set once)
+  struct alignas(128) Group {
+    unsigned count = 0;
+  } group[kBarrierGroups];  // first-level counters, one cache line each
 };
 struct PersistState {
   StepState st;             // constants; the per-step pointers rotate inside the kernel
@@ -103,7 +108,9 @@ struct PersistState {
   GridBarrier* bar = nullptr;  // zeroed before the launch
   unsigned extra_arrivals = 0; // test hook: barriers wait for this many blocks more than launched
 };
-// blocks: set to the grid size used (all blocks resident). Volumetric lasers are not covered.
+// blocks: set to the grid size used (all blocks resident; when that covers every patch, each
+// block keeps its patch tables in shared memory for the whole sequence). Volumetric lasers
+// are not covered.
 cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, const PersistState& ps, int cap,
                                     int* blocks, cudaStream_t s);
 

@@ -21,23 +21,16 @@ inline unsigned grid_for(int64_t n, int bs = kBS) { return (unsigned)((n + bs - 
 template <int CAP>
 __global__ void k_update_f64(int64_t n, int B, double* __restrict__ T, double* __restrict__ f,
                              double* __restrict__ Cacc, const double* __restrict__ invC0, const NodalCap nc,
-                             const uint8_t* __restrict__ dirichlet, double T_dir, double dt, const PullMap pm) {
+                             const uint8_t* __restrict__ dirichlet, double T_dir, double dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int d = B == 1 ? i : i / B, inst = i - d * B;
-  double fi = f[i];
+  const int d = B == 1 ? i : i / B;
+  const double fi = f[i];
   f[i] = 0.0;
   double ci = 0.0;
   if (CAP == CAP_QUADRATURE) {
     ci = Cacc[i];
     Cacc[i] = 0.0;
-  }
-  if (pm.ptr) {  // contributions of hanging nodes whose master d is (P_h^T f_h, pulled)
-    for (int e = pm.ptr[d]; e < pm.ptr[d + 1]; ++e) {
-      const int j = pm.row[e] * B + inst;
-      fi += pm.w[e] * ((const double*)pm.fh)[j];
-      if (CAP == CAP_QUADRATURE) ci += pm.w[e] * ((const double*)pm.Ch)[j];
-    }
   }
   if (dirichlet[d]) {
     T[i] = T_dir;
@@ -60,23 +53,16 @@ template <int CAP>
 __global__ void k_update_f32(int64_t n, int B, double* __restrict__ Tw, float* __restrict__ Tf,
                              float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
                              const NodalCap nc, const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir,
-                             float dt, const PullMap pm) {
+                             float dt) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const int d = B == 1 ? i : i / B, inst = i - d * B;
-  float fi = f[i];
+  const int d = B == 1 ? i : i / B;
+  const float fi = f[i];
   f[i] = 0.f;
   float ci = 0.f;
   if (CAP == CAP_QUADRATURE) {
     ci = Cacc[i];
     Cacc[i] = 0.f;
-  }
-  if (pm.ptr) {  // contributions of hanging nodes whose master d is (P_h^T f_h, pulled)
-    for (int e = pm.ptr[d]; e < pm.ptr[d + 1]; ++e) {
-      const int j = pm.row[e] * B + inst;
-      fi += pm.wf[e] * ((const float*)pm.fh)[j];
-      if (CAP == CAP_QUADRATURE) ci += pm.wf[e] * ((const float*)pm.Ch)[j];
-    }
   }
   if (dirichlet[d]) {
     Tw[i] = tw_dir;
@@ -96,13 +82,44 @@ __global__ void k_capacity_nodal(int64_t n, int B, const double* __restrict__ C0
   out[i] = C0[i / B] * (1.0 + nc.lat_ratio * exp(-0.5 * z * z));
 }
 
-// The same FP32-form update for one instance without hanging contributions to pull, four
-// dofs per thread with 16-byte loads and stores (arrays from cudaMalloc are 256-byte aligned).
+// The same FP32-form update for one instance, four dofs per thread with 16-byte loads and
+// stores (arrays from cudaMalloc are 256-byte aligned).
 template <int CAP>
 __device__ __forceinline__ void update_one(float fi, float ci, float ic, bool fixed, double& tw, float& tf,
                                            const NodalCap& nc, double tw_dir, float tf_dir, float dt) {
   tw = euler_f32<CAP>(tw, fi, ci, ic, fixed, nc, tw_dir, dt);
   tf = fixed ? tf_dir : d2f_rn(tw);
+}
+
+// Batches with B a multiple of 4: four instances of one dof per thread (16-byte accesses,
+// one load of the dof's capacity and Dirichlet flag).
+template <int CAP>
+__global__ void k_update_f32_b4(int64_t n4, int B, double* __restrict__ Tw, float* __restrict__ Tf,
+                                float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
+                                const NodalCap nc, const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir,
+                                float dt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n4) return;
+  const int64_t i0 = 4 * t;
+  const int64_t d = i0 / B;
+  const float4 f4 = *reinterpret_cast<const float4*>(f + i0);
+  *reinterpret_cast<float4*>(f + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (CAP == CAP_QUADRATURE) {
+    c4 = *reinterpret_cast<const float4*>(Cacc + i0);
+    *reinterpret_cast<float4*>(Cacc + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  const float ic = CAP == CAP_QUADRATURE ? 0.f : __ldg(&invC0[d]);
+  const bool fixed = __ldg(&dirichlet[d]) != 0;
+  double2 a = *reinterpret_cast<const double2*>(Tw + i0), b = *reinterpret_cast<const double2*>(Tw + i0 + 2);
+  float4 t4;
+  update_one<CAP>(f4.x, c4.x, ic, fixed, a.x, t4.x, nc, tw_dir, tf_dir, dt);
+  update_one<CAP>(f4.y, c4.y, ic, fixed, a.y, t4.y, nc, tw_dir, tf_dir, dt);
+  update_one<CAP>(f4.z, c4.z, ic, fixed, b.x, t4.z, nc, tw_dir, tf_dir, dt);
+  update_one<CAP>(f4.w, c4.w, ic, fixed, b.y, t4.w, nc, tw_dir, tf_dir, dt);
+  *reinterpret_cast<double2*>(Tw + i0) = a;
+  *reinterpret_cast<double2*>(Tw + i0 + 2) = b;
+  *reinterpret_cast<float4*>(Tf + i0) = t4;
 }
 
 template <int CAP>
@@ -633,30 +650,37 @@ __global__ void k_transfer(int64_t n_new, int B, const int32_t* __restrict__ ptr
 
 cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double* f, double* Cacc,
                               const double* invC0, const NodalCap& nc, const uint8_t* dirichlet, double T_dir,
-                              double dt, cudaStream_t s, const PullMap& pm) {
+                              double dt, cudaStream_t s) {
   const int64_t n = n_dofs * B;
   if (n == 0) return cudaSuccess;
-  if (cap == CAP_QUADRATURE) k_update_f64<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt, pm);
-  else if (cap == CAP_NODAL) k_update_f64<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt, pm);
-  else k_update_f64<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt, pm);
+  if (cap == CAP_QUADRATURE) k_update_f64<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt);
+  else if (cap == CAP_NODAL) k_update_f64<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt);
+  else k_update_f64<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, T, f, Cacc, invC0, nc, dirichlet, T_dir, dt);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float* Tf, float* f, float* Cacc,
                               const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, double tw_dir,
-                              float tf_dir, float dt, cudaStream_t s, const PullMap& pm) {
+                              float tf_dir, float dt, cudaStream_t s) {
   const int64_t n = n_dofs * B;
   if (n == 0) return cudaSuccess;
-  if (B == 1 && pm.ptr == nullptr) {
+  if (B > 1 && B % 4 == 0) {
+    const int64_t n4 = n / 4;
+    if (cap == CAP_QUADRATURE) k_update_f32_b4<CAP_QUADRATURE><<<grid_for(n4), kBS, 0, s>>>(n4, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+    else if (cap == CAP_NODAL) k_update_f32_b4<CAP_NODAL><<<grid_for(n4), kBS, 0, s>>>(n4, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+    else k_update_f32_b4<CAP_CONST><<<grid_for(n4), kBS, 0, s>>>(n4, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+    return cudaGetLastError();
+  }
+  if (B == 1) {
     const int64_t nt = (n + 3) / 4;
     if (cap == CAP_QUADRATURE) k_update_f32_x4<CAP_QUADRATURE><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
     else if (cap == CAP_NODAL) k_update_f32_x4<CAP_NODAL><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
     else k_update_f32_x4<CAP_CONST><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
     return cudaGetLastError();
   }
-  if (cap == CAP_QUADRATURE) k_update_f32<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
-  else if (cap == CAP_NODAL) k_update_f32<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
-  else k_update_f32<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt, pm);
+  if (cap == CAP_QUADRATURE) k_update_f32<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+  else if (cap == CAP_NODAL) k_update_f32<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
+  else k_update_f32<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
   return cudaGetLastError();
 }
 

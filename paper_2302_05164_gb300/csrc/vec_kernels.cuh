@@ -20,6 +20,9 @@ enum { CAP_CONST = 0, CAP_QUADRATURE = 1, CAP_NODAL = 2 };
 struct NodalCap {
   double lat_ratio = 0.0, Tm = 0.0, inv_sigma = 0.0;  // c_app/c = 1 + lat_ratio exp(-((T-Tm) inv_sigma)^2/2)
   float lat_ratio_f = 0.f, tm_off_f = 0.f, inv_sigma_f = 0.f;  // FP32 form on T - T_ref
+  // z^2 beyond which lat_ratio exp(-z^2/2) < 2^-26, so that 1 + lat_ratio exp(-z^2/2) rounds
+  // to 1 in FP32 and the FP32 forms skip the exponential and the division
+  float z2_cut_f = 0.f;
 };
 // The FP32-operator increment dt f / C~ of one dof (Eq. forward_euler), formed in FP32. C~ is
 // the accumulated quadrature row sum ci, or comes from the inverse lumped capacity ic of the
@@ -31,7 +34,9 @@ __device__ __forceinline__ float increment_f32(float value, float fi, float ci, 
   if (CAP == CAP_QUADRATURE) return dt * fi / ci;
   if (CAP == CAP_NODAL) {
     const float z = (value + nc.tm_off_f) * nc.inv_sigma_f;
-    return __fdividef(dt * fi * ic, 1.f + nc.lat_ratio_f * __expf(-0.5f * z * z));
+    const float z2 = z * z;
+    const float r = dt * fi * ic;
+    return z2 < nc.z2_cut_f ? __fdividef(r, 1.f + nc.lat_ratio_f * __expf(-0.5f * z2)) : r;
   }
   return dt * fi * ic;
 }
@@ -45,23 +50,13 @@ __device__ __forceinline__ double euler_f32(double tw, float fi, float ci, float
   return tw + f2d(increment_f32<CAP>(CAP == CAP_NODAL ? d2f_rn(tw) : 0.f, fi, ci, ic, nc, dt));
 }
 
-// Transposed constraint map: for dof d the hanging rows r (weight w) that have d as a master;
-// with it the update kernel pulls f_h (and C_h) instead of a separate scatter kernel.
-struct PullMap {
-  const int32_t* ptr = nullptr;  // [n_dofs + 1]; null: nothing to pull
-  const int32_t* row = nullptr;
-  const double* w = nullptr;
-  const float* wf = nullptr;
-  const void* fh = nullptr;      // [n_hang][batch] accumulators of the operator precision
-  const void* Ch = nullptr;
-};
 cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double* f, double* Cacc,
                               const double* invC0, const NodalCap& nc, const uint8_t* dirichlet, double T_dir,
-                              double dt, cudaStream_t s, const PullMap& pm);
+                              double dt, cudaStream_t s);
 cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float* Tf, float* f, float* Cacc,
                               const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, double tw_dir,
-                              float tf_dir, float dt, cudaStream_t s, const PullMap& pm);
-// x_h = P_h x with f_h (and C_h, nullable) cleared, for the pulled form
+                              float tf_dir, float dt, cudaStream_t s);
+// x_h = P_h x with f_h (and C_h, nullable) cleared
 cudaError_t launch_hang_values_zero(bool f32, const DevMesh& M, const void* x, void* out, void* fh, void* Ch,
                                     cudaStream_t s);
 // C_out[d][b] = C0[d] c_app(T[d][b]) / c (nodal lumping) in FP64

@@ -236,3 +236,16 @@ def test_c2_full_size_residual_and_step(P, oracle_mod):
     for prec, tol in ((P.PBF_F64, TOL64), (P.PBF_F32OP, TOL32_T)):
         got = run_gpu_steps(P, desc, mat, T, ls, t, dt, 1, prec)
         assert rel(got, ref) < tol
+    # the fused shapes the benchmark chooses from, three steps each; at this size the
+    # persistent form has fewer blocks than patches (blocks take several patches per step)
+    ref3 = om.explicit(mat, T, ls, t, dt, 3)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F32OP)
+    for shape in (4, 5, 6):
+        P.pbf_ctx_set_kernel_shape(ctx.h, shape)
+        Td = to_dev(T)
+        P.pbf_explicit_step(ctx.h, Td, ls, t, dt, 3)
+        torch.cuda.synchronize()
+        assert rel(Td.cpu().numpy(), ref3) < TOL32_T, shape
+    ctx.close()
+    m.close()
