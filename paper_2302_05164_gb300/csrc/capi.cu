@@ -489,7 +489,7 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->f, nv * rsz);
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->fvol, nv * rsz);
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->Cacc, (c->latent ? nv : 1) * rsz);
-  if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->Tw, nv);
+  if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->Tlo, nv);
   if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->Tf, nv);
   const size_t nh = std::max<size_t>(1, (size_t)c->n_hang * (size_t)batch);
   if (e == cudaSuccess) e = dalloc(c.get(), (char**)&c->xh, nh * rsz);
@@ -749,7 +749,7 @@ cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_d
   L.x = T_dev;
   cudaError_t e = cudaSuccess;
   if (f32) {
-    e = launch_prepare_f32(nv, T_dev, mat.T_ref, nullptr, Tf, s);
+    e = launch_prepare_f32(nv, T_dev, mat.T_ref, Tf, nullptr, s);
     L.xf = Tf;
     ++launches;
   }
@@ -806,11 +806,12 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
   const int64_t nv = n_dofs * batch;
   cudaError_t e = cudaSuccess;
-  const double tw_dir = mat.T_dirichlet - mat.T_ref;
-  const float tf_dir = (float)tw_dir;
+  const double xd = mat.T_dirichlet - mat.T_ref;
+  const float xd_hi = (float)xd;
+  const float2 x_dir = make_float2(xd_hi, (float)(xd - (double)xd_hi));
   if (f32) {
-    // FP64 working state Tw = T - T_ref and its FP32 copy for the whole call
-    e = launch_prepare_f32(nv, T_dev, mat.T_ref, Tw, Tf, s);
+    // working state T - T_ref as the FP32 pair Tf + Tlo for the whole call
+    e = launch_prepare_f32(nv, T_dev, mat.T_ref, Tf, Tlo, s);
     ++launches;
     L.xf = Tf;
     L.xfh = (const float*)xh;
@@ -845,8 +846,8 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
     }
     if (e == cudaSuccess) {
       if (f32)
-        e = launch_update_f32(cap, n_dofs, batch, Tw, Tf, (float*)f, (float*)Cacc, invC0_f, nodal, dirichlet, tw_dir,
-                              tf_dir, (float)dt, s);
+        e = launch_update_f32(cap, n_dofs, batch, Tf, Tlo, (float*)f, (float*)Cacc, invC0_f, nodal, dirichlet, x_dir,
+                              (float)dt, s);
       else
         e = launch_update_f64(cap, n_dofs, batch, T_dev, (double*)f, (double*)Cacc, invC0_d, nodal, dirichlet,
                               mat.T_dirichlet, dt, s);
@@ -854,7 +855,7 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
     ++launches;
   }
   if (f32 && e == cudaSuccess) {
-    e = launch_finish_f32(nv, Tw, mat.T_ref, T_dev, s);
+    e = launch_finish_f32(nv, Tf, Tlo, mat.T_ref, T_dev, s);
     ++launches;
   }
   // every accumulator is zero between calls: the distribution cleared f_h and C_h

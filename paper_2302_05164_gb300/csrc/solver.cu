@@ -394,7 +394,7 @@ struct Adjoint {
     CellLaunch L = c->base;
     const bool qpc = c->cap == CAP_QUADRATURE;
     if (c->f32) {
-      if (e == cudaSuccess) e = launch_prepare_f32(nv, Tk, c->mat.T_ref, nullptr, c->Tf, s);
+      if (e == cudaSuccess) e = launch_prepare_f32(nv, Tk, c->mat.T_ref, c->Tf, nullptr, s);
       if (e == cudaSuccess) e = launch_round_f32(nv, v, vf, s);
       if (e == cudaSuccess && qpc) e = launch_round_f32(nv, mu, muf, s);
       L.xf = c->Tf;

@@ -54,8 +54,8 @@ struct CtxBase {
   void* f = nullptr;     // operator accumulator (FP32 or FP64) [n_dofs][batch]
   void* fvol = nullptr;  // laser accumulator [n_dofs][batch]
   void* Cacc = nullptr;  // capacity accumulator (latent heat) [n_dofs][batch]
-  double* Tw = nullptr;  // FP32 operator: FP64 working state T - T_ref [n_dofs][batch]
-  float* Tf = nullptr;   // FP32 operator: its FP32 rounding, gathered by the cell kernel
+  float* Tf = nullptr;   // FP32 operator: working state T - T_ref rounded to FP32 [n_dofs][batch], gathered
+  float* Tlo = nullptr;  // ... and the low part of the FP32 pair Tf + Tlo (explicit steps)
   void* xh = nullptr;    // input values at hanging nodes (FP32 or FP64) [n_hang][batch]
   double* xh64 = nullptr;  // FP64 hanging values for FP64-operator launches of an FP32 context
   void* fh = nullptr;    // operator accumulator at hanging nodes [n_hang][batch]

@@ -40,20 +40,8 @@ inline int step_smem_bytes(int npc, int max_nu32, int max_hent8) {
   return npc * kStepCells * 2 + max_nu32 * 3 * 4 + max_hent8 * (2 + 4);
 }
 
-// The fused sequence keeps the working state T - T_ref as an unevaluated sum hi + lo of two
-// FP32 numbers (about 48 significant bits; |lo| <= ulp(hi) / 2, so hi is the state rounded to
-// FP32, the value the FP32 operator reads). The FP32 increment dt f / C~ is added exactly with
-// an error-free transformation (TwoSum) and renormalised (Fast2Sum), so that no FP64
-// operation or conversion is left in the step: on this GPU both run at about 1/60 of the
-// FP32 rate.
-__device__ __forceinline__ float2 ff_add(float2 x, float b) {
-  const float s = x.x + b;
-  const float bb = s - x.x;
-  const float err = (x.x - (s - bb)) + (b - bb);  // s + err == x.x + b exactly
-  const float t = x.y + err;
-  const float hi = s + t;
-  return make_float2(hi, t - (hi - s));
-}
+// The fused sequence keeps the working state T - T_ref as an unevaluated pair hi + lo of two
+// FP32 numbers (ff_add): hi is the state rounded to FP32, the value the FP32 operator reads.
 
 // One step n of the fused sequence. The kernel first completes step n-1 on the fly:
 // T_n = T_{n-1} + dt f_{n-1} / C~ for every slot it stages (the owner stores T_n), then

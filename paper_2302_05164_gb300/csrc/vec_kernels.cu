@@ -46,34 +46,6 @@ __global__ void k_update_f64(int64_t n, int B, double* __restrict__ T, double* _
   }
 }
 
-// FP32 operator: the increment dt f / C~ is formed in FP32 and added to the FP64 working
-// state Tw = T - T_ref (one FP64 add per dof); the FP32 copy Tf = round(Tw) that the cell
-// kernel gathers is refreshed in the same pass.
-template <int CAP>
-__global__ void k_update_f32(int64_t n, int B, double* __restrict__ Tw, float* __restrict__ Tf,
-                             float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
-                             const NodalCap nc, const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir,
-                             float dt) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const int d = B == 1 ? i : i / B;
-  const float fi = f[i];
-  f[i] = 0.f;
-  float ci = 0.f;
-  if (CAP == CAP_QUADRATURE) {
-    ci = Cacc[i];
-    Cacc[i] = 0.f;
-  }
-  if (dirichlet[d]) {
-    Tw[i] = tw_dir;
-    Tf[i] = tf_dir;
-    return;
-  }
-  const double t = euler_f32<CAP>(Tw[i], fi, ci, CAP == CAP_QUADRATURE ? 0.f : invC0[d], false, nc, tw_dir, dt);
-  Tw[i] = t;
-  Tf[i] = d2f_rn(t);
-}
-
 __global__ void k_capacity_nodal(int64_t n, int B, const double* __restrict__ C0, const double* __restrict__ T,
                                  const NodalCap nc, double* __restrict__ out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,26 +54,57 @@ __global__ void k_capacity_nodal(int64_t n, int B, const double* __restrict__ C0
   out[i] = C0[i / B] * (1.0 + nc.lat_ratio * exp(-0.5 * z * z));
 }
 
-// The same FP32-form update for one instance, four dofs per thread with 16-byte loads and
-// stores (arrays from cudaMalloc are 256-byte aligned).
+// FP32 operator: the working state T - T_ref is an unevaluated FP32 pair hi + lo (about 48
+// significant bits; hi is the state rounded to FP32, the value the cell kernel gathers). The
+// increment dt f / C~ is formed in FP32 from hi and added exactly (update_pair), so the step
+// has no FP64 arithmetic; f (and the capacity accumulator) are cleared for the next step.
+// Dirichlet dofs take the pair (hd, ld) of T_D - T_ref.
 template <int CAP>
-__device__ __forceinline__ void update_one(float fi, float ci, float ic, bool fixed, double& tw, float& tf,
-                                           const NodalCap& nc, double tw_dir, float tf_dir, float dt) {
-  tw = euler_f32<CAP>(tw, fi, ci, ic, fixed, nc, tw_dir, dt);
-  tf = fixed ? tf_dir : d2f_rn(tw);
+__device__ __forceinline__ void update_pair(float& hi, float& lo, float fi, float ci, float ic, bool fixed,
+                                            const NodalCap& nc, float hd, float ld, float dt) {
+  if (fixed) {
+    hi = hd;
+    lo = ld;
+    return;
+  }
+  const float2 r = ff_add(make_float2(hi, lo), increment_f32<CAP>(hi, fi, ci, ic, nc, dt));
+  hi = r.x;
+  lo = r.y;
 }
 
-// Batches with B a multiple of 4: four instances of one dof per thread (16-byte accesses,
-// one load of the dof's capacity and Dirichlet flag).
+// One element (dof, instance) per thread, any batch size.
 template <int CAP>
-__global__ void k_update_f32_b4(int64_t n4, int B, double* __restrict__ Tw, float* __restrict__ Tf,
-                                float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
-                                const NodalCap nc, const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir,
-                                float dt) {
+__global__ void k_update_pair(int64_t n, int B, float* __restrict__ hi, float* __restrict__ lo, float* __restrict__ f,
+                              float* __restrict__ Cacc, const float* __restrict__ invC0, const NodalCap nc,
+                              const uint8_t* __restrict__ dirichlet, float hd, float ld, float dt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int64_t d = B == 1 ? i : i / B;
+  const float fi = f[i];
+  f[i] = 0.f;
+  float ci = 0.f;
+  if (CAP == CAP_QUADRATURE) {
+    ci = Cacc[i];
+    Cacc[i] = 0.f;
+  }
+  float h = hi[i], l = lo[i];
+  update_pair<CAP>(h, l, fi, ci, CAP == CAP_QUADRATURE ? 0.f : __ldg(&invC0[d]), __ldg(&dirichlet[d]) != 0, nc, hd, ld,
+                   dt);
+  hi[i] = h;
+  lo[i] = l;
+}
+
+// Four consecutive elements per thread with 16-byte accesses (arrays from cudaMalloc are
+// 256-byte aligned; n a multiple of 4). PER_DOF: one instance, four dofs; otherwise B is a
+// multiple of 4 and the four elements are instances of one dof.
+template <int CAP, bool PER_DOF>
+__global__ void k_update_pair_x4(int64_t n4, int B, float* __restrict__ hi, float* __restrict__ lo,
+                                 float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
+                                 const NodalCap nc, const uint8_t* __restrict__ dirichlet, float hd, float ld,
+                                 float dt) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n4) return;
   const int64_t i0 = 4 * t;
-  const int64_t d = i0 / B;
   const float4 f4 = *reinterpret_cast<const float4*>(f + i0);
   *reinterpret_cast<float4*>(f + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
   float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -109,75 +112,43 @@ __global__ void k_update_f32_b4(int64_t n4, int B, double* __restrict__ Tw, floa
     c4 = *reinterpret_cast<const float4*>(Cacc + i0);
     *reinterpret_cast<float4*>(Cacc + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  const float ic = CAP == CAP_QUADRATURE ? 0.f : __ldg(&invC0[d]);
-  const bool fixed = __ldg(&dirichlet[d]) != 0;
-  double2 a = *reinterpret_cast<const double2*>(Tw + i0), b = *reinterpret_cast<const double2*>(Tw + i0 + 2);
-  float4 t4;
-  update_one<CAP>(f4.x, c4.x, ic, fixed, a.x, t4.x, nc, tw_dir, tf_dir, dt);
-  update_one<CAP>(f4.y, c4.y, ic, fixed, a.y, t4.y, nc, tw_dir, tf_dir, dt);
-  update_one<CAP>(f4.z, c4.z, ic, fixed, b.x, t4.z, nc, tw_dir, tf_dir, dt);
-  update_one<CAP>(f4.w, c4.w, ic, fixed, b.y, t4.w, nc, tw_dir, tf_dir, dt);
-  *reinterpret_cast<double2*>(Tw + i0) = a;
-  *reinterpret_cast<double2*>(Tw + i0 + 2) = b;
-  *reinterpret_cast<float4*>(Tf + i0) = t4;
+  float4 ic4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  uchar4 fx4;
+  if (PER_DOF) {
+    if (CAP != CAP_QUADRATURE) ic4 = __ldg(reinterpret_cast<const float4*>(invC0 + i0));
+    fx4 = __ldg(reinterpret_cast<const uchar4*>(dirichlet + i0));
+  } else {
+    const int64_t d = i0 / B;
+    const float ic = CAP == CAP_QUADRATURE ? 0.f : __ldg(&invC0[d]);
+    ic4 = make_float4(ic, ic, ic, ic);
+    const unsigned char fx = __ldg(&dirichlet[d]);
+    fx4 = make_uchar4(fx, fx, fx, fx);
+  }
+  float4 h4 = *reinterpret_cast<const float4*>(hi + i0), l4 = *reinterpret_cast<const float4*>(lo + i0);
+  update_pair<CAP>(h4.x, l4.x, f4.x, c4.x, ic4.x, fx4.x != 0, nc, hd, ld, dt);
+  update_pair<CAP>(h4.y, l4.y, f4.y, c4.y, ic4.y, fx4.y != 0, nc, hd, ld, dt);
+  update_pair<CAP>(h4.z, l4.z, f4.z, c4.z, ic4.z, fx4.z != 0, nc, hd, ld, dt);
+  update_pair<CAP>(h4.w, l4.w, f4.w, c4.w, ic4.w, fx4.w != 0, nc, hd, ld, dt);
+  *reinterpret_cast<float4*>(hi + i0) = h4;
+  *reinterpret_cast<float4*>(lo + i0) = l4;
 }
 
-template <int CAP>
-__global__ void k_update_f32_x4(int n, double* __restrict__ Tw, float* __restrict__ Tf, float* __restrict__ f,
-                                float* __restrict__ Cacc, const float* __restrict__ invC0, const NodalCap nc,
-                                const uint8_t* __restrict__ dirichlet, double tw_dir, float tf_dir, float dt) {
-  const int i0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-  if (i0 >= n) return;
-  if (i0 + 3 < n) {
-    const float4 f4 = *reinterpret_cast<const float4*>(f + i0);
-    *reinterpret_cast<float4*>(f + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (CAP == CAP_QUADRATURE) {
-      c4 = *reinterpret_cast<const float4*>(Cacc + i0);
-      *reinterpret_cast<float4*>(Cacc + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    const float4 ic4 = *reinterpret_cast<const float4*>(invC0 + i0);
-    const uchar4 d4 = *reinterpret_cast<const uchar4*>(dirichlet + i0);
-    double2 a = *reinterpret_cast<const double2*>(Tw + i0), b = *reinterpret_cast<const double2*>(Tw + i0 + 2);
-    float4 t4;
-    update_one<CAP>(f4.x, c4.x, ic4.x, d4.x, a.x, t4.x, nc, tw_dir, tf_dir, dt);
-    update_one<CAP>(f4.y, c4.y, ic4.y, d4.y, a.y, t4.y, nc, tw_dir, tf_dir, dt);
-    update_one<CAP>(f4.z, c4.z, ic4.z, d4.z, b.x, t4.z, nc, tw_dir, tf_dir, dt);
-    update_one<CAP>(f4.w, c4.w, ic4.w, d4.w, b.y, t4.w, nc, tw_dir, tf_dir, dt);
-    *reinterpret_cast<double2*>(Tw + i0) = a;
-    *reinterpret_cast<double2*>(Tw + i0 + 2) = b;
-    *reinterpret_cast<float4*>(Tf + i0) = t4;
-    return;
-  }
-  for (int i = i0; i < n; ++i) {  // ragged tail
-    const float fi = f[i];
-    f[i] = 0.f;
-    float ci = 0.f;
-    if (CAP == CAP_QUADRATURE) {
-      ci = Cacc[i];
-      Cacc[i] = 0.f;
-    }
-    double tw = Tw[i];
-    float tf;
-    update_one<CAP>(fi, ci, invC0[i], dirichlet[i] != 0, tw, tf, nc, tw_dir, tf_dir, dt);
-    Tw[i] = tw;
-    Tf[i] = tf;
-  }
-}
-
-// Tw = T - off (FP64), Tf = round_to_f32(Tw); Tw may be null
-__global__ void k_prepare_f32(int64_t n, const double* __restrict__ T, double off, double* __restrict__ Tw,
-                              float* __restrict__ Tf) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+// hi + lo = T - off (lo may be null: hi only)
+__global__ void k_prepare_f32(int64_t n, const double* __restrict__ T, double off, float* __restrict__ hi,
+                              float* __restrict__ lo) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const double t = T[i] - off;
-  if (Tw) Tw[i] = t;
-  Tf[i] = d2f_rn(t);
+  const float h = d2f_rn(t);
+  hi[i] = h;
+  if (lo) lo[i] = d2f_rn(t - f2d(h));
 }
 
-__global__ void k_finish_f32(int64_t n, const double* __restrict__ Tw, double off, double* __restrict__ T) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) T[i] = Tw[i] + off;
+// T = off + (hi + lo), formed in FP64
+__global__ void k_finish_f32(int64_t n, const float* __restrict__ hi, const float* __restrict__ lo, double off,
+                             double* __restrict__ T) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) T[i] = off + (f2d(hi[i]) + f2d(lo[i]));
 }
 
 // ---- laser on top faces ------------------------------------------------------------------
@@ -659,29 +630,31 @@ cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double*
   return cudaGetLastError();
 }
 
-cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float* Tf, float* f, float* Cacc,
-                              const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, double tw_dir,
-                              float tf_dir, float dt, cudaStream_t s) {
+template <int CAP>
+cudaError_t update_pair_cap(int64_t n_dofs, int B, float* hi, float* lo, float* f, float* Cacc, const float* invC0,
+                            const NodalCap& nc, const uint8_t* dirichlet, float hd, float ld, float dt, cudaStream_t s) {
   const int64_t n = n_dofs * B;
-  if (n == 0) return cudaSuccess;
-  if (B > 1 && B % 4 == 0) {
+  if (B % 4 == 0 || (B == 1 && n % 4 == 0)) {
     const int64_t n4 = n / 4;
-    if (cap == CAP_QUADRATURE) k_update_f32_b4<CAP_QUADRATURE><<<grid_for(n4), kBS, 0, s>>>(n4, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-    else if (cap == CAP_NODAL) k_update_f32_b4<CAP_NODAL><<<grid_for(n4), kBS, 0, s>>>(n4, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-    else k_update_f32_b4<CAP_CONST><<<grid_for(n4), kBS, 0, s>>>(n4, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-    return cudaGetLastError();
+    if (B == 1)
+      k_update_pair_x4<CAP, true><<<grid_for(n4), kBS, 0, s>>>(n4, B, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
+    else
+      k_update_pair_x4<CAP, false><<<grid_for(n4), kBS, 0, s>>>(n4, B, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
+  } else {
+    k_update_pair<CAP><<<grid_for(n), kBS, 0, s>>>(n, B, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
   }
-  if (B == 1) {
-    const int64_t nt = (n + 3) / 4;
-    if (cap == CAP_QUADRATURE) k_update_f32_x4<CAP_QUADRATURE><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-    else if (cap == CAP_NODAL) k_update_f32_x4<CAP_NODAL><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-    else k_update_f32_x4<CAP_CONST><<<grid_for(nt), kBS, 0, s>>>((int)n, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-    return cudaGetLastError();
-  }
-  if (cap == CAP_QUADRATURE) k_update_f32<CAP_QUADRATURE><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-  else if (cap == CAP_NODAL) k_update_f32<CAP_NODAL><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
-  else k_update_f32<CAP_CONST><<<grid_for(n), kBS, 0, s>>>(n, B, Tw, Tf, f, Cacc, invC0, nc, dirichlet, tw_dir, tf_dir, dt);
   return cudaGetLastError();
+}
+
+cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, float* hi, float* lo, float* f, float* Cacc,
+                              const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, float2 x_dir, float dt,
+                              cudaStream_t s) {
+  if (n_dofs * B == 0) return cudaSuccess;
+  if (cap == CAP_QUADRATURE)
+    return update_pair_cap<CAP_QUADRATURE>(n_dofs, B, hi, lo, f, Cacc, invC0, nc, dirichlet, x_dir.x, x_dir.y, dt, s);
+  if (cap == CAP_NODAL)
+    return update_pair_cap<CAP_NODAL>(n_dofs, B, hi, lo, f, Cacc, invC0, nc, dirichlet, x_dir.x, x_dir.y, dt, s);
+  return update_pair_cap<CAP_CONST>(n_dofs, B, hi, lo, f, Cacc, invC0, nc, dirichlet, x_dir.x, x_dir.y, dt, s);
 }
 
 cudaError_t launch_hang_values_zero(bool f32, const DevMesh& M, const void* x, void* out, void* fh, void* Ch,
@@ -701,15 +674,15 @@ cudaError_t launch_capacity_nodal(int64_t n_dofs, int B, const double* C0, const
   return cudaGetLastError();
 }
 
-cudaError_t launch_prepare_f32(int64_t n, const double* T, double off, double* Tw, float* Tf, cudaStream_t s) {
+cudaError_t launch_prepare_f32(int64_t n, const double* T, double off, float* hi, float* lo, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_prepare_f32<<<grid_for(n), kBS, 0, s>>>(n, T, off, Tw, Tf);
+  k_prepare_f32<<<grid_for(n), kBS, 0, s>>>(n, T, off, hi, lo);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish_f32(int64_t n, const double* Tw, double off, double* T, cudaStream_t s) {
+cudaError_t launch_finish_f32(int64_t n, const float* hi, const float* lo, double off, double* T, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  k_finish_f32<<<grid_for(n), kBS, 0, s>>>(n, Tw, off, T);
+  k_finish_f32<<<grid_for(n), kBS, 0, s>>>(n, hi, lo, off, T);
   return cudaGetLastError();
 }
 

@@ -41,29 +41,36 @@ __device__ __forceinline__ float increment_f32(float value, float fi, float ci, 
   return dt * fi * ic;
 }
 
-// The FP32-operator update of the FP64 working state tw (one FP64 add); Dirichlet dofs take
-// tw_dir.
-template <int CAP>
-__device__ __forceinline__ double euler_f32(double tw, float fi, float ci, float ic, bool fixed, const NodalCap& nc,
-                                            double tw_dir, float dt) {
-  if (fixed) return tw_dir;
-  return tw + f2d(increment_f32<CAP>(CAP == CAP_NODAL ? d2f_rn(tw) : 0.f, fi, ci, ic, nc, dt));
+// x + b for an unevaluated FP32 pair x = hi + lo (|lo| <= ulp(hi) / 2) and an FP32 b: the
+// sum is formed exactly by TwoSum and renormalised by Fast2Sum (Knuth; Dekker), so the pair
+// keeps about 48 significant bits without FP64 arithmetic (on this GPU FP64 operations and
+// conversions run at about 1/60 of the FP32 rate).
+__device__ __forceinline__ float2 ff_add(float2 x, float b) {
+  const float s = x.x + b;
+  const float bb = s - x.x;
+  const float err = (x.x - (s - bb)) + (b - bb);  // s + err == x.x + b exactly
+  const float t = x.y + err;
+  const float hi = s + t;
+  return make_float2(hi, t - (hi - s));
 }
 
 cudaError_t launch_update_f64(int cap, int64_t n_dofs, int B, double* T, double* f, double* Cacc,
                               const double* invC0, const NodalCap& nc, const uint8_t* dirichlet, double T_dir,
                               double dt, cudaStream_t s);
-cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, double* Tw, float* Tf, float* f, float* Cacc,
-                              const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, double tw_dir,
-                              float tf_dir, float dt, cudaStream_t s);
+// The FP32-operator update of the pair state hi + lo = T - T_ref ([n_dofs][B]); x_dir is the
+// pair of T_D - T_ref.
+cudaError_t launch_update_f32(int cap, int64_t n_dofs, int B, float* hi, float* lo, float* f, float* Cacc,
+                              const float* invC0, const NodalCap& nc, const uint8_t* dirichlet, float2 x_dir, float dt,
+                              cudaStream_t s);
 // x_h = P_h x with f_h (and C_h, nullable) cleared
 cudaError_t launch_hang_values_zero(bool f32, const DevMesh& M, const void* x, void* out, void* fh, void* Ch,
                                     cudaStream_t s);
 // C_out[d][b] = C0[d] c_app(T[d][b]) / c (nodal lumping) in FP64
 cudaError_t launch_capacity_nodal(int64_t n_dofs, int B, const double* C0, const double* T, const NodalCap& nc,
                                   double* C_out, cudaStream_t s);
-cudaError_t launch_prepare_f32(int64_t n, const double* T, double off, double* Tw, float* Tf, cudaStream_t s);
-cudaError_t launch_finish_f32(int64_t n, const double* Tw, double off, double* T, cudaStream_t s);
+// hi + lo = T - off as an FP32 pair (lo nullable: hi only) / T = off + (hi + lo) in FP64
+cudaError_t launch_prepare_f32(int64_t n, const double* T, double off, float* hi, float* lo, cudaStream_t s);
+cudaError_t launch_finish_f32(int64_t n, const float* hi, const float* lo, double off, double* T, cudaStream_t s);
 cudaError_t launch_round_f32(int64_t n, const double* x, float* y, cudaStream_t s);
 cudaError_t launch_f32_to_f64(int64_t n, const float* x, double* y, cudaStream_t s);
 cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const double* power,
