@@ -189,11 +189,17 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10, sh
     cell_ms, cell_n = pbf.pbf_ctx_kernel_time(ctx.h)
     rate = n * batch * chunk * K / (ms * 1e-3) / 1e9
     hbm = peaks.get("hbm_gbs", 6800.0)
+    n_cells = mesh.info()["n_active"]
+    cell_us = 1e3 * cell_ms / max(cell_n, 1)
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    cell_tflops = flops_per_cell_q2_nonlinear() * n_cells * batch / (cell_us * 1e-6) / 1e12
     ctx.close()
     mesh.close()
     return {"workload": f"C4: Q2 1.0x0.5x0.25 mm, {n} dofs x {batch} instances (own powers and k scales)",
             "value": rate, "unit": "GDoF/s", "explicit_steps_per_step": chunk, "steps": K,
-            "cell_kernel_avg_us": 1e3 * cell_ms / max(cell_n, 1), "step_shape": SHAPES[variant],
+            "cell_kernel_avg_us": cell_us, "step_shape": SHAPES[variant],
+            "cell_kernel_roofline": {"bound": "alu", "achieved": cell_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                                     "frac": cell_tflops / fp32_peak, "cells_x_instances": n_cells * batch},
             "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / hbm, "l2": "state > L2; flushed between timed steps"}
 
 
@@ -222,6 +228,41 @@ def bench_adjoint(pbf, I, torch, stream, batch=8, nsteps=200, ckpt=10):
     mesh.close()
     return {"workload": f"C4 mesh ({n} dofs) x {batch} instances, {nsteps} steps, {ckpt} stored states",
             "seconds": a.elapsed_time(b) * 1e-3, "forward_steps": fwd, "finite": bool(np.isfinite(g).all())}
+
+
+def bench_implicit(pbf, I, torch, stream, nsteps=20):
+    """Configuration 3: the interlayer cool-down. The C1 brick with a newly activated three-cell
+    powder layer (42,900 dofs), backward Euler at dt = 1e-2 s, Chebyshev(5)-Jacobi CG to a
+    1e-8 relative residual with bounds from 30 Lanczos steps, FP64 and FP32 operators."""
+    mesh = pbf.Mesh(I.c3_mesh())
+    pbf.pbf_mesh_activate_layer(mesh.h, I.C3_LAYER_TOP, 1, I.T0)
+    n = mesh.info()["n_dofs"]
+    desc = I.c3_mesh(active_top_z=I.C3_LAYER_TOP)
+    tab = mesh.tables()
+    xyz = np.array(desc["origin"]) + np.array(desc["tree_h"]) * tab["dof_coord"] / (2 * 2.0 ** desc["max_level"])
+    T0 = I.melt_pool_field(xyz, (0.5e-3, 0.25e-3, 0.25e-3), 1500.0, 120e-6, seed=4, noise=0.01)
+    out = {"workload": f"C3: C1 brick + 3-cell powder layer, {n} dofs, backward Euler dt = 1e-2 s, {nsteps} steps",
+           "rtol": 1e-8, "cheb_degree": 5}
+    dt = 1e-2
+    for name, prec in (("f64", pbf.PBF_F64), ("f32op", pbf.PBF_F32OP)):
+        ctx = pbf.Context(mesh, I.TI64_CONST, prec)
+        lo, hi = pbf.pbf_cheb_bounds(ctx.h, dt, None, 30, stream=stream)
+        bounds = (lo, 1.1 * hi)
+        T = torch.tensor(T0, dtype=torch.float64, device="cuda")
+        pbf.pbf_implicit_solve(ctx.h, T, dt, 2, 1e-8, 500, 5, np.array(bounds), stream=stream)  # warm-up
+        T = torch.tensor(T0, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        st, iters = pbf.pbf_implicit_solve(ctx.h, T, dt, nsteps, 1e-8, 500, 5, np.array(bounds), stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms = a.elapsed_time(b)
+        out[name] = {"status": int(st), "ms_per_step": ms / nsteps, "cg_iterations_per_step": float(np.mean(iters)),
+                     "us_per_cg_iteration": 1e3 * ms / max(1, int(np.sum(iters)))}
+        ctx.close()
+    mesh.close()
+    return out
 
 
 def dist_setup():
@@ -462,6 +503,7 @@ def main():
                       "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8}
         out["batched"] = bench_batched(pbf, I, torch, stream, flush, peaks, K)
         out["adjoint"] = bench_adjoint(pbf, I, torch, stream)
+        out["implicit"] = bench_implicit(pbf, I, torch, stream)
         if rank == 0 and ws >= 1:
             rate, n_s, done, secs = time_oracle(3, max_seconds=25.0)
             out["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

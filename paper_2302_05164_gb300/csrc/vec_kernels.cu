@@ -94,43 +94,55 @@ __global__ void k_update_pair(int64_t n, int B, float* __restrict__ hi, float* _
   lo[i] = l;
 }
 
-// Four consecutive elements per thread with 16-byte accesses (arrays from cudaMalloc are
-// 256-byte aligned; n a multiple of 4). PER_DOF: one instance, four dofs; otherwise B is a
-// multiple of 4 and the four elements are instances of one dof.
+// Streaming form: each thread takes kUpdGroups groups of four consecutive elements with
+// 16-byte accesses (arrays from cudaMalloc are 256-byte aligned; n a multiple of 4) and
+// issues every load of its groups before the first use, so that enough bytes are in flight
+// per SM. PER_DOF: one instance, a group is four dofs; otherwise B is a multiple of 4 and a
+// group is four instances of dof t / B4 (32-bit indices: n_dofs x B < 2^31).
+constexpr int kUpdGroups = 2;
 template <int CAP, bool PER_DOF>
-__global__ void k_update_pair_x4(int64_t n4, int B, float* __restrict__ hi, float* __restrict__ lo,
-                                 float* __restrict__ f, float* __restrict__ Cacc, const float* __restrict__ invC0,
-                                 const NodalCap nc, const uint8_t* __restrict__ dirichlet, float hd, float ld,
-                                 float dt) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n4) return;
-  const int64_t i0 = 4 * t;
-  const float4 f4 = *reinterpret_cast<const float4*>(f + i0);
-  *reinterpret_cast<float4*>(f + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
-  float4 c4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (CAP == CAP_QUADRATURE) {
-    c4 = *reinterpret_cast<const float4*>(Cacc + i0);
-    *reinterpret_cast<float4*>(Cacc + i0) = make_float4(0.f, 0.f, 0.f, 0.f);
+__global__ void __launch_bounds__(256) k_update_pair_x4(int n4, int B4, float* __restrict__ hi,
+                                                         float* __restrict__ lo, float* __restrict__ f,
+                                                         float* __restrict__ Cacc, const float* __restrict__ invC0,
+                                                         const NodalCap nc, const uint8_t* __restrict__ dirichlet,
+                                                         float hd, float ld, float dt) {
+  const int t0 = blockIdx.x * (blockDim.x * kUpdGroups) + threadIdx.x;
+  float4 f4[kUpdGroups], c4[kUpdGroups], h4[kUpdGroups], l4[kUpdGroups], ic4[kUpdGroups];
+  uchar4 fx4[kUpdGroups];
+#pragma unroll
+  for (int k = 0; k < kUpdGroups; ++k) {
+    const int t = t0 + k * blockDim.x;
+    if (t >= n4) continue;
+    const int i0 = 4 * t;
+    f4[k] = __ldcs(reinterpret_cast<const float4*>(f + i0));
+    c4[k] = CAP == CAP_QUADRATURE ? __ldcs(reinterpret_cast<const float4*>(Cacc + i0)) : make_float4(0.f, 0.f, 0.f, 0.f);
+    h4[k] = __ldcs(reinterpret_cast<const float4*>(hi + i0));
+    l4[k] = __ldcs(reinterpret_cast<const float4*>(lo + i0));
+    if (PER_DOF) {
+      ic4[k] = CAP == CAP_QUADRATURE ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldg(reinterpret_cast<const float4*>(invC0 + i0));
+      fx4[k] = __ldg(reinterpret_cast<const uchar4*>(dirichlet + i0));
+    } else {
+      const int d = t / B4;
+      const float ic = CAP == CAP_QUADRATURE ? 0.f : __ldg(&invC0[d]);
+      ic4[k] = make_float4(ic, ic, ic, ic);
+      const unsigned char fx = __ldg(&dirichlet[d]);
+      fx4[k] = make_uchar4(fx, fx, fx, fx);
+    }
   }
-  float4 ic4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  uchar4 fx4;
-  if (PER_DOF) {
-    if (CAP != CAP_QUADRATURE) ic4 = __ldg(reinterpret_cast<const float4*>(invC0 + i0));
-    fx4 = __ldg(reinterpret_cast<const uchar4*>(dirichlet + i0));
-  } else {
-    const int64_t d = i0 / B;
-    const float ic = CAP == CAP_QUADRATURE ? 0.f : __ldg(&invC0[d]);
-    ic4 = make_float4(ic, ic, ic, ic);
-    const unsigned char fx = __ldg(&dirichlet[d]);
-    fx4 = make_uchar4(fx, fx, fx, fx);
+#pragma unroll
+  for (int k = 0; k < kUpdGroups; ++k) {
+    const int t = t0 + k * blockDim.x;
+    if (t >= n4) continue;
+    const int i0 = 4 * t;
+    update_pair<CAP>(h4[k].x, l4[k].x, f4[k].x, c4[k].x, ic4[k].x, fx4[k].x != 0, nc, hd, ld, dt);
+    update_pair<CAP>(h4[k].y, l4[k].y, f4[k].y, c4[k].y, ic4[k].y, fx4[k].y != 0, nc, hd, ld, dt);
+    update_pair<CAP>(h4[k].z, l4[k].z, f4[k].z, c4[k].z, ic4[k].z, fx4[k].z != 0, nc, hd, ld, dt);
+    update_pair<CAP>(h4[k].w, l4[k].w, f4[k].w, c4[k].w, ic4[k].w, fx4[k].w != 0, nc, hd, ld, dt);
+    __stcs(reinterpret_cast<float4*>(hi + i0), h4[k]);
+    __stcs(reinterpret_cast<float4*>(lo + i0), l4[k]);
+    __stcs(reinterpret_cast<float4*>(f + i0), make_float4(0.f, 0.f, 0.f, 0.f));
+    if (CAP == CAP_QUADRATURE) __stcs(reinterpret_cast<float4*>(Cacc + i0), make_float4(0.f, 0.f, 0.f, 0.f));
   }
-  float4 h4 = *reinterpret_cast<const float4*>(hi + i0), l4 = *reinterpret_cast<const float4*>(lo + i0);
-  update_pair<CAP>(h4.x, l4.x, f4.x, c4.x, ic4.x, fx4.x != 0, nc, hd, ld, dt);
-  update_pair<CAP>(h4.y, l4.y, f4.y, c4.y, ic4.y, fx4.y != 0, nc, hd, ld, dt);
-  update_pair<CAP>(h4.z, l4.z, f4.z, c4.z, ic4.z, fx4.z != 0, nc, hd, ld, dt);
-  update_pair<CAP>(h4.w, l4.w, f4.w, c4.w, ic4.w, fx4.w != 0, nc, hd, ld, dt);
-  *reinterpret_cast<float4*>(hi + i0) = h4;
-  *reinterpret_cast<float4*>(lo + i0) = l4;
 }
 
 // hi + lo = T - off (lo may be null: hi only)
@@ -635,11 +647,12 @@ cudaError_t update_pair_cap(int64_t n_dofs, int B, float* hi, float* lo, float* 
                             const NodalCap& nc, const uint8_t* dirichlet, float hd, float ld, float dt, cudaStream_t s) {
   const int64_t n = n_dofs * B;
   if (B % 4 == 0 || (B == 1 && n % 4 == 0)) {
-    const int64_t n4 = n / 4;
+    const int n4 = (int)(n / 4);
+    const unsigned grid = grid_for(n4, kBS * kUpdGroups);
     if (B == 1)
-      k_update_pair_x4<CAP, true><<<grid_for(n4), kBS, 0, s>>>(n4, B, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
+      k_update_pair_x4<CAP, true><<<grid, kBS, 0, s>>>(n4, 1, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
     else
-      k_update_pair_x4<CAP, false><<<grid_for(n4), kBS, 0, s>>>(n4, B, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
+      k_update_pair_x4<CAP, false><<<grid, kBS, 0, s>>>(n4, B / 4, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
   } else {
     k_update_pair<CAP><<<grid_for(n), kBS, 0, s>>>(n, B, hi, lo, f, Cacc, invC0, nc, dirichlet, hd, ld, dt);
   }
