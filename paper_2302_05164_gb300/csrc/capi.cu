@@ -641,6 +641,10 @@ void CtxBase::set_material_constants(double dt) {
 }
 
 void CtxBase::release() {
+  if (cheb_exec) cudaGraphExecDestroy(cheb_exec);
+  cheb_exec = nullptr;
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  cap_stream = nullptr;
   for (void* p : allocs) cudaFree(p);
   allocs.clear();
   for (auto& ev : events) {

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <cstdio>
 #include <string>
 #include <vector>
@@ -101,6 +102,53 @@ struct Implicit {
       ++c->launches;
       rho = rho_new;
     }
+  }
+
+  // The same application as one CUDA-graph launch. For fixed (dt, bounds, degree) and vectors
+  // the preconditioner is a fixed sequence of about 6 (deg + 1) small launches, which at the
+  // sizes of an interlayer cool-down cost more in launch latency than in work; it is captured
+  // once on a private stream and replayed on the caller's stream.
+  void precondition(const double* r, double* z, int deg, double lmin, double lmax, double* res, double* d,
+                    double* Ad) {
+    if (e != cudaSuccess) return;
+    const double key[12] = {dt, lmin, lmax, (double)deg, (double)(uintptr_t)r, (double)(uintptr_t)z,
+                            (double)(uintptr_t)res, (double)(uintptr_t)d, (double)(uintptr_t)Ad,
+                            (double)(uintptr_t)c->diag, (double)(uintptr_t)c->Tf, (double)(uintptr_t)c->f};
+    if (!c->cheb_exec || std::memcmp(key, c->cheb_key, sizeof key) != 0) {
+      if (c->cheb_exec) {
+        e = cudaGraphExecDestroy(c->cheb_exec);
+        c->cheb_exec = nullptr;
+        if (e != cudaSuccess) return;
+      }
+      if (!c->cap_stream) {
+        e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return;
+      }
+      const long long l0 = c->launches;
+      const bool timing = c->timing;
+      c->timing = false;  // no event records inside the graph
+      cudaStream_t user = s;
+      e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        c->timing = timing;
+        return;
+      }
+      s = c->cap_stream;
+      chebyshev(r, z, deg, lmin, lmax, res, d, Ad);
+      s = user;
+      cudaGraph_t g = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &g);
+      c->timing = timing;
+      if (e == cudaSuccess) e = ec;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cheb_exec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) return;
+      c->cheb_launches = c->launches - l0;
+      c->launches = l0;
+      std::memcpy(c->cheb_key, key, sizeof key);
+    }
+    e = cudaGraphLaunch(c->cheb_exec, s);
+    c->launches += c->cheb_launches;
   }
 };
 
@@ -260,23 +308,29 @@ extern "C" pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt,
     double rn = r0;
     int it = 0;
     if (r0 > 0.0) {
-      I.chebyshev(r, z, cheb_degree, bounds[0], bounds[1], res, d, Ad);
+      // the CG scalars stay on the device (rz in sc[4] / sc[6], alternating; p.Ap in sc[5]);
+      // the host reads r.r (through sc[0], Implicit::dot) once per iteration for the stopping
+      // test
+      double* sc = ctx->scal;
+      double* rz = sc + 4;
+      double* rz_new = sc + 6;
+      I.precondition(r, z, cheb_degree, bounds[0], bounds[1], res, d, Ad);
       if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(p, z, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
-      double rz = I.dot(r, z);
+      if (I.e == cudaSuccess) I.e = launch_dot(n, 1, r, z, nullptr, nullptr, ctx->part, rz, s);
+      ctx->launches += 2;
       while (rn > rtol * r0 && it < max_it && I.e == cudaSuccess) {
         I.apply(p, Ap);
-        const double alpha = rz / I.dot(p, Ap);
-        if (I.e == cudaSuccess) I.e = launch_axpy2(n, alpha, p, Ap, x, r, s);
-        ++ctx->launches;
+        if (I.e == cudaSuccess) I.e = launch_dot(n, 1, p, Ap, nullptr, nullptr, ctx->part, sc + 5, s);
+        if (I.e == cudaSuccess) I.e = launch_axpy2_dev(n, rz, sc + 5, p, Ap, x, r, s);
+        ctx->launches += 3;
         ++it;
         rn = std::sqrt(I.dot(r, r));
         if (rn <= rtol * r0) break;
-        I.chebyshev(r, z, cheb_degree, bounds[0], bounds[1], res, d, Ad);
-        const double rz_new = I.dot(r, z);
-        const double beta = rz_new / rz;
-        rz = rz_new;
-        if (I.e == cudaSuccess) I.e = launch_xpby(n, z, beta, p, s);
-        ++ctx->launches;
+        I.precondition(r, z, cheb_degree, bounds[0], bounds[1], res, d, Ad);
+        if (I.e == cudaSuccess) I.e = launch_dot(n, 1, r, z, nullptr, nullptr, ctx->part, rz_new, s);
+        if (I.e == cudaSuccess) I.e = launch_xpby_dev(n, z, rz_new, rz, p, s);
+        ctx->launches += 3;
+        std::swap(rz, rz_new);
       }
     }
     if (rn > rtol * r0) converged = false;

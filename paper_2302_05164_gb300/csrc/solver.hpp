@@ -81,6 +81,13 @@ struct CtxBase {
   // implicit-operator diagonal cache
   double* diag = nullptr;
   double diag_dt = -1.0;
+  // the Chebyshev preconditioner application of the implicit solve as a CUDA graph: captured
+  // on a private stream, launched on the caller's; rebuilt when its key (dt, bounds, degree,
+  // vectors) changes
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t cheb_exec = nullptr;
+  double cheb_key[12] = {};
+  long long cheb_launches = 0;
   // state
   bool poisoned = false;
   bool timing = false;

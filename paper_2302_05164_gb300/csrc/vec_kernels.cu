@@ -420,6 +420,24 @@ __global__ void k_axpy2(int64_t n, double alpha, const double* __restrict__ p, c
   r[i] -= alpha * Ap[i];
 }
 
+// The same recurrences with the CG scalars read from device memory (alpha = num / den, beta =
+// num / den), so that a CG iteration needs no host round trip for them.
+__global__ void k_axpy2_dev(int64_t n, const double* __restrict__ num, const double* __restrict__ den,
+                            const double* __restrict__ p, const double* __restrict__ Ap, double* __restrict__ x,
+                            double* __restrict__ r) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double alpha = num[0] / den[0];
+  x[i] += alpha * p[i];
+  r[i] -= alpha * Ap[i];
+}
+
+__global__ void k_xpby_dev(int64_t n, const double* __restrict__ z, const double* __restrict__ num,
+                           const double* __restrict__ den, double* __restrict__ p) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) p[i] = z[i] + (num[0] / den[0]) * p[i];
+}
+
 __global__ void k_xpby(int64_t n, const double* __restrict__ z, double beta, double* __restrict__ p) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = z[i] + beta * p[i];
@@ -781,6 +799,18 @@ cudaError_t launch_axpy2(int64_t n, double alpha, const double* p, const double*
                          cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_axpy2<<<grid_for(n), kBS, 0, s>>>(n, alpha, p, Ap, x, r);
+  return cudaGetLastError();
+}
+cudaError_t launch_axpy2_dev(int64_t n, const double* num, const double* den, const double* p, const double* Ap,
+                             double* x, double* r, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_axpy2_dev<<<grid_for(n), kBS, 0, s>>>(n, num, den, p, Ap, x, r);
+  return cudaGetLastError();
+}
+cudaError_t launch_xpby_dev(int64_t n, const double* z, const double* num, const double* den, double* p,
+                            cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  k_xpby_dev<<<grid_for(n), kBS, 0, s>>>(n, z, num, den, p);
   return cudaGetLastError();
 }
 cudaError_t launch_xpby(int64_t n, const double* z, double beta, double* p, cudaStream_t s) {

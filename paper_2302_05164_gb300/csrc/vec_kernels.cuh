@@ -86,6 +86,11 @@ cudaError_t launch_hang_distribute(bool f32, const DevMesh& M, void* fh, void* f
 cudaError_t launch_axpy2(int64_t n, double alpha, const double* p, const double* Ap, double* x, double* r,
                          cudaStream_t s);
 cudaError_t launch_xpby(int64_t n, const double* z, double beta, double* p, cudaStream_t s);
+// x += (num/den) p, r -= (num/den) Ap and p = z + (num/den) p with the scalars in device memory
+cudaError_t launch_axpy2_dev(int64_t n, const double* num, const double* den, const double* p, const double* Ap,
+                             double* x, double* r, cudaStream_t s);
+cudaError_t launch_xpby_dev(int64_t n, const double* z, const double* num, const double* den, double* p,
+                            cudaStream_t s);
 cudaError_t launch_cheb_init(int64_t n, const double* r, const double* diag, double inv_theta, double* res, double* d,
                              double* z, const uint8_t* mask, cudaStream_t s);
 cudaError_t launch_cheb_update(int64_t n, const double* Ad, double* res, double* d, double* z, const double* diag,

@@ -108,6 +108,26 @@ def test_implicit_cooldown_matches_oracle(P, c3, prec):
     assert got.max() < T.max()  # the hot track cools
 
 
+def test_implicit_changing_dt_and_bounds_on_one_context(P, c3):
+    """The preconditioner runs as a CUDA graph captured for one (dt, bounds, degree); solves
+    with another dt and other bounds on the same context, and back, still match the oracle
+    (the graph is rebuilt whenever its parameters change)."""
+    om, T = c3["om"], c3["T"]
+    dt2 = 2.5e-3
+    lmin, lmax = om.lanczos_bounds(I.TI64_CONST, dt2, c3["b"], 30)
+    bounds2 = (lmin, 1.1 * lmax)
+    ref2, it2, st = om.implicit(I.TI64_CONST, T, dt2, 1, RTOL, 400, 5, *bounds2)
+    assert st == 0
+    m = gpu_c3(P)
+    ctx = P.Context(m, I.TI64_CONST, P.PBF_F64)
+    for dt, bounds, ref in ((c3["dt"], c3["bounds"], c3["ref"]), (dt2, bounds2, ref2),
+                            (c3["dt"], c3["bounds"], c3["ref"])):
+        Td = to_dev(T)
+        status, iters = P.pbf_implicit_solve(ctx.h, Td, dt, 1, RTOL, 400, 5, np.array(bounds))
+        assert status == 0
+        assert rel(Td.cpu().numpy(), ref) < 1e-10
+
+
 def test_implicit_reports_nonconvergence_and_bad_inputs(P, c3):
     m = gpu_c3(P)
     ctx = P.Context(m, I.TI64_CONST, P.PBF_F64)
