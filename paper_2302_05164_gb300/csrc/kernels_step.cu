@@ -13,7 +13,7 @@
 //  4. pushes hanging-node sums to their masters in shared memory (G_e^T P^T) and adds each
 //     dof slot's sum to global memory once, in ascending dof order.
 // Compared with a per-cell gather / atomic scatter plus a separate update kernel, a dof's
-// value is read about 1.4 times instead of once per adjacent cell (up to 8 for Q2 vertices),
+// value is read about 1.5 times instead of once per adjacent cell (up to 8 for Q2 vertices),
 // its contributions are added with one global atomic per patch instead of one per cell, and
 // the update costs no launch of its own.
 #include <algorithm>
@@ -29,7 +29,7 @@ __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepco
 __device__ __forceinline__ void grid_dependency_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 constexpr int kStepMinBlocks = 10;  // 64-thread blocks: at most 102 registers per thread
-constexpr int kStageUnroll = 8;     // dof slots each thread has in flight while staging
+constexpr int kStageUnroll = 14;    // dof slots each thread has in flight while staging
 
 // Loads of data that changes between steps: through the read-only path when each step is its
 // own launch, through L2 only (coherent with other blocks' stores) inside a persistent launch.

@@ -30,7 +30,7 @@ struct StepTables {
 };
 
 // Shared-memory position of slot j of a patch: an XOR swizzle within each 32-slot block.
-// Slots of consecutive Z-order cells are about 8 apart (the new nodes per Q2 cell), so the
+// Slots of consecutive Morton-order cells are about 8 apart (the new nodes per Q2 cell), so the
 // same local node of the 32 cells of a warp would fall into 4 banks; the swizzle spreads them
 // over all 32, and keeps a warp's 32 consecutive slots conflict-free.
 __host__ __device__ inline int step_swizzle(int j) { return j ^ ((j >> 5) & 31); }

@@ -382,8 +382,7 @@ __global__ void k_hang_values(int n_hang, int B, const int32_t* __restrict__ ptr
   out[i] = s;
 }
 
-// x_h = P_h x and f_h <- 0, C_h <- 0 (before a cell kernel whose hanging contributions the
-// update kernel pulls)
+// x_h = P_h x and f_h <- 0, C_h <- 0 (before a cell kernel of the per-cell explicit step)
 template <typename R>
 __global__ void k_hang_values_zero(int n_hang, int B, const int32_t* __restrict__ ptr, const int32_t* __restrict__ idx,
                                    const R* __restrict__ w, const R* __restrict__ x, R* __restrict__ out,
