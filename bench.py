@@ -203,6 +203,47 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10, sh
             "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / hbm, "l2": "state > L2; flushed between timed steps"}
 
 
+def bench_large(pbf, I, torch, stream, flush, peaks, K=5, chunk=20):
+    """The C2 block and material with a 500 um refinement ball (5 um cells): 2.29 M cells,
+    18.2 M dofs, one instance. Its state and tables (about 0.7 GB) exceed the L2, so the fused
+    step runs from HBM over about 24 waves of patches instead of 1.4."""
+    desc = I.mesh_desc((50, 50, 25), (40e-6,) * 3, 2, 3, I.c2_spot_regions(1.0e-3, 1.0e-3, radius=500e-6))
+    mat = I.TI64_NONLIN_Q2
+    t0 = time.perf_counter()
+    mesh = pbf.Mesh(desc)
+    info = mesh.info()
+    n = info["n_dofs"]
+    tab = mesh.tables()
+    xyz = np.array(desc["origin"]) + np.array(desc["tree_h"]) * tab["dof_coord"] / (2 * 2.0 ** desc["max_level"])
+    T0 = I.melt_pool_field(xyz, (1.0e-3, 1.0e-3, 1.0e-3), 2600.0, 50e-6, seed=23, noise=0.01)
+    ls = I.laser([(0.6e-3, 1.0e-3, 1.4e-3, 1.0e-3, 0.0, 4e-4)], [200.0], eta=0.35, radius=40e-6)
+    ctx = pbf.Context(mesh, mat, pbf.PBF_F32OP)
+    setup_s = time.perf_counter() - t0
+    T = torch.tensor(T0, dtype=torch.float64, device="cuda")
+    dt = 2e-8
+    variant, shape_us = pbf.pbf_ctx_autotune(ctx.h, T, reps=3, stream=stream, times=True)
+    for k in range(2):
+        pbf.pbf_explicit_step(ctx.h, T, ls, k * chunk * dt, dt, chunk, stream=stream)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for k in range(K):
+        flush.fill_(k & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        pbf.pbf_explicit_step(ctx.h, T, ls, (2 + k) * chunk * dt, dt, chunk, stream=stream)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    rate = n * chunk * K / (ms * 1e-3) / 1e9
+    ok = bool(torch.isfinite(T).all().item())
+    ctx.close()
+    mesh.close()
+    return {"workload": f"C2 block and material, 500 um refinement ball: {info['n_active']} cells, {n} dofs, one instance",
+            "value": rate, "unit": "GDoF/s", "us_per_explicit_step": 1e3 * ms / (K * chunk), "step_shape": SHAPES[variant],
+            "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / peaks.get("hbm_gbs", 6800.0), "finite": ok,
+            "host_setup_s": setup_s, "l2": "state and tables > L2; flushed between timed steps"}
+
+
 def bench_adjoint(pbf, I, torch, stream, batch=8, nsteps=200, ckpt=10):
     """Adjoint sweep of configuration 4 on a reduced window: 8 instances, 200 steps, 10 stored
     states (binomial schedule), FP32 operator, gradients for 16 segment powers and s."""
@@ -336,8 +377,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="timed loop only (for profiler launch lists)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
-                    help="c4: only the batched forward steps of configuration 4 (for profiler runs)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "large"],
+                    help="c4 / large: only the batched C4 steps / the 18 M-dof single instance (profiler runs)")
     ap.add_argument("--shape", type=int, default=-1,
                     help="explicit-step kernel shape to use instead of the autotuner's pick (0-6)")
     args = ap.parse_args()
@@ -353,9 +394,12 @@ def main():
     dev = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(dev)
     W, K = max(3, args.warmup), args.steps
-    if args.workload == "c4":
+    if args.workload in ("c4", "large"):
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-        out = bench_batched(pbf, I, torch, torch.cuda.current_stream(), flush, load_peaks()[0], K, shape=args.shape)
+        if args.workload == "c4":
+            out = bench_batched(pbf, I, torch, torch.cuda.current_stream(), flush, load_peaks()[0], K, shape=args.shape)
+        else:
+            out = bench_large(pbf, I, torch, torch.cuda.current_stream(), flush, load_peaks()[0], K=K)
         if rank == 0:
             print(json.dumps(out))
         return
@@ -504,6 +548,7 @@ def main():
         out["batched"] = bench_batched(pbf, I, torch, stream, flush, peaks, K)
         out["adjoint"] = bench_adjoint(pbf, I, torch, stream)
         out["implicit"] = bench_implicit(pbf, I, torch, stream)
+        out["large"] = bench_large(pbf, I, torch, stream, flush, peaks)
         if rank == 0 and ws >= 1:
             rate, n_s, done, secs = time_oracle(3, max_seconds=25.0)
             out["cpu_baseline"] = {"value": rate / 1e9, "unit": "GDoF/s", "cores": 1, "kind": "oracle",

@@ -17,13 +17,6 @@
 namespace pbf {
 namespace {
 
-template <typename R>
-__device__ __forceinline__ R weight_of(const DevMesh& M, int e);
-template <>
-__device__ __forceinline__ float weight_of<float>(const DevMesh& M, int e) { return M.con_wf[e]; }
-template <>
-__device__ __forceinline__ double weight_of<double>(const DevMesh& M, int e) { return M.con_w[e]; }
-
 // Gather T_e = P G_e x. Slot a of a cell holds a dof d >= 0 or a hanging node -1-r; hanging
 // values were computed beforehand (x_h = P_h x, one small kernel), so every slot is one load
 // from one of two arrays, selected without branching: all loads of a cell issue back to back.
