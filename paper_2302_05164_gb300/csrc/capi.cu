@@ -641,10 +641,14 @@ void CtxBase::set_material_constants(double dt) {
 }
 
 void CtxBase::release() {
-  if (cheb_exec) cudaGraphExecDestroy(cheb_exec);
-  cheb_exec = nullptr;
+  for (GraphSlot* g : {&cheb_graph, &iter_graph}) {
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    g->exec = nullptr;
+  }
   if (cap_stream) cudaStreamDestroy(cap_stream);
   cap_stream = nullptr;
+  if (pinned) cudaFreeHost(pinned);
+  pinned = nullptr;
   for (void* p : allocs) cudaFree(p);
   allocs.clear();
   for (auto& ev : events) {

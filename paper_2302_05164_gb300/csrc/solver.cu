@@ -104,20 +104,18 @@ struct Implicit {
     }
   }
 
-  // The same application as one CUDA-graph launch. For fixed (dt, bounds, degree) and vectors
-  // the preconditioner is a fixed sequence of about 6 (deg + 1) small launches, which at the
-  // sizes of an interlayer cool-down cost more in launch latency than in work; it is captured
-  // once on a private stream and replayed on the caller's stream.
-  void precondition(const double* r, double* z, int deg, double lmin, double lmax, double* res, double* d,
-                    double* Ad) {
+  // Replays the launch sequence that `body` enqueues as one CUDA graph. For a fixed key the
+  // sequence is fixed, and at the sizes of an interlayer cool-down its small launches cost
+  // more in launch latency than in work; it is captured once on the context's private stream
+  // (the caller's stream may be the legacy default stream, which cannot be captured) and
+  // replayed on the caller's stream.
+  template <typename F>
+  void replay(pbf_ctx::GraphSlot& g, const double* key, F body) {
     if (e != cudaSuccess) return;
-    const double key[12] = {dt, lmin, lmax, (double)deg, (double)(uintptr_t)r, (double)(uintptr_t)z,
-                            (double)(uintptr_t)res, (double)(uintptr_t)d, (double)(uintptr_t)Ad,
-                            (double)(uintptr_t)c->diag, (double)(uintptr_t)c->Tf, (double)(uintptr_t)c->f};
-    if (!c->cheb_exec || std::memcmp(key, c->cheb_key, sizeof key) != 0) {
-      if (c->cheb_exec) {
-        e = cudaGraphExecDestroy(c->cheb_exec);
-        c->cheb_exec = nullptr;
+    if (!g.exec || std::memcmp(key, g.key, sizeof g.key) != 0) {
+      if (g.exec) {
+        e = cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
         if (e != cudaSuccess) return;
       }
       if (!c->cap_stream) {
@@ -126,7 +124,7 @@ struct Implicit {
       }
       const long long l0 = c->launches;
       const bool timing = c->timing;
-      c->timing = false;  // no event records inside the graph
+      c->timing = false;  // no event records inside a graph
       cudaStream_t user = s;
       e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) {
@@ -134,21 +132,44 @@ struct Implicit {
         return;
       }
       s = c->cap_stream;
-      chebyshev(r, z, deg, lmin, lmax, res, d, Ad);
+      body();
       s = user;
-      cudaGraph_t g = nullptr;
-      const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &g);
+      cudaGraph_t graph = nullptr;
+      const cudaError_t ec = cudaStreamEndCapture(c->cap_stream, &graph);
       c->timing = timing;
       if (e == cudaSuccess) e = ec;
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->cheb_exec, g, 0);
-      if (g) cudaGraphDestroy(g);
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
       if (e != cudaSuccess) return;
-      c->cheb_launches = c->launches - l0;
+      g.launches = c->launches - l0;
       c->launches = l0;
-      std::memcpy(c->cheb_key, key, sizeof key);
+      std::memcpy(g.key, key, sizeof g.key);
     }
-    e = cudaGraphLaunch(c->cheb_exec, s);
-    c->launches += c->cheb_launches;
+    e = cudaGraphLaunch(g.exec, s);
+    c->launches += g.launches;
+  }
+
+  // the key of the implicit solve's graphs: dt, bounds, degree and every buffer they touch
+  void graph_key(double* key, int deg, double lmin, double lmax, const double* const* vecs, int nv) {
+    for (int i = 0; i < 16; ++i) key[i] = 0.0;
+    key[0] = dt;
+    key[1] = lmin;
+    key[2] = lmax;
+    key[3] = (double)deg;
+    key[4] = (double)(uintptr_t)c->diag;
+    key[5] = (double)(uintptr_t)c->Tf;
+    key[6] = (double)(uintptr_t)c->f;
+    key[7] = (double)(uintptr_t)c->scal;
+    for (int i = 0; i < nv && 8 + i < 16; ++i) key[8 + i] = (double)(uintptr_t)vecs[i];
+  }
+
+  // z = p(D^-1 A) D^-1 r as one graph launch
+  void precondition(const double* r, double* z, int deg, double lmin, double lmax, double* res, double* d,
+                    double* Ad) {
+    double key[16];
+    const double* v[] = {r, z, res, d, Ad};
+    graph_key(key, deg, lmin, lmax, v, 5);
+    replay(c->cheb_graph, key, [&] { chebyshev(r, z, deg, lmin, lmax, res, d, Ad); });
   }
 };
 
@@ -308,29 +329,52 @@ extern "C" pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt,
     double rn = r0;
     int it = 0;
     if (r0 > 0.0) {
-      // the CG scalars stay on the device (rz in sc[4] / sc[6], alternating; p.Ap in sc[5]);
-      // the host reads r.r (through sc[0], Implicit::dot) once per iteration for the stopping
-      // test
+      // the CG scalars stay on the device (rz in sc[4], the new r.z in sc[6], p.Ap in sc[5],
+      // r.r in sc[0]); the host reads r.r once per iteration for the stopping test
       double* sc = ctx->scal;
-      double* rz = sc + 4;
-      double* rz_new = sc + 6;
+      double* const rz = sc + 4;
+      double* const rz_new = sc + 6;
       I.precondition(r, z, cheb_degree, bounds[0], bounds[1], res, d, Ad);
       if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(p, z, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
       if (I.e == cudaSuccess) I.e = launch_dot(n, 1, r, z, nullptr, nullptr, ctx->part, rz, s);
       ctx->launches += 2;
-      while (rn > rtol * r0 && it < max_it && I.e == cudaSuccess) {
+      // first iteration with separate launches; the following ones, preconditioner and
+      // search direction of iteration k followed by the update of iteration k + 1, as one
+      // graph launch and one host round trip (r.r into page-locked memory)
+      if (!ctx->pinned && I.e == cudaSuccess) I.e = cudaMallocHost(&ctx->pinned, sizeof(double));
+      auto update = [&] {  // x += alpha p, r -= alpha Ap, alpha = rz / p.Ap; sc[0] = r.r
         I.apply(p, Ap);
-        if (I.e == cudaSuccess) I.e = launch_dot(n, 1, p, Ap, nullptr, nullptr, ctx->part, sc + 5, s);
-        if (I.e == cudaSuccess) I.e = launch_axpy2_dev(n, rz, sc + 5, p, Ap, x, r, s);
+        if (I.e == cudaSuccess) I.e = launch_dot(n, 1, p, Ap, nullptr, nullptr, ctx->part, sc + 5, I.s);
+        if (I.e == cudaSuccess) I.e = launch_axpy2_dev(n, rz, sc + 5, p, Ap, x, r, I.s);
+        if (I.e == cudaSuccess) I.e = launch_dot(n, 1, r, r, nullptr, nullptr, ctx->part, sc, I.s);
+        if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(ctx->pinned, sc, sizeof(double), cudaMemcpyDeviceToHost, I.s);
+        ctx->launches += 5;
+      };
+      auto direction = [&] {  // z = M^-1 r, beta = r.z / rz, p = z + beta p, rz = r.z
+        I.chebyshev(r, z, cheb_degree, bounds[0], bounds[1], res, d, Ad);
+        if (I.e == cudaSuccess) I.e = launch_dot(n, 1, r, z, nullptr, nullptr, ctx->part, rz_new, I.s);
+        if (I.e == cudaSuccess) I.e = launch_xpby_dev(n, z, rz_new, rz, p, I.s);
+        if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(rz, rz_new, sizeof(double), cudaMemcpyDeviceToDevice, I.s);
         ctx->launches += 3;
+      };
+      double key[16];
+      const double* kv[] = {r, z, p, Ap, x, res, d, Ad};
+      I.graph_key(key, cheb_degree, bounds[0], bounds[1], kv, 8);
+      bool first = true;
+      while (rn > rtol * r0 && it < max_it && I.e == cudaSuccess) {
+        if (first) {
+          update();
+          first = false;
+        } else {
+          I.replay(ctx->iter_graph, key, [&] {
+            direction();
+            update();
+          });
+        }
+        if (I.e == cudaSuccess) I.e = cudaStreamSynchronize(s);
+        if (I.e != cudaSuccess) break;
         ++it;
-        rn = std::sqrt(I.dot(r, r));
-        if (rn <= rtol * r0) break;
-        I.precondition(r, z, cheb_degree, bounds[0], bounds[1], res, d, Ad);
-        if (I.e == cudaSuccess) I.e = launch_dot(n, 1, r, z, nullptr, nullptr, ctx->part, rz_new, s);
-        if (I.e == cudaSuccess) I.e = launch_xpby_dev(n, z, rz_new, rz, p, s);
-        ctx->launches += 3;
-        std::swap(rz, rz_new);
+        rn = std::sqrt(*ctx->pinned);
       }
     }
     if (rn > rtol * r0) converged = false;

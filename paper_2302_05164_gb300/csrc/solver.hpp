@@ -81,13 +81,17 @@ struct CtxBase {
   // implicit-operator diagonal cache
   double* diag = nullptr;
   double diag_dt = -1.0;
-  // the Chebyshev preconditioner application of the implicit solve as a CUDA graph: captured
-  // on a private stream, launched on the caller's; rebuilt when its key (dt, bounds, degree,
-  // vectors) changes
+  // launch sequences of the implicit solve replayed as CUDA graphs (the Chebyshev
+  // preconditioner; one whole CG iteration): captured on a private stream, launched on the
+  // caller's, rebuilt when their key (dt, bounds, degree, vectors) changes
+  struct GraphSlot {
+    cudaGraphExec_t exec = nullptr;
+    double key[16] = {};
+    long long launches = 0;
+  };
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t cheb_exec = nullptr;
-  double cheb_key[12] = {};
-  long long cheb_launches = 0;
+  GraphSlot cheb_graph, iter_graph;
+  double* pinned = nullptr;  // page-locked host scalar: r.r of the last CG iteration
   // state
   bool poisoned = false;
   bool timing = false;
