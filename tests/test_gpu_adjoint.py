@@ -68,3 +68,39 @@ def test_adjoint_matches_oracle(P, oracle_mod, p, lumping, prec, batch, ckpt):
         assert fwd == nsteps + nsteps * (nsteps - 1) // 2  # no snapshots: quadratic recomputation
     # the state passed in is not modified
     assert np.array_equal(T0d.cpu().numpy(), T0)
+
+
+@pytest.mark.parametrize("p,lumping", [(1, I.LUMP_QUADRATURE), (2, I.LUMP_NODAL)])
+def test_adjoint_matches_central_differences(P, oracle_mod, p, lumping):
+    """The GPU adjoint's gradient against central finite differences of the GPU's own
+    objective (h = 1e-4 relative per parameter, FP64 operator). The perturbed runs are extra
+    instances of the same batch: instance 0 holds the parameters, instances 2k+1 / 2k+2 the
+    +h / -h perturbation of parameter k (three segment powers, then the conductivity scale)."""
+    d = I.mesh_desc((4, 2, 2), (62.5e-6,) * 3, p, 1, [I.uniform_region(1)])
+    xyz = oracle_mod.Mesh(d).dof_xyz()
+    mat = dict(I.TI64_NONLIN, lumping=lumping)
+    T0 = I.smooth_field(xyz, seed=11, lo=353.0, hi=2400.0)
+    dt, nst = 2e-7, 12
+    P0, s0 = np.array([180.0, 220.0, 240.0]), 1.05
+    params = np.concatenate([P0, [s0]])
+    m_par = params.size
+    h = 1e-4 * params
+    B = 1 + 2 * m_par
+    powers = np.tile(P0, (B, 1))
+    scales = np.full(B, s0)
+    for k in range(m_par):
+        for sign, b in ((1.0, 2 * k + 1), (-1.0, 2 * k + 2)):
+            if k < P0.size:
+                powers[b, k] += sign * h[k]
+            else:
+                scales[b] += sign * h[k]
+    ls = I.c4_laser(powers, n_seg=3, steps_per_seg=4, dt=dt, v=0.5, y=0.25e-3)
+    m = P.Mesh(d)
+    ctx = P.Context(m, mat, P.PBF_F64, B)
+    P.pbf_ctx_set_k_scale(ctx.h, scales)
+    T0d = torch.tensor(np.repeat(T0[:, None], B, axis=1), dtype=torch.float64, device="cuda")
+    J, g, _ = P.pbf_adjoint_sweep(ctx.h, T0d, ls, 0.0, dt, nst, 4, batch=B)
+    assert J[0] > 0 and np.all(np.isfinite(g))
+    fd = np.array([(J[2 * k + 1] - J[2 * k + 2]) / (2 * h[k]) for k in range(m_par)])
+    for k in range(m_par):
+        assert abs(g[0, k] - fd[k]) < 1e-5 * max(abs(fd[k]), 1e-3 * np.abs(g[0]).max()), (k, g[0, k], fd[k])
