@@ -104,3 +104,33 @@ def test_adjoint_matches_central_differences(P, oracle_mod, p, lumping):
     fd = np.array([(J[2 * k + 1] - J[2 * k + 2]) / (2 * h[k]) for k in range(m_par)])
     for k in range(m_par):
         assert abs(g[0, k] - fd[k]) < 1e-5 * max(abs(fd[k]), 1e-3 * np.abs(g[0]).max()), (k, g[0, k], fd[k])
+
+
+def test_autograd_function_gives_the_adjoint_gradient(P, oracle_mod):
+    """ThermalObjective (torch.autograd.Function over pbf_adjoint_sweep): J and the gradients
+    that torch's backward delivers for P and s, with a non-uniform upstream gradient, equal
+    the oracle's adjoint per instance (FP64 operator, 1e-10)."""
+    from paper_2302_05164_gb300.autograd import ThermalObjective
+    batch = 2
+    d, mat, dt, ls, s = setup(2, I.LUMP_NODAL, batch)
+    om = oracle_mod.Mesh(d)
+    T0 = np.stack([I.melt_pool_field(om.dof_xyz(), (0.08e-3, 0.06e-3, 0.125e-3), 2500.0 + 50 * b, 50e-6, seed=b,
+                                     noise=0.01) for b in range(batch)], axis=1)
+    nsteps = 12
+    ref = oracle_ref(oracle_mod, d, mat, T0, ls, dt, nsteps, s)
+    m = P.Mesh(d)
+    ctx = P.Context(m, mat, P.PBF_F64, batch)
+    T0d = torch.tensor(np.ascontiguousarray(T0), dtype=torch.float64, device="cuda")
+    Pt = torch.tensor(np.asarray(ls["power"]), dtype=torch.float64, requires_grad=True)
+    st = torch.tensor(s, dtype=torch.float64, requires_grad=True)
+    J = ThermalObjective.apply(Pt, st, ctx.h, T0d, ls, 0.0, dt, nsteps, 4)
+    w = torch.tensor([0.7, -1.3], dtype=torch.float64)
+    (w * J).sum().backward()
+    n_seg = Pt.shape[1]
+    for b in range(batch):
+        Jr, gr = ref[b]
+        assert abs(float(J[b].detach()) - Jr) < 1e-10 * abs(Jr)
+        got = np.concatenate([Pt.grad[b].numpy(), [float(st.grad[b])]])
+        assert got.shape == (n_seg + 1,)
+        assert np.max(np.abs(got - float(w[b]) * gr)) < 1e-10 * np.max(np.abs(gr))
+    assert np.array_equal(T0d.cpu().numpy(), T0)
