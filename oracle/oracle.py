@@ -41,6 +41,15 @@ class _Mat(C.Structure):
                                           "sigma", "powder_k_scale", "T_dirichlet")] + [("lumping", C.c_int)]
 
 
+class _Loss(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("emissivity", "T_amb", "C_P", "C_T", "C_M", "T_v", "h_v", "c_h", "T_h0",
+                                          "T_max")]
+
+
+def surface_loss(q: dict) -> _Loss:
+    return _Loss(*[float(q[n]) for n, _ in _Loss._fields_])
+
+
 class _Laser(C.Structure):
     _fields_ = [("n_seg", C.c_int), ("seg", C.c_void_p), ("power", C.c_void_p),
                 ("eta", C.c_double), ("radius", C.c_double), ("volumetric", C.c_int),
@@ -63,6 +72,7 @@ def lib():
         L.or_objective.restype = C.c_double
         L.or_capp.restype = C.c_double
         L.or_cond.restype = C.c_double
+        L.or_surface_flux.restype = C.c_double
         L.or_implicit.restype = C.c_int
     return _lib
 
@@ -145,6 +155,12 @@ class Mesh:
     def set_material(self, mat_active: np.ndarray):
         m = np.ascontiguousarray(mat_active, np.uint8)
         lib().or_mesh_set_material(C.c_void_p(self.h), _ptr(m))
+
+    def set_surface_loss(self, q):
+        """Radiation / evaporation on the top faces (dict of `surface_loss` fields; None: off)
+        for every later residual and explicit step; the adjoint and objective refuse it."""
+        self._loss = None if q is None else surface_loss(q)
+        lib().or_set_surface_loss(C.c_void_p(self.h), None if q is None else C.byref(self._loss))
 
     # ---- operators -------------------------------------------------------------------
     def residual(self, mat, T, ls=None, t=0.0, s=1.0, instance=0):
@@ -235,6 +251,10 @@ def transfer(old: Mesh, T_old, new: Mesh, T_init):
     T_old = _f64(T_old)
     lib().or_transfer(C.c_void_p(old.h), _ptr(T_old), C.c_void_p(new.h), C.c_double(T_init), _ptr(out))
     return out
+
+
+def surface_flux(q, T):
+    return lib().or_surface_flux(C.byref(surface_loss(q)), C.c_double(T))
 
 
 def capp(mat, T):

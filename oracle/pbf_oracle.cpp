@@ -59,6 +59,16 @@ typedef struct {
   int lumping;  // 0: row sum with c_app at quadrature points, 1: c_app at the node x row-sum mass
 } or_material;
 
+// Radiation and evaporation on the free top surface (Sec. 2, Eqs. bc_rad_evap, bc_radiation,
+// bc_evaporation): q = q_rad + q_evap leaves through the active top faces,
+//   q_rad  = emissivity sigma_S (T^4 - T_amb^4),
+//   q_evap = 0.82 C_P exp(-C_T (1/[T] - 1/T_v)) sqrt(C_M/[T]) (h_v + c_h ([T] - T_h0)) if [T] > T_v,
+// with [T] = min(T, T_max). emissivity = 0 / C_P = 0 switch a part off.
+typedef struct {
+  double emissivity, T_amb;
+  double C_P, C_T, C_M, T_v, h_v, c_h, T_h0, T_max;
+} or_surface_loss;
+
 typedef struct {
   int n_seg;
   const double* seg;    // [n_seg][6]: x0, y0, x1, y1, t0, t1
@@ -116,6 +126,8 @@ struct Mesh {
   std::vector<int64_t> hang_coord;
   int n_colours = 0;
   std::unordered_map<uint64_t, NodeInfo> nodes;
+  bool has_loss = false;
+  or_surface_loss loss{};  // radiation / evaporation on the top faces (when has_loss)
 
   int npc() const { return (p + 1) * (p + 1) * (p + 1); }
   int64_t size(const Leaf& l) const { return (int64_t)1 << (L - l.level); }
@@ -614,11 +626,26 @@ struct Fields {
   std::vector<double> fdiff, fvol, C;
 };
 
+const double kStefanBoltzmann = 5.670374419e-8;  // W m^-2 K^-4
+
+// Outward heat flux of the free surface at temperature T (Eqs. bc_radiation, bc_evaporation).
+double surface_flux(const or_surface_loss& q, double T) {
+  double flux = q.emissivity * kStefanBoltzmann * (T * T * T * T - q.T_amb * q.T_amb * q.T_amb * q.T_amb);
+  const double Tc = std::min(T, q.T_max);
+  if (q.C_P > 0.0 && Tc > q.T_v) {
+    const double mdot = 0.82 * q.C_P * std::exp(-q.C_T * (1.0 / Tc - 1.0 / q.T_v)) * std::sqrt(q.C_M / Tc);
+    flux += mdot * (q.h_v + q.c_h * (Tc - q.T_h0));
+  }
+  return flux;
+}
+
 // f_diff, f_vol and the row-sum lumped capacity C~ = P^T int rho c_app(T_h) N_i at T.
 // f_diff,i = - sum_e int k(T_h) grad N_i . grad T_h  (Eq. diffusive_term_evaluation)
 // C~_ii = sum_j C_ij = int rho c_app(T_h) N_i because sum_j N_j = 1 (Sec. 3.2)
 // f_vol: surface Gaussian 2 eta P/(pi r^2) exp(-2 d^2/r^2) on the active top faces, or the
-// cylinder source of Eq. (heat_soruce_cylindrical) read with -h_powder < z^ < 0.
+// cylinder source of Eq. (heat_soruce_cylindrical) read with -h_powder < z^ < 0; with a
+// surface loss also the boundary term -int_{Gamma_RE} N_i (q_rad + q_evap)(T_h) dA of the weak
+// form (Eq. weak_form), (p+1)^2 Gauss points per top face.
 void residual(const Mesh& m, const or_material& mt, double s, const double* T, const or_laser* ls, double t,
               Fields& F, bool with_C = true) {
   const int p = m.p, npc = m.npc(), nq = p + 1;
@@ -680,6 +707,18 @@ void residual(const Mesh& m, const or_material& mt, double s, const double* T, c
           double R = ls->radius;
           double q = 2.0 * ls->eta * P / (kPi * R * R) * std::exp(-2.0 * d2 / (R * R));
           for (int i = 0; i < npc; ++i) ve[i] += W * q * N[i];
+        }
+    }
+    if (m.has_loss && m.top[(size_t)c]) {
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          double xi[3] = {gx[qx], gx[qy], 1.0};
+          double W = gw[qx] * gw[qy] * g.h[0] * g.h[1];
+          basis(p, xi, N.data(), dN.data());
+          double Tq = 0.0;
+          for (int a = 0; a < npc; ++a) Tq += N[a] * Te[a];
+          const double q = surface_flux(m.loss, Tq);
+          for (int i = 0; i < npc; ++i) ve[i] -= W * q * N[i];
         }
     }
     scatter(m, c, fe.data(), F.fdiff.data());
@@ -960,6 +999,16 @@ void or_mesh_tables(void* h, long long* leaves, unsigned char* material, int* ce
   std::copy(m->top.begin(), m->top.end(), top);
 }
 
+// Radiation / evaporation on the top faces for every later residual and explicit step of this
+// mesh (null: off).
+void or_set_surface_loss(void* h, const or_surface_loss* q) {
+  Mesh* m = (Mesh*)h;
+  m->has_loss = q != nullptr;
+  if (q) m->loss = *q;
+}
+
+double or_surface_flux(const or_surface_loss* q, double T) { return surface_flux(*q, T); }
+
 // Override material ids of active cells (layer activation marks new cells).
 void or_mesh_set_material(void* h, const unsigned char* mat_active) {
   Mesh* m = (Mesh*)h;
@@ -1145,6 +1194,7 @@ int or_implicit(void* h, const or_material* mt, double* T, double dt, int nsteps
 double or_adjoint(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0, double dt,
                   int nsteps, double T_target, double p_exp, double* grad) {
   Mesh* m = (Mesh*)h;
+  if (m->has_loss) return std::nan("");  // the adjoint covers no surface loss
   const Mesh& M = *m;
   size_t n = (size_t)M.n_dofs;
   Objective obj;
@@ -1264,6 +1314,7 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
 double or_objective(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0,
                     double dt, int nsteps, double T_target, double p_exp) {
   Mesh* m = (Mesh*)h;
+  if (m->has_loss) return std::nan("");  // as the adjoint
   size_t n = (size_t)m->n_dofs;
   Objective obj;
   obj.T_target = T_target;

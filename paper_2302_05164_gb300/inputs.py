@@ -53,6 +53,14 @@ BRIDGE = dict(rho=7430.0, c=965.0, k0=20.0, k1=20.0, Tk0=303.0, Tk1=303.0,
 
 T0 = 353.0
 
+# Radiation and evaporation on the free top surface (Eqs. bc_radiation, bc_evaporation) with
+# the constants of the paper's material table (Sec. 5.1): emissivity 0.7, boiling point
+# 3000 K, C_P = 54 kPa, C_T = 50,000 K, C_M = 0.001 K s^2/m^2, latent heat of evaporation
+# 6.0 MJ/kg, enthalpy reference 663 K, [T] capped at T_v + 1000 K; the ambient temperature and
+# the heat capacity of the enthalpy term follow the Ti-6Al-4V-like workloads (353 K, 526 J/kgK).
+SURFACE_LOSS = dict(emissivity=0.7, T_amb=T0, C_P=54.0e3, C_T=5.0e4, C_M=1.0e-3, T_v=3000.0, h_v=6.0e6, c_h=526.0,
+                    T_h0=663.0, T_max=4000.0)
+
 
 def mesh_desc(ntree, tree_h, degree, max_level, regions=(), origin=(0.0, 0.0, 0.0),
               active_top_z=1e30, dirichlet_faces=DIRICHLET_BOTTOM, tree_exists=None,

@@ -349,3 +349,92 @@ def test_transfer_reproduces_polynomials_and_fills_new_cells(oracle_mod, p):
     assert old.sum() < b.n_dofs
     assert np.max(np.abs(Tb[old] - u(xb[old]))) < 1e-12 * np.abs(u(xb)).max()
     assert np.all(Tb[~old] == -7.0)
+
+
+# ---- radiation and evaporation on the free top surface (Eqs. bc_rad_evap, bc_radiation,
+# bc_evaporation) ------------------------------------------------------------------------
+
+def paper_surface_flux(q, T):
+    """Transcription of Eqs. bc_radiation and bc_evaporation for the checks below."""
+    out = q["emissivity"] * 5.670374419e-8 * (T ** 4 - q["T_amb"] ** 4)
+    Tc = min(T, q["T_max"])
+    if q["C_P"] > 0 and Tc > q["T_v"]:
+        mdot = 0.82 * q["C_P"] * math.exp(-q["C_T"] * (1.0 / Tc - 1.0 / q["T_v"])) * math.sqrt(q["C_M"] / Tc)
+        out += mdot * (q["h_v"] + q["c_h"] * (Tc - q["T_h0"]))
+    return out
+
+
+def test_surface_flux_branches(oracle_mod):
+    q = I.SURFACE_LOSS
+    for T in (353.0, 1500.0, 2999.0, 3000.0, 3001.0, 3500.0, 4000.0, 4500.0):
+        got = oracle_mod.surface_flux(q, T)
+        assert abs(got - paper_surface_flux(q, T)) <= 1e-13 * abs(got) + 1e-9
+    # capped: the evaporation part is constant above T_max, radiation keeps growing
+    rad = lambda T: q["emissivity"] * 5.670374419e-8 * (T ** 4 - q["T_amb"] ** 4)
+    e1 = oracle_mod.surface_flux(q, 4200.0) - rad(4200.0)
+    e2 = oracle_mod.surface_flux(q, 4700.0) - rad(4700.0)
+    assert abs(e1 - e2) < 1e-9 * abs(e1) and e1 > 0
+    assert oracle_mod.surface_flux(q, q["T_amb"]) == 0.0
+    assert oracle_mod.surface_flux(dict(q, emissivity=0.0), 2900.0) == 0.0
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_surface_loss_of_a_constant_field(oracle_mod, p):
+    """Constant T: the boundary term is -q(T) int_top N_i dA: it sums to -q(T) times the top
+    area (partition of unity, constraint rows summing to 1 across hanging faces), vanishes off
+    the top surface, and for a uniform Q1 brick each top node carries a quarter face per
+    adjacent top face."""
+    q = I.SURFACE_LOSS
+    regions = [(I.BALL, (0.3e-3, 0.25e-3, 0.25e-3), (0, 0, 0), 120e-6, 2)] if p == 2 else [I.uniform_region(1)]
+    d = I.mesh_desc((4, 2, 2), (125e-6,) * 3, p, 2, regions)
+    m = oracle_mod.Mesh(d)
+    m.set_surface_loss(q)
+    Tc = 3400.0
+    T = np.full(m.n_dofs, Tc)
+    fd, fv, _ = m.residual(I.TI64_CONST, T)
+    area = 4 * 125e-6 * 2 * 125e-6
+    assert abs(fv.sum() + paper_surface_flux(q, Tc) * area) < 1e-12 * paper_surface_flux(q, Tc) * area
+    assert np.abs(fd).max() < 1e-9 * np.abs(fv).max()
+    z = m.dof_xyz()[:, 2]
+    assert np.all(fv[z < z.max() - 1e-12] == 0.0) and np.all(fv[z > z.max() - 1e-12] < 0.0)
+    if p == 1:  # uniform 62.5 um cells: weights h^2/4 per adjacent top face
+        h = 62.5e-6
+        xy = m.dof_xyz()[:, :2]
+        top = z > z.max() - 1e-12
+        on_x = (np.abs(xy[:, 0]) < 1e-12) | (np.abs(xy[:, 0] - 0.5e-3) < 1e-12)
+        on_y = (np.abs(xy[:, 1]) < 1e-12) | (np.abs(xy[:, 1] - 0.25e-3) < 1e-12)
+        faces = np.where(on_x & on_y, 1, np.where(on_x | on_y, 2, 4))
+        expect = -paper_surface_flux(q, Tc) * faces * h * h / 4
+        assert np.abs(fv[top] - expect[top]).max() < 1e-12 * np.abs(expect[top]).max()
+    m.set_surface_loss(None)
+    _, fv0, _ = m.residual(I.TI64_CONST, T)
+    assert np.all(fv0 == 0.0)
+
+
+def test_radiating_slab_reaches_the_flux_balance(oracle_mod):
+    """A column (1 mm, Dirichlet bottom at 2500 K, insulated sides, radiating top) relaxes to
+    the steady state of the continuum problem: a linear profile whose conductive flux
+    k (T_D - T_top) / L equals the radiation q_rad(T_top), with T_top the root of that scalar
+    equation (bisection here). Q1 represents the linear profile exactly, so the nodal values
+    agree with the continuum solution once the transient has decayed."""
+    q = dict(I.SURFACE_LOSS, C_P=0.0)
+    mat = dict(I.TI64_CONST, T_dirichlet=2500.0)
+    L, kk = 1.0e-3, mat["k0"]
+    d = I.mesh_desc((1, 1, 8), (125e-6,) * 3, 1, 0, [])
+    m = oracle_mod.Mesh(d)
+    m.set_surface_loss(q)
+    lam, _ = m.lambda_max(mat, I.start_vector(m.n_dofs), max_iter=400, rtol=1e-10)
+    dt = 0.5 * 2.0 / lam
+    T = m.explicit(mat, np.full(m.n_dofs, 2500.0), None, 0.0, dt, int(4.0 / dt))
+    lo, hi = 353.0, 2500.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if kk * (2500.0 - mid) / L > paper_surface_flux(q, mid):
+            lo = mid
+        else:
+            hi = mid
+    T_top = 0.5 * (lo + hi)
+    z = m.dof_xyz()[:, 2]
+    expect = 2500.0 + (T_top - 2500.0) * z / L
+    assert 2000.0 < T_top < 2450.0
+    assert np.abs(T - expect).max() < 1e-6
