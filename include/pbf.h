@@ -204,7 +204,8 @@ pbf_status pbf_ctx_set_k_scale(pbf_ctx* ctx, const double* s_host);
 /* Evaluates, at state T_dev and time t, the three parts of the semi-discrete right-hand
  * side (Eq. semi-discrete) and the row-sum lumped capacity (Sec. 3.2):
  *   fdiff_dev = -P^T sum_e int k(T_h) grad N . grad T_h   (Eq. diffusive_term_evaluation)
- *   fvol_dev  = P^T sum_e laser source against N
+ *   fvol_dev  = P^T sum_e laser source against N (plus, with a surface loss set by
+ *               pbf_ctx_set_surface_loss, the term -int_top N (q_rad + q_evap)(T_h) dA)
  *   C_dev     = P^T sum_e int rho c_app(T_h) N
  * Any output may be NULL. Outputs [n_dofs][batch] FP64. laser may be NULL (no source). */
 pbf_status pbf_eval_residual(pbf_ctx* ctx, const double* T_dev, const pbf_laser* laser, double t,
@@ -297,6 +298,25 @@ pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* va
 
 /* Selects an explicit-step shape directly (0..6, see pbf_ctx_autotune). */
 pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape);
+
+/* Radiation and evaporation on the free top surface (Sec. 2, Eqs. bc_rad_evap, bc_radiation,
+ * bc_evaporation): on the active top faces the outward heat flux
+ *   q_rad  = emissivity sigma_S (T^4 - T_amb^4)   (sigma_S = 5.670374419e-8 W m^-2 K^-4),
+ *   q_evap = 0.82 C_P exp(-C_T (1/[T] - 1/T_v)) sqrt(C_M/[T]) (h_v + c_h ([T] - T_h0)) when
+ *            [T] > T_v, with [T] = min(T, T_max),
+ * enters the right-hand side as the boundary term -int_top N_i (q_rad + q_evap)(T_h) dA of the
+ * weak form, (p+1)^2 Gauss points per face, evaluated at the state of each step (explicit, as
+ * in the paper). emissivity = 0 or C_P = 0 switch a part off. */
+typedef struct {
+  double emissivity, T_amb;
+  double C_P, C_T, C_M, T_v, h_v, c_h, T_h0, T_max;
+} pbf_surface_loss;
+
+/* Sets (q != NULL) or clears (NULL) the surface loss of a context for its later residual
+ * evaluations (added to fvol_dev) and explicit steps. With a surface loss the explicit steps
+ * run the per-cell form (shapes 4-6 act as shape 1), and pbf_implicit_solve and
+ * pbf_adjoint_sweep return PBF_EINVAL. Bad parameters: PBF_EINVAL. Host only. */
+pbf_status pbf_ctx_set_surface_loss(pbf_ctx* ctx, const pbf_surface_loss* q);
 
 /* Test hook for the time-out path of shape 6 (no counterpart in the paper): while
  * extra_blocks > 0 the persistent form's grid barrier waits for that many blocks more than

@@ -766,6 +766,11 @@ cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_d
     e = launch_laser(degree, f32, lsetup, L.mesh, power, spot_at(lsetup.k, t), fvol, s);
     ++launches;
   }
+  if (e == cudaSuccess && has_loss) {
+    e = launch_surface_loss(degree, f32, lsetup, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev,
+                            f32 ? mat.T_ref : 0.0, loss, fvol, s);
+    ++launches;
+  }
   if (e == cudaSuccess && fdiff_dev) e = launch_to_f64(f32, nv, f, fdiff_dev, s);
   if (e == cudaSuccess && fvol_dev) e = launch_to_f64(f32, nv, fvol, fvol_dev, s);
   if (e == cudaSuccess && C_dev) {
@@ -839,6 +844,11 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
     if (ev.first) timing_end(ev, s);
     if (e == cudaSuccess && volumetric && sp.seg >= 0) {
       e = launch_laser(degree, f32, lsetup, L.mesh, power, sp, f, s);
+      ++launches;
+    }
+    if (e == cudaSuccess && has_loss) {  // radiation / evaporation at the state of step n
+      e = launch_surface_loss(degree, f32, lsetup, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev,
+                              f32 ? mat.T_ref : 0.0, loss, f, s);
       ++launches;
     }
     // hanging-node contributions to their masters (P_h^T f_h), one thread per row and
@@ -1087,6 +1097,30 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
 extern "C" pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape) {
   if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, 6]");
   ctx->base.variant = shape;
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_ctx_set_surface_loss(pbf_ctx* ctx, const pbf_surface_loss* q) {
+  if (!ctx) return fail(PBF_EINVAL, "null context");
+  if (!q) {
+    ctx->has_loss = false;
+    return PBF_OK;
+  }
+  if (!(q->emissivity >= 0.0) || !(q->T_amb >= 0.0) || !(q->C_P >= 0.0) ||
+      (q->C_P > 0.0 && !(q->T_v > 0.0 && q->T_max > q->T_v && q->C_M > 0.0)))
+    return fail(PBF_EINVAL, "surface loss: need emissivity, T_amb, C_P >= 0 and, with evaporation, 0 < T_v < T_max, C_M > 0");
+  LossK& k = ctx->loss;
+  k.emissivity = q->emissivity;
+  k.T_amb = q->T_amb;
+  k.C_P = q->C_P;
+  k.C_T = q->C_T;
+  k.C_M = q->C_M;
+  k.T_v = q->T_v;
+  k.h_v = q->h_v;
+  k.c_h = q->c_h;
+  k.T_h0 = q->T_h0;
+  k.T_max = q->T_max;
+  ctx->has_loss = true;
   return PBF_OK;
 }
 

@@ -221,6 +221,7 @@ void splitmix_vector(std::vector<double>& v, uint64_t seed) {
 
 pbf_status check_linear(pbf_ctx* c) {
   if (c->batch != 1) return err(PBF_EINVAL, "the implicit solve runs one instance (batch 1)");
+  if (c->has_loss) return err(PBF_EINVAL, "the implicit solve covers no radiation / evaporation surface loss");
   if ((c->mat.Tk1 > c->mat.Tk0 && c->mat.k1 != c->mat.k0) || c->cap != CAP_CONST)
     return err(PBF_EINVAL, "the implicit solve needs a linear material (constant k and c)");
   return PBF_OK;
@@ -604,6 +605,7 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
   if (!ctx || !T0_dev || !laser || !J_out || !grad_out) return err(PBF_EINVAL, "null argument");
   if (nsteps < 1 || n_checkpoints < 1 || !(dt > 0) || !(p_exp >= 1)) return err(PBF_EINVAL, "bad sweep parameters");
   if (laser->n_seg < 1) return err(PBF_EINVAL, "the adjoint needs a laser with at least one segment");
+  if (ctx->has_loss) return err(PBF_EINVAL, "the adjoint covers no radiation / evaporation surface loss");
   pbf_status st = ctx->check_usable();
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;

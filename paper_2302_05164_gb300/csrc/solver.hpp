@@ -25,6 +25,8 @@ struct CtxBase {
   int cap = 0;          // CAP_CONST, CAP_QUADRATURE or CAP_NODAL
   NodalCap nodal;
   pbf_material mat{};
+  bool has_loss = false;  // radiation / evaporation on the top faces (pbf_ctx_set_surface_loss)
+  LossK loss;
   CellLaunch base;
   LaserSetup lsetup;
   std::vector<void*> allocs;
@@ -116,7 +118,7 @@ struct CtxBase {
   cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
   cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, cudaStream_t s);
   cudaError_t explicit_steps_persistent(double* T, double t0, double dt, int nsteps, cudaStream_t s);
-  bool fused_ok() const { return f32 && batch == 1 && cap != CAP_QUADRATURE && step.n_patches > 0; }
+  bool fused_ok() const { return f32 && batch == 1 && cap != CAP_QUADRATURE && !has_loss && step.n_patches > 0; }
   // the surface laser of the cell kernels at time t (off for the volumetric source)
   LaserInline inline_laser(double t, Spot* sp) const;
   // CUDA events around one timed launch (kernel timing on)

@@ -217,6 +217,79 @@ __global__ void k_laser_surface(int n_top, int B, const int32_t* __restrict__ to
     }
 }
 
+// Radiation and evaporation on the active top faces (Eqs. bc_rad_evap, bc_radiation,
+// bc_evaporation; Stefan-Boltzmann constant 5.670374419e-8 W m^-2 K^-4): one thread per
+// (face, instance) gathers the face's (P+1)^2 node values (hanging ones interpolated from
+// their constraint rows), evaluates T at the face's Gauss points, the outward flux
+// q = q_rad + q_evap there, and adds -int N_i q dA to the dofs (masters of hanging nodes
+// through the same rows).
+template <int P, typename R>
+__global__ void k_surface_loss(int n_top, int B, const int32_t* __restrict__ top_cell,
+                               const double* __restrict__ top_geo, const DevMesh M, const R* __restrict__ x,
+                               double T_off, const LossK q, R* __restrict__ f) {
+  constexpr int N = P + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_top * B) return;
+  const int face = B == 1 ? i : i / B, inst = i - face * B;
+  const int cell = top_cell[face];
+  const R hx = R(top_geo[4 * face + 2]), hy = R(top_geo[4 * face + 3]);
+  R Tn[N][N];
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int d = M.cell_dofs[(k + N * (j + N * P)) * M.n_cells + cell];
+      R v = R(0);
+      if (d >= 0) {
+        v = x[(int64_t)d * B + inst];
+      } else {
+        for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
+          v += R(M.con_w[e]) * x[(int64_t)M.con_idx[e] * B + inst];
+      }
+      Tn[j][k] = v + R(T_off);
+    }
+  const R eps_s = R(q.emissivity * 5.670374419e-8), Ta4 = R(q.T_amb * q.T_amb * q.T_amb * q.T_amb);
+  R fe[N][N];
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int k = 0; k < N; ++k) fe[j][k] = R(0);
+#pragma unroll
+  for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+    for (int qx = 0; qx < N; ++qx) {
+      R T = R(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int k = 0; k < N; ++k) T += R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k)) * Tn[j][k];
+      const R T2 = T * T;
+      R flux = eps_s * (T2 * T2 - Ta4);
+      const R Tc = T < R(q.T_max) ? T : R(q.T_max);
+      if (q.C_P > 0.0 && Tc > R(q.T_v)) {
+        const R mdot = R(0.82 * q.C_P) * expo_r(R(-q.C_T) * (R(1) / Tc - R(1.0 / q.T_v))) * sqrt(R(q.C_M) / Tc);
+        flux += mdot * (R(q.h_v) + R(q.c_h) * (Tc - R(q.T_h0)));
+      }
+      const R wq = flux * R(Basis<P>::W(qx) * Basis<P>::W(qy)) * hx * hy;
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int k = 0; k < N; ++k) fe[j][k] -= wq * R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
+    }
+#pragma unroll
+  for (int j = 0; j < N; ++j)
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const int d = M.cell_dofs[(k + N * (j + N * P)) * M.n_cells + cell];
+      if (d >= 0) {
+        atomicAdd(&f[(int64_t)d * B + inst], fe[j][k]);
+      } else {
+        for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
+          atomicAdd(&f[(int64_t)M.con_idx[e] * B + inst], R(M.con_w[e]) * fe[j][k]);
+      }
+    }
+}
+
 // Cylinder source of depth h_powder below the active top (Eq. heat_soruce_cylindrical with
 // the bound read as -h_powder < z^ < 0), integrated with (P+1)^3 Gauss points per cell.
 template <int P, typename R>
@@ -752,6 +825,22 @@ cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMe
   } else {
     if (f32) k_laser_surface<2, float><<<grid_for(n, 128), 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, ls.k, power, sp, (float*)f);
     else k_laser_surface<2, double><<<grid_for(n, 128), 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, ls.k, power, sp, (double*)f);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_surface_loss(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const void* x,
+                                double T_off, const LossK& q, void* f, cudaStream_t s) {
+  const int B = M.batch;
+  const int64_t n = (int64_t)ls.n_top * B;
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = grid_for(n, 128);
+  if (degree == 1) {
+    if (f32) k_surface_loss<1, float><<<grid, 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, (const float*)x, T_off, q, (float*)f);
+    else k_surface_loss<1, double><<<grid, 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, (const double*)x, T_off, q, (double*)f);
+  } else {
+    if (f32) k_surface_loss<2, float><<<grid, 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, (const float*)x, T_off, q, (float*)f);
+    else k_surface_loss<2, double><<<grid, 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, (const double*)x, T_off, q, (double*)f);
   }
   return cudaGetLastError();
 }

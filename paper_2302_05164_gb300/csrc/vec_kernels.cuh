@@ -14,6 +14,13 @@ struct LaserSetup {
   const double* level_h = nullptr;    // [levels][3]
 };
 
+// Radiation and evaporation on the free top surface (Eqs. bc_radiation, bc_evaporation):
+// outward flux q_rad + q_evap of the temperature, see pbf_surface_loss.
+struct LossK {
+  double emissivity = 0.0, T_amb = 0.0;
+  double C_P = 0.0, C_T = 0.0, C_M = 0.0, T_v = 0.0, h_v = 0.0, c_h = 0.0, T_h0 = 0.0, T_max = 0.0;
+};
+
 // Lumped-capacity forms of the update: constant c, quadrature-point row sum accumulated by
 // the cell kernel, or nodal apparent capacity c_app(T_i) x row-sum mass.
 enum { CAP_CONST = 0, CAP_QUADRATURE = 1, CAP_NODAL = 2 };
@@ -75,6 +82,11 @@ cudaError_t launch_round_f32(int64_t n, const double* x, float* y, cudaStream_t 
 cudaError_t launch_f32_to_f64(int64_t n, const float* x, double* y, cudaStream_t s);
 cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const double* power,
                          const Spot& sp, void* f, cudaStream_t s);
+// f += -int_{top faces} N_i (q_rad + q_evap)(T_h) dA, (p+1)^2 Gauss points per face, for the
+// state x ([n_dofs][batch] in the operator precision; T = x + T_off; hanging values from the
+// constraint rows), constraint-resolved atomic additions onto f.
+cudaError_t launch_surface_loss(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const void* x,
+                                double T_off, const LossK& q, void* f, cudaStream_t s);
 cudaError_t launch_to_f64(bool f32, int64_t n, const void* a, double* out, cudaStream_t s);
 cudaError_t launch_broadcast_dofs(int64_t n_dofs, int B, const double* a, double* out, cudaStream_t s);
 // inv_d = 1 / c, inv_f = its FP32 rounding; inv_fx (nullable) the same with -1 at Dirichlet dofs

@@ -31,6 +31,11 @@ class Region(C.Structure):
                 ("radius", C.c_double)]
 
 
+class SurfaceLoss(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("emissivity", "T_amb", "C_P", "C_T", "C_M", "T_v", "h_v", "c_h", "T_h0",
+                                          "T_max")]
+
+
 class MeshDesc(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("ntree", C.c_int * 3), ("tree_h", C.c_double * 3),
                 ("degree", C.c_int), ("max_level", C.c_int), ("tree_exists", C.c_void_p),
@@ -92,6 +97,7 @@ _SIGS = {
     "pbf_ctx_autotune": ([C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int), C.c_void_p, C.c_void_p], C.c_int),
     "pbf_ctx_set_kernel_shape": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_set_barrier_test": ([C.c_void_p, C.c_int], C.c_int),
+    "pbf_ctx_set_surface_loss": ([C.c_void_p, C.POINTER(SurfaceLoss)], C.c_int),
     "pbf_ctx_set_timing": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_kernel_time": ([C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
     "pbf_ctx_launch_count": ([C.c_void_p, C.POINTER(C.c_longlong)], C.c_int),
@@ -315,6 +321,15 @@ def pbf_ctx_autotune(h, T, reps=5, stream=None, times=False):
 
 def pbf_ctx_set_kernel_shape(h, shape):
     _check(lib().pbf_ctx_set_kernel_shape(h, int(shape)))
+
+
+def pbf_ctx_set_surface_loss(h, q):
+    """q: dict with the SurfaceLoss fields, or None to switch the surface loss off."""
+    if q is None:
+        _check(lib().pbf_ctx_set_surface_loss(h, None))
+    else:
+        s = SurfaceLoss(*[float(q[n]) for n, _ in SurfaceLoss._fields_])
+        _check(lib().pbf_ctx_set_surface_loss(h, C.byref(s)))
 
 
 def pbf_ctx_set_barrier_test(h, extra_blocks):

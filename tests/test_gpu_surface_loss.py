@@ -1,0 +1,113 @@
+"""GPU parity of the radiation / evaporation surface loss on the free top surface (Sec. 2,
+Eqs. bc_rad_evap, bc_radiation, bc_evaporation) with the oracle, through the C ABI:
+residual terms and explicit steps on adaptive Q1/Q2 meshes with hanging nodes on the top
+surface, a field that crosses the boiling point and the evaporation cap, FP64 and FP32
+operators; calls that do not cover the surface loss refuse it.
+
+Tolerances as for the other parity tests: FP64 1e-10 relative; FP32 operator 2e-5 of max|f|
+for residual terms and 2e-4 relative max-norm on temperatures."""
+import numpy as np
+import pytest
+
+from paper_2302_05164_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32_F, TOL32_T = 1e-10, 2e-5, 2e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_05164_gb300 import pbf
+    return pbf
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def to_dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def mesh(degree):
+    regions = [(I.BALL, (0.3e-3, 0.25e-3, 0.25e-3), (0, 0, 0), 120e-6, 3)]
+    return I.mesh_desc((8, 4, 2), (125e-6,) * 3, degree, 3, regions)
+
+
+def hot_field(om):
+    # up to 4300 K at the top: radiation everywhere, evaporation above 3000 K, cap at 4000 K
+    return I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 4300.0, 70e-6, seed=41, noise=0.01)
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_surface_loss_residual_matches_oracle(P, oracle_mod, degree, prec):
+    desc = mesh(degree)
+    om = oracle_mod.Mesh(desc)
+    om.set_surface_loss(I.SURFACE_LOSS)
+    mat = I.TI64_NONLIN_Q2
+    T = hot_field(om)
+    ls = I.laser([(0.1e-3, 0.25e-3, 0.9e-3, 0.25e-3, 0.0, 1e-3)], [200.0], eta=0.35, radius=40e-6)
+    fd, fv, _ = om.residual(mat, T, ls, 2e-4)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
+    P.pbf_ctx_set_surface_loss(ctx.h, I.SURFACE_LOSS)
+    out = [torch.zeros(om.n_dofs, dtype=torch.float64, device="cuda") for _ in range(3)]
+    P.pbf_eval_residual(ctx.h, to_dev(T), ls, 2e-4, *out)
+    gd, gv = out[0].cpu().numpy(), out[1].cpu().numpy()
+    tol = TOL64 if prec == "f64" else TOL32_F
+    assert rel(gd, fd) < tol and rel(gv, fv) < tol
+    # the loss dominates the top rows here: without it the source term differs
+    _, fv0, _ = oracle_mod.Mesh(desc).residual(mat, T, ls, 2e-4)
+    assert rel(fv0, fv) > 1e-2
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_explicit_steps_with_surface_loss_match_oracle(P, oracle_mod, prec):
+    """Six steps; the fused shape is requested but the surface loss runs the per-cell form."""
+    desc = mesh(2)
+    om = oracle_mod.Mesh(desc)
+    om.set_surface_loss(I.SURFACE_LOSS)
+    mat = I.TI64_NONLIN_Q2
+    T0 = I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 3700.0, 70e-6, seed=42, noise=0.01)
+    ls = I.laser([(0.1e-3, 0.25e-3, 0.9e-3, 0.25e-3, 0.0, 1e-3)], [200.0], eta=0.35, radius=40e-6)
+    dt = 1e-8
+    ref = om.explicit(mat, T0, ls, 1e-4, dt, 6)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
+    P.pbf_ctx_set_surface_loss(ctx.h, I.SURFACE_LOSS)
+    P.pbf_ctx_set_kernel_shape(ctx.h, 5)
+    Td = to_dev(T0)
+    P.pbf_explicit_step(ctx.h, Td, ls, 1e-4, dt, 6)
+    torch.cuda.synchronize()
+    got = Td.cpu().numpy()
+    assert rel(got, ref) < (TOL64 if prec == "f64" else TOL32_T)
+    assert np.abs(ref - T0).max() > 0.1
+    # switched off again: the plain operator (the oracle without the loss)
+    P.pbf_ctx_set_surface_loss(ctx.h, None)
+    Td = to_dev(T0)
+    P.pbf_explicit_step(ctx.h, Td, ls, 1e-4, dt, 6)
+    torch.cuda.synchronize()
+    ref0 = oracle_mod.Mesh(desc).explicit(mat, T0, ls, 1e-4, dt, 6)
+    assert rel(Td.cpu().numpy(), ref0) < (TOL64 if prec == "f64" else TOL32_T)
+
+
+def test_calls_without_surface_loss_refuse_it(P):
+    desc = mesh(1)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, I.TI64_CONST, P.PBF_F64)
+    P.pbf_ctx_set_surface_loss(ctx.h, I.SURFACE_LOSS)
+    n = m.info()["n_dofs"]
+    T = torch.full((n,), 500.0, dtype=torch.float64, device="cuda")
+    status, _ = P.pbf_implicit_solve(ctx.h, T, 1e-2, 1, 1e-8, 10, 5, np.array([0.5, 2.0]))
+    assert status == 1
+    ls = I.laser([(0.1e-3, 0.25e-3, 0.9e-3, 0.25e-3, 0.0, 1e-3)], [200.0])
+    with pytest.raises(P.PbfError) as e:
+        P.pbf_adjoint_sweep(ctx.h, T, ls, 0.0, 1e-8, 4, 2)
+    assert e.value.status == 1
+    with pytest.raises(P.PbfError):
+        P.pbf_ctx_set_surface_loss(ctx.h, dict(I.SURFACE_LOSS, T_max=2000.0))  # cap below T_v
