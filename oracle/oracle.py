@@ -46,6 +46,10 @@ class _Loss(C.Structure):
                                           "T_max")]
 
 
+class _Phase(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("T_s", "T_l", "k_p", "k_m", "k_s")]
+
+
 def surface_loss(q: dict) -> _Loss:
     return _Loss(*[float(q[n]) for n, _ in _Loss._fields_])
 
@@ -155,6 +159,13 @@ class Mesh:
     def set_material(self, mat_active: np.ndarray):
         m = np.ascontiguousarray(mat_active, np.uint8)
         lib().or_mesh_set_material(C.c_void_p(self.h), _ptr(m))
+
+    def set_phase(self, ph):
+        """Phase-dependent conductivity k(T, r_c) with the consolidated-fraction history per
+        quadrature point (dict T_s, T_l, k_p, k_m, k_s; None: off); setting it restarts the
+        history from the cell materials. Explicit steps update the history, residuals read it."""
+        self._phase = None if ph is None else _Phase(*[float(ph[n]) for n, _ in _Phase._fields_])
+        lib().or_set_phase(C.c_void_p(self.h), None if ph is None else C.byref(self._phase))
 
     def set_surface_loss(self, q):
         """Radiation / evaporation on the top faces (dict of `surface_loss` fields; None: off)

@@ -69,6 +69,15 @@ typedef struct {
   double C_P, C_T, C_M, T_v, h_v, c_h, T_h0, T_max;
 } or_surface_loss;
 
+// Phase-dependent conductivity with history (Sec. 2, Eqs. liquid_fraction,
+// consolidated_fraction, phase_fractions, material_parameter_interp): liquid fraction
+// g(T) = clamp((T - T_s)/(T_l - T_s), 0, 1), consolidated fraction r_c = max of g over the
+// states so far (starting at 1 in consolidated cells, 0 in powder cells), and
+// k = (1 - r_c) k_p + g k_m + (r_c - g) k_s.
+typedef struct {
+  double T_s, T_l, k_p, k_m, k_s;
+} or_phase;
+
 typedef struct {
   int n_seg;
   const double* seg;    // [n_seg][6]: x0, y0, x1, y1, t0, t1
@@ -128,6 +137,9 @@ struct Mesh {
   std::unordered_map<uint64_t, NodeInfo> nodes;
   bool has_loss = false;
   or_surface_loss loss{};  // radiation / evaporation on the top faces (when has_loss)
+  bool has_phase = false;
+  or_phase phase{};                // phase-dependent conductivity (when has_phase)
+  mutable std::vector<double> rc;  // consolidated fraction per active cell and quadrature point
 
   int npc() const { return (p + 1) * (p + 1) * (p + 1); }
   int64_t size(const Leaf& l) const { return (int64_t)1 << (L - l.level); }
@@ -646,8 +658,10 @@ double surface_flux(const or_surface_loss& q, double T) {
 // cylinder source of Eq. (heat_soruce_cylindrical) read with -h_powder < z^ < 0; with a
 // surface loss also the boundary term -int_{Gamma_RE} N_i (q_rad + q_evap)(T_h) dA of the weak
 // form (Eq. weak_form), (p+1)^2 Gauss points per top face.
+// phase: 0 plain material; with a phase model set on the mesh, 1 uses k(T, r_c) with
+// r_c = max(stored r_c, g(T)), 2 also stores that r_c (an explicit step).
 void residual(const Mesh& m, const or_material& mt, double s, const double* T, const or_laser* ls, double t,
-              Fields& F, bool with_C = true) {
+              Fields& F, bool with_C = true, int phase = 0) {
   const int p = m.p, npc = m.npc(), nq = p + 1;
   F.fdiff.assign((size_t)m.n_dofs, 0.0);
   F.fvol.assign((size_t)m.n_dofs, 0.0);
@@ -678,6 +692,15 @@ void residual(const Mesh& m, const or_material& mt, double s, const double* T, c
             for (int d = 0; d < 3; ++d) grad[d] += dN[3 * a + d] / g.h[d] * Te[a];
           }
           double k = cond(mt, Tq, mat, s);
+          if (phase && m.has_phase) {
+            const or_phase& ph = m.phase;
+            double g = (Tq - ph.T_s) / (ph.T_l - ph.T_s);
+            g = g < 0.0 ? 0.0 : (g > 1.0 ? 1.0 : g);
+            double& stored = m.rc[((size_t)c * nq + (size_t)qz) * (size_t)(nq * nq) + (size_t)(qy * nq + qx)];
+            const double rc = std::max(stored, g);
+            if (phase == 2) stored = rc;
+            k = ((1.0 - rc) * ph.k_p + g * ph.k_m + (rc - g) * ph.k_s) * s;
+          }
           for (int i = 0; i < npc; ++i) {
             double dot = 0.0;
             for (int d = 0; d < 3; ++d) dot += dN[3 * i + d] / g.h[d] * grad[d];
@@ -943,7 +966,7 @@ double pnorm_max(const Objective& o, const double* T, std::vector<double>* grad)
 // hold the prescribed temperature.
 void euler_step(const Mesh& m, const or_material& mt, double s, double* T, const or_laser* ls, double t, double dt,
                 Fields& F) {
-  residual(m, mt, s, T, ls, t, F);
+  residual(m, mt, s, T, ls, t, F, true, 2);
   for (int i = 0; i < m.n_dofs; ++i) {
     if (m.dirichlet[(size_t)i]) T[i] = mt.T_dirichlet;
     else T[i] = T[i] + dt * (F.fdiff[(size_t)i] + F.fvol[(size_t)i]) / F.C[(size_t)i];
@@ -1009,6 +1032,21 @@ void or_set_surface_loss(void* h, const or_surface_loss* q) {
 
 double or_surface_flux(const or_surface_loss* q, double T) { return surface_flux(*q, T); }
 
+// Phase-dependent conductivity with history for later residuals and explicit steps (null:
+// off). Setting it (re)starts the history: r_c = 0 in powder cells (material 1), 1 elsewhere.
+void or_set_phase(void* h, const or_phase* ph) {
+  Mesh* m = (Mesh*)h;
+  m->has_phase = ph != nullptr;
+  m->rc.clear();
+  if (!ph) return;
+  m->phase = *ph;
+  const size_t nq3 = (size_t)(m->p + 1) * (size_t)(m->p + 1) * (size_t)(m->p + 1);
+  m->rc.assign(m->acell.size() * nq3, 1.0);
+  for (size_t c = 0; c < m->acell.size(); ++c)
+    if (m->material[(size_t)m->acell[c]] == 1)
+      for (size_t q = 0; q < nq3; ++q) m->rc[c * nq3 + q] = 0.0;
+}
+
 // Override material ids of active cells (layer activation marks new cells).
 void or_mesh_set_material(void* h, const unsigned char* mat_active) {
   Mesh* m = (Mesh*)h;
@@ -1019,7 +1057,7 @@ void or_residual(void* h, const or_material* mt, double s, const double* T, cons
                  double* fvol, double* C) {
   Mesh* m = (Mesh*)h;
   Fields F;
-  residual(*m, *mt, s, T, ls, t, F);
+  residual(*m, *mt, s, T, ls, t, F, true, 1);
   std::copy(F.fdiff.begin(), F.fdiff.end(), fdiff);
   std::copy(F.fvol.begin(), F.fvol.end(), fvol);
   std::copy(F.C.begin(), F.C.end(), C);
@@ -1194,7 +1232,7 @@ int or_implicit(void* h, const or_material* mt, double* T, double dt, int nsteps
 double or_adjoint(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0, double dt,
                   int nsteps, double T_target, double p_exp, double* grad) {
   Mesh* m = (Mesh*)h;
-  if (m->has_loss) return std::nan("");  // the adjoint covers no surface loss
+  if (m->has_loss || m->has_phase) return std::nan("");  // the adjoint covers neither
   const Mesh& M = *m;
   size_t n = (size_t)M.n_dofs;
   Objective obj;
@@ -1314,7 +1352,7 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
 double or_objective(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0,
                     double dt, int nsteps, double T_target, double p_exp) {
   Mesh* m = (Mesh*)h;
-  if (m->has_loss) return std::nan("");  // as the adjoint
+  if (m->has_loss || m->has_phase) return std::nan("");  // as the adjoint
   size_t n = (size_t)m->n_dofs;
   Objective obj;
   obj.T_target = T_target;

@@ -58,6 +58,11 @@ T0 = 353.0
 # 3000 K, C_P = 54 kPa, C_T = 50,000 K, C_M = 0.001 K s^2/m^2, latent heat of evaporation
 # 6.0 MJ/kg, enthalpy reference 663 K, [T] capped at T_v + 1000 K; the ambient temperature and
 # the heat capacity of the enthalpy term follow the Ti-6Al-4V-like workloads (353 K, 526 J/kgK).
+# Phase-dependent conductivity with history (Eqs. liquid_fraction .. material_parameter_interp)
+# with the paper's material table (Sec. 5.1): solidus 1500 K, liquidus 1900 K, powder 0.2 W/mK,
+# melt and solid 20 W/mK.
+PHASE = dict(T_s=1500.0, T_l=1900.0, k_p=0.2, k_m=20.0, k_s=20.0)
+
 SURFACE_LOSS = dict(emissivity=0.7, T_amb=T0, C_P=54.0e3, C_T=5.0e4, C_M=1.0e-3, T_v=3000.0, h_v=6.0e6, c_h=526.0,
                     T_h0=663.0, T_max=4000.0)
 

@@ -438,3 +438,58 @@ def test_radiating_slab_reaches_the_flux_balance(oracle_mod):
     expect = 2500.0 + (T_top - 2500.0) * z / L
     assert 2000.0 < T_top < 2450.0
     assert np.abs(T - expect).max() < 1e-6
+
+
+# ---- phase-dependent conductivity with history (Eqs. liquid_fraction, consolidated_fraction,
+# phase_fractions, material_parameter_interp) ---------------------------------------------
+
+def _phase_mesh(oracle_mod, p, powder):
+    regions = [(I.BALL, (0.3e-3, 0.25e-3, 0.25e-3), (0, 0, 0), 120e-6, 2)]
+    z0, z1 = (-1.0, 1.0) if powder else (1e30, 1e30)
+    return oracle_mod.Mesh(I.mesh_desc((4, 2, 2), (125e-6,) * 3, p, 2, regions, powder_z0=z0, powder_z1=z1))
+
+
+def _ramp(k_lo, k_hi, ph):
+    return dict(I.TI64_CONST, k0=k_lo, k1=k_hi, Tk0=ph["T_s"], Tk1=ph["T_l"], powder_k_scale=1.0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_phase_conductivity_of_consolidated_material_is_the_solid_to_melt_ramp(oracle_mod, p):
+    """r_c = 1: k = k_s + g(T) (k_m - k_s), i.e. the clamped linear ramp from k_s at T_s to
+    k_m at T_l; the residual of a field across solid, mushy and melt equals the ramp
+    material's."""
+    ph = dict(I.PHASE, k_m=30.0)
+    m = _phase_mesh(oracle_mod, p, powder=False)
+    T = I.smooth_field(m.dof_xyz(), seed=31, lo=1200.0, hi=2300.0)
+    ref, _, _ = m.residual(_ramp(ph["k_s"], ph["k_m"], ph), T)
+    m.set_phase(ph)
+    fd, _, _ = m.residual(I.TI64_CONST, T)
+    assert np.abs(fd - ref).max() < 1e-12 * np.abs(ref).max()
+    assert np.abs(ref).max() > 0
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_phase_conductivity_of_powder_before_and_after_melting(oracle_mod, p):
+    """Powder (r_c = 0 before): k = k_p + g (k_m - k_p), the ramp from k_p to k_m (the residual
+    reads r_c = max(stored, g) without storing it). After an explicit step at a melted state the
+    history holds r_c = 1: a field below T_s then sees k_s, not k_p (irreversible
+    consolidation)."""
+    ph = dict(I.PHASE, k_m=30.0, k_s=25.0)
+    m = _phase_mesh(oracle_mod, p, powder=True)
+    m.set_phase(ph)
+    T = I.smooth_field(m.dof_xyz(), seed=32, lo=1200.0, hi=2300.0)
+    fd, _, _ = m.residual(I.TI64_CONST, T)
+    ref, _, _ = _phase_mesh(oracle_mod, p, powder=True).residual(_ramp(ph["k_p"], ph["k_m"], ph), T)
+    assert np.abs(fd - ref).max() < 1e-12 * np.abs(ref).max()
+    cool = I.smooth_field(m.dof_xyz(), seed=33, lo=400.0, hi=1400.0)
+    plain = _phase_mesh(oracle_mod, p, powder=True)
+    k_p_res, _, _ = plain.residual(dict(I.TI64_CONST, k0=ph["k_p"], k1=ph["k_p"], powder_k_scale=1.0), cool)
+    fd, _, _ = m.residual(I.TI64_CONST, cool)
+    assert np.abs(fd - k_p_res).max() < 1e-12 * np.abs(k_p_res).max()  # residuals did not consolidate
+    m.explicit(I.TI64_CONST, np.full(m.n_dofs, 2600.0), None, 0.0, 1e-12, 1)
+    k_s_res, _, _ = plain.residual(dict(I.TI64_CONST, k0=ph["k_s"], k1=ph["k_s"], powder_k_scale=1.0), cool)
+    fd, _, _ = m.residual(I.TI64_CONST, cool)
+    assert np.abs(fd - k_s_res).max() < 1e-12 * np.abs(k_s_res).max()
+    m.set_phase(ph)  # setting the model again restarts the history
+    fd, _, _ = m.residual(I.TI64_CONST, cool)
+    assert np.abs(fd - k_p_res).max() < 1e-12 * np.abs(k_p_res).max()
