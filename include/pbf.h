@@ -318,6 +318,25 @@ typedef struct {
  * pbf_adjoint_sweep return PBF_EINVAL. Bad parameters: PBF_EINVAL. Host only. */
 pbf_status pbf_ctx_set_surface_loss(pbf_ctx* ctx, const pbf_surface_loss* q);
 
+/* Phase-dependent conductivity with history (Sec. 2, Eqs. liquid_fraction,
+ * consolidated_fraction, phase_fractions, material_parameter_interp): liquid fraction
+ * g(T) = clamp((T - T_s)/(T_l - T_s), 0, 1); consolidated fraction r_c per quadrature point and
+ * instance, starting at 0 in powder cells (material 1) and 1 elsewhere; k(T, r_c) =
+ * (1 - r_c) k_p + g k_m + (r_c - g) k_s, times the instance's conductivity scale (the material's
+ * k(T) and powder scale are not used). Each explicit step uses and stores
+ * r_c = max(stored r_c, g(T_n)) at its state; residual evaluations use that maximum without
+ * storing it. */
+typedef struct {
+  double T_s, T_l, k_p, k_m, k_s;
+} pbf_phase;
+
+/* Sets (ph != NULL; the history restarts from the cell materials) or clears (NULL) the phase
+ * model of a context. With it the explicit steps run the per-cell form (shapes 4-6 act as
+ * shape 1), and pbf_implicit_solve and pbf_adjoint_sweep return PBF_EINVAL. PBF_EINVAL for
+ * bad parameters or the quadrature-point capacity. Allocates the history once
+ * ((p+1)^3 n_cells batch values); synchronises. */
+pbf_status pbf_ctx_set_phase(pbf_ctx* ctx, const pbf_phase* ph);
+
 /* Test hook for the time-out path of shape 6 (no counterpart in the paper): while
  * extra_blocks > 0 the persistent form's grid barrier waits for that many blocks more than
  * were launched, so its first wait runs out (after one second) and the call returns

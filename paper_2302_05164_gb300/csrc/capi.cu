@@ -755,6 +755,7 @@ cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_d
   const size_t rsz = f32 ? 4 : 8;
   CellLaunch L = base;
   L.x = T_dev;
+  set_phase(L, false);
   cudaError_t e = cudaSuccess;
   if (f32) {
     e = launch_prepare_f32(nv, T_dev, mat.T_ref, Tf, nullptr, s);
@@ -816,6 +817,7 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
                ? explicit_steps_persistent(T_dev, t0, dt, nsteps, s)
                : explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant == 5, s);
   CellLaunch L = base;
+  set_phase(L, true);
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
   const int64_t nv = n_dofs * batch;
   cudaError_t e = cudaSuccess;
@@ -1121,6 +1123,38 @@ extern "C" pbf_status pbf_ctx_set_surface_loss(pbf_ctx* ctx, const pbf_surface_l
   k.T_h0 = q->T_h0;
   k.T_max = q->T_max;
   ctx->has_loss = true;
+  return PBF_OK;
+}
+
+extern "C" pbf_status pbf_ctx_set_phase(pbf_ctx* ctx, const pbf_phase* ph) {
+  if (!ctx) return fail(PBF_EINVAL, "null context");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  if (!ph) {
+    ctx->has_phase = false;
+    return PBF_OK;
+  }
+  if (!(ph->T_l > ph->T_s) || !(ph->k_p >= 0.0) || !(ph->k_m >= 0.0) || !(ph->k_s >= 0.0))
+    return fail(PBF_EINVAL, "phase model: need T_l > T_s and non-negative conductivities");
+  if (ctx->cap == CAP_QUADRATURE) return fail(PBF_EINVAL, "phase model: needs the constant or nodal capacity");
+  const int nq = ctx->npc;  // (p+1)^3 quadrature points per cell, as many as nodes
+  if (!ctx->rc) {
+    char* p = nullptr;
+    const cudaError_t e = dalloc(ctx, &p, (size_t)nq * (size_t)ctx->n_cells * (size_t)ctx->batch * (ctx->f32 ? 4 : 8));
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(e == cudaErrorMemoryAllocation ? PBF_ENOMEM : PBF_ECUDA, "phase model: %s", cudaGetErrorString(e));
+    }
+    ctx->rc = p;
+  }
+  const double t_off = ctx->mat.T_ref - ph->T_s, inv = 1.0 / (ph->T_l - ph->T_s);
+  ctx->phd = PhaseR<double>{t_off, inv, ph->k_p, ph->k_s - ph->k_p, ph->k_m - ph->k_s};
+  ctx->phf = PhaseR<float>{(float)t_off, (float)inv, (float)ph->k_p, (float)(ph->k_s - ph->k_p), (float)(ph->k_m - ph->k_s)};
+  cudaError_t e = launch_phase_init(ctx->f32, nq, ctx->base.mesh, ctx->rc, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  ++ctx->launches;
+  if (e != cudaSuccess) return ctx->cuda(e, "phase model");
+  ctx->has_phase = true;
   return PBF_OK;
 }
 

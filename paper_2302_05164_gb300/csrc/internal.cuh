@@ -125,6 +125,15 @@ struct MatR {
   R m_impl;                               // rho c / dt of the implicit operator
 };
 
+// Phase-dependent conductivity with history (Sec. 2, Eqs. liquid_fraction ..
+// material_parameter_interp) in the kernel's precision: g = clamp((v + t_off) inv_dT, 0, 1)
+// with v = T - T_ref, r_c = max(stored r_c, g), k = k_p + r_c dks + g dkm
+// (dks = k_s - k_p, dkm = k_m - k_s).
+template <typename R>
+struct PhaseR {
+  R t_off, inv_dT, kp, dks, dkm;
+};
+
 struct LaserK {
   int n_seg = 0;
   int volumetric = 0;
@@ -196,6 +205,13 @@ struct CellLaunch {
   int f32 = 0;
   int variant = 0;  // launch shape of the FP32 residual kernel (see kCellVariants)
   LaserInline las;
+  // phase-dependent conductivity (residual mode): r_c per quadrature point, [q][n_cells][batch]
+  // in the operator precision, read from rc_in and stored to rc_out (null: read only)
+  int phase = 0;
+  PhaseR<float> phf;
+  PhaseR<double> phd;
+  const void* rc_in = nullptr;
+  void* rc_out = nullptr;
 };
 
 // Explicit-step shapes the autotuner chooses from for the FP32 operator. 0-3: the per-cell

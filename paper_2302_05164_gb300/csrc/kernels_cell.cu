@@ -74,7 +74,15 @@ __device__ __forceinline__ void scatter(const DevMesh& M, R* __restrict__ f, R* 
 }
 
 // One kernel for the residual / capacity / stiffness / implicit-operator modes.
-template <int P, typename R, int MODE, bool NLK, bool LAT, int BS = 128, int MINB = 1>
+template <typename R>
+__device__ __forceinline__ const PhaseR<R>& phase_of(const CellLaunch& L);
+template <>
+__device__ __forceinline__ const PhaseR<float>& phase_of<float>(const CellLaunch& L) { return L.phf; }
+template <>
+__device__ __forceinline__ const PhaseR<double>& phase_of<double>(const CellLaunch& L) { return L.phd; }
+
+// PH: conductivity from the phase model with history (residual mode) instead of the k(T) ramp.
+template <int P, typename R, int MODE, bool NLK, bool LAT, int BS = 128, int MINB = 1, bool PH = false>
 __global__ void __launch_bounds__(BS, MINB) k_cell(const CellLaunch L, R* __restrict__ f, R* __restrict__ fh,
                                                    R* __restrict__ C, R* __restrict__ Ch) {
   constexpr int N = P + 1, NP = N * N * N;
@@ -118,7 +126,22 @@ __global__ void __launch_bounds__(BS, MINB) k_cell(const CellLaunch L, R* __rest
   const R scale = (mat == 1 ? mt.powder_scale : R(1)) * (ks ? ks[inst] : R(1));
   const R sgn = (MODE == MODE_RESIDUAL) ? R(-1) : R(1);
   R kw[NP];
-  {
+  if (PH) {
+    // k(T, r_c) with r_c = max(stored r_c, g(T)) per quadrature point; stored in explicit steps
+    const PhaseR<R>& ph = phase_of<R>(L);
+    const R is = ks ? ks[inst] : R(1);
+    const R* rc_in = static_cast<const R*>(L.rc_in);
+    R* rc_out = static_cast<R*>(L.rc_out);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const R g = clamp01((v[q] + ph.t_off) * ph.inv_dT);
+      const int64_t j = ((int64_t)q * M.n_cells + cell) * B + inst;
+      R rc = rc_in[j];
+      rc = rc > g ? rc : g;
+      if (rc_out) rc_out[j] = rc;
+      kw[q] = sgn * ((ph.kp + rc * ph.dks + g * ph.dkm) * is) * (R(wq3<P>(q)) * detJ);
+    }
+  } else {
     const R k0 = mt.k0 * scale, dk = mt.dk * scale;
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -317,12 +340,12 @@ cudaError_t dispatch_adj(const CellLaunch& L, bool qpc, void* g, void* gh, cudaS
   return go_adj<P, R, false, false>(L, g, gh, s);
 }
 
-template <int P, typename R, int MODE, bool NLK, bool LAT, int BS = 128, int MINB = 1>
+template <int P, typename R, int MODE, bool NLK, bool LAT, int BS = 128, int MINB = 1, bool PH = false>
 cudaError_t go_shape(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
   const int64_t n = (int64_t)L.mesh.n_cells * L.mesh.batch;
   if (n == 0) return cudaSuccess;
   const int64_t grid = (n + BS - 1) / BS;
-  k_cell<P, R, MODE, NLK, LAT, BS, MINB><<<(unsigned)grid, BS, 0, s>>>(L, (R*)f, (R*)fh, (R*)C, (R*)Ch);
+  k_cell<P, R, MODE, NLK, LAT, BS, MINB, PH><<<(unsigned)grid, BS, 0, s>>>(L, (R*)f, (R*)fh, (R*)C, (R*)Ch);
   return cudaGetLastError();
 }
 
@@ -330,6 +353,8 @@ cudaError_t go_shape(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, 
 // shapes; every other combination uses 128 threads with no register cap.
 template <int P, typename R, int MODE, bool NLK, bool LAT>
 cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaStream_t s) {
+  if (MODE == MODE_RESIDUAL && !LAT && L.phase)  // phase model: one launch shape
+    return go_shape<P, R, MODE, false, false, 128, 1, true>(L, f, fh, C, Ch, s);
   if (std::is_same<R, float>::value && MODE == MODE_RESIDUAL && !LAT) {
     switch (L.variant) {
       case 1:

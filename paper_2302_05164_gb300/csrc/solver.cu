@@ -222,6 +222,7 @@ void splitmix_vector(std::vector<double>& v, uint64_t seed) {
 pbf_status check_linear(pbf_ctx* c) {
   if (c->batch != 1) return err(PBF_EINVAL, "the implicit solve runs one instance (batch 1)");
   if (c->has_loss) return err(PBF_EINVAL, "the implicit solve covers no radiation / evaporation surface loss");
+  if (c->has_phase) return err(PBF_EINVAL, "the implicit solve covers no phase-dependent conductivity");
   if ((c->mat.Tk1 > c->mat.Tk0 && c->mat.k1 != c->mat.k0) || c->cap != CAP_CONST)
     return err(PBF_EINVAL, "the implicit solve needs a linear material (constant k and c)");
   return PBF_OK;
@@ -606,6 +607,7 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
   if (nsteps < 1 || n_checkpoints < 1 || !(dt > 0) || !(p_exp >= 1)) return err(PBF_EINVAL, "bad sweep parameters");
   if (laser->n_seg < 1) return err(PBF_EINVAL, "the adjoint needs a laser with at least one segment");
   if (ctx->has_loss) return err(PBF_EINVAL, "the adjoint covers no radiation / evaporation surface loss");
+  if (ctx->has_phase) return err(PBF_EINVAL, "the adjoint covers no phase-dependent conductivity");
   pbf_status st = ctx->check_usable();
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;

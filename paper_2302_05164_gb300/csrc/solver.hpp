@@ -27,6 +27,10 @@ struct CtxBase {
   pbf_material mat{};
   bool has_loss = false;  // radiation / evaporation on the top faces (pbf_ctx_set_surface_loss)
   LossK loss;
+  bool has_phase = false;  // phase-dependent conductivity with history (pbf_ctx_set_phase)
+  PhaseR<float> phf;
+  PhaseR<double> phd;
+  void* rc = nullptr;      // consolidated fraction [q][n_cells][batch], operator precision
   CellLaunch base;
   LaserSetup lsetup;
   std::vector<void*> allocs;
@@ -118,7 +122,17 @@ struct CtxBase {
   cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
   cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, cudaStream_t s);
   cudaError_t explicit_steps_persistent(double* T, double t0, double dt, int nsteps, cudaStream_t s);
-  bool fused_ok() const { return f32 && batch == 1 && cap != CAP_QUADRATURE && !has_loss && step.n_patches > 0; }
+  bool fused_ok() const {
+    return f32 && batch == 1 && cap != CAP_QUADRATURE && !has_loss && !has_phase && step.n_patches > 0;
+  }
+  // the phase model's fields of a residual-mode launch (store: an explicit step)
+  void set_phase(CellLaunch& L, bool store) const {
+    L.phase = has_phase ? 1 : 0;
+    L.phf = phf;
+    L.phd = phd;
+    L.rc_in = has_phase ? rc : nullptr;
+    L.rc_out = has_phase && store ? rc : nullptr;
+  }
   // the surface laser of the cell kernels at time t (off for the volumetric source)
   LaserInline inline_laser(double t, Spot* sp) const;
   // CUDA events around one timed launch (kernel timing on)

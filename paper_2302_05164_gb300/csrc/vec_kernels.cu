@@ -290,6 +290,16 @@ __global__ void k_surface_loss(int n_top, int B, const int32_t* __restrict__ top
     }
 }
 
+// Start of the consolidated-fraction history: r_c = 0 in powder cells (material 1), 1 in
+// consolidated ones, for every quadrature point and instance ([q][n_cells][batch]).
+template <typename R>
+__global__ void k_phase_init(int64_t n, int n_cells, int B, const uint8_t* __restrict__ cell_mat, R* __restrict__ rc) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int cell = (int)((i / B) % n_cells);
+  rc[i] = cell_mat[cell] == 1 ? R(0) : R(1);
+}
+
 // Cylinder source of depth h_powder below the active top (Eq. heat_soruce_cylindrical with
 // the bound read as -h_powder < z^ < 0), integrated with (P+1)^3 Gauss points per cell.
 template <int P, typename R>
@@ -826,6 +836,14 @@ cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMe
     if (f32) k_laser_surface<2, float><<<grid_for(n, 128), 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, ls.k, power, sp, (float*)f);
     else k_laser_surface<2, double><<<grid_for(n, 128), 128, 0, s>>>(ls.n_top, B, ls.top_cell, ls.top_geo, M, ls.k, power, sp, (double*)f);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_init(bool f32, int nq, const DevMesh& M, void* rc, cudaStream_t s) {
+  const int64_t n = (int64_t)nq * M.n_cells * M.batch;
+  if (n == 0) return cudaSuccess;
+  if (f32) k_phase_init<float><<<grid_for(n), kBS, 0, s>>>(n, M.n_cells, M.batch, M.cell_mat, (float*)rc);
+  else k_phase_init<double><<<grid_for(n), kBS, 0, s>>>(n, M.n_cells, M.batch, M.cell_mat, (double*)rc);
   return cudaGetLastError();
 }
 

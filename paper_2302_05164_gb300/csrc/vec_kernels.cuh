@@ -87,6 +87,8 @@ cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMe
 // constraint rows), constraint-resolved atomic additions onto f.
 cudaError_t launch_surface_loss(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const void* x,
                                 double T_off, const LossK& q, void* f, cudaStream_t s);
+// r_c = 0 in powder cells, 1 elsewhere, for the nq quadrature points of every cell and instance
+cudaError_t launch_phase_init(bool f32, int nq, const DevMesh& M, void* rc, cudaStream_t s);
 cudaError_t launch_to_f64(bool f32, int64_t n, const void* a, double* out, cudaStream_t s);
 cudaError_t launch_broadcast_dofs(int64_t n_dofs, int B, const double* a, double* out, cudaStream_t s);
 // inv_d = 1 / c, inv_f = its FP32 rounding; inv_fx (nullable) the same with -1 at Dirichlet dofs

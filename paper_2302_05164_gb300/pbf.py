@@ -36,6 +36,10 @@ class SurfaceLoss(C.Structure):
                                           "T_max")]
 
 
+class Phase(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("T_s", "T_l", "k_p", "k_m", "k_s")]
+
+
 class MeshDesc(C.Structure):
     _fields_ = [("origin", C.c_double * 3), ("ntree", C.c_int * 3), ("tree_h", C.c_double * 3),
                 ("degree", C.c_int), ("max_level", C.c_int), ("tree_exists", C.c_void_p),
@@ -98,6 +102,7 @@ _SIGS = {
     "pbf_ctx_set_kernel_shape": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_set_barrier_test": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_set_surface_loss": ([C.c_void_p, C.POINTER(SurfaceLoss)], C.c_int),
+    "pbf_ctx_set_phase": ([C.c_void_p, C.POINTER(Phase)], C.c_int),
     "pbf_ctx_set_timing": ([C.c_void_p, C.c_int], C.c_int),
     "pbf_ctx_kernel_time": ([C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)], C.c_int),
     "pbf_ctx_launch_count": ([C.c_void_p, C.POINTER(C.c_longlong)], C.c_int),
@@ -330,6 +335,15 @@ def pbf_ctx_set_surface_loss(h, q):
     else:
         s = SurfaceLoss(*[float(q[n]) for n, _ in SurfaceLoss._fields_])
         _check(lib().pbf_ctx_set_surface_loss(h, C.byref(s)))
+
+
+def pbf_ctx_set_phase(h, ph):
+    """ph: dict with the Phase fields (T_s, T_l, k_p, k_m, k_s), or None to switch it off."""
+    if ph is None:
+        _check(lib().pbf_ctx_set_phase(h, None))
+    else:
+        p = Phase(*[float(ph[n]) for n, _ in Phase._fields_])
+        _check(lib().pbf_ctx_set_phase(h, C.byref(p)))
 
 
 def pbf_ctx_set_barrier_test(h, extra_blocks):

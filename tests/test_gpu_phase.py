@@ -1,0 +1,112 @@
+"""GPU parity of the phase-dependent conductivity with its consolidated-fraction history
+(Sec. 2, Eqs. liquid_fraction, consolidated_fraction, phase_fractions,
+material_parameter_interp) with the oracle, through the C ABI: residual terms at the initial
+history, explicit steps that melt part of a powder layer (history stored per quadrature point),
+and a residual at a cool state afterwards that must see the consolidated material; FP64 and
+FP32 operators, Q1 and Q2 with hanging nodes. Calls that do not cover the model refuse it.
+
+Tolerances: FP64 1e-10 relative; FP32 operator 2e-5 of max|f| (residual terms), 2e-4 relative
+max-norm on temperatures, and 5e-3 of max|f| for a residual that reads a history built by FP32
+steps."""
+import numpy as np
+import pytest
+
+from paper_2302_05164_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL64, TOL32_F, TOL32_T = 1e-10, 2e-5, 2e-4
+PH = dict(I.PHASE, k_m=30.0, k_s=25.0)
+
+
+@pytest.fixture(scope="module")
+def P():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2302_05164_gb300 import pbf
+    return pbf
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def to_dev(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+
+
+def mesh(degree):
+    regions = [(I.BALL, (0.3e-3, 0.25e-3, 0.25e-3), (0, 0, 0), 120e-6, 3)]
+    return I.mesh_desc((8, 4, 2), (125e-6,) * 3, degree, 3, regions, powder_z0=0.17e-3, powder_z1=1.0)
+
+
+def gpu_residual(P, ctx, T, n):
+    out = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    P.pbf_eval_residual(ctx.h, to_dev(T), None, 0.0, *out)
+    return out[0].cpu().numpy()
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_phase_residual_matches_oracle(P, oracle_mod, degree, prec):
+    desc = mesh(degree)
+    om = oracle_mod.Mesh(desc)
+    om.set_phase(PH)
+    T = I.smooth_field(om.dof_xyz(), seed=51, lo=1200.0, hi=2300.0)
+    fd, _, _ = om.residual(I.TI64_CONST, T)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, I.TI64_CONST, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
+    P.pbf_ctx_set_phase(ctx.h, PH)
+    gd = gpu_residual(P, ctx, T, om.n_dofs)
+    assert rel(gd, fd) < (TOL64 if prec == "f64" else TOL32_F)
+    # residual evaluations do not store the history: a second one is the same
+    assert rel(gpu_residual(P, ctx, T, om.n_dofs), fd) < (TOL64 if prec == "f64" else TOL32_F)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_phase_history_through_explicit_steps(P, oracle_mod, prec):
+    desc = mesh(2)
+    om = oracle_mod.Mesh(desc)
+    om.set_phase(PH)
+    mat = I.TI64_CONST
+    lam, _ = oracle_mod.Mesh(desc).lambda_max(dict(mat, k0=30.0, k1=30.0, powder_k_scale=1.0),
+                                              I.start_vector(om.n_dofs), max_iter=300, rtol=1e-8)
+    dt = 0.4 * 2.0 / lam
+    T0 = I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 2600.0, 60e-6, seed=52, noise=0.01)
+    ref = om.explicit(mat, T0, None, 0.0, dt, 8)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
+    P.pbf_ctx_set_phase(ctx.h, PH)
+    P.pbf_ctx_set_kernel_shape(ctx.h, 5)  # requested fused shape: the phase model runs per cell
+    Td = to_dev(T0)
+    P.pbf_explicit_step(ctx.h, Td, None, 0.0, dt, 8)
+    torch.cuda.synchronize()
+    assert rel(Td.cpu().numpy(), ref) < (TOL64 if prec == "f64" else TOL32_T)
+    assert np.abs(ref - T0).max() > 1.0
+    # a cool state now sees the consolidated powder where the steps melted it
+    cool = I.smooth_field(om.dof_xyz(), seed=53, lo=400.0, hi=1400.0)
+    fd, _, _ = om.residual(mat, cool)
+    fresh = oracle_mod.Mesh(desc)
+    fresh.set_phase(PH)
+    fd0, _, _ = fresh.residual(mat, cool)
+    assert rel(fd0, fd) > 1e-3  # the history changed the operator
+    # the FP32 form's history follows its own states (within 2e-4 of the oracle's); g(T) turns a
+    # state difference dT into dT / (T_l - T_s) of r_c, about 1e-3 here
+    assert rel(gpu_residual(P, ctx, cool, om.n_dofs), fd) < (TOL64 if prec == "f64" else 5e-3)
+
+
+def test_calls_without_phase_model_refuse_it(P):
+    m = P.Mesh(mesh(1))
+    ctx = P.Context(m, I.TI64_CONST, P.PBF_F64)
+    with pytest.raises(P.PbfError):
+        P.pbf_ctx_set_phase(ctx.h, dict(PH, T_l=1400.0))  # liquidus below solidus
+    P.pbf_ctx_set_phase(ctx.h, PH)
+    n = m.info()["n_dofs"]
+    T = torch.full((n,), 500.0, dtype=torch.float64, device="cuda")
+    status, _ = P.pbf_implicit_solve(ctx.h, T, 1e-2, 1, 1e-8, 10, 5, np.array([0.5, 2.0]))
+    assert status == 1
+    ls = I.laser([(0.1e-3, 0.25e-3, 0.9e-3, 0.25e-3, 0.0, 1e-3)], [200.0])
+    with pytest.raises(P.PbfError) as e:
+        P.pbf_adjoint_sweep(ctx.h, T, ls, 0.0, 1e-8, 4, 2)
+    assert e.value.status == 1
