@@ -193,7 +193,10 @@ typedef struct {
 
 /* Uploads the mesh tables and the material; allocates work space for `batch` instances
  * (1 <= batch <= 1024). precision PBF_F64: operator in FP64; PBF_F32OP: operator arithmetic
- * and cell accumulation in FP32, state, update, reductions in FP64. */
+ * and cell accumulation in FP32; within an explicit-step call the state T - T_ref is kept as
+ * an unevaluated pair of FP32 numbers (about 48 bits) and updated without rounding error,
+ * between calls it is the caller's FP64 array; CG vectors, dot products and adjoint
+ * accumulation stay in FP64. */
 pbf_status pbf_ctx_create(const pbf_mesh* mesh, const pbf_material* mat, pbf_precision prec, int batch,
                           pbf_ctx** out);
 pbf_status pbf_ctx_destroy(pbf_ctx* ctx);
