@@ -180,6 +180,21 @@ def test_laser_total_power(oracle_mod):
     assert np.all(fv0 == 0)
 
 
+def test_volumetric_source_total_power_and_depth(oracle_mod):
+    """The cylinder source 2 eta P/(pi r^2 h_p) exp(-2 d^2/r^2) on -h_p < z^ < 0 (Eq.
+    heat_soruce_cylindrical, bound read as below the active top) integrates to eta P when the
+    cylinder lies inside the domain with cell faces at depth h_p, and loads only the dofs of
+    cells that reach into the powder band."""
+    d = I.mesh_desc((4, 4, 1), (100e-6, 100e-6, 100e-6), 2, 3, [I.uniform_region(3)], active_top_z=0.1e-3)
+    m = oracle_mod.Mesh(d)
+    ls = I.laser([(0.2e-3, 0.2e-3, 0.2e-3, 0.2e-3, 0.0, 1.0)], [200.0], eta=0.35, radius=40e-6, volumetric=True,
+                 h_powder=50e-6)
+    _, fv, _ = m.residual(I.TI64_CONST, np.full(m.n_dofs, 353.0), ls, t=0.5)
+    assert abs(fv.sum() - 70.0) < 1e-4 * 70.0
+    z = m.dof_xyz()[:, 2]
+    assert np.all(fv[z < 0.05e-3 - 1e-12] == 0.0) and fv[z > 0.05e-3 + 1e-12].max() > 0.0
+
+
 def test_critical_time_step_closed_form_and_paper_value(oracle_mod):
     # uniform Q1, lumped capacity, Neumann: lambda_max(C~^-1 K) = 4 alpha / h^2 exactly
     d = I.mesh_desc((2, 2, 2), (1.0, 1.0, 1.0), 1, 2, [I.uniform_region(2)], dirichlet_faces=0)
