@@ -21,9 +21,16 @@
 //   Z-curve (Morton) cell order, Sec. 4.1
 //   diffusive term per cell, Eqs. (diffusive_term_evaluation), (vector_evaluation), Sec. 4.2
 //   linearised operator incl. the dk/dT term L_e, Eq. (matrix_free_eval), Sec. 4.2
+//   radiation and evaporation on the free surface, Eqs. (bc_rad_evap), (bc_radiation),
+//   (bc_evaporation), Sec. 2                                       -> surface_flux(), residual()
+//   phase fractions and history conductivity, Eqs. (liquid_fraction) .. (material_parameter_interp)
 // Parts that the paper does not fix (surface Gaussian flux, linear k(T), Gaussian apparent
 // capacity, Chebyshev-Jacobi CG, the adjoint objective) follow the readings listed in the
 // design notes of this repository; each function below states the reading it implements.
+// Parity unpinned: no value printed in the paper fixes the width of the Gaussian apparent
+// capacity, the laser-segment timing or the adjoint objective; they are pinned only to their
+// own closed forms (the latent heat integrates to L, the surface flux to eta P) and to finite
+// differences (the adjoint).
 
 #include <algorithm>
 #include <cmath>
