@@ -13,7 +13,7 @@
  *  - pbf_stream is a cudaStream_t (0 = legacy default stream). Work is enqueued on it; a call
  *    synchronises only when it must return values computed on the device (stated below).
  *  - pbf_mesh and pbf_ctx are opaque, library-owned, and freed by their destroy calls.
- *  - After PBF_ECUDA or PBF_EFAULT a context refuses further work with PBF_ESTATE.
+ *  - After PBF_ECUDA a context refuses further work with PBF_ESTATE.
  */
 #ifndef PBF_H
 #define PBF_H
@@ -31,9 +31,9 @@ typedef enum {
   PBF_ENOMEM = 2,   /* host or device allocation failed */
   PBF_ECUDA = 3,    /* a CUDA runtime call failed */
   PBF_ENOCONV = 4,  /* an iterative solve missed its tolerance */
-  PBF_ENAN = 5,     /* a non-finite value was found in the state */
+  PBF_ENAN = 5,     /* reserved for a check of the state for non-finite values (no call returns it) */
   PBF_ETIMEOUT = 6, /* a bounded device wait expired */
-  PBF_EFAULT = 7,   /* a device-side index check failed */
+  PBF_EFAULT = 7,   /* reserved for device-side index checks (no call returns it) */
   PBF_ESTATE = 8    /* object is poisoned or out of date (mesh changed under a context) */
 } pbf_status;
 
