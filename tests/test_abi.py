@@ -39,3 +39,19 @@ def test_host_entry_points_validate_arguments():
     with pytest.raises(pbf.PbfError):
         pbf.pbf_mesh_transfer(m.h, None, None, stream=0)  # nothing pending / null pointers
     assert pbf.pbf_mesh_info(m.h)["generation"] == 1
+
+
+def test_options_and_schedules_validate_arguments_without_a_gpu():
+    """Host-side checks of the option entry points and the checkpoint schedule (no context,
+    no device work)."""
+    for call in (lambda: pbf.pbf_ctx_set_surface_loss(None, I.SURFACE_LOSS),
+                 lambda: pbf.pbf_ctx_set_surface_loss(None, None),
+                 lambda: pbf.pbf_ctx_set_phase(None, I.PHASE),
+                 lambda: pbf.pbf_ctx_set_kernel_shape(None, 5),
+                 lambda: pbf.pbf_revolve_cost(0, 3),
+                 lambda: pbf.pbf_revolve_cost(10, 0)):
+        with pytest.raises(pbf.PbfError) as e:
+            call()
+        assert e.value.status == 1
+    # revolve: 2000 steps with 40 stored states cost 5097 forward steps (Griewank-Walther)
+    assert pbf.pbf_revolve_cost(2000, 40) == 5097
