@@ -53,16 +53,16 @@ BRIDGE = dict(rho=7430.0, c=965.0, k0=20.0, k1=20.0, Tk0=303.0, Tk1=303.0,
 
 T0 = 353.0
 
-# Radiation and evaporation on the free top surface (Eqs. bc_radiation, bc_evaporation) with
-# the constants of the paper's material table (Sec. 5.1): emissivity 0.7, boiling point
-# 3000 K, C_P = 54 kPa, C_T = 50,000 K, C_M = 0.001 K s^2/m^2, latent heat of evaporation
-# 6.0 MJ/kg, enthalpy reference 663 K, [T] capped at T_v + 1000 K; the ambient temperature and
-# the heat capacity of the enthalpy term follow the Ti-6Al-4V-like workloads (353 K, 526 J/kgK).
 # Phase-dependent conductivity with history (Eqs. liquid_fraction .. material_parameter_interp)
 # with the paper's material table (Sec. 5.1): solidus 1500 K, liquidus 1900 K, powder 0.2 W/mK,
 # melt and solid 20 W/mK.
 PHASE = dict(T_s=1500.0, T_l=1900.0, k_p=0.2, k_m=20.0, k_s=20.0)
 
+# Radiation and evaporation on the free top surface (Eqs. bc_radiation, bc_evaporation) with
+# the constants of the paper's material table (Sec. 5.1): emissivity 0.7, boiling point
+# 3000 K, C_P = 54 kPa, C_T = 50,000 K, C_M = 0.001 K s^2/m^2, latent heat of evaporation
+# 6.0 MJ/kg, enthalpy reference 663 K, [T] capped at T_v + 1000 K; the ambient temperature and
+# the heat capacity of the enthalpy term follow the Ti-6Al-4V-like workloads (353 K, 526 J/kgK).
 SURFACE_LOSS = dict(emissivity=0.7, T_amb=T0, C_P=54.0e3, C_T=5.0e4, C_M=1.0e-3, T_v=3000.0, h_v=6.0e6, c_h=526.0,
                     T_h0=663.0, T_max=4000.0)
 
@@ -155,6 +155,34 @@ def c4_laser(powers, v=0.8, n_seg=16, steps_per_seg=125, dt=None, y=0.25e-3):
         dur = steps_per_seg * dt
         segs = [(v * k * dur, y, v * (k + 1) * dur, y, k * dur, (k + 1) * dur) for k in range(n_seg)]
     return laser(segs, powers, eta=0.35, radius=40e-6)
+
+
+C5_TREE_H = (0.625e-3, 0.625e-3, 0.64e-3)
+C5_BASE_TOP = 3 * C5_TREE_H[2]        # baseplate: three tree layers, 1.92 mm
+C5_LAYER = 40e-6
+C5_RIBS_X = (1, 3, 6, 9, 12, 14)      # tree columns of the 12 support ribs (6 x 2 pillars)
+C5_RIBS_Y = (2, 5)
+
+
+def c5_mesh(layer=1, level=5, haz_layers=4, degree=2):
+    """Synthetic cantilever-like part on a baseplate (a stand-in for the part-scale build of
+    configuration 5): trees of 0.625 x 0.625 x 0.64 mm, 16 x 8 footprint (10 x 5 mm), three
+    tree layers of baseplate (1.92 mm) and two of build chamber; in the chamber only the 12
+    rib pillars (one tree each) exist. Layer `layer` of 40 um is active and is powder; the
+    layer and `haz_layers` layers below it (the heat-affected zone, 4 x 40 um as in the paper)
+    are refined to `level` (level 4: 39 x 39 x 40 um cells, one per layer; level 5: two), with
+    2:1 grading below. Dirichlet bottom."""
+    nt = (16, 8, 5)
+    exists = np.zeros(nt[::-1], np.uint8)
+    exists[:3] = 1
+    for x in C5_RIBS_X:
+        for y in C5_RIBS_Y:
+            exists[3:, y, x] = 1
+    top = C5_BASE_TOP + layer * C5_LAYER
+    lo = top - (1 + haz_layers) * C5_LAYER
+    region = (BOX, (0.0, 0.0, lo), (nt[0] * C5_TREE_H[0], nt[1] * C5_TREE_H[1], top), 1e-9, level)
+    return mesh_desc(nt, C5_TREE_H, degree, level, [region], active_top_z=top, tree_exists=exists,
+                     powder_z0=top - C5_LAYER, powder_z1=top)
 
 
 def c4_params(batch, n_seg=16, seed=2302):

@@ -53,9 +53,11 @@ def test_random_meshes_bit_exact(oracle_mod, seed, p):
     compare(ot, lt, KEYS + ("material",))
 
 
-@pytest.mark.parametrize("name", ["c1", "c2", "c4"])
+@pytest.mark.parametrize("name", ["c1", "c2", "c4", "c5"])
 def test_workload_meshes_bit_exact(oracle_mod, name):
-    d = {"c1": I.c1_mesh, "c2": I.c2_mesh, "c4": I.c4_mesh}[name]()
+    # c5: the part-scale stand-in's first layer at level 4 (213,120 cells, 1.72 M dofs; rib
+    # pillars as a tree mask, a powder layer, the heat-affected zone refined)
+    d = {"c1": I.c1_mesh, "c2": I.c2_mesh, "c4": I.c4_mesh, "c5": lambda: I.c5_mesh(level=4)}[name]()
     om, lm = oracle_mod.Mesh(d), pbf.Mesh(d)
     compare(om.tables(), lm.tables())
 
