@@ -235,8 +235,11 @@ pbf_status pbf_estimate_dt(pbf_ctx* ctx, const double* x0_dev, int max_iter, dou
  * return; y_dev [n_dofs] is overwritten (last K x). The partial sums of its reductions live
  * in a fixed static device array of 32,768 + 64 doubles (262,656 bytes) that every GPU
  * loading the library keeps until the process exits; meshes with more than 134,217,728 dofs
- * are rejected with PBF_EINVAL. The first call on a device looks up that array's device
- * address (once per device), so make the first call before any stream capture. All calls
+ * are rejected with PBF_EINVAL, and so are x_dev and y_dev when their ranges overlap. The
+ * one-time set-up on a device happens in pbf_ctx_create (which may allocate): it looks up the
+ * array's device address and runs the iteration once on temporary vectors, so that every
+ * kernel of this call is loaded (the CUDA runtime loads kernels lazily on first launch, and
+ * loading allocates device memory). Create the context before any stream capture. All calls
  * share the array and find the last call's contents in it; calls whose work overlaps on the
  * GPU race on it. No cudaMalloc, cudaFree or allocating library routine is called.
  * Synchronises. */

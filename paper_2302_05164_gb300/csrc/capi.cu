@@ -606,6 +606,12 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
       return fail(PBF_ECUDA, "capacity setup: %s", cudaGetErrorString(e));
     }
   }
+  // the allocation-free entry point's one-time set-up on this device
+  const pbf_status pst = noalloc_prepare(c.get());
+  if (pst != PBF_OK) {
+    c->release();
+    return pst;
+  }
   *out = c.release();
   return PBF_OK;
 }
@@ -694,6 +700,9 @@ extern "C" pbf_status pbf_ctx_set_k_scale(pbf_ctx* ctx, const double* s_host) {
   }
   cudaError_t e = cudaMemcpy(ctx->k_scale_d, s_host, (size_t)ctx->batch * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(ctx->k_scale_f, f.data(), (size_t)ctx->batch * 4, cudaMemcpyHostToDevice);
+  // the implicit operator's diagonal depends on s: rebuild it on the next solve (the CG graphs
+  // read s and the diagonal through their device pointers and stay valid)
+  ctx->diag_dt = -1.0;
   return ctx->cuda(e, "set_k_scale");
 }
 

@@ -8,6 +8,7 @@
 
 #include <cmath>
 #include <mutex>
+#include <vector>
 
 #include "pbf.h"
 #include "solver.hpp"
@@ -86,23 +87,14 @@ cudaError_t dot(int64_t n, const double* x, const double* y, const double* w, do
   return e;
 }
 
-}  // namespace
-
-extern "C" pbf_status pbf_estimate_dt_noalloc(pbf_ctx* ctx, double* x_dev, double* y_dev, int max_iter, double rtol,
-                                              double* lambda_out, double* dt_crit_out, int* iters_out,
-                                              pbf_stream stream) {
-  if (!ctx || !x_dev || !y_dev) return set_error(PBF_EINVAL, "null argument");
-  if (max_iter < 1) return set_error(PBF_EINVAL, "max_iter must be positive");
-  pbf_status st = ctx->check_usable();
-  if (st) return st;
+// The power iteration on the caller's vectors x and y with the static scratch (no
+// allocation): the body of pbf_estimate_dt_noalloc, also run once by noalloc_prepare.
+pbf_status run_noalloc(pbf_ctx* ctx, double* x_dev, double* y_dev, int max_iter, double rtol, double* lambda_out,
+                       double* dt_crit_out, int* iters_out, cudaStream_t s) {
   const int64_t n = ctx->n_dofs;
-  if ((n + kChunk - 1) / kChunk > kMaxPartials)
-    return set_error(PBF_EINVAL, "pbf_estimate_dt_noalloc handles at most 134,217,728 dofs "
-                                 "(its fixed reduction scratch holds 32,768 partial sums)");
   double* scratch = nullptr;
   cudaError_t e = scratch_address(&scratch);
   if (e != cudaSuccess) return ctx->cuda(e, "estimate_dt_noalloc scratch set-up");
-  cudaStream_t s = (cudaStream_t)stream;
   CellLaunch L = ctx->base;
   L.f32 = 0;
   L.nonlin_k = 0;
@@ -142,4 +134,56 @@ extern "C" pbf_status pbf_estimate_dt_noalloc(pbf_ctx* ctx, double* x_dev, doubl
   if (dt_crit_out) *dt_crit_out = lambda > 0 ? 2.0 / lambda : INFINITY;
   if (iters_out) *iters_out = it;
   return PBF_OK;
+}
+
+}  // namespace
+
+namespace pbf {
+
+// Set-up of the allocation-free entry point for the current device, run by pbf_ctx_create
+// (which may allocate): looks up the static array's device address and runs one iteration
+// of the power iteration on temporary vectors, so that every kernel the entry point launches
+// is loaded. The CUDA runtime loads kernels lazily, on their first launch, and loading one
+// allocates device memory; after this set-up a call of the entry point allocates nothing.
+pbf_status noalloc_prepare(CtxBase* base) {
+  pbf_ctx* ctx = static_cast<pbf_ctx*>(base);
+  const int64_t n = ctx->n_dofs;
+  if (n == 0 || (n + kChunk - 1) / kChunk > kMaxPartials) return PBF_OK;  // the entry point rejects these
+  double *x = nullptr, *y = nullptr;
+  cudaError_t e = cudaMalloc(&x, (size_t)n * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&y, (size_t)n * 8);
+  pbf_status st = PBF_OK;
+  if (e == cudaSuccess) {
+    std::vector<double> one((size_t)n, 1.0);
+    e = cudaMemcpy(x, one.data(), (size_t)n * 8, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) {
+    st = run_noalloc(ctx, x, y, 1, 0.0, nullptr, nullptr, nullptr, 0);
+    if (st == PBF_EINVAL) st = PBF_OK;  // every dof is a Dirichlet dof: the kernels loaded all the same
+  }
+  if (x) cudaFree(x);
+  if (y) cudaFree(y);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(e == cudaErrorMemoryAllocation ? PBF_ENOMEM : PBF_ECUDA, cudaGetErrorString(e));
+  }
+  return st;
+}
+
+}  // namespace pbf
+
+extern "C" pbf_status pbf_estimate_dt_noalloc(pbf_ctx* ctx, double* x_dev, double* y_dev, int max_iter, double rtol,
+                                              double* lambda_out, double* dt_crit_out, int* iters_out,
+                                              pbf_stream stream) {
+  if (!ctx || !x_dev || !y_dev) return set_error(PBF_EINVAL, "null argument");
+  if (max_iter < 1) return set_error(PBF_EINVAL, "max_iter must be positive");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  const int64_t n = ctx->n_dofs;
+  if ((n + kChunk - 1) / kChunk > kMaxPartials)
+    return set_error(PBF_EINVAL, "pbf_estimate_dt_noalloc handles at most 134,217,728 dofs "
+                                 "(its fixed reduction scratch holds 32,768 partial sums)");
+  const uintptr_t xa = (uintptr_t)x_dev, ya = (uintptr_t)y_dev, nb = (uintptr_t)n * 8;
+  if (xa < ya + nb && ya < xa + nb) return set_error(PBF_EINVAL, "x_dev and y_dev overlap");
+  return run_noalloc(ctx, x_dev, y_dev, max_iter, rtol, lambda_out, dt_crit_out, iters_out, (cudaStream_t)stream);
 }

@@ -151,7 +151,7 @@ struct Implicit {
 
   // the key of the implicit solve's graphs: dt, bounds, degree and every buffer they touch
   void graph_key(double* key, int deg, double lmin, double lmax, const double* const* vecs, int nv) {
-    for (int i = 0; i < 16; ++i) key[i] = 0.0;
+    for (int i = 0; i < CtxBase::kGraphKey; ++i) key[i] = 0.0;
     key[0] = dt;
     key[1] = lmin;
     key[2] = lmax;
@@ -161,12 +161,13 @@ struct Implicit {
     key[6] = (double)(uintptr_t)c->f;
     key[7] = (double)(uintptr_t)c->scal;
     for (int i = 0; i < nv && 8 + i < 16; ++i) key[8 + i] = (double)(uintptr_t)vecs[i];
+    key[16] = (double)c->base.variant;  // the launch shape of the captured cell kernels
   }
 
   // z = p(D^-1 A) D^-1 r as one graph launch
   void precondition(const double* r, double* z, int deg, double lmin, double lmax, double* res, double* d,
                     double* Ad) {
-    double key[16];
+    double key[CtxBase::kGraphKey];
     const double* v[] = {r, z, res, d, Ad};
     graph_key(key, deg, lmin, lmax, v, 5);
     replay(c->cheb_graph, key, [&] { chebyshev(r, z, deg, lmin, lmax, res, d, Ad); });
@@ -359,7 +360,7 @@ extern "C" pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt,
         if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(rz, rz_new, sizeof(double), cudaMemcpyDeviceToDevice, I.s);
         ctx->launches += 3;
       };
-      double key[16];
+      double key[CtxBase::kGraphKey];
       const double* kv[] = {r, z, p, Ap, x, res, d, Ad};
       I.graph_key(key, cheb_degree, bounds[0], bounds[1], kv, 8);
       bool first = true;

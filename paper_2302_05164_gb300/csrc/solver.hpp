@@ -16,6 +16,11 @@ namespace pbf {
 
 pbf_status set_error(pbf_status s, const char* msg);
 
+struct CtxBase;
+// Set-up of pbf_estimate_dt_noalloc on the current device (noalloc.cu), run by
+// pbf_ctx_create: after it the entry point allocates nothing.
+pbf_status noalloc_prepare(CtxBase* ctx);
+
 struct CtxBase {
   const HostMesh* mesh = nullptr;
   int64_t generation = 0;
@@ -89,10 +94,11 @@ struct CtxBase {
   double diag_dt = -1.0;
   // launch sequences of the implicit solve replayed as CUDA graphs (the Chebyshev
   // preconditioner; one whole CG iteration): captured on a private stream, launched on the
-  // caller's, rebuilt when their key (dt, bounds, degree, vectors) changes
+  // caller's, rebuilt when their key (dt, bounds, degree, vectors, launch shape) changes
+  static constexpr int kGraphKey = 17;
   struct GraphSlot {
     cudaGraphExec_t exec = nullptr;
-    double key[16] = {};
+    double key[kGraphKey] = {};
     long long launches = 0;
   };
   cudaStream_t cap_stream = nullptr;

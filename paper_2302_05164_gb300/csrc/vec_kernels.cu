@@ -391,7 +391,10 @@ __global__ void k_reciprocal(int64_t n, const double* __restrict__ c, double* __
 // sum_i w_i x_i y_i per instance (w may be null; a mask m zeroes dofs with m != 0). Each
 // block reduces a fixed slice in a fixed order; the second pass adds the block partials in
 // order, so the result does not depend on scheduling.
-constexpr int kRedBlocks = 304;  // 2 x 152 SMs
+// The block count is a constant, not derived from the device, so that the order of the
+// additions, and with it every dot product, is the same on any GPU (two blocks per SM of a
+// 152-SM GB300).
+constexpr int kRedBlocks = 304;
 
 __global__ void k_dot_partial(int64_t n_dofs, int B, const double* __restrict__ x, const double* __restrict__ y,
                               const double* __restrict__ w, const uint8_t* __restrict__ skip,
