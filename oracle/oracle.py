@@ -244,6 +244,15 @@ class Mesh:
                              C.c_double(p_exp), _ptr(grad))
         return J, grad
 
+    def step_transpose(self, mat, T, ls, t, dt, w, s=1.0, instance=0):
+        """(dT_{n+1}/dT_n)^T w for one explicit step at state T and time t (Dirichlet rows zero)."""
+        T, w = _f64(T), _f64(w)
+        out = np.zeros(self.n_dofs)
+        lh = _LaserHolder(ls, instance) if ls is not None else None
+        lib().or_step_transpose(C.c_void_p(self.h), C.byref(material(mat)), C.c_double(s), _ptr(T),
+                                lh.ref if lh else None, C.c_double(t), C.c_double(dt), _ptr(w), _ptr(out))
+        return out
+
     def objective(self, mat, T0, ls, t0, dt, nsteps, T_target=2300.0, p_exp=16.0, s=1.0, instance=0):
         lh = _LaserHolder(ls, instance)
         T0 = _f64(T0)

@@ -980,6 +980,81 @@ void euler_step(const Mesh& m, const or_material& mt, double s, double* T, const
   }
 }
 
+
+// Row-sum lumped mass times rho c with the plain c (the nodal apparent capacity scales it by
+// c_app(T_i)/c); empty unless the material uses the nodal capacity with latent heat.
+void plain_capacity(const Mesh& M, const or_material& mt, double s, const double* T, std::vector<double>& plainC) {
+  plainC.clear();
+  if (!(mt.lumping == 1 && mt.sigma > 0.0)) return;
+  or_material plain = mt;
+  plain.sigma = 0.0;
+  plain.lumping = 0;
+  Fields G;
+  residual(M, plain, s, T, nullptr, 0.0, G, true);
+  plainC = G.C;
+}
+
+// g = (du/dT (T))^T lam for u = C~(T)^-1 f(T) on free dofs, u = 0 on Dirichlet dofs: the
+// transposed linearisation of Eq. (matrix_free_eval), with the conductivity term, the k'(T)
+// term L_e and the derivative of the lumped capacity (through c_app'(T) at the quadrature
+// points, or at the node for the nodal capacity). F holds f and C~ at T, plainC comes from
+// plain_capacity.
+void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, const double* T, const Fields& F,
+                             const std::vector<double>& plainC, const std::vector<double>& lam, std::vector<double>& g) {
+  const size_t n = (size_t)M.n_dofs;
+  const int p = M.p, npc = M.npc(), nq = p + 1;
+  double gx[3], gw[3];
+  gauss(nq, gx, gw);
+  const bool nodal = mt.lumping == 1 && mt.sigma > 0.0;
+  std::vector<double> Te(npc), ve(npc), me(npc), ge(npc), N(npc);
+  std::vector<double> dN((size_t)npc * 3);
+  // v = lambda/C~, mu = lambda f / C~^2 on free dofs
+  std::vector<double> v(n, 0.0), mu(n, 0.0);
+  g.assign(n, 0.0);
+  for (size_t i = 0; i < n; ++i) {
+    if (M.dirichlet[i]) continue;
+    v[i] = lam[i] / F.C[i];
+    mu[i] = lam[i] * (F.fdiff[i] + F.fvol[i]) / (F.C[i] * F.C[i]);
+  }
+  // g_j = sum_i v_i df_i/dT_j - sum_i mu_i dC~_i/dT_j
+  for (int c = 0; c < (int)M.acell.size(); ++c) {
+    CellGeo geo = cell_geo(M, c);
+    int mat = M.material[(size_t)M.acell[(size_t)c]];
+    double detJ = geo.h[0] * geo.h[1] * geo.h[2];
+    gather(M, c, T, Te.data());
+    gather(M, c, v.data(), ve.data());
+    gather(M, c, mu.data(), me.data());
+    std::fill(ge.begin(), ge.end(), 0.0);
+    for (int qz = 0; qz < nq; ++qz)
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          double xi[3] = {gx[qx], gx[qy], gx[qz]};
+          double W = gw[qx] * gw[qy] * gw[qz] * detJ;
+          basis(p, xi, N.data(), dN.data());
+          double Tq = 0, muq = 0, gT[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+          for (int a = 0; a < npc; ++a) {
+            Tq += N[a] * Te[a];
+            muq += N[a] * me[a];
+            for (int d = 0; d < 3; ++d) {
+              gT[d] += dN[3 * a + d] / geo.h[d] * Te[a];
+              gv[d] += dN[3 * a + d] / geo.h[d] * ve[a];
+            }
+          }
+          double kq = cond(mt, Tq, mat, s), dk = cond_deriv(mt, Tq, mat, s);
+          double gvgT = gv[0] * gT[0] + gv[1] * gT[1] + gv[2] * gT[2];
+          double cap_term = nodal ? 0.0 : mt.rho * capp_deriv(mt, Tq) * muq;
+          for (int j = 0; j < npc; ++j) {
+            double gjv = 0.0;
+            for (int d = 0; d < 3; ++d) gjv += dN[3 * j + d] / geo.h[d] * gv[d];
+            ge[j] += W * (-kq * gjv - dk * gvgT * N[j] - cap_term * N[j]);
+          }
+        }
+    scatter(M, c, ge.data(), g.data());
+  }
+  // nodal lumping: dC~_i/dT_j = delta_ij rho M_i c_app'(T_i), M the lumped mass
+  if (nodal)
+    for (size_t i = 0; i < n; ++i) g[i] -= mu[i] * plainC[i] / mt.c * capp_deriv(mt, T[i]);
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -1266,21 +1341,9 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
     double Mn = pnorm_max(obj, states[(size_t)nsteps].data(), &gM);
     for (size_t i = 0; i < n; ++i) lam[i] = 2.0 * (Mn - T_target) / nsteps * gM[i];
   }
-  const int p = M.p, npc = M.npc(), nq = p + 1;
-  double gx[3], gw[3];
-  gauss(nq, gx, gw);
-  const bool nodal = mt->lumping == 1 && mt->sigma > 0.0;
   std::vector<double> plainC;
-  if (nodal) {
-    or_material plain = *mt;
-    plain.sigma = 0.0;
-    plain.lumping = 0;
-    Fields G;
-    residual(M, plain, s, T0, nullptr, 0.0, G, true);
-    plainC = G.C;
-  }
-  std::vector<double> Te(npc), ve(npc), me(npc), ge(npc), N(npc);
-  std::vector<double> dN((size_t)npc * 3);
+  plain_capacity(M, *mt, s, T0, plainC);
+  std::vector<double> g;
   for (int k = nsteps - 1; k >= 0; --k) {
     const double* T = states[(size_t)k].data();
     double t = t0 + k * dt;
@@ -1295,51 +1358,7 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
     }
     grad[nseg] += gs;
     if (seg >= 0) grad[seg] += gp;
-    // v = lambda/C~, mu = lambda f / C~^2 on free dofs
-    std::vector<double> v(n, 0.0), mu(n, 0.0), g(n, 0.0);
-    for (size_t i = 0; i < n; ++i) {
-      if (M.dirichlet[i]) continue;
-      v[i] = lam[i] / F.C[i];
-      mu[i] = lam[i] * (F.fdiff[i] + F.fvol[i]) / (F.C[i] * F.C[i]);
-    }
-    // g_j = sum_i v_i df_i/dT_j - sum_i mu_i dC~_i/dT_j
-    for (int c = 0; c < (int)M.acell.size(); ++c) {
-      CellGeo geo = cell_geo(M, c);
-      int mat = M.material[(size_t)M.acell[(size_t)c]];
-      double detJ = geo.h[0] * geo.h[1] * geo.h[2];
-      gather(M, c, T, Te.data());
-      gather(M, c, v.data(), ve.data());
-      gather(M, c, mu.data(), me.data());
-      std::fill(ge.begin(), ge.end(), 0.0);
-      for (int qz = 0; qz < nq; ++qz)
-        for (int qy = 0; qy < nq; ++qy)
-          for (int qx = 0; qx < nq; ++qx) {
-            double xi[3] = {gx[qx], gx[qy], gx[qz]};
-            double W = gw[qx] * gw[qy] * gw[qz] * detJ;
-            basis(p, xi, N.data(), dN.data());
-            double Tq = 0, muq = 0, gT[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
-            for (int a = 0; a < npc; ++a) {
-              Tq += N[a] * Te[a];
-              muq += N[a] * me[a];
-              for (int d = 0; d < 3; ++d) {
-                gT[d] += dN[3 * a + d] / geo.h[d] * Te[a];
-                gv[d] += dN[3 * a + d] / geo.h[d] * ve[a];
-              }
-            }
-            double kq = cond(*mt, Tq, mat, s), dk = cond_deriv(*mt, Tq, mat, s);
-            double gvgT = gv[0] * gT[0] + gv[1] * gT[1] + gv[2] * gT[2];
-            double cap_term = nodal ? 0.0 : mt->rho * capp_deriv(*mt, Tq) * muq;
-            for (int j = 0; j < npc; ++j) {
-              double gjv = 0.0;
-              for (int d = 0; d < 3; ++d) gjv += dN[3 * j + d] / geo.h[d] * gv[d];
-              ge[j] += W * (-kq * gjv - dk * gvgT * N[j] - cap_term * N[j]);
-            }
-          }
-      scatter(M, c, ge.data(), g.data());
-    }
-    // nodal lumping: dC~_i/dT_j = delta_ij rho M_i c_app'(T_i), M the lumped mass
-    if (nodal)
-      for (size_t i = 0; i < n; ++i) g[i] -= mu[i] * plainC[i] / mt->c * capp_deriv(*mt, T[i]);
+    step_jacobian_transpose(M, *mt, s, T, F, plainC, lam, g);
     std::vector<double> lam_new(n, 0.0);
     if (k > 0) {
       double Mn = pnorm_max(obj, T, &gM);
@@ -1353,6 +1372,25 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
     lam.swap(lam_new);
   }
   return J;
+}
+
+// One transposed step of the explicit stepper: out = dT_{n+1}/dT_n (T)^T w for
+// T_{n+1} = T_n + dt u(T_n) on free dofs and T_{n+1} = T_D on Dirichlet dofs, i.e.
+// out = w_free + dt (du/dT)^T w_free (zero on Dirichlet dofs); the recursion step of the
+// adjoint sweep without the objective term (for the dot-product test against a forward
+// linearisation).
+void or_step_transpose(void* h, const or_material* mt, double s, const double* T, const or_laser* ls, double t,
+                       double dt, const double* w, double* out) {
+  Mesh* m = (Mesh*)h;
+  const Mesh& M = *m;
+  const size_t n = (size_t)M.n_dofs;
+  Fields F;
+  residual(M, *mt, s, T, ls, t, F);
+  std::vector<double> plainC, g, lam(n, 0.0);
+  plain_capacity(M, *mt, s, T, plainC);
+  for (size_t i = 0; i < n; ++i) lam[i] = M.dirichlet[i] ? 0.0 : w[i];
+  step_jacobian_transpose(M, *mt, s, T, F, plainC, lam, g);
+  for (size_t i = 0; i < n; ++i) out[i] = M.dirichlet[i] ? 0.0 : lam[i] + dt * g[i];
 }
 
 // Objective alone, for finite-difference checks.
