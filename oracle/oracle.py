@@ -78,6 +78,7 @@ def lib():
         L.or_cond.restype = C.c_double
         L.or_surface_flux.restype = C.c_double
         L.or_implicit.restype = C.c_int
+        L.or_implicit_newton.restype = C.c_int
     return _lib
 
 
@@ -234,6 +235,32 @@ class Mesh:
                                C.c_int(nsteps), C.c_double(rtol), C.c_int(max_it), C.c_int(degree),
                                C.c_double(lmin), C.c_double(lmax), _ptr(iters))
         return T, iters, st
+
+    def newton_residual(self, mat, T, Tn, dt):
+        """r(T) = C (T - T_n)/dt - f_diff(T) on free dofs, 0 on Dirichlet dofs."""
+        T, Tn = _f64(T), _f64(Tn)
+        r = np.zeros(self.n_dofs)
+        lib().or_newton_residual(C.c_void_p(self.h), C.byref(material(mat)), _ptr(T), _ptr(Tn), C.c_double(dt),
+                                 _ptr(r))
+        return r
+
+    def newton_jacobian(self, mat, T, dt, v):
+        """J(T) v of the nonlinear backward-Euler residual (identity rows on Dirichlet dofs)."""
+        T, v = _f64(T), _f64(v)
+        y = np.zeros(self.n_dofs)
+        lib().or_newton_jacobian(C.c_void_p(self.h), C.byref(material(mat)), _ptr(T), C.c_double(dt), _ptr(v),
+                                 _ptr(y))
+        return y
+
+    def implicit_newton(self, mat, T, dt, nsteps, newton_rtol, newton_max, lin_rtol, lin_max, degree, lmin, lmax):
+        T = _f64(T).copy()
+        nit = np.zeros(nsteps, np.int32)
+        lit = np.zeros(nsteps, np.int32)
+        st = lib().or_implicit_newton(C.c_void_p(self.h), C.byref(material(mat)), _ptr(T), C.c_double(dt),
+                                      C.c_int(nsteps), C.c_double(newton_rtol), C.c_int(newton_max),
+                                      C.c_double(lin_rtol), C.c_int(lin_max), C.c_int(degree), C.c_double(lmin),
+                                      C.c_double(lmax), _ptr(nit), _ptr(lit))
+        return T, nit, lit, st
 
     def adjoint(self, mat, T0, ls, t0, dt, nsteps, T_target=2300.0, p_exp=16.0, s=1.0, instance=0):
         lh = _LaserHolder(ls, instance)

@@ -16,7 +16,8 @@
 //   semi-discrete system C dT/dt = f_diff + f_RE + f_vol, Eq. (semi-discrete)
 //   forward Euler with row-sum lumped capacity, Eq. (forward_euler), Sec. 3.2
 //   critical time step 2 / rho(C~^-1 K_diff), Eq. (explicit_time_step)
-//   backward Euler, Eq. (backward_euler_nonlinear), linear case, Sec. 3.2
+//   backward Euler, Eq. (backward_euler_nonlinear), Sec. 3.2: the linear case by CG, the
+//   nonlinear case by Newton-Raphson, Eqs. (Newton_1), (Newton_2), with BiCGStab
 //   octree mesh with 2:1 balance, inactive cells above the active layer, Sec. 4.1
 //   Z-curve (Morton) cell order, Sec. 4.1
 //   diffusive term per cell, Eqs. (diffusive_term_evaluation), (vector_evaluation), Sec. 4.2
@@ -1055,6 +1056,111 @@ void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, con
   if (nodal)
     for (size_t i = 0; i < n; ++i) g[i] -= mu[i] * plainC[i] / mt.c * capp_deriv(mt, T[i]);
 }
+
+// Nonlinear backward Euler (Sec. 3.2, Eq. backward_euler_nonlinear) without surface terms or
+// source: r(T) = C (T - T_n)/dt - f_diff(T) on free dofs, r = 0 on Dirichlet dofs (they hold
+// T_D). C is the consistent capacity with the plain c (reading: Eq. Newton_1 differentiates
+// only f_diff, so C does not depend on T).
+void newton_residual(const Mesh& m, const or_material& mt, const double* T, const double* Tn, double dt, double* r) {
+  const size_t n = (size_t)m.n_dofs;
+  std::vector<double> d(n), Cd(n);
+  for (size_t i = 0; i < n; ++i) d[i] = T[i] - Tn[i];
+  apply_mass(m, mt, d.data(), Cd.data());
+  Fields F;
+  residual(m, mt, 1.0, T, nullptr, 0.0, F, false);
+  for (size_t i = 0; i < n; ++i) r[i] = m.dirichlet[i] ? 0.0 : Cd[i] / dt - F.fdiff[i];
+}
+
+// Jacobian of the residual at T applied to v (Eq. Newton_1, the linearisation of
+// Eq. matrix_free_eval): J v = C v/dt + int k(T) grad N_i . grad v + int k'(T) v grad N_i . grad T
+// (the L_e term) on free rows; v is taken as zero on Dirichlet dofs and those rows are the
+// identity (increments vanish there).
+void newton_jacobian(const Mesh& m, const or_material& mt, const double* T, double dt, const double* v_in,
+                     double* y) {
+  const size_t n = (size_t)m.n_dofs;
+  const int p = m.p, npc = m.npc(), nq = p + 1;
+  double gx[3], gw[3];
+  gauss(nq, gx, gw);
+  std::vector<double> v(v_in, v_in + n);
+  for (size_t i = 0; i < n; ++i)
+    if (m.dirichlet[i]) v[i] = 0.0;
+  std::fill(y, y + n, 0.0);
+  std::vector<double> Te(npc), ve(npc), ye(npc), N(npc);
+  std::vector<double> dN((size_t)npc * 3);
+  for (int c = 0; c < (int)m.acell.size(); ++c) {
+    CellGeo geo = cell_geo(m, c);
+    int mat = m.material[(size_t)m.acell[(size_t)c]];
+    double detJ = geo.h[0] * geo.h[1] * geo.h[2];
+    gather(m, c, T, Te.data());
+    gather(m, c, v.data(), ve.data());
+    std::fill(ye.begin(), ye.end(), 0.0);
+    for (int qz = 0; qz < nq; ++qz)
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          double xi[3] = {gx[qx], gx[qy], gx[qz]};
+          double W = gw[qx] * gw[qy] * gw[qz] * detJ;
+          basis(p, xi, N.data(), dN.data());
+          double Tq = 0, vq = 0, gT[3] = {0, 0, 0}, gv[3] = {0, 0, 0};
+          for (int a = 0; a < npc; ++a) {
+            Tq += N[a] * Te[a];
+            vq += N[a] * ve[a];
+            for (int d = 0; d < 3; ++d) {
+              gT[d] += dN[3 * a + d] / geo.h[d] * Te[a];
+              gv[d] += dN[3 * a + d] / geo.h[d] * ve[a];
+            }
+          }
+          double kq = cond(mt, Tq, mat, 1.0), dk = cond_deriv(mt, Tq, mat, 1.0);
+          for (int j = 0; j < npc; ++j) {
+            double flux = 0.0;
+            for (int d = 0; d < 3; ++d) flux += dN[3 * j + d] / geo.h[d] * (kq * gv[d] + dk * vq * gT[d]);
+            ye[j] += W * (mt.rho * mt.c / dt * vq * N[j] + flux);
+          }
+        }
+    scatter(m, c, ye.data(), y);
+  }
+  for (size_t i = 0; i < n; ++i)
+    if (m.dirichlet[i]) y[i] = v_in[i];
+}
+
+// BiCGStab (van der Vorst 1992, preconditioned form) for J x = b from x = 0 with the
+// preconditioner z = p(D^-1 A) D^-1 r of the linear operator A = C/dt + K(k0) (the
+// Chebyshev-Jacobi polynomial of the linear solver); stops when ||r||_2 <= rtol ||b||_2 or
+// after max_it iterations. Returns the iterations used.
+int bicgstab(const Mesh& m, const or_material& mt, const double* T, double dt, const std::vector<double>& diag,
+             int degree, double lmin, double lmax, const std::vector<double>& b, std::vector<double>& x,
+             double rtol, int max_it) {
+  const size_t n = (size_t)m.n_dofs;
+  x.assign(n, 0.0);
+  std::vector<double> r = b, rh = b, p(n, 0.0), v(n, 0.0), s(n), t(n), y, z;
+  const double bn = std::sqrt(dot(b, b));
+  if (bn == 0.0) return 0;
+  double rho = 1.0, alpha = 1.0, omega = 1.0;
+  int it = 0;
+  while (it < max_it) {
+    ++it;
+    const double rho_new = dot(rh, r);
+    const double beta = (rho_new / rho) * (alpha / omega);
+    for (size_t i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - omega * v[i]);
+    chebyshev(m, mt, dt, diag, degree, lmin, lmax, p, y);
+    newton_jacobian(m, mt, T, dt, y.data(), v.data());
+    alpha = rho_new / dot(rh, v);
+    for (size_t i = 0; i < n; ++i) {
+      s[i] = r[i] - alpha * v[i];
+      x[i] += alpha * y[i];
+    }
+    if (std::sqrt(dot(s, s)) <= rtol * bn) break;
+    chebyshev(m, mt, dt, diag, degree, lmin, lmax, s, z);
+    newton_jacobian(m, mt, T, dt, z.data(), t.data());
+    omega = dot(t, s) / dot(t, t);
+    for (size_t i = 0; i < n; ++i) {
+      x[i] += omega * z[i];
+      r[i] = s[i] - omega * t[i];
+    }
+    rho = rho_new;
+    if (std::sqrt(dot(r, r)) <= rtol * bn) break;
+  }
+  return it;
+}
 }  // namespace
 
 // ---------------------------------------------------------------------------------------
@@ -1297,6 +1403,51 @@ int or_implicit(void* h, const or_material* mt, double* T, double dt, int nsteps
     if (rn > rtol * r0) status = 1;
     if (iters_out) iters_out[step] = it;
     for (size_t i = 0; i < n; ++i) T[i] += x[i];
+  }
+  return status;
+}
+
+void or_newton_residual(void* h, const or_material* mt, const double* T, const double* Tn, double dt, double* r) {
+  newton_residual(*(Mesh*)h, *mt, T, Tn, dt, r);
+}
+
+void or_newton_jacobian(void* h, const or_material* mt, const double* T, double dt, const double* v, double* y) {
+  newton_jacobian(*(Mesh*)h, *mt, T, dt, v, y);
+}
+
+// Nonlinear backward Euler steps (Eq. backward_euler_nonlinear) by Newton-Raphson (Eqs. Newton_1,
+// Newton_2): from T^0 = T_n, solve J(T^i) dT = -r(T^i) by BiCGStab with the Chebyshev-Jacobi
+// preconditioner of the linear operator to lin_rtol, T^{i+1} = T^i + dT, until
+// ||r(T^i)||_2 <= newton_rtol ||r(T^0)||_2 or newton_max corrections. Dirichlet dofs hold T_D.
+// newton_iters[nsteps] (corrections) and lin_iters[nsteps] (BiCGStab iterations summed over
+// the step), both nullable. Returns 0, or 1 when a step missed newton_rtol.
+int or_implicit_newton(void* h, const or_material* mt, double* T, double dt, int nsteps, double newton_rtol,
+                       int newton_max, double lin_rtol, int lin_max, int degree, double lmin, double lmax,
+                       int* newton_iters, int* lin_iters) {
+  Mesh* m = (Mesh*)h;
+  const size_t n = (size_t)m->n_dofs;
+  std::vector<double> diag(n), Tn(n), r(n), b(n), dT;
+  implicit_diagonal(*m, *mt, dt, diag.data());
+  int status = 0;
+  for (int step = 0; step < nsteps; ++step) {
+    std::copy(T, T + n, Tn.begin());
+    for (size_t i = 0; i < n; ++i)
+      if (m->dirichlet[i]) T[i] = mt->T_dirichlet;
+    newton_residual(*m, *mt, T, Tn.data(), dt, r.data());
+    const double r0 = std::sqrt(dot(r, r));
+    double rn = r0;
+    int it = 0, lin = 0;
+    while (rn > newton_rtol * r0 && it < newton_max) {
+      for (size_t i = 0; i < n; ++i) b[i] = -r[i];
+      lin += bicgstab(*m, *mt, T, dt, diag, degree, lmin, lmax, b, dT, lin_rtol, lin_max);
+      for (size_t i = 0; i < n; ++i) T[i] += dT[i];
+      ++it;
+      newton_residual(*m, *mt, T, Tn.data(), dt, r.data());
+      rn = std::sqrt(dot(r, r));
+    }
+    if (rn > newton_rtol * r0) status = 1;
+    if (newton_iters) newton_iters[step] = it;
+    if (lin_iters) lin_iters[step] = lin;
   }
   return status;
 }
