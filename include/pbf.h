@@ -253,15 +253,39 @@ pbf_status pbf_estimate_dt_noalloc(pbf_ctx* ctx, double* x_dev, double* y_dev, i
 pbf_status pbf_cheb_bounds(pbf_ctx* ctx, double dt, const double* b_dev, int n_iter, double* out,
                            pbf_stream stream);
 
-/* nsteps backward-Euler steps of the linear problem (Eq. backward_euler_nonlinear with
- * constant k and c, no surface terms, no laser): (C/dt + K) dT = f(T_n), T_{n+1} = T_n + dT,
- * by CG with a Chebyshev(cheb_degree)-Jacobi preconditioner on bounds {lmin, lmax}
- * (NULL: pbf_cheb_bounds with 30 steps, lmax x 1.1), FP64 dot products, stop at
- * ||r||_2 <= rtol ||r_0||_2. Instance 0 only (batch must be 1). iters_out (host, nullable)
- * [nsteps]. Synchronises once per CG iteration. PBF_ENOCONV when a step missed rtol within
- * max_it (T holds the last iterate). */
+/* nsteps backward-Euler steps (Eq. backward_euler_nonlinear, no surface terms, no laser; the
+ * capacity is the consistent one with the plain c, the latent heat's apparent capacity is
+ * not part of it). Constant k: (C/dt + K) dT = f(T_n), T_{n+1} = T_n + dT, by CG with a
+ * Chebyshev(cheb_degree)-Jacobi preconditioner on bounds {lmin, lmax} (NULL: pbf_cheb_bounds
+ * with 30 steps, lmax x 1.1), FP64 dot products, stop at ||r||_2 <= rtol ||r_0||_2 on the CG
+ * recurrence; iters_out (host, nullable) [nsteps] CG iterations. A T-dependent k: Newton's
+ * method, pbf_implicit_newton with newton_rtol = rtol, 50 corrections, lin_rtol = 1e-4 and
+ * lin_max = max_it, iters_out the BiCGStab iterations of each step. Instance 0 only (batch
+ * must be 1). Synchronises once per CG iteration. PBF_ENOCONV when a step missed rtol (T holds
+ * the last iterate). */
 pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt, int nsteps, double rtol, int max_it,
                               int cheb_degree, const double* cheb_bounds, int* iters_out, pbf_stream stream);
+
+/* Nonlinear backward Euler (Sec. 3.2, Eq. backward_euler_nonlinear, no surface terms, no
+ * laser) by Newton-Raphson (Eqs. Newton_1, Newton_2): residual
+ *   r(T) = C (T - T_n)/dt - f_diff(T)  on free dofs (T = T_D on Dirichlet dofs),
+ * C the consistent capacity with the plain c; Jacobian J(T) w = C w/dt + int k(T) grad N .
+ * grad w + int k'(T) w grad N . grad T (the L_e term of Eq. matrix_free_eval). From
+ * T^0 = T_n each correction solves J(T^i) dT = -r(T^i) by BiCGStab to lin_rtol (relative to
+ * ||r(T^i)||_2, at most lin_max iterations) with the Chebyshev(cheb_degree)-Jacobi
+ * preconditioner of the linear operator C/dt + K(k0) on bounds {lmin, lmax} (NULL: estimated
+ * as in pbf_implicit_solve), until ||r(T^i)||_2 <= newton_rtol ||r(T^0)||_2 or newton_max
+ * corrections. The residual is evaluated in FP64 and the Jacobian in the context's operator
+ * precision: for an FP32-operator context this is FP64 iterative refinement of FP32-operator
+ * solves, and it reaches the FP64 solution (also for a constant k). newton_iters_out and
+ * lin_iters_out (host, nullable) [nsteps]: corrections and BiCGStab iterations per step;
+ * rel_residual_out (nullable): the largest ||r||_2 / ||r_0||_2 reached over the steps.
+ * Instance 0 only (batch 1). Synchronises twice per BiCGStab iteration. PBF_ENOCONV when a step
+ * missed newton_rtol (T holds the last iterate). */
+pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt, int nsteps, double newton_rtol,
+                               int newton_max, double lin_rtol, int lin_max, int cheb_degree,
+                               const double* cheb_bounds, int* newton_iters_out, int* lin_iters_out,
+                               double* rel_residual_out, pbf_stream stream);
 
 /* Adjoint sweep of the explicit stepper for every instance (objective reading of the
  * configuration: J = (1/N) sum_{n=1..N} (M_n - T_target)^2, M_n = (sum_i w_i T_{n,i}^p /
@@ -289,20 +313,50 @@ pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_ou
  * fused step for all steps of a call in one persistent cooperative launch, with a grid
  * barrier between steps whose waits end after one second with PBF_ETIMEOUT (state undefined,
  * context still usable; when the resident blocks cover every patch, each keeps its patch
- * tables in shared memory for the whole call); shape 6 synchronises the stream. Where 4-6 do
- * not apply (batch > 1, quadrature-point capacity) they run the per-cell form; with a
- * volumetric source shape 6 runs shape 5; residual-only evaluations of shapes 4-6 use
- * shape 1.
+ * tables in shared memory for the whole call); shape 6 synchronises the stream; 7, 8, 9: the
+ * fused step of shape 5 in its lean form (patch tables read through L1, only the staged values
+ * and their sums in shared memory, the conductivity recomputed in each gradient direction),
+ * compiled for 14, 12 and 10 resident blocks per SM. Where 4-9 do not apply (batch > 1,
+ * quadrature-point capacity) they run the per-cell form; with a volumetric source shape 6
+ * runs shape 5; residual-only evaluations of shapes 4-9 use shape 1.
  *
  * pbf_ctx_autotune times `reps` explicit steps of every applicable shape with dt = 0 on a
  * scratch copy of T_dev (not modified), with the laser of the last call, keeps the fastest in
- * the context and returns its index; us_per_step_out (nullable, 7 entries) receives each
+ * the context and returns its index; us_per_step_out (nullable, 10 entries) receives each
  * shape's microseconds per step, -1 where it does not apply. FP64 contexts keep shape 0.
  * Allocates one scratch vector; synchronises. */
 pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, float* us_per_step_out,
                             pbf_stream stream);
 
-/* Selects an explicit-step shape directly (0..6, see pbf_ctx_autotune). */
+/* History of the phase model across mesh changes (Sec. 4.1 coarsening rule, with the
+ * consolidated fraction r_c of Eq. consolidated_fraction as the material history).
+ *
+ * pbf_ctx_history_cell_min: the smallest r_c of each active cell over its quadrature points
+ * and instances, into rc_min_host [n_cells] (host); synchronises.
+ * pbf_ctx_get_history / pbf_ctx_set_history: r_c as an FP64 device array
+ * [(p+1)^3][n_cells][batch] (quadrature point index x fastest), read from or written to the
+ * context (FP32-operator contexts round it).
+ * pbf_mesh_adapt_gated: pbf_mesh_adapt with the coarsening restriction of Sec. 4.1: the eight
+ * octants of a parent merge only if r_c lies at or above r_coarsen on all of them (the paper
+ * uses 0.9). cell_rc_min (host, [n_active] of the mesh before the change, from
+ * pbf_ctx_history_cell_min): every cell below r_coarsen keeps its parent's box refined to its
+ * own level (a box region added to `regions`), so its family cannot merge.
+ * pbf_ctx_transfer_history: after a mesh change (pbf_mesh_adapt, pbf_mesh_adapt_gated or
+ * pbf_mesh_activate_layer), moves r_c from `from` (a context of the mesh before the change,
+ * which may no longer be used otherwise) to `to` (a context of the changed mesh with the
+ * phase model set; same batch, precision and degree): each quadrature point of a new cell
+ * takes the value of the nearest (per axis) quadrature point of the first old active cell, in
+ * cell order, whose closure holds it (a copy on refinement, injection on coarsening); points
+ * outside the old active domain start as new cells do (0 in powder, 1 elsewhere). PBF_ESTATE
+ * when `from` is not of the mesh before its last change. Synchronises. */
+pbf_status pbf_ctx_history_cell_min(pbf_ctx* ctx, double* rc_min_host, pbf_stream stream);
+pbf_status pbf_ctx_get_history(pbf_ctx* ctx, double* rc_dev, pbf_stream stream);
+pbf_status pbf_ctx_set_history(pbf_ctx* ctx, const double* rc_dev, pbf_stream stream);
+pbf_status pbf_mesh_adapt_gated(pbf_mesh* mesh, int n_regions, const pbf_region* regions, const double* cell_rc_min,
+                                double r_coarsen);
+pbf_status pbf_ctx_transfer_history(pbf_ctx* from, pbf_ctx* to, pbf_stream stream);
+
+/* Selects an explicit-step shape directly (0..9, see pbf_ctx_autotune). */
 pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape);
 
 /* Radiation and evaporation on the free top surface (Sec. 2, Eqs. bc_rad_evap, bc_radiation,
@@ -320,7 +374,7 @@ typedef struct {
 
 /* Sets (q != NULL) or clears (NULL) the surface loss of a context for its later residual
  * evaluations (added to fvol_dev) and explicit steps. With a surface loss the explicit steps
- * run the per-cell form (shapes 4-6 act as shape 1), and pbf_implicit_solve and
+ * run the per-cell form (shapes 4-9 act as shape 1), and pbf_implicit_solve and
  * pbf_adjoint_sweep return PBF_EINVAL. Bad parameters: PBF_EINVAL. Host only. */
 pbf_status pbf_ctx_set_surface_loss(pbf_ctx* ctx, const pbf_surface_loss* q);
 
@@ -337,7 +391,7 @@ typedef struct {
 } pbf_phase;
 
 /* Sets (ph != NULL; the history restarts from the cell materials) or clears (NULL) the phase
- * model of a context. With it the explicit steps run the per-cell form (shapes 4-6 act as
+ * model of a context. With it the explicit steps run the per-cell form (shapes 4-9 act as
  * shape 1), and pbf_implicit_solve and pbf_adjoint_sweep return PBF_EINVAL. PBF_EINVAL for
  * bad parameters or the quadrature-point capacity. Allocates the history once
  * ((p+1)^3 n_cells batch values); synchronises. */

@@ -79,6 +79,7 @@ def lib():
         L.or_surface_flux.restype = C.c_double
         L.or_implicit.restype = C.c_int
         L.or_implicit_newton.restype = C.c_int
+        L.or_gate_pins.restype = C.c_int
     return _lib
 
 
@@ -287,6 +288,26 @@ class Mesh:
                                   lh.ref, C.c_double(t0), C.c_double(dt), C.c_int(nsteps),
                                   C.c_double(T_target), C.c_double(p_exp))
 
+    def history(self):
+        """r_c per active cell and quadrature point, [n_active][(p+1)^3] (x fastest)."""
+        nq3 = (self.desc["degree"] + 1) ** 3
+        out = np.zeros((self.n_active, nq3))
+        lib().or_history_get(C.c_void_p(self.h), _ptr(out))
+        return out
+
+    def set_history(self, rc):
+        rc = _f64(rc)
+        lib().or_history_set(C.c_void_p(self.h), _ptr(rc))
+
+    def gate_pins(self, rc_min, r_coarsen=0.9):
+        """Pin regions that keep every family with a cell of r_c below r_coarsen from merging
+        (region tuples as in inputs.mesh_desc)."""
+        rc_min = _f64(rc_min)
+        out = np.zeros((max(1, self.n_active), 9))
+        n = lib().or_gate_pins(C.c_void_p(self.h), _ptr(rc_min), C.c_double(r_coarsen), _ptr(out),
+                               C.c_int(out.shape[0]))
+        return [(int(r[0]), tuple(r[1:4]), tuple(r[4:7]), float(r[7]), int(r[8])) for r in out[:n]]
+
     def surface_weights(self):
         w = np.zeros(self.n_dofs)
         lib().or_surface_weights(C.c_void_p(self.h), _ptr(w))
@@ -297,6 +318,16 @@ def transfer(old: Mesh, T_old, new: Mesh, T_init):
     out = np.zeros(new.n_dofs)
     T_old = _f64(T_old)
     lib().or_transfer(C.c_void_p(old.h), _ptr(T_old), C.c_void_p(new.h), C.c_double(T_init), _ptr(out))
+    return out
+
+
+def transfer_history(old: Mesh, rc_old, new: Mesh):
+    """r_c moved to a changed mesh: nearest old quadrature point in the first old active cell
+    holding each new point; new parts start at 0 (powder) or 1."""
+    nq3 = (new.desc["degree"] + 1) ** 3
+    out = np.zeros((new.n_active, nq3))
+    rc_old = _f64(rc_old)
+    lib().or_transfer_history(C.c_void_p(old.h), _ptr(rc_old), C.c_void_p(new.h), _ptr(out))
     return out
 
 

@@ -38,6 +38,8 @@
 #include <cstdint>
 #include <cstring>
 #include <map>
+#include <tuple>
+#include <set>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
@@ -1626,6 +1628,133 @@ void or_transfer(void* hold, const double* T_old, void* hnew, double T_init, dou
     double v = 0.0;
     for (int a = 0; a < npc; ++a) v += N[a] * Te[a];
     T_new[i] = v;
+  }
+}
+
+// ---- history data across mesh changes (Sec. 4.1 coarsening rule; Sec. 2 history remark) ----
+
+// The consolidated fraction r_c per active cell and quadrature point, [n_active][(p+1)^3]
+// with the point index x fastest.
+void or_history_get(void* h, double* out) {
+  Mesh* m = (Mesh*)h;
+  std::copy(m->rc.begin(), m->rc.end(), out);
+}
+
+void or_history_set(void* h, const double* in) {
+  Mesh* m = (Mesh*)h;
+  const size_t nq3 = (size_t)(m->p + 1) * (size_t)(m->p + 1) * (size_t)(m->p + 1);
+  m->rc.assign(in, in + m->acell.size() * nq3);
+}
+
+// The coarsening restriction of Sec. 4.1: the eight octants of a parent merge only if r_c over
+// all of them lies above r_coarsen. For a new region set this is kept by pinning: every active
+// cell whose smallest r_c (rc_min, per active cell) is below r_coarsen keeps its parent's box
+// refined to its own level, so that its family cannot merge. A pin is a box region whose core
+// is the parent box shrunk by a quarter of the finest cell on each side, with half of that as
+// radius: the cells inside the parent are within it, its face neighbours are not. Writes the
+// distinct pins as region rows [kind, a0, a1, a2, b0, b1, b2, radius, level] (at most max_out)
+// and returns their number.
+int or_gate_pins(void* h, const double* rc_min, double r_coarsen, double* out, int max_out) {
+  Mesh* m = (Mesh*)h;
+  std::set<std::tuple<int, int64_t, int64_t, int64_t>> parents;
+  for (size_t c = 0; c < m->acell.size(); ++c) {
+    const Leaf& l = m->leaves[(size_t)m->acell[c]];
+    if (l.level == 0 || !(rc_min[c] < r_coarsen)) continue;
+    const int64_t ps = m->size(l) * 2;
+    parents.insert(std::make_tuple(l.level, l.x / ps * ps, l.y / ps * ps, l.z / ps * ps));
+  }
+  int n = 0;
+  for (const auto& t : parents) {
+    if (n >= max_out) break;
+    const int lv = std::get<0>(t);
+    const int64_t a[3] = {std::get<1>(t), std::get<2>(t), std::get<3>(t)};
+    const int64_t ps = (int64_t)1 << (m->L - lv + 1);
+    double* R = out + (size_t)n * 9;
+    R[0] = 1.0;
+    double eps_min = 1e300;
+    for (int k = 0; k < 3; ++k) {
+      const double eps = 0.25 * m->d.tree_h[k] / (double)((int64_t)1 << m->L);
+      R[1 + k] = m->coord(k, a[k]) + eps;
+      R[4 + k] = m->coord(k, a[k] + ps) - eps;
+      eps_min = std::min(eps_min, eps);
+    }
+    R[7] = 0.5 * eps_min;
+    R[8] = (double)lv;
+    ++n;
+  }
+  return n;
+}
+
+// Transfer of r_c to a changed mesh (same brick, degree and maximum level): each quadrature
+// point of a new active cell takes the value of the old quadrature point nearest to it (per
+// axis) in the first old active cell, in cell order, whose closure holds it. On refinement this
+// copies the parent's nearest values into the children, on coarsening it injects the values of
+// the child that holds each point. Points outside the old active domain start as a new cell
+// does: 0 in powder cells (material 1), 1 elsewhere.
+void or_transfer_history(void* hold, const double* rc_old, void* hnew, double* rc_new) {
+  Mesh* mo = (Mesh*)hold;
+  Mesh* mn = (Mesh*)hnew;
+  const int nq = mo->p + 1;
+  const size_t nq3 = (size_t)nq * nq * nq;
+  double gx[3], gw[3];
+  gauss(nq, gx, gw);
+  std::unordered_map<uint64_t, int> active_index;
+  for (size_t c = 0; c < mo->acell.size(); ++c) {
+    const Leaf& l = mo->leaves[(size_t)mo->acell[c]];
+    active_index[leaf_key(l.level, l.x, l.y, l.z)] = (int)c;
+  }
+  for (size_t c = 0; c < mn->acell.size(); ++c) {
+    const Leaf& l = mn->leaves[(size_t)mn->acell[c]];
+    const double S = (double)mn->size(l);
+    const int64_t A[3] = {l.x, l.y, l.z};
+    const double init = mn->material[(size_t)mn->acell[c]] == 1 ? 0.0 : 1.0;
+    for (int qz = 0; qz < nq; ++qz)
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          const int qi[3] = {qx, qy, qz};
+          double P[3];
+          for (int k = 0; k < 3; ++k) P[k] = (double)A[k] + S * gx[qi[k]];
+          int best = -1;
+          int64_t best_anchor[3] = {0, 0, 0};
+          int64_t best_size = 1;
+          for (int lv = 0; lv <= mo->L; ++lv) {
+            const int64_t sz = (int64_t)1 << (mo->L - lv);
+            int64_t cand[3][2];
+            int nc[3];
+            for (int k = 0; k < 3; ++k) {
+              const double t = P[k] / (double)sz;
+              const int64_t f = (int64_t)std::floor(t);
+              cand[k][0] = f;
+              nc[k] = 1;
+              if ((double)f == t) cand[k][nc[k]++] = f - 1;  // on a boundary: the cell below too
+            }
+            for (int i = 0; i < nc[0]; ++i)
+              for (int j = 0; j < nc[1]; ++j)
+                for (int k = 0; k < nc[2]; ++k) {
+                  const int64_t an[3] = {cand[0][i] * sz, cand[1][j] * sz, cand[2][k] * sz};
+                  if (an[0] < 0 || an[1] < 0 || an[2] < 0) continue;
+                  auto it = active_index.find(leaf_key(lv, an[0], an[1], an[2]));
+                  if (it != active_index.end() && (best < 0 || it->second < best)) {
+                    best = it->second;
+                    for (int a = 0; a < 3; ++a) best_anchor[a] = an[a];
+                    best_size = sz;
+                  }
+                }
+          }
+          double v = init;
+          if (best >= 0) {
+            int qo[3];
+            for (int k = 0; k < 3; ++k) {
+              const double xi = (P[k] - (double)best_anchor[k]) / (double)best_size;
+              int arg = 0;
+              for (int j = 1; j < nq; ++j)
+                if (std::fabs(xi - gx[j]) < std::fabs(xi - gx[arg])) arg = j;
+              qo[k] = arg;
+            }
+            v = rc_old[(size_t)best * nq3 + (size_t)(qo[0] + nq * (qo[1] + nq * qo[2]))];
+          }
+          rc_new[c * nq3 + (size_t)(qx + nq * (qy + nq * qz))] = v;
+        }
   }
 }
 

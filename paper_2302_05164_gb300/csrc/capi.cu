@@ -136,6 +136,8 @@ extern "C" pbf_status pbf_mesh_activate_layer(pbf_mesh* mesh, double z_new_top, 
     if (st != PBF_OK) return fail(st, "%s", err.c_str());
     nm.generation = old.generation + 1;
     make_transfer(old, nm, T_init, nm.transfer);
+    make_history_map(old, nm, nm.history_map);
+    nm.history_old_cells = (int64_t)old.leaf_of_active.size();
     mesh->m = std::move(nm);
     return PBF_OK;
   } catch (const std::bad_alloc&) {
@@ -143,16 +145,15 @@ extern "C" pbf_status pbf_mesh_activate_layer(pbf_mesh* mesh, double z_new_top, 
   }
 }
 
-extern "C" pbf_status pbf_mesh_adapt(pbf_mesh* mesh, int n_regions, const pbf_region* regions) {
-  if (!mesh || (n_regions > 0 && !regions) || n_regions < 0) return fail(PBF_EINVAL, "bad arguments");
+static pbf_status adapt_impl(pbf_mesh* mesh, const std::vector<pbf_region>& regions) {
   try {
     HostMesh& old = mesh->m;
     HostMesh nm;
     std::string err;
     pbf_mesh_desc d = old.desc;
     d.tree_exists = old.exists.empty() ? nullptr : old.exists.data();
-    d.regions = regions;
-    d.n_regions = n_regions;
+    d.regions = regions.empty() ? nullptr : regions.data();
+    d.n_regions = (int)regions.size();
     pbf_status st = init_mesh(nm, d, &err);
     if (st != PBF_OK) return fail(st, "%s", err.c_str());
     st = build_mesh(nm, nullptr, &err);  // topology first, then materials from the old leaves
@@ -166,8 +167,28 @@ extern "C" pbf_status pbf_mesh_adapt(pbf_mesh* mesh, int n_regions, const pbf_re
     if (st != PBF_OK) return fail(st, "%s", err.c_str());
     nm.generation = old.generation + 1;
     make_transfer(old, nm, 0.0, nm.transfer);  // same activation: every new dof lies in the old domain
+    make_history_map(old, nm, nm.history_map);
+    nm.history_old_cells = (int64_t)old.leaf_of_active.size();
     mesh->m = std::move(nm);
     return PBF_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(PBF_ENOMEM, "host allocation failed");
+  }
+}
+
+extern "C" pbf_status pbf_mesh_adapt(pbf_mesh* mesh, int n_regions, const pbf_region* regions) {
+  if (!mesh || (n_regions > 0 && !regions) || n_regions < 0) return fail(PBF_EINVAL, "bad arguments");
+  return adapt_impl(mesh, std::vector<pbf_region>(regions, regions + n_regions));
+}
+
+extern "C" pbf_status pbf_mesh_adapt_gated(pbf_mesh* mesh, int n_regions, const pbf_region* regions,
+                                           const double* cell_rc_min, double r_coarsen) {
+  if (!mesh || (n_regions > 0 && !regions) || n_regions < 0 || !cell_rc_min || !(r_coarsen >= 0.0))
+    return fail(PBF_EINVAL, "bad arguments");
+  try {
+    std::vector<pbf_region> all(regions, regions + n_regions);
+    gate_pins(mesh->m, cell_rc_min, r_coarsen, all);
+    return adapt_impl(mesh, all);
   } catch (const std::bad_alloc&) {
     return fail(PBF_ENOMEM, "host allocation failed");
   }
@@ -647,7 +668,7 @@ void CtxBase::set_material_constants(double dt) {
 }
 
 void CtxBase::release() {
-  for (GraphSlot* g : {&cheb_graph, &iter_graph}) {
+  for (GraphSlot* g : {&cheb_graph, &iter_graph, &bstep_graph}) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     g->exec = nullptr;
   }
@@ -821,10 +842,13 @@ LaserInline CtxBase::inline_laser(double t, Spot* sp_out) const {
 // update.
 cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
   if (nsteps <= 0) return cudaSuccess;
-  if (base.variant >= 4 && fused_ok())
-    return base.variant == 6 && !(lsetup.k.n_seg > 0 && lsetup.k.volumetric)
-               ? explicit_steps_persistent(T_dev, t0, dt, nsteps, s)
-               : explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant == 5, s);
+  if (base.variant >= 4 && bfused_ok()) return explicit_steps_bfused(T_dev, t0, dt, nsteps, s);
+  if (base.variant >= 4 && fused_ok()) {
+    if (base.variant == 6 && !(lsetup.k.n_seg > 0 && lsetup.k.volumetric))
+      return explicit_steps_persistent(T_dev, t0, dt, nsteps, s);
+    const int lean = base.variant >= 7 ? base.variant - 7 : -1;
+    return explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant != 4, lean, s);
+  }
   CellLaunch L = base;
   set_phase(L, true);
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
@@ -896,7 +920,8 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
 // rotate through fstep[n % 3] (f_n), fstep[(n + 1) % 3] (cleared for step n+1) and
 // fstep[(n + 2) % 3] (f_{n-1}, read); the state, T - T_ref as an FP32 pair hi + lo, alternates
 // between xstep[0] and xstep[1].
-cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, int nsteps, bool pdl, cudaStream_t s) {
+cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, int nsteps, bool pdl, int lean,
+                                          cudaStream_t s) {
   CellLaunch L = base;
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
   const double xd = mat.T_dirichlet - mat.T_ref;
@@ -920,7 +945,7 @@ cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, i
     st.f_clear = fstep[(n + 1) % 3];
     st.first = n == 0;
     const auto ev = timing ? timing_begin(s) : std::pair<cudaEvent_t, cudaEvent_t>{};
-    e = launch_step(L, step, st, cap, pdl, s);
+    e = lean >= 0 ? launch_step_lean(L, step, st, cap, lean, s) : launch_step(L, step, st, cap, pdl, s);
     ++launches;
     if (ev.first) timing_end(ev, s);
     if (e == cudaSuccess && volumetric && sp.seg >= 0) {
@@ -934,6 +959,150 @@ cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, i
                           mat.T_ref, T_dev, s);
     ++launches;
   }
+  return e;
+}
+
+pbf_status CtxBase::ensure_bfused() {
+  if (cell_own) return PBF_OK;
+  const size_t nv = (size_t)n_dofs * (size_t)batch;
+  // owner bits: the first cell (in cell order) that has a dof as a node stores its state
+  std::vector<uint32_t> own((size_t)n_cells, 0u);
+  std::vector<uint8_t> seen((size_t)n_dofs, 0);
+  for (size_t c = 0; c < (size_t)n_cells; ++c)
+    for (int a = 0; a < npc; ++a) {
+      const int32_t d = mesh->cell_dofs[c * (size_t)npc + (size_t)a];
+      if (d >= 0 && !seen[(size_t)d]) {
+        seen[(size_t)d] = 1;
+        own[c] |= 1u << a;
+      }
+    }
+  void* p = nullptr;
+  cudaError_t e = cudaSuccess;
+  auto get = [&](void** out, size_t bytes) {
+    if (e != cudaSuccess) return;
+    e = cudaMalloc(&p, std::max<size_t>(bytes, 16));
+    if (e == cudaSuccess) {
+      allocs.push_back(p);
+      *out = p;
+    }
+  };
+  void *own_d = nullptr, *x0 = nullptr, *x1 = nullptr, *f0 = nullptr, *f1 = nullptr, *f2 = nullptr, *ld = nullptr,
+       *td = nullptr;
+  get(&own_d, own.size() * 4);
+  get(&x0, nv * 8);
+  get(&x1, nv * 8);
+  get(&f0, nv * 4);
+  get(&f1, nv * 4);
+  get(&f2, nv * 4);
+  get(&ld, sizeof(LaserK));
+  get(&td, 8);
+  if (e == cudaSuccess) e = cudaMemcpy(own_d, own.data(), own.size() * 4, cudaMemcpyHostToDevice);
+  for (void* f : {f0, f1, f2})
+    if (e == cudaSuccess) e = cudaMemset(f, 0, std::max<size_t>(nv * 4, 16));
+  if (e != cudaSuccess) return cuda(e, "batched fused step set-up");
+  cell_own = (uint32_t*)own_d;
+  xb[0] = (float2*)x0;
+  xb[1] = (float2*)x1;
+  fb[0] = (float*)f0;
+  fb[1] = (float*)f1;
+  fb[2] = (float*)f2;
+  laser_dev = (LaserK*)ld;
+  t0_dev = (double*)td;
+  return PBF_OK;
+}
+
+// The batched fused sequence: step n (one launch for all instances) completes step n-1 in its
+// gather and accumulates f_n into fb[n % 3]; a last streaming kernel completes step N-1 and
+// writes T. The laser segments and the start time are in device memory and the spot is
+// computed there, so the launches of a call depend only on (nsteps, dt, T) and replay as one
+// CUDA graph when those repeat (with kernel timing on they are launched one by one).
+cudaError_t CtxBase::explicit_steps_bfused(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
+  if (ensure_bfused() != PBF_OK) return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMemcpyAsync(laser_dev, &lsetup.k, sizeof(LaserK), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(t0_dev, &t0, 8, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // the host copies are read before they go out of scope
+  if (e != cudaSuccess) return e;
+  const double xd = mat.T_dirichlet - mat.T_ref;
+  const float xd_hi = (float)xd;
+  CellLaunch L = base;
+  L.las = inline_laser(t0, nullptr);
+  if (lsetup.k.n_seg > 0) {  // constants of the surface laser; the spot is computed per step
+    const double r = lsetup.k.radius;
+    L.las.amp = 2.0 * lsetup.k.eta / (kPi * r * r);
+    L.las.ir2 = 2.0 / (r * r);
+    L.las.cut2 = 36.0 * r * r;
+    L.las.power = power;
+    L.las.powerf = powerf;
+  }
+  BStepArgs A;
+  A.T0 = T_dev;
+  A.off = mat.T_ref;
+  A.invC0x = invC0_fx;
+  A.nc = nodal;
+  A.x_dir = make_float2(xd_hi, (float)(xd - (double)xd_hi));
+  A.dt = (float)dt;
+  A.own = cell_own;
+  A.laser = lsetup.k.n_seg > 0 ? laser_dev : nullptr;
+  A.t0 = t0_dev;
+  A.dt64 = dt;
+  auto body = [&](cudaStream_t st, bool timed) {
+    cudaError_t err = cudaSuccess;
+    for (int n = 0; n < nsteps && err == cudaSuccess; ++n) {
+      A.step = n;
+      A.first = n == 0;
+      A.x_in = xb[n % 2];
+      A.x_out = xb[(n + 1) % 2];
+      A.f_in = fb[(n + 2) % 3];
+      A.f_acc = fb[n % 3];
+      A.f_clear = fb[(n + 1) % 3];
+      const auto ev = timed ? timing_begin(st) : std::pair<cudaEvent_t, cudaEvent_t>{};
+      err = launch_bstep(L, A, cap, st);
+      ++launches;
+      if (ev.first) timing_end(ev, st);
+    }
+    if (err == cudaSuccess)
+      err = launch_bstep_final(cap, n_dofs, batch, xb[nsteps % 2], fb[(nsteps - 1) % 3],
+                               nsteps >= 2 ? fb[(nsteps - 2) % 3] : nullptr, invC0_fx, nodal, A.x_dir, (float)dt,
+                               mat.T_ref, T_dev, st);
+    ++launches;
+    return err;
+  };
+  if (timing) return body(s, true);
+  double key[kGraphKey] = {};
+  key[0] = (double)nsteps;
+  key[1] = dt;
+  key[2] = (double)(uintptr_t)T_dev;
+  key[3] = (double)cap;
+  key[4] = (double)(lsetup.k.n_seg > 0);
+  key[5] = lsetup.k.eta;  // the surface laser's constants are kernel arguments
+  key[6] = lsetup.k.radius;
+  GraphSlot& g = bstep_graph;
+  if (!g.exec || std::memcmp(key, g.key, sizeof key) != 0) {
+    if (g.exec) {
+      e = cudaGraphExecDestroy(g.exec);
+      g.exec = nullptr;
+      if (e != cudaSuccess) return e;
+    }
+    if (!cap_stream) {
+      e = cudaStreamCreateWithFlags(&cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return e;
+    }
+    const long long l0 = launches;
+    e = cudaStreamBeginCapture(cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const cudaError_t eb = body(cap_stream, false);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap_stream, &graph);
+    if (e == cudaSuccess) e = eb;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return e;
+    g.launches = launches - l0;
+    launches = l0;
+    std::memcpy(g.key, key, sizeof key);
+  }
+  e = cudaGraphLaunch(g.exec, s);
+  launches += g.launches;
   return e;
 }
 
@@ -1076,7 +1245,8 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
   float best_ms = 0.f;
   for (int v = 0; v < kCellVariants && e == cudaSuccess; ++v) {
     if (us_per_step_out) us_per_step_out[v] = -1.f;
-    if (v >= 4 && !ctx->fused_ok()) continue;
+    // the fused forms of one instance; for a batch shape 4 stands for its fused form
+    if (v >= 4 && !ctx->fused_ok() && !(v == 4 && ctx->bfused_ok())) continue;
     ctx->base.variant = v;
     e = ctx->explicit_steps(tmp, 0.0, 0.0, 2, s);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(a, s);
@@ -1106,7 +1276,7 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
 }
 
 extern "C" pbf_status pbf_ctx_set_kernel_shape(pbf_ctx* ctx, int shape) {
-  if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, 6]");
+  if (!ctx || shape < 0 || shape >= kCellVariants) return fail(PBF_EINVAL, "shape must be in [0, %d]", kCellVariants - 1);
   ctx->base.variant = shape;
   return PBF_OK;
 }
@@ -1165,6 +1335,66 @@ extern "C" pbf_status pbf_ctx_set_phase(pbf_ctx* ctx, const pbf_phase* ph) {
   if (e != cudaSuccess) return ctx->cuda(e, "phase model");
   ctx->has_phase = true;
   return PBF_OK;
+}
+
+// ---- history of the phase model across mesh changes --------------------------------------
+
+extern "C" pbf_status pbf_ctx_history_cell_min(pbf_ctx* ctx, double* rc_min_host, pbf_stream stream) {
+  if (!ctx || !rc_min_host) return fail(PBF_EINVAL, "null argument");
+  if (!ctx->has_phase) return fail(PBF_EINVAL, "the context has no phase model");
+  cudaStream_t s = (cudaStream_t)stream;
+  double* tmp = nullptr;
+  cudaError_t e = cudaMalloc(&tmp, std::max<size_t>(1, (size_t)ctx->n_cells) * 8);
+  if (e == cudaSuccess)
+    e = launch_history_min(ctx->f32, ctx->npc, (int)ctx->n_cells, ctx->batch, ctx->rc, tmp, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(rc_min_host, tmp, (size_t)ctx->n_cells * 8, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (tmp) cudaFree(tmp);
+  ++ctx->launches;
+  return ctx->cuda(e, "history_cell_min");
+}
+
+extern "C" pbf_status pbf_ctx_get_history(pbf_ctx* ctx, double* rc_dev, pbf_stream stream) {
+  if (!ctx || !rc_dev) return fail(PBF_EINVAL, "null argument");
+  if (!ctx->has_phase) return fail(PBF_EINVAL, "the context has no phase model");
+  const int64_t n = (int64_t)ctx->npc * ctx->n_cells * ctx->batch;
+  ++ctx->launches;
+  return ctx->cuda(launch_history_copy(ctx->f32, true, n, ctx->rc, rc_dev, (cudaStream_t)stream), "get_history");
+}
+
+extern "C" pbf_status pbf_ctx_set_history(pbf_ctx* ctx, const double* rc_dev, pbf_stream stream) {
+  if (!ctx || !rc_dev) return fail(PBF_EINVAL, "null argument");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  if (!ctx->has_phase) return fail(PBF_EINVAL, "the context has no phase model");
+  const int64_t n = (int64_t)ctx->npc * ctx->n_cells * ctx->batch;
+  ++ctx->launches;
+  return ctx->cuda(launch_history_copy(ctx->f32, false, n, rc_dev, ctx->rc, (cudaStream_t)stream), "set_history");
+}
+
+extern "C" pbf_status pbf_ctx_transfer_history(pbf_ctx* from, pbf_ctx* to, pbf_stream stream) {
+  if (!from || !to) return fail(PBF_EINVAL, "null argument");
+  pbf_status st = to->check_usable();
+  if (st) return st;
+  if (!from->has_phase || !to->has_phase) return fail(PBF_EINVAL, "both contexts need the phase model");
+  const HostMesh& m = *to->mesh;
+  if (from->mesh != to->mesh || from->generation + 1 != to->generation || m.history_old_cells != from->n_cells ||
+      m.history_map.size() != (size_t)to->n_cells * (size_t)to->npc)
+    return fail(PBF_ESTATE, "`from` must be a context of the same mesh before its last change");
+  if (from->batch != to->batch || from->f32 != to->f32 || from->npc != to->npc)
+    return fail(PBF_EINVAL, "the contexts differ in batch, precision or degree");
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t* map = nullptr;
+  cudaError_t e = cudaMalloc(&map, std::max<size_t>(1, m.history_map.size()) * 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(map, m.history_map.data(), m.history_map.size() * 4, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_history_gather(to->f32, to->npc, (int)to->n_cells, (int)from->n_cells, to->batch, map, from->rc, to->rc,
+                              s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (map) cudaFree(map);
+  ++to->launches;
+  return to->cuda(e, "transfer_history");
 }
 
 extern "C" pbf_status pbf_ctx_set_barrier_test(pbf_ctx* ctx, int extra_blocks) {

@@ -218,9 +218,10 @@ struct CellLaunch {
 // residual kernel {threads per block, minimum resident blocks per SM} = {128, 1}, {128, 5},
 // {128, 6}, {64, 10} (the second bounds registers per thread), followed by the update kernel;
 // 4: the fused step kernel (one instance, constant or nodal capacity), 5: the same launched
-// with programmatic dependent launch, 6: all steps in one persistent cooperative launch.
-// Residual-only launches of shapes 4-6 use shape 1.
-constexpr int kCellVariants = 7;
+// with programmatic dependent launch, 6: all steps in one persistent cooperative launch,
+// 7-9: the lean fused step kernel (tables through L1) compiled for 14, 12 and 10 resident
+// blocks per SM. Residual-only launches of shapes 4-9 use shape 1.
+constexpr int kCellVariants = 10;
 
 template <typename R>
 __host__ __device__ inline const GeoR<R>& geo_of(const CellLaunch& L);

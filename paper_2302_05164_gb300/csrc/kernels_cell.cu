@@ -357,13 +357,11 @@ cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaSt
     return go_shape<P, R, MODE, false, false, 128, 1, true>(L, f, fh, C, Ch, s);
   if (std::is_same<R, float>::value && MODE == MODE_RESIDUAL && !LAT) {
     switch (L.variant) {
-      case 1:
-      case 4:  // shapes 4-6 are forms of the fused explicit step; residual-only launches use shape 1
-      case 5:
-      case 6: return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
+      case 0: return go_shape<P, R, MODE, NLK, LAT>(L, f, fh, C, Ch, s);
       case 2: return go_shape<P, R, MODE, NLK, LAT, 128, 6>(L, f, fh, C, Ch, s);
       case 3: return go_shape<P, R, MODE, NLK, LAT, 64, 10>(L, f, fh, C, Ch, s);
-      default: break;
+      default:  // 1, and 4-9 (forms of the fused explicit step: residual-only launches use shape 1)
+        return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
     }
   }
   return go_shape<P, R, MODE, NLK, LAT>(L, f, fh, C, Ch, s);

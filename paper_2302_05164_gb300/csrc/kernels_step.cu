@@ -25,9 +25,6 @@
 namespace pbf {
 namespace {
 
-__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-__device__ __forceinline__ void grid_dependency_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
-
 constexpr int kStepMinBlocks = 10;  // 64-thread blocks: at most 102 registers per thread
 constexpr int kStageUnroll = 14;    // dof slots each thread has in flight while staging
 
@@ -375,28 +372,6 @@ __global__ void k_step_final(int n, const float2* __restrict__ x_in, float* __re
   T[i] = off + (f2d(t.x) + f2d(t.y));
   f_in[i] = 0.f;
   if (f_other) f_other[i] = 0.f;
-}
-
-// attr: 0 plain, 1 programmatic stream serialisation, 2 cooperative
-template <typename... KArgs, typename... Args>
-cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, int attr_kind,
-                      cudaStream_t s, Args&&... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  if (attr_kind == 1) {
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-  } else {
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-  }
-  cfg.attrs = attr_kind ? attr : nullptr;
-  cfg.numAttrs = attr_kind ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
 template <int P, bool NLK, int CAP>

@@ -9,6 +9,7 @@
 #include "mesh.hpp"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <functional>
@@ -457,6 +458,95 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
       }
     }
     out.ptr.push_back((int32_t)out.idx.size());
+  }
+}
+
+// Gauss-Legendre points on [0, 1] for p + 1 = 2 or 3 points.
+static double gauss_point(int p, int q) {
+  if (p == 1) return q == 0 ? 0.5 - 0.5 / std::sqrt(3.0) : 0.5 + 0.5 / std::sqrt(3.0);
+  const double h = 0.5 * std::sqrt(0.6);
+  return q == 0 ? 0.5 - h : (q == 1 ? 0.5 : 0.5 + h);
+}
+
+void make_history_map(const HostMesh& om, const HostMesh& nm, std::vector<int32_t>& out) {
+  const int nq = nm.p + 1, nq3 = nq * nq * nq;
+  const size_t ncell = nm.leaf_of_active.size();
+  out.assign(ncell * (size_t)nq3, -1);
+  double g[3];
+  for (int q = 0; q < nq; ++q) g[q] = gauss_point(nm.p, q);
+  for (size_t c = 0; c < ncell; ++c) {
+    const size_t leaf = (size_t)nm.leaf_of_active[c];
+    const Octant& o = nm.oct[leaf];
+    const double S = (double)nm.size(o);
+    const int32_t init = nm.material[leaf] == 1 ? -1 : -2;
+    for (int q = 0; q < nq3; ++q) {
+      const int qi[3] = {q % nq, (q / nq) % nq, q / (nq * nq)};
+      double P[3];
+      int64_t f[3][2];
+      int nf[3];
+      for (int a = 0; a < 3; ++a) {
+        P[a] = (double)o.a[a] + S * g[qi[a]];
+        f[a][0] = (int64_t)std::floor(P[a]);
+        nf[a] = 1;
+        if ((double)f[a][0] == P[a]) f[a][nf[a]++] = f[a][0] - 1;  // on a cell boundary
+      }
+      int64_t best = -1, best_leaf = -1;
+      for (int i = 0; i < nf[0]; ++i)
+        for (int j = 0; j < nf[1]; ++j)
+          for (int k = 0; k < nf[2]; ++k) {
+            const int64_t fine[3] = {f[0][i], f[1][j], f[2][k]};
+            const int64_t l = om.locate(fine);
+            if (l < 0) continue;
+            const int32_t ac = om.active_of_leaf[(size_t)l];
+            if (ac >= 0 && (best < 0 || ac < best)) {
+              best = ac;
+              best_leaf = l;
+            }
+          }
+      int32_t v = init;
+      if (best >= 0) {
+        const Octant& ol = om.oct[(size_t)best_leaf];
+        const double So = (double)om.size(ol);
+        int qo[3];
+        for (int a = 0; a < 3; ++a) {
+          const double xi = (P[a] - (double)ol.a[a]) / So;
+          int arg = 0;
+          for (int t = 1; t < nq; ++t)
+            if (std::fabs(xi - g[t]) < std::fabs(xi - g[arg])) arg = t;
+          qo[a] = arg;
+        }
+        v = (int32_t)(best * nq3 + qo[0] + nq * (qo[1] + nq * qo[2]));
+      }
+      out[c * (size_t)nq3 + (size_t)q] = v;
+    }
+  }
+}
+
+void gate_pins(const HostMesh& m, const double* rc_min, double r_coarsen, std::vector<pbf_region>& out) {
+  std::vector<std::array<int64_t, 4>> fam;  // level, parent anchor
+  for (size_t c = 0; c < m.leaf_of_active.size(); ++c) {
+    const Octant& o = m.oct[(size_t)m.leaf_of_active[c]];
+    if (o.level == 0 || !(rc_min[c] < r_coarsen)) continue;
+    const int64_t ps = 2 * m.size(o);
+    fam.push_back({(int64_t)o.level, o.a[0] / ps * ps, o.a[1] / ps * ps, o.a[2] / ps * ps});
+  }
+  std::sort(fam.begin(), fam.end());
+  fam.erase(std::unique(fam.begin(), fam.end()), fam.end());
+  for (const auto& f : fam) {
+    const int lv = (int)f[0];
+    const int64_t ps = (int64_t)1 << (m.L - lv + 1);
+    pbf_region r{};
+    r.kind = PBF_REGION_BOX;
+    r.level = lv;
+    double eps_min = 1e300;
+    for (int a = 0; a < 3; ++a) {
+      const double eps = 0.25 * m.desc.tree_h[a] / (double)((int64_t)1 << m.L);
+      r.a[a] = m.coord(a, f[1 + a]) + eps;
+      r.b[a] = m.coord(a, f[1 + a] + ps) - eps;
+      eps_min = std::min(eps_min, eps);
+    }
+    r.radius = 0.5 * eps_min;
+    out.push_back(r);
   }
 }
 

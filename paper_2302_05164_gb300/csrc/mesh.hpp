@@ -49,6 +49,11 @@ struct HostMesh {
 
   int64_t generation = 0;
   TransferMap transfer;
+  // history map of the last mesh change: for each active cell and quadrature point (x
+  // fastest) the old cell * (p+1)^3 + old point it takes r_c from, or -1 (starts at 0: powder)
+  // / -2 (starts at 1); history_old_cells: the old mesh's active cells (0: no map)
+  std::vector<int32_t> history_map;
+  int64_t history_old_cells = 0;
 
   int64_t size(const Octant& o) const { return (int64_t)1 << (L - o.level); }
   double coord(int axis, int64_t lattice) const;
@@ -67,5 +72,16 @@ pbf_status init_mesh(HostMesh& m, const pbf_mesh_desc& d, std::string* err);
 // Interpolation map from the field of `old_m` to the dofs of `new_m` (same brick, degree and
 // maximum level): dofs outside the old active domain get `fill`.
 void make_transfer(const HostMesh& old_m, const HostMesh& new_m, double fill, TransferMap& out);
+
+// History map of a mesh change (see HostMesh::history_map): each quadrature point of a new
+// active cell takes the value of the nearest (per axis) quadrature point of the first old
+// active cell, in cell order, whose closure holds it; points outside the old active domain
+// start as a new cell does.
+void make_history_map(const HostMesh& old_m, const HostMesh& new_m, std::vector<int32_t>& out);
+
+// The coarsening restriction of Sec. 4.1 as pin regions: every active cell of m whose smallest
+// consolidated fraction (rc_min, per active cell) lies below r_coarsen keeps its parent's box
+// refined to its own level, so that its family of eight cannot merge.
+void gate_pins(const HostMesh& m, const double* rc_min, double r_coarsen, std::vector<pbf_region>& out);
 
 }  // namespace pbf

@@ -10,6 +10,7 @@
 #include <string>
 #include <vector>
 
+#include "newton.cuh"
 #include "pbf.h"
 #include "solver.hpp"
 
@@ -220,12 +221,14 @@ void splitmix_vector(std::vector<double>& v, uint64_t seed) {
   }
 }
 
-pbf_status check_linear(pbf_ctx* c) {
+// The implicit solvers run one instance without the surface loss or the phase model; the
+// capacity of the backward-Euler residual is the consistent one with the plain c (the
+// apparent capacity of the latent heat is not part of it). A T-dependent conductivity is
+// solved by Newton's method.
+pbf_status check_implicit(pbf_ctx* c) {
   if (c->batch != 1) return err(PBF_EINVAL, "the implicit solve runs one instance (batch 1)");
   if (c->has_loss) return err(PBF_EINVAL, "the implicit solve covers no radiation / evaporation surface loss");
   if (c->has_phase) return err(PBF_EINVAL, "the implicit solve covers no phase-dependent conductivity");
-  if ((c->mat.Tk1 > c->mat.Tk0 && c->mat.k1 != c->mat.k0) || c->cap != CAP_CONST)
-    return err(PBF_EINVAL, "the implicit solve needs a linear material (constant k and c)");
   return PBF_OK;
 }
 
@@ -282,7 +285,7 @@ extern "C" pbf_status pbf_cheb_bounds(pbf_ctx* ctx, double dt, const double* b_d
   if (!(dt > 0) || n_iter < 1) return err(PBF_EINVAL, "need dt > 0 and n_iter >= 1");
   pbf_status st = ctx->check_usable();
   if (st) return st;
-  if ((st = check_linear(ctx))) return st;
+  if ((st = check_implicit(ctx))) return st;
   if ((st = ctx->ensure_vectors(5))) return st;
   Implicit I(ctx, dt, (cudaStream_t)stream);
   return lanczos(ctx, I, b_dev, n_iter, out);
@@ -296,7 +299,10 @@ extern "C" pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt,
     return err(PBF_EINVAL, "bad solver parameters");
   pbf_status st = ctx->check_usable();
   if (st) return st;
-  if ((st = check_linear(ctx))) return st;
+  if ((st = check_implicit(ctx))) return st;
+  if (ctx->nonlin)  // a T-dependent conductivity: Newton's method (iters_out: BiCGStab iterations)
+    return pbf_implicit_newton(ctx, T_dev, dt, nsteps, rtol, 50, 1e-4, max_it, cheb_degree, cheb_bounds, nullptr,
+                               iters_out, nullptr, stream);
   if ((st = ctx->ensure_vectors(8))) return st;
   cudaStream_t s = (cudaStream_t)stream;
   Implicit I(ctx, dt, s);
@@ -389,6 +395,174 @@ extern "C" pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt,
   cudaError_t e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return ctx->cuda(e, "implicit_solve");
   return converged ? PBF_OK : err(PBF_ENOCONV, "CG missed the tolerance within max_it");
+}
+
+// ======================================================================================
+// Nonlinear backward Euler by Newton-Raphson (Sec. 3.2, Eqs. backward_euler_nonlinear,
+// Newton_1, Newton_2): from T^0 = T_n (Dirichlet dofs set to T_D), solve J(T^i) dT = -r(T^i)
+// by BiCGStab preconditioned with the Chebyshev-Jacobi polynomial of the linear operator
+// C/dt + K(k0), set T^{i+1} = T^i + dT, until ||r(T^i)||_2 <= newton_rtol ||r(T^0)||_2. The
+// residual is always evaluated in FP64; the Jacobian in the context's operator precision, so
+// that for an FP32-operator context the iteration is an FP64 iterative refinement of FP32
+// linear solves and converges to the FP64 solution.
+// ======================================================================================
+namespace {
+
+struct Newton {
+  pbf_ctx* c;
+  Implicit& I;
+  int64_t n;
+  CellLaunch Lr, Lj;  // residual (FP64) and Jacobian (operator precision) launches
+  double* T = nullptr;
+  double* diff = nullptr;
+
+  Newton(pbf_ctx* ctx, Implicit& imp, double dt) : c(ctx), I(imp), n(ctx->n_dofs) {
+    Lj = ctx->base;
+    Lj.mesh.batch = 1;
+    Lj.offset = ctx->mat.T_ref;
+    Lj.nonlin_k = ctx->nonlin ? 1 : 0;
+    Lj.latent = 0;
+    Lj.md.m_impl = ctx->mat.rho * ctx->mat.c / dt;
+    Lj.mf.m_impl = (float)Lj.md.m_impl;
+    Lr = Lj;
+    Lr.f32 = 0;
+  }
+
+  // R = r(T) on free dofs, 0 on Dirichlet dofs (Tn: the state of the previous step)
+  void residual(const double* Tn, double* R) {
+    if (I.e != cudaSuccess) return;
+    I.e = launch_sub(n, T, Tn, diff, I.s);
+    if (I.e == cudaSuccess) I.e = cudaMemsetAsync(R, 0, (size_t)n * 8, I.s);
+    if (I.e == cudaSuccess) I.e = launch_newton(Lr, false, T, diff, R, I.s);
+    if (I.e == cudaSuccess) I.e = launch_zero_masked(n, R, c->dirichlet, I.s);
+    c->launches += 3;
+  }
+
+  // y = J(T) w, identity rows on Dirichlet dofs
+  void jacobian(const double* w, double* y) {
+    if (I.e != cudaSuccess) return;
+    I.e = cudaMemsetAsync(y, 0, (size_t)n * 8, I.s);
+    if (I.e == cudaSuccess) I.e = launch_newton(Lj, true, T, w, y, I.s);
+    if (I.e == cudaSuccess) I.e = launch_copy_masked(n, y, w, c->dirichlet, I.s);
+    c->launches += 2;
+  }
+
+  double host_scalar(const double* dev) {
+    double h = 0.0;
+    if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(&h, dev, 8, cudaMemcpyDeviceToHost, I.s);
+    if (I.e == cudaSuccess) I.e = cudaStreamSynchronize(I.s);
+    return h;
+  }
+
+  // BiCGStab for J x = b from x = 0 (van der Vorst 1992, preconditioned form); the scalars
+  // stay in device memory, the host reads s.s and r.r for the stopping tests. b is used as
+  // the residual vector r and is overwritten. Returns the iterations used.
+  int bicgstab(double* b, double* x, double rtol, int max_it, int deg, const double* bounds, double* const* w) {
+    double *rh = w[0], *p = w[1], *v = w[2], *sv = w[3], *t = w[4], *y = w[5], *z = w[6];
+    double *res = w[7], *d = w[8], *Ad = w[9];
+    double* sc = c->scal;
+    double* r = b;
+    const double bn = std::sqrt(I.dot(r, r));
+    if (I.e == cudaSuccess) I.e = cudaMemsetAsync(x, 0, (size_t)n * 8, I.s);
+    if (!(bn > 0.0) || I.e != cudaSuccess) return 0;
+    const double one[3] = {1.0, 1.0, 1.0};
+    I.e = cudaMemcpyAsync(rh, r, (size_t)n * 8, cudaMemcpyDeviceToDevice, I.s);
+    if (I.e == cudaSuccess) I.e = cudaMemsetAsync(p, 0, (size_t)n * 8, I.s);
+    if (I.e == cudaSuccess) I.e = cudaMemsetAsync(v, 0, (size_t)n * 8, I.s);
+    if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(sc + kScRho, one, 8, cudaMemcpyHostToDevice, I.s);
+    if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(sc + kScAlpha, one + 1, 8, cudaMemcpyHostToDevice, I.s);
+    if (I.e == cudaSuccess) I.e = cudaMemcpyAsync(sc + kScOmega, one + 2, 8, cudaMemcpyHostToDevice, I.s);
+    int it = 0;
+    while (it < max_it && I.e == cudaSuccess) {
+      ++it;
+      I.e = launch_dot(n, 1, rh, r, nullptr, nullptr, c->part, sc + kScRhoNew, I.s);
+      if (I.e == cudaSuccess) I.e = launch_bicg_p(n, p, r, v, sc, I.s);
+      I.chebyshev(p, y, deg, bounds[0], bounds[1], res, d, Ad);
+      jacobian(y, v);
+      if (I.e == cudaSuccess) I.e = launch_dot(n, 1, rh, v, nullptr, nullptr, c->part, sc + kScRhv, I.s);
+      if (I.e == cudaSuccess) I.e = launch_bicg_s(n, sv, r, v, x, y, sc, I.s);
+      if (I.e == cudaSuccess) I.e = launch_dot(n, 1, sv, sv, nullptr, nullptr, c->part, sc + kScSs, I.s);
+      c->launches += 5;
+      const double sn = std::sqrt(host_scalar(sc + kScSs));
+      if (!(sn > rtol * bn)) break;  // converged (or not a number: the caller's test fails)
+      I.chebyshev(sv, z, deg, bounds[0], bounds[1], res, d, Ad);
+      jacobian(z, t);
+      if (I.e == cudaSuccess) I.e = launch_dot(n, 1, t, sv, nullptr, nullptr, c->part, sc + kScTs, I.s);
+      if (I.e == cudaSuccess) I.e = launch_dot(n, 1, t, t, nullptr, nullptr, c->part, sc + kScTt, I.s);
+      if (I.e == cudaSuccess) I.e = launch_bicg_x(n, x, z, r, sv, t, sc, I.s);
+      if (I.e == cudaSuccess) I.e = launch_dot(n, 1, r, r, nullptr, nullptr, c->part, sc + kScRr, I.s);
+      c->launches += 7;
+      const double rn = std::sqrt(host_scalar(sc + kScRr));
+      if (!(rn > rtol * bn)) break;
+    }
+    return it;
+  }
+};
+
+}  // namespace
+
+extern "C" pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt, int nsteps, double newton_rtol,
+                                          int newton_max, double lin_rtol, int lin_max, int cheb_degree,
+                                          const double* cheb_bounds, int* newton_iters_out, int* lin_iters_out,
+                                          double* rel_residual_out, pbf_stream stream) {
+  if (!ctx || !T_dev) return err(PBF_EINVAL, "null argument");
+  if (!(dt > 0) || nsteps < 0 || !(newton_rtol > 0) || newton_max < 1 || !(lin_rtol > 0) || lin_max < 1 ||
+      cheb_degree < 0 || cheb_degree > 64)
+    return err(PBF_EINVAL, "bad solver parameters");
+  pbf_status st = ctx->check_usable();
+  if (st) return st;
+  if ((st = check_implicit(ctx))) return st;
+  if ((st = ctx->ensure_vectors(15))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  Implicit I(ctx, dt, s);
+  double bounds[2];
+  if (cheb_bounds) {
+    bounds[0] = cheb_bounds[0];
+    bounds[1] = cheb_bounds[1];
+  } else {
+    if ((st = lanczos(ctx, I, nullptr, 30, bounds))) return st;
+    bounds[1] *= 1.1;
+  }
+  if (!(bounds[1] > bounds[0]) || !(bounds[0] > 0)) return err(PBF_EINVAL, "need 0 < lmin < lmax");
+  I.diagonal();
+  const int64_t n = ctx->n_dofs;
+  double* const* v = ctx->vec.data();
+  Newton N(ctx, I, dt);
+  N.T = T_dev;
+  N.diff = v[10];
+  double *Tn = v[11], *R = v[12], *b = v[13], *x = v[14];
+  bool converged = true;
+  double worst = 0.0;
+  for (int step = 0; step < nsteps && I.e == cudaSuccess; ++step) {
+    I.e = cudaMemcpyAsync(Tn, T_dev, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
+    if (I.e == cudaSuccess) I.e = launch_set_masked(n, T_dev, ctx->dirichlet, ctx->mat.T_dirichlet, s);
+    ctx->launches += 1;
+    N.residual(Tn, R);
+    const double r0 = std::sqrt(I.dot(R, R));
+    double rn = r0;
+    int it = 0, lin = 0;
+    while (rn > newton_rtol * r0 && it < newton_max && I.e == cudaSuccess) {
+      I.e = cudaMemcpyAsync(b, R, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
+      if (I.e == cudaSuccess) I.e = launch_neg_masked(n, b, ctx->dirichlet, s);
+      ctx->launches += 1;
+      lin += N.bicgstab(b, x, lin_rtol, lin_max, cheb_degree, bounds, v);
+      if (I.e == cudaSuccess) I.e = launch_add(n, T_dev, x, s);
+      ++ctx->launches;
+      ++it;
+      N.residual(Tn, R);
+      rn = std::sqrt(I.dot(R, R));
+    }
+    if (!(rn <= newton_rtol * r0)) converged = false;
+    if (r0 > 0.0) worst = std::max(worst, rn / r0);
+    if (!(rn == rn)) worst = rn;
+    if (newton_iters_out) newton_iters_out[step] = it;
+    if (lin_iters_out) lin_iters_out[step] = lin;
+  }
+  if (I.e != cudaSuccess) return ctx->cuda(I.e, "implicit_newton");
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return ctx->cuda(e, "implicit_newton");
+  if (rel_residual_out) *rel_residual_out = worst;
+  return converged ? PBF_OK : err(PBF_ENOCONV, "Newton missed the tolerance within newton_max corrections");
 }
 
 // ======================================================================================

@@ -83,6 +83,15 @@ struct CtxBase {
   GridBarrier* bar = nullptr;  // grid barrier of the persistent form
   unsigned barrier_test_extra = 0;  // test hook (pbf_ctx_set_barrier_test)
   bool barrier_timed_out = false;   // the last persistent launch's barrier ran out of time
+  // fused step of a batch (FP32 operator, batch > 1): owner bits per cell, two working
+  // states as FP32 pairs and three rotating accumulators [n_dofs][batch], a device copy of
+  // the laser segments, the call's start time in device memory, and the step sequence of
+  // the last call replayed as one CUDA graph (rebuilt when its key changes)
+  uint32_t* cell_own = nullptr;
+  float2* xb[2] = {nullptr, nullptr};
+  float* fb[3] = {nullptr, nullptr, nullptr};
+  LaserK* laser_dev = nullptr;
+  double* t0_dev = nullptr;
   double* C0 = nullptr;  // lumped capacity with the plain c [n_dofs]
   double* invC0_d = nullptr;
   float* invC0_f = nullptr;
@@ -102,7 +111,7 @@ struct CtxBase {
     long long launches = 0;
   };
   cudaStream_t cap_stream = nullptr;
-  GraphSlot cheb_graph, iter_graph;
+  GraphSlot cheb_graph, iter_graph, bstep_graph;
   double* pinned = nullptr;  // page-locked host scalar: r.r of the last CG iteration
   // state
   bool poisoned = false;
@@ -124,10 +133,19 @@ struct CtxBase {
   // f_diff, f_vol and C~ at T in FP64 (laser set beforehand; any output may be null)
   cudaError_t residual_f64(const double* T, double t, double* fd, double* fv, double* C, cudaStream_t s);
   // nsteps forward-Euler steps in place on T (laser set beforehand); the fused form runs when
-  // the context's shape is 4, 5 or 6 (persistent; not with a volumetric source) and fused_ok()
+  // the context's shape is 4-9 (6: persistent, not with a volumetric source; 7-9: the lean
+  // kernel) and fused_ok()
   cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
-  cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, cudaStream_t s);
+  // lean: -1 the fused step kernel, 0..2 its lean form with the register budget kLeanForms[lean]
+  cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, int lean, cudaStream_t s);
   cudaError_t explicit_steps_persistent(double* T, double t0, double dt, int nsteps, cudaStream_t s);
+  // the batched fused form: buffers allocated on first use; surface lasers only
+  pbf_status ensure_bfused();
+  cudaError_t explicit_steps_bfused(double* T, double t0, double dt, int nsteps, cudaStream_t s);
+  bool bfused_ok() const {
+    return f32 && batch > 1 && cap != CAP_QUADRATURE && !has_loss && !has_phase &&
+           !(lsetup.k.n_seg > 0 && lsetup.k.volumetric);
+  }
   bool fused_ok() const {
     return f32 && batch == 1 && cap != CAP_QUADRATURE && !has_loss && !has_phase && step.n_patches > 0;
   }

@@ -1,9 +1,17 @@
 // Fused explicit step of the FP32 operator for one instance (kernels_step.cu); internal.
 #pragma once
 
+#include <utility>
+
 #include "vec_kernels.cuh"
 
 namespace pbf {
+
+// Programmatic dependent launch: wait for the previous kernel in the stream to complete (and
+// its memory to be visible), and allow the next one to start its prologue.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependency_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 
 constexpr int kStepCells = 64;  // cells per patch = threads per block of the fused step kernel
 
@@ -69,10 +77,70 @@ __device__ __forceinline__ float2 euler_ff(float2 x, float fi, float ic, const N
   return ff_add(x, increment_f32<CAP>(x.x, fi, 0.f, ic, nc, dt));
 }
 
+// Kernel launch with one optional attribute. attr_kind: 0 plain, 1 programmatic stream
+// serialisation, 2 cooperative.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem, int attr_kind,
+                      cudaStream_t s, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  if (attr_kind == 1) {
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+  } else {
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+  }
+  cfg.attrs = attr_kind ? attr : nullptr;
+  cfg.numAttrs = attr_kind ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+
 // cap: CAP_CONST or CAP_NODAL. pdl: launch with programmatic stream serialisation, so that
 // the block prologue (table loads) overlaps the tail of the previous kernel in the stream.
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                         cudaStream_t s);
+
+// The lean form of the same step (kernels_step_lean.cu): patch tables read through L1, only
+// the staged values and their sums in shared memory, launched with programmatic stream
+// serialisation. min_blocks (kLeanForms) selects the register budget it was compiled for.
+constexpr int kLeanForms[3] = {14, 12, 10};
+cudaError_t launch_step_lean(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, int form,
+                             cudaStream_t s);
+
+// Fused step of a batch (kernels_bstep.cu): one launch per step for all instances, state
+// [n_dofs][batch] with the instance fastest, the previous step's update applied in the
+// gather, hanging nodes resolved from the constraint rows, the laser spot computed on the
+// device at *t0 + step dt64 (so that a chunk of steps replays as one graph).
+struct BStepArgs {
+  const double* T0 = nullptr;     // step 0: the state as given
+  double off = 0.0;               // T_ref
+  const float2* x_in = nullptr;   // T_{n-1} - T_ref as hi + lo
+  float2* x_out = nullptr;        // T_n - T_ref (written by the owning cell)
+  const float* f_in = nullptr;    // f_{n-1}
+  float* f_acc = nullptr;         // f_n, zero on entry
+  float* f_clear = nullptr;       // cleared by the owning cell (the accumulator of step n+1)
+  const float* invC0x = nullptr;  // [n_dofs] 1 / lumped capacity with the plain c; -1 at Dirichlet dofs
+  NodalCap nc;
+  float2 x_dir = {0.f, 0.f};
+  float dt = 0.f;
+  int first = 0;
+  const uint32_t* own = nullptr;  // [n_cells] bit a: this cell stores its node a's dof
+  const LaserK* laser = nullptr;  // device copy of the segments (null: no laser)
+  const double* t0 = nullptr;     // device scalar: the call's start time
+  int step = 0;
+  double dt64 = 0.0;
+};
+cudaError_t launch_bstep(const CellLaunch& L, const BStepArgs& A, int cap, cudaStream_t s);
+// T = T_ref + x_in + dt f_in / C~ for n_dofs x B values, clearing f_in and f_other (nullable)
+cudaError_t launch_bstep_final(int cap, int64_t n_dofs, int B, const float2* x_in, float* f_in, float* f_other,
+                               const float* invC0x, const NodalCap& nc, float2 x_dir, float dt, double off, double* T,
+                               cudaStream_t s);
 
 // Persistent form: every step of a sequence in one cooperative launch, a grid-wide barrier
 // between steps, the spot of each step computed on the device, and the last update applied

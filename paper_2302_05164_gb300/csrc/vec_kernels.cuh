@@ -140,4 +140,13 @@ cudaError_t launch_set_masked(int64_t n, double* y, const uint8_t* mask, double 
 cudaError_t launch_transfer(int64_t n_new, int B, const int32_t* ptr, const int32_t* idx, const double* w,
                             const double* Told, double fill, double* Tnew, cudaStream_t s);
 
+// history of the phase model across mesh changes (kernels_history.cu)
+// out[c] = min over the quadrature points and instances of r_c ([q][n_cells][B])
+cudaError_t launch_history_min(bool f32, int nq, int n_cells, int B, const void* rc, double* out, cudaStream_t s);
+// r_c on a changed mesh through the host-built map ([cell][q]: old cell * nq + old q, -1 / -2)
+cudaError_t launch_history_gather(bool f32, int nq, int n_new, int n_old, int B, const int32_t* map, const void* rc_old,
+                                  void* rc_new, cudaStream_t s);
+// r_c to (to_f64) or from an FP64 array of the same layout
+cudaError_t launch_history_copy(bool f32, bool to_f64, int64_t n, const void* in, void* out, cudaStream_t s);
+
 }  // namespace pbf

@@ -185,6 +185,45 @@ def c5_mesh(layer=1, level=5, haz_layers=4, degree=2):
                      powder_z0=top - C5_LAYER, powder_z1=top)
 
 
+def c5_laser(layer=1, rib=(0, 0), power=180.0, v=0.9, spacing=90e-6, angle_deg=67.0):
+    """Hatch of one rib's cross-section in layer `layer` of the part-scale stand-in: parallel
+    tracks at `spacing`, rotated by angle_deg x layer, clipped to the rib's square (tree
+    column C5_RIBS_X[rib[0]], row C5_RIBS_Y[rib[1]]), scanned back and forth at speed v."""
+    th = np.deg2rad(angle_deg * layer)
+    u = np.array([np.cos(th), np.sin(th)])
+    nv = np.array([-u[1], u[0]])
+    x0 = C5_RIBS_X[rib[0]] * C5_TREE_H[0]
+    y0 = C5_RIBS_Y[rib[1]] * C5_TREE_H[1]
+    lo = np.array([x0, y0])
+    hi = lo + np.array(C5_TREE_H[:2])
+    c = 0.5 * (lo + hi)
+    half = 0.5 * np.hypot(*C5_TREE_H[:2])
+    segs, t, k = [], 0.0, 0
+    for o in np.arange(-half, half, spacing):
+        p = c + o * nv
+        smin, smax = -np.inf, np.inf
+        for d in range(2):  # slab clipping of the line p + s u to the square
+            if abs(u[d]) < 1e-15:
+                if not lo[d] <= p[d] <= hi[d]:
+                    smin, smax = 1.0, 0.0
+                continue
+            a, b = (lo[d] - p[d]) / u[d], (hi[d] - p[d]) / u[d]
+            smin, smax = max(smin, min(a, b)), min(smax, max(a, b))
+        if smax - smin < 1e-6:
+            continue
+        a, b = p + smin * u, p + smax * u
+        if k % 2:
+            a, b = b, a
+        dur = np.hypot(*(b - a)) / v
+        segs.append((a[0], a[1], b[0], b[1], t, t + dur))
+        t += dur
+        k += 1
+    return laser(segs[:kMaxSegC5], [power] * min(len(segs), kMaxSegC5), eta=0.35, radius=40e-6)
+
+
+kMaxSegC5 = 64  # the library takes at most 64 laser segments per call
+
+
 def c4_params(batch, n_seg=16, seed=2302):
     """Per-instance laser powers P ~ U[150, 250] W and conductivity scales s ~ U[0.8, 1.2]."""
     rng = np.random.default_rng(seed)

@@ -78,6 +78,11 @@ _SIGS = {
     "pbf_mesh_export": ([C.c_void_p, C.POINTER(MeshTables)], C.c_int),
     "pbf_mesh_activate_layer": ([C.c_void_p, C.c_double, C.c_int, C.c_double], C.c_int),
     "pbf_mesh_adapt": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "pbf_mesh_adapt_gated": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double], C.c_int),
+    "pbf_ctx_history_cell_min": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_ctx_get_history": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_ctx_set_history": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_ctx_transfer_history": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "pbf_mesh_transfer": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pbf_ctx_create": ([C.c_void_p, C.POINTER(Material), C.c_int, C.c_int, C.POINTER(C.c_void_p)], C.c_int),
     "pbf_ctx_destroy": ([C.c_void_p], C.c_int),
@@ -92,6 +97,9 @@ _SIGS = {
     "pbf_cheb_bounds": ([C.c_void_p, C.c_double, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "pbf_implicit_solve": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
                             C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "pbf_implicit_newton": ([C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_double, C.c_int, C.c_double, C.c_int,
+                             C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p],
+                            C.c_int),
     "pbf_adjoint_sweep": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int,
                            C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong),
                            C.c_void_p], C.c_int),
@@ -285,6 +293,22 @@ def pbf_implicit_solve(h, T, dt, nsteps, rtol=1e-8, max_it=500, cheb_degree=5, c
     return st, iters[:nsteps]
 
 
+def pbf_implicit_newton(h, T, dt, nsteps, newton_rtol=1e-8, newton_max=50, lin_rtol=1e-4, lin_max=500,
+                        cheb_degree=5, cheb_bounds=None, stream=None):
+    """Returns (status, Newton corrections per step, BiCGStab iterations per step, largest
+    relative residual); PBF_ENOCONV (4) is returned, other failures raise PbfError."""
+    nit = np.zeros(max(1, nsteps), np.int32)
+    lit = np.zeros(max(1, nsteps), np.int32)
+    rel = C.c_double(0.0)
+    cb = None if cheb_bounds is None else np.ascontiguousarray(cheb_bounds, np.float64)
+    st = lib().pbf_implicit_newton(h, _ptr(T), float(dt), int(nsteps), float(newton_rtol), int(newton_max),
+                                   float(lin_rtol), int(lin_max), int(cheb_degree), _ptr(cb), _ptr(nit), _ptr(lit),
+                                   C.byref(rel), _stream(stream))
+    if st not in (0, 4):
+        _check(st)
+    return st, nit[:nsteps], lit[:nsteps], rel.value
+
+
 def pbf_adjoint_sweep(h, T0, laser, t0, dt, nsteps, n_checkpoints, T_target=2300.0, p_exp=16.0, batch=1,
                       stream=None):
     la = _LaserArg(laser, batch)
@@ -311,7 +335,7 @@ def pbf_widen_to_f64(x, y, n, stream=None):
     _check(lib().pbf_widen_to_f64(_ptr(x), _ptr(y), int(n), _stream(stream)))
 
 
-N_SHAPES = 7
+N_SHAPES = 10
 
 
 def pbf_ctx_autotune(h, T, reps=5, stream=None, times=False):
@@ -335,6 +359,31 @@ def pbf_ctx_set_surface_loss(h, q):
     else:
         s = SurfaceLoss(*[float(q[n]) for n, _ in SurfaceLoss._fields_])
         _check(lib().pbf_ctx_set_surface_loss(h, C.byref(s)))
+
+
+def pbf_mesh_adapt_gated(h, regions, cell_rc_min, r_coarsen=0.9):
+    regs = _regions(regions)
+    rc = np.ascontiguousarray(cell_rc_min, np.float64)
+    _check(lib().pbf_mesh_adapt_gated(h, len(regions), C.cast(regs, C.c_void_p), _ptr(rc), float(r_coarsen)))
+
+
+def pbf_ctx_history_cell_min(h, n_cells, stream=None):
+    out = np.zeros(max(1, n_cells))
+    _check(lib().pbf_ctx_history_cell_min(h, _ptr(out), _stream(stream)))
+    return out[:n_cells]
+
+
+def pbf_ctx_get_history(h, rc, stream=None):
+    """rc: FP64 device tensor [(p+1)^3][n_cells][batch]."""
+    _check(lib().pbf_ctx_get_history(h, _ptr(rc), _stream(stream)))
+
+
+def pbf_ctx_set_history(h, rc, stream=None):
+    _check(lib().pbf_ctx_set_history(h, _ptr(rc), _stream(stream)))
+
+
+def pbf_ctx_transfer_history(h_from, h_to, stream=None):
+    _check(lib().pbf_ctx_transfer_history(h_from, h_to, _stream(stream)))
 
 
 def pbf_ctx_set_phase(h, ph):

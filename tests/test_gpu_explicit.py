@@ -1,20 +1,18 @@
 """GPU parity of the explicit hot path (cell operator, material, laser, lumped capacity,
 fused Euler update, CFL estimate) against the oracle, through the C ABI.
 
-Tolerances: FP64 operator 1e-10 relative max-norm (max |gpu - oracle| / max |oracle|); FP32
-operator 2e-4 relative max-norm on temperatures; single residual evaluations in FP32 are
-held to 2e-5 of max |f| (FP32 rounding of ~30-term sums of O(1) relative size)."""
+Tolerances (tests/gates.py): FP64 operator 1e-10 relative max-norm (max |gpu - oracle| /
+max |oracle|); FP32 operator 2e-4 relative max-norm and L2 on temperatures and 1e-3 of the
+change the steps made (max |gpu - oracle| / max |oracle - T_0|); single residual evaluations
+in FP32 are held to 2e-5 of max |f| (FP32 rounding of ~30-term sums of O(1) relative size)."""
 import numpy as np
 import pytest
 
 from paper_2302_05164_gb300 import inputs as I
+from tests.gates import TOL32_F, TOL64, check_f32_steps, check_f64_steps, rel
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-TOL64 = 1e-10
-TOL32_T = 2e-4
-TOL32_F = 2e-5
 
 
 @pytest.fixture(scope="module")
@@ -23,10 +21,6 @@ def P():
         pytest.skip("no CUDA device")
     from paper_2302_05164_gb300 import pbf
     return pbf
-
-
-def rel(a, b):
-    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
 def amr_q2():
@@ -116,7 +110,10 @@ def test_c1_single_track_200_steps(P, oracle_mod, prec):
     ref = om.explicit(I.TI64_CONST, T0, ls, 0.0, dt, 200)
     assert ref.max() > 900.0  # the track has heated the block well above T0
     got = run_gpu_steps(P, desc, I.TI64_CONST, T0, ls, 0.0, dt, 200, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
-    assert rel(got, ref) < (TOL64 if prec == "f64" else TOL32_T)
+    if prec == "f64":
+        check_f64_steps(got, ref, T0)
+    else:
+        print("C1 200 steps, FP32 operator:", check_f32_steps(got, ref, T0, min_change=500.0))
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])
@@ -131,10 +128,13 @@ def test_amr_q2_nonlinear_latent_steps(P, oracle_mod, prec):
     ls = laser_over(desc, power=300.0)
     ref = om.explicit(mat, T0, ls, 1e-4, dt, 25)
     got = run_gpu_steps(P, desc, mat, T0, ls, 1e-4, dt, 25, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
-    assert rel(got, ref) < (TOL64 if prec == "f64" else TOL32_T)
+    if prec == "f64":
+        check_f64_steps(got, ref, T0)
+    else:
+        print("AMR Q2 25 steps, FP32 operator:", check_f32_steps(got, ref, T0, min_change=50.0))
 
 
-@pytest.mark.parametrize("shape", [0, 1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("shape", list(range(10)))
 def test_every_kernel_shape_matches_oracle(P, oracle_mod, shape):
     """Each explicit-step shape the autotuner can pick (the per-cell kernel's launch shapes,
     and the fused patch step kernel with and without programmatic dependent launch) gives the
@@ -153,7 +153,7 @@ def test_every_kernel_shape_matches_oracle(P, oracle_mod, shape):
     Td = to_dev(T0)
     P.pbf_explicit_step(ctx.h, Td, ls, 1e-4, dt, 10)
     torch.cuda.synchronize()
-    assert rel(Td.cpu().numpy(), ref) < TOL32_T
+    check_f32_steps(Td.cpu().numpy(), ref, T0, min_change=20.0)
     # a residual evaluation after the steps finds every accumulator cleared
     fd, fv, Cm = om.residual(mat, Td.cpu().numpy(), ls, 1e-4)
     out = [torch.zeros(om.n_dofs, dtype=torch.float64, device="cuda") for _ in range(3)]
@@ -178,7 +178,7 @@ def test_batched_instances_match_independent_runs(P, oracle_mod):
     got = run_gpu_steps(P, desc, mat, T0, ls, 0.0, dt, 10, P.PBF_F64, batch=B, kscale=s).reshape(-1, B)
     for b in range(B):
         ref = om.explicit(mat, T0[:, b], ls, 0.0, dt, 10, s=s[b], instance=b)
-        assert rel(got[:, b], ref) < TOL64
+        check_f64_steps(got[:, b], ref, T0[:, b])
 
 
 def test_cfl_estimate_matches_oracle(P, oracle_mod):
@@ -218,8 +218,9 @@ def test_edge_cases(P, oracle_mod):
 
 
 def test_c2_full_size_residual_and_step(P, oracle_mod):
-    """Configuration 2 at full size (Q2, ~1.07M dofs, 39.6k hanging nodes): the residual and
-    one explicit step of both precisions in the launch configuration the benchmark times."""
+    """Configuration 2 at full size (Q2, ~1.07M dofs, 39.6k hanging nodes): the residual, and
+    five explicit steps at half the critical step in both precisions and in every launch
+    configuration the benchmark chooses from."""
     desc = I.c2_mesh()
     om = oracle_mod.Mesh(desc)
     mat = I.TI64_NONLIN_Q2
@@ -231,21 +232,26 @@ def test_c2_full_size_residual_and_step(P, oracle_mod):
     assert rel(gd, fd) < TOL64 and rel(gv, fv) < TOL64 and rel(gC, Cm) < TOL64
     gd, gv, gC = gpu_residual(P, desc, mat, T, ls, t, P.PBF_F32OP)
     assert rel(gd, fd) < TOL32_F and rel(gC, Cm) < TOL32_F
-    dt = 1e-8
-    ref = om.explicit(mat, T, ls, t, dt, 1)
-    for prec, tol in ((P.PBF_F64, TOL64), (P.PBF_F32OP, TOL32_T)):
-        got = run_gpu_steps(P, desc, mat, T, ls, t, dt, 1, prec)
-        assert rel(got, ref) < tol
-    # the fused shapes the benchmark chooses from, three steps each; at this size the
-    # persistent form has fewer blocks than patches (blocks take several patches per step)
-    ref3 = om.explicit(mat, T, ls, t, dt, 3)
+    # steps at half the critical step of the finest cells (k at its largest value), taken from
+    # the oracle's power iteration on a uniform block of 5 um Q2 cells
+    ob = oracle_mod.Mesh(I.mesh_desc((2, 2, 2), (40e-6,) * 3, 2, 3, [I.uniform_region(3)], dirichlet_faces=0))
+    lam, _ = ob.lambda_max(dict(mat, k0=28.0), I.start_vector(ob.n_dofs), max_iter=300, rtol=1e-8)
+    dt = 0.5 * 2.0 / lam
+    nsteps = 5
+    ref = om.explicit(mat, T, ls, t, dt, nsteps)
+    got = run_gpu_steps(P, desc, mat, T, ls, t, dt, nsteps, P.PBF_F64)
+    check_f64_steps(got, ref, T)
+    got = run_gpu_steps(P, desc, mat, T, ls, t, dt, nsteps, P.PBF_F32OP)
+    print("C2 full size, 5 steps, FP32 operator (autotuner's default shape):", check_f32_steps(got, ref, T, 20.0))
+    # the fused shapes the benchmark chooses from; at this size the persistent form has
+    # fewer blocks than patches (blocks take several patches per step)
     m = P.Mesh(desc)
     ctx = P.Context(m, mat, P.PBF_F32OP)
-    for shape in (4, 5, 6):
+    for shape in (4, 5, 6, 7, 8, 9):
         P.pbf_ctx_set_kernel_shape(ctx.h, shape)
         Td = to_dev(T)
-        P.pbf_explicit_step(ctx.h, Td, ls, t, dt, 3)
+        P.pbf_explicit_step(ctx.h, Td, ls, t, dt, nsteps)
         torch.cuda.synchronize()
-        assert rel(Td.cpu().numpy(), ref3) < TOL32_T, shape
+        print(f"C2 full size, shape {shape}:", check_f32_steps(Td.cpu().numpy(), ref, T, 20.0))
     ctx.close()
     m.close()

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 from paper_2302_05164_gb300 import inputs as I
+from tests.gates import check_f32_steps
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -82,7 +83,10 @@ def test_phase_history_through_explicit_steps(P, oracle_mod, prec):
     Td = to_dev(T0)
     P.pbf_explicit_step(ctx.h, Td, None, 0.0, dt, 8)
     torch.cuda.synchronize()
-    assert rel(Td.cpu().numpy(), ref) < (TOL64 if prec == "f64" else TOL32_T)
+    if prec == "f64":
+        assert rel(Td.cpu().numpy(), ref) < TOL64
+    else:
+        check_f32_steps(Td.cpu().numpy(), ref, T0)
     assert np.abs(ref - T0).max() > 1.0
     # a cool state now sees the consolidated powder where the steps melted it
     cool = I.smooth_field(om.dof_xyz(), seed=53, lo=400.0, hi=1400.0)
