@@ -274,8 +274,9 @@ pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt, int nsteps
  * T^0 = T_n each correction solves J(T^i) dT = -r(T^i) by BiCGStab to lin_rtol (relative to
  * ||r(T^i)||_2, at most lin_max iterations) with the Chebyshev(cheb_degree)-Jacobi
  * preconditioner of the linear operator C/dt + K(k0) on bounds {lmin, lmax} (NULL: estimated
- * as in pbf_implicit_solve), until ||r(T^i)||_2 <= newton_rtol ||r(T^0)||_2 or newton_max
- * corrections. The residual is evaluated in FP64 and the Jacobian in the context's operator
+ * as in pbf_implicit_solve), until ||r(T^i)||_2 <= newton_rtol ||r(T^0)||_2, or a correction
+ * with ||dT||_2 <= 1e-13 ||T||_2 (the rounding level of T, below which the residual cannot be
+ * reduced), or newton_max corrections. The residual is evaluated in FP64 and the Jacobian in the context's operator
  * precision: for an FP32-operator context this is FP64 iterative refinement of FP32-operator
  * solves, and it reaches the FP64 solution (also for a constant k). newton_iters_out and
  * lin_iters_out (host, nullable) [nsteps]: corrections and BiCGStab iterations per step;

@@ -1420,7 +1420,9 @@ void or_newton_jacobian(void* h, const or_material* mt, const double* T, double 
 // Nonlinear backward Euler steps (Eq. backward_euler_nonlinear) by Newton-Raphson (Eqs. Newton_1,
 // Newton_2): from T^0 = T_n, solve J(T^i) dT = -r(T^i) by BiCGStab with the Chebyshev-Jacobi
 // preconditioner of the linear operator to lin_rtol, T^{i+1} = T^i + dT, until
-// ||r(T^i)||_2 <= newton_rtol ||r(T^0)||_2 or newton_max corrections. Dirichlet dofs hold T_D.
+// ||r(T^i)||_2 <= newton_rtol ||r(T^0)||_2, or a correction with ||dT||_2 <= 1e-13 ||T||_2 (the
+// rounding level of T, below which the residual cannot be reduced), or newton_max
+// corrections. Dirichlet dofs hold T_D.
 // newton_iters[nsteps] (corrections) and lin_iters[nsteps] (BiCGStab iterations summed over
 // the step), both nullable. Returns 0, or 1 when a step missed newton_rtol.
 int or_implicit_newton(void* h, const or_material* mt, double* T, double dt, int nsteps, double newton_rtol,
@@ -1439,15 +1441,21 @@ int or_implicit_newton(void* h, const or_material* mt, double* T, double dt, int
     const double r0 = std::sqrt(dot(r, r));
     double rn = r0;
     int it = 0, lin = 0;
-    while (rn > newton_rtol * r0 && it < newton_max) {
+    bool done = !(rn > newton_rtol * r0);
+    while (!done && it < newton_max) {
       for (size_t i = 0; i < n; ++i) b[i] = -r[i];
       lin += bicgstab(*m, *mt, T, dt, diag, degree, lmin, lmax, b, dT, lin_rtol, lin_max);
       for (size_t i = 0; i < n; ++i) T[i] += dT[i];
       ++it;
       newton_residual(*m, *mt, T, Tn.data(), dt, r.data());
       rn = std::sqrt(dot(r, r));
+      // converged: the residual criterion, or a correction at the rounding level of T (the
+      // residual cannot be evaluated more accurately than that)
+      double tn = 0.0;
+      for (size_t i = 0; i < n; ++i) tn += T[i] * T[i];
+      done = !(rn > newton_rtol * r0) || std::sqrt(dot(dT, dT)) <= 1e-13 * std::sqrt(tn);
     }
-    if (rn > newton_rtol * r0) status = 1;
+    if (!done) status = 1;
     if (newton_iters) newton_iters[step] = it;
     if (lin_iters) lin_iters[step] = lin;
   }

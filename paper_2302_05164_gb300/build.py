@@ -44,10 +44,24 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def _openmp_flags():
+    """-fopenmp for the host mesh code when the compiler can build and link it (the mesh
+    builder runs its independent loops on all host cores); no flags otherwise."""
+    src = os.path.join(OUT_DIR, "omp_probe.cpp")
+    out = os.path.join(OUT_DIR, "omp_probe.so")
+    with open(src, "w") as f:
+        f.write("#include <omp.h>\nint probe() { int s = 0;\n#pragma omp parallel reduction(+ : s)\n"
+                "s += omp_get_num_threads(); return s; }\n")
+    r = subprocess.run(["g++", "-fopenmp", "-fPIC", "-shared", "-o", out, src], stdout=subprocess.PIPE,
+                       stderr=subprocess.STDOUT)
+    return (["-fopenmp"], ["-lgomp"]) if r.returncode == 0 else ([], [])
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and not _stale():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
+    omp_cflags, omp_libs = _openmp_flags()
     nvcc = _nvcc()
     procs, objs = [], []
     for src in sources():
@@ -56,7 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if src.endswith(".cu"):
             cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
         else:
-            cmd = ["g++", *GXX_FLAGS, "-c", src, "-o", obj]
+            cmd = ["g++", *GXX_FLAGS, *omp_cflags, "-c", src, "-o", obj]
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -70,7 +84,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if errors:
         raise RuntimeError("CUDA library build failed:\n" + "\n".join(errors))
     tmp = LIB + f".tmp{os.getpid()}"
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lrt", "-lpthread"])
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart_static", "-ldl", "-lrt", "-lpthread",
+                           *omp_libs])
     os.replace(tmp, LIB)
     return LIB
 

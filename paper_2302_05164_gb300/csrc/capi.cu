@@ -156,15 +156,13 @@ static pbf_status adapt_impl(pbf_mesh* mesh, const std::vector<pbf_region>& regi
     d.n_regions = (int)regions.size();
     pbf_status st = init_mesh(nm, d, &err);
     if (st != PBF_OK) return fail(st, "%s", err.c_str());
-    st = build_mesh(nm, nullptr, &err);  // topology first, then materials from the old leaves
+    st = build_mesh(nm, nullptr, &err);
     if (st != PBF_OK) return fail(st, "%s", err.c_str());
-    std::vector<uint8_t> mat(nm.oct.size());
+    // materials from the old leaves (nothing else of the mesh depends on them)
     for (size_t i = 0; i < nm.oct.size(); ++i) {
       int64_t j = old.locate(nm.oct[i].a);
-      mat[i] = j >= 0 ? old.material[(size_t)j] : 0;
+      nm.material[i] = j >= 0 ? old.material[(size_t)j] : 0;
     }
-    st = build_mesh(nm, &mat, &err);
-    if (st != PBF_OK) return fail(st, "%s", err.c_str());
     nm.generation = old.generation + 1;
     make_transfer(old, nm, 0.0, nm.transfer);  // same activation: every new dof lies in the old domain
     make_history_map(old, nm, nm.history_map);

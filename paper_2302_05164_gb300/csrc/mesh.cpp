@@ -9,6 +9,9 @@
 #include "mesh.hpp"
 
 #include <algorithm>
+#ifdef _OPENMP
+#include <parallel/algorithm>
+#endif
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -128,18 +131,23 @@ static void rekey(HostMesh& m) {
 
 static void balance(HostMesh& m) {
   for (;;) {
+    // mark the leaves that are more than one level coarser than a vertex neighbour (the
+    // leaves are scanned in parallel; a mark is only ever set to 1)
     std::vector<uint8_t> split(m.oct.size(), 0);
-    bool any = false;
-    for (size_t i = 0; i < m.oct.size(); ++i) {
-      const Octant& o = m.oct[i];
+    int any = 0;
+    const int64_t nl = (int64_t)m.oct.size();
+#pragma omp parallel for schedule(static, 4096) reduction(| : any)
+    for (int64_t i = 0; i < nl; ++i) {
+      const Octant& o = m.oct[(size_t)i];
       int64_t s = m.size(o);
       for (int nb = 0; nb < 27; ++nb) {
         if (nb == 13) continue;
         int64_t q[3] = {o.a[0] + (nb % 3 - 1) * s, o.a[1] + ((nb / 3) % 3 - 1) * s, o.a[2] + (nb / 9 - 1) * s};
         int64_t j = m.locate(q);
-        if (j >= 0 && m.oct[(size_t)j].level < o.level - 1 && !split[(size_t)j]) {
+        if (j >= 0 && m.oct[(size_t)j].level < o.level - 1) {
+#pragma omp atomic write
           split[(size_t)j] = 1;
-          any = true;
+          any = 1;
         }
       }
     }
@@ -213,6 +221,15 @@ static int32_t first_coarse_holder(const HostMesh& m, const int64_t n[3]) {
   return best;
 }
 
+// Sorts (node key, slot) pairs; with OpenMP the pieces are sorted in parallel and merged.
+static void sort_pairs(std::vector<std::pair<uint64_t, int64_t>>& v) {
+#ifdef _OPENMP
+  __gnu_parallel::sort(v.begin(), v.end());
+#else
+  std::sort(v.begin(), v.end());
+#endif
+}
+
 pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::string* err) {
   const int p = m.p;
   // forest
@@ -247,19 +264,19 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
   size_t na = m.leaf_of_active.size();
   const int npc = m.npc;
   // node table: sort (node key, slot)
-  std::vector<std::pair<uint64_t, int64_t>> ents;
-  ents.reserve(na * (size_t)npc);
-  for (size_t c = 0; c < na; ++c) {
-    const Octant& o = m.oct[(size_t)m.leaf_of_active[c]];
+  std::vector<std::pair<uint64_t, int64_t>> ents(na * (size_t)npc);
+#pragma omp parallel for schedule(static, 1024)
+  for (int64_t c = 0; c < (int64_t)na; ++c) {
+    const Octant& o = m.oct[(size_t)m.leaf_of_active[(size_t)c]];
     int64_t s = m.size(o);
     for (int l = 0; l < npc; ++l) {
       int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
       int64_t n[3];
       for (int a = 0; a < 3; ++a) n[a] = p * o.a[a] + ijk[a] * s;
-      ents.push_back({pack_node(n), (int64_t)(c * (size_t)npc + (size_t)l)});
+      ents[(size_t)c * (size_t)npc + (size_t)l] = {pack_node(n), (int64_t)((size_t)c * (size_t)npc + (size_t)l)};
     }
   }
-  std::sort(ents.begin(), ents.end());
+  sort_pairs(ents);  // a total order (the slots are distinct): the same result in parallel
   NodeTable nodes;
   std::vector<int32_t> node_of_slot(na * (size_t)npc);
   for (size_t e = 0; e < ents.size(); ++e) {
@@ -274,7 +291,8 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
   }
   size_t nn = nodes.keys.size();
   std::vector<int32_t> holder(nn);
-  for (size_t i = 0; i < nn; ++i) holder[i] = first_coarse_holder(m, &nodes.xyz[i * 3]);
+#pragma omp parallel for schedule(static, 4096)
+  for (int64_t i = 0; i < (int64_t)nn; ++i) holder[(size_t)i] = first_coarse_holder(m, &nodes.xyz[(size_t)i * 3]);
   // first-touch numbering of dofs and of constraint rows
   std::vector<int32_t> dof(nn, -1), row(nn, -1);
   m.n_dofs = 0;
@@ -406,29 +424,31 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
   out.n_old = om.n_dofs;
   out.n_new = nm.n_dofs;
   out.fill = fill;
-  out.ptr.assign(1, 0);
-  out.idx.clear();
-  out.w.clear();
-  std::vector<std::pair<int32_t, double>> acc;
-  for (int64_t i = 0; i < nm.n_dofs; ++i) {
-    const int64_t* n = &nm.dof_xyz[(size_t)i * 3];
-    // first old active cell (cell order) whose closure holds the point
-    int32_t best = -1;
-    for (int o = 0; o < 8; ++o) {
-      int64_t q[3];
-      bool ok = true;
-      for (int a = 0; a < 3; ++a) {
-        int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);
-        if (h2 < 0) { ok = false; break; }
-        q[a] = h2 / (2 * p);
+  // the rows are built in parallel (one per new dof) and concatenated in dof order
+  std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nm.n_dofs);
+#pragma omp parallel
+  {
+    std::vector<std::pair<int32_t, double>> acc;
+#pragma omp for schedule(static, 1024)
+    for (int64_t i = 0; i < nm.n_dofs; ++i) {
+      const int64_t* n = &nm.dof_xyz[(size_t)i * 3];
+      // first old active cell (cell order) whose closure holds the point
+      int32_t best = -1;
+      for (int o = 0; o < 8; ++o) {
+        int64_t q[3];
+        bool ok = true;
+        for (int a = 0; a < 3; ++a) {
+          int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);
+          if (h2 < 0) { ok = false; break; }
+          q[a] = h2 / (2 * p);
+        }
+        if (!ok) continue;
+        int64_t leaf = om.locate(q);
+        if (leaf < 0 || !om.active[(size_t)leaf]) continue;
+        int32_t ai = om.active_of_leaf[(size_t)leaf];
+        if (best < 0 || ai < best) best = ai;
       }
-      if (!ok) continue;
-      int64_t leaf = om.locate(q);
-      if (leaf < 0 || !om.active[(size_t)leaf]) continue;
-      int32_t ai = om.active_of_leaf[(size_t)leaf];
-      if (best < 0 || ai < best) best = ai;
-    }
-    if (best >= 0) {
+      if (best < 0) continue;
       const Octant& c = om.oct[(size_t)om.leaf_of_active[(size_t)best]];
       int64_t s = om.size(c);
       double w1[3][3];
@@ -446,16 +466,23 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
       }
       std::stable_sort(acc.begin(), acc.end(),
                        [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
+      auto& row = rows[(size_t)i];
       for (size_t e = 0; e < acc.size();) {
         size_t f = e;
         double sum = 0.0;
         while (f < acc.size() && acc[f].first == acc[e].first) sum += acc[f++].second;
-        if (sum != 0.0) {
-          out.idx.push_back(acc[e].first);
-          out.w.push_back(sum);
-        }
+        if (sum != 0.0) row.push_back({acc[e].first, sum});
         e = f;
       }
+    }
+  }
+  out.ptr.assign(1, 0);
+  out.idx.clear();
+  out.w.clear();
+  for (const auto& row : rows) {
+    for (const auto& e : row) {
+      out.idx.push_back(e.first);
+      out.w.push_back(e.second);
     }
     out.ptr.push_back((int32_t)out.idx.size());
   }
@@ -474,7 +501,9 @@ void make_history_map(const HostMesh& om, const HostMesh& nm, std::vector<int32_
   out.assign(ncell * (size_t)nq3, -1);
   double g[3];
   for (int q = 0; q < nq; ++q) g[q] = gauss_point(nm.p, q);
-  for (size_t c = 0; c < ncell; ++c) {
+#pragma omp parallel for schedule(static, 256)
+  for (int64_t ci = 0; ci < (int64_t)ncell; ++ci) {
+    const size_t c = (size_t)ci;
     const size_t leaf = (size_t)nm.leaf_of_active[c];
     const Octant& o = nm.oct[leaf];
     const double S = (double)nm.size(o);

@@ -541,7 +541,8 @@ extern "C" pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt
     const double r0 = std::sqrt(I.dot(R, R));
     double rn = r0;
     int it = 0, lin = 0;
-    while (rn > newton_rtol * r0 && it < newton_max && I.e == cudaSuccess) {
+    bool done = !(rn > newton_rtol * r0);
+    while (!done && it < newton_max && I.e == cudaSuccess) {
       I.e = cudaMemcpyAsync(b, R, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
       if (I.e == cudaSuccess) I.e = launch_neg_masked(n, b, ctx->dirichlet, s);
       ctx->launches += 1;
@@ -551,8 +552,11 @@ extern "C" pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt
       ++it;
       N.residual(Tn, R);
       rn = std::sqrt(I.dot(R, R));
+      // converged: the residual criterion, or a correction at the rounding level of T
+      const double xn = std::sqrt(I.dot(x, x)), tn = std::sqrt(I.dot(T_dev, T_dev));
+      done = !(rn > newton_rtol * r0) || xn <= 1e-13 * tn;
     }
-    if (!(rn <= newton_rtol * r0)) converged = false;
+    if (!done) converged = false;
     if (r0 > 0.0) worst = std::max(worst, rn / r0);
     if (!(rn == rn)) worst = rn;
     if (newton_iters_out) newton_iters_out[step] = it;
