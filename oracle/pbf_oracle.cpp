@@ -1059,24 +1059,49 @@ void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, con
     for (size_t i = 0; i < n; ++i) g[i] -= mu[i] * plainC[i] / mt.c * capp_deriv(mt, T[i]);
 }
 
-// Nonlinear backward Euler (Sec. 3.2, Eq. backward_euler_nonlinear) without surface terms or
-// source: r(T) = C (T - T_n)/dt - f_diff(T) on free dofs, r = 0 on Dirichlet dofs (they hold
-// T_D). C is the consistent capacity with the plain c (reading: Eq. Newton_1 differentiates
-// only f_diff, so C does not depend on T).
+// Nonlinear backward Euler (Sec. 3.2, Eq. backward_euler_nonlinear) without a source:
+// r(T) = C (T - T_n)/dt - f_diff(T) - f_RE(T_n) on free dofs, r = 0 on Dirichlet dofs (they
+// hold T_D). C is the consistent capacity with the plain c (reading: Eq. Newton_1
+// differentiates only f_diff, so C does not depend on T). With the phase model f_diff uses
+// k(T, r_c) with r_c = max(stored r_c, g(T)) (the stored history is not changed here); with
+// the surface loss, f_RE is its boundary term at the previous state T_n, as the paper states.
 void newton_residual(const Mesh& m, const or_material& mt, const double* T, const double* Tn, double dt, double* r) {
   const size_t n = (size_t)m.n_dofs;
   std::vector<double> d(n), Cd(n);
   for (size_t i = 0; i < n; ++i) d[i] = T[i] - Tn[i];
   apply_mass(m, mt, d.data(), Cd.data());
-  Fields F;
-  residual(m, mt, 1.0, T, nullptr, 0.0, F, false);
-  for (size_t i = 0; i < n; ++i) r[i] = m.dirichlet[i] ? 0.0 : Cd[i] / dt - F.fdiff[i];
+  Fields F, Fn;
+  const int phase = m.has_phase ? 1 : 0;
+  residual(m, mt, 1.0, T, nullptr, 0.0, F, false, phase);
+  if (m.has_loss) residual(m, mt, 1.0, Tn, nullptr, 0.0, Fn, false, phase);  // f_vol = f_RE(T_n), no laser
+  for (size_t i = 0; i < n; ++i)
+    r[i] = m.dirichlet[i] ? 0.0 : Cd[i] / dt - F.fdiff[i] - (m.has_loss ? Fn.fvol[i] : 0.0);
+}
+
+// Conductivity and its derivative with respect to T at one quadrature point: the material
+// ramp (cond, cond_deriv), or with the phase model k(T, r_c) of Eq. material_parameter_interp
+// with r_c = max(stored, g(T)); where g(T) exceeds the stored value r_c follows g.
+void cond_and_deriv(const Mesh& m, const or_material& mt, double T, int mat, double stored, double* k, double* dk) {
+  if (!m.has_phase) {
+    *k = cond(mt, T, mat, 1.0);
+    *dk = cond_deriv(mt, T, mat, 1.0);
+    return;
+  }
+  const or_phase& ph = m.phase;
+  const double z = (T - ph.T_s) / (ph.T_l - ph.T_s);
+  const double g = std::min(1.0, std::max(0.0, z));
+  const double rc = std::max(stored, g);
+  *k = (1.0 - rc) * ph.k_p + g * ph.k_m + (rc - g) * ph.k_s;
+  *dk = 0.0;
+  if (z > 0.0 && z < 1.0)
+    *dk = (g > stored ? ph.k_m - ph.k_p : ph.k_m - ph.k_s) / (ph.T_l - ph.T_s);
 }
 
 // Jacobian of the residual at T applied to v (Eq. Newton_1, the linearisation of
 // Eq. matrix_free_eval): J v = C v/dt + int k(T) grad N_i . grad v + int k'(T) v grad N_i . grad T
-// (the L_e term) on free rows; v is taken as zero on Dirichlet dofs and those rows are the
-// identity (increments vanish there).
+// (the L_e term) on free rows, with k and k' from the material ramp or the phase model
+// (cond_and_deriv; f_RE(T_n) does not depend on T); v is taken as zero on Dirichlet dofs and
+// those rows are the identity (increments vanish there).
 void newton_jacobian(const Mesh& m, const or_material& mt, const double* T, double dt, const double* v_in,
                      double* y) {
   const size_t n = (size_t)m.n_dofs;
@@ -1111,7 +1136,10 @@ void newton_jacobian(const Mesh& m, const or_material& mt, const double* T, doub
               gv[d] += dN[3 * a + d] / geo.h[d] * ve[a];
             }
           }
-          double kq = cond(mt, Tq, mat, 1.0), dk = cond_deriv(mt, Tq, mat, 1.0);
+          const double stored =
+              m.has_phase ? m.rc[((size_t)c * nq + (size_t)qz) * (size_t)(nq * nq) + (size_t)(qy * nq + qx)] : 0.0;
+          double kq, dk;
+          cond_and_deriv(m, mt, Tq, mat, stored, &kq, &dk);
           for (int j = 0; j < npc; ++j) {
             double flux = 0.0;
             for (int d = 0; d < 3; ++d) flux += dN[3 * j + d] / geo.h[d] * (kq * gv[d] + dk * vq * gT[d]);
@@ -1456,6 +1484,10 @@ int or_implicit_newton(void* h, const or_material* mt, double* T, double dt, int
       done = !(rn > newton_rtol * r0) || std::sqrt(dot(dT, dT)) <= 1e-13 * std::sqrt(tn);
     }
     if (!done) status = 1;
+    if (m->has_phase) {  // the history keeps the converged state: r_c = max(r_c, g(T_{n+1}))
+      Fields F;
+      residual(*m, *mt, 1.0, T, nullptr, 0.0, F, false, 2);
+    }
     if (newton_iters) newton_iters[step] = it;
     if (lin_iters) lin_iters[step] = lin;
   }

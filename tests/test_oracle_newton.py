@@ -132,3 +132,73 @@ def test_newton_on_a_linear_material_is_one_dense_solve(oracle_mod, p):
     ff = np.ix_(free, free)
     ref[free] += np.linalg.solve(A[ff], -(K @ Tn)[free])
     assert np.max(np.abs(got - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+PHASE = dict(T_s=1.5, T_l=2.5, k_p=0.2, k_m=9.0, k_s=6.0)
+# evaporation switched on below the fields (T_v = 1) with an O(1) flux, radiation negligible at T ~ 2
+LOSS = dict(emissivity=0.7, T_amb=1.0, C_P=1.0, C_T=0.0, C_M=1.0, T_v=1.0, h_v=1.0, c_h=0.0, T_h0=0.0, T_max=1e9)
+
+
+def phase_mesh(oracle_mod, p):
+    """The tiny mesh with the phase model: cells of the upper band are powder (r_c = 0, never
+    melted), the rest consolidated (r_c = 1); the field spans the melting range."""
+    m, desc = mesh(oracle_mod, p)
+    m.set_phase(PHASE)
+    return m, desc
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_newton_jacobian_with_phase_model_and_surface_loss(oracle_mod, p):
+    """With the phase model (Eq. material_parameter_interp, r_c = max(stored, g(T))) the
+    Jacobian's k'(T) follows the branch of the max, and the surface loss enters the residual at
+    T_n only (Eq. backward_euler_nonlinear): J v equals differences of the residual. The stored
+    history is 0 (powder) or 1 (consolidated), so no quadrature point sits on the max's kink."""
+    m, _ = phase_mesh(oracle_mod, p)
+    m.set_surface_loss(LOSS)
+    dt = 0.05
+    T, Tn = field(m, 1.6, 2.4, 13), field(m, 1.6, 2.4, 14)
+    free = m.tables()["dirichlet"] == 0
+    v = np.random.default_rng(15).normal(size=m.n_dofs) * free
+
+    def cd(eps):
+        return (m.newton_residual(NONLIN, T + eps * v, Tn, dt) - m.newton_residual(NONLIN, T - eps * v, Tn, dt)) / (
+            2 * eps)
+
+    eps = 1e-4
+    ref = (4 * cd(eps / 2) - cd(eps)) / 3
+    Jv = m.newton_jacobian(NONLIN, T, dt, v)
+    assert np.max(np.abs(Jv[free] - ref[free])) <= 1e-7 * np.max(np.abs(ref))
+    # the surface loss moves the residual (evaluated at T_n), not the Jacobian
+    r_loss = m.newton_residual(NONLIN, T, Tn, dt)
+    m.set_surface_loss(None)
+    assert np.max(np.abs(m.newton_residual(NONLIN, T, Tn, dt) - r_loss)) > 1e-6 * np.max(np.abs(r_loss))
+    assert np.array_equal(m.newton_jacobian(NONLIN, T, dt, v), Jv)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_newton_step_with_phase_model_matches_dense_newton(oracle_mod, p):
+    """The oracle's Newton step with the phase model and the surface loss equals a dense Newton
+    iteration on its residual and Jacobian to 1e-11, and the converged step stores the history
+    r_c = max(r_c, g(T_{n+1}))."""
+    m, _ = phase_mesh(oracle_mod, p)
+    m.set_surface_loss(LOSS)
+    free = m.tables()["dirichlet"] == 0
+    dt = 0.05
+    Tn = field(m, 1.6, 2.8, 16)
+    Tn[~free] = NONLIN["T_dirichlet"]
+    h0 = m.history()
+    lmin, lmax = m.lanczos_bounds(NONLIN, dt, np.random.default_rng(8).normal(size=m.n_dofs), 30)
+    T = Tn.copy()
+    norms = []
+    for _ in range(10):
+        r = m.newton_residual(NONLIN, T, Tn, dt)
+        norms.append(np.linalg.norm(r))
+        if norms[-1] <= 1e-14 * norms[0]:
+            break
+        T = T + np.linalg.solve(dense_jacobian(m, NONLIN, T, dt), -r)
+    assert norms[-1] <= 1e-13 * norms[0]
+    got, nit, lit, st = m.implicit_newton(NONLIN, Tn, dt, 1, 1e-13, 20, 1e-12, 400, 5, lmin, 1.1 * lmax)
+    assert st == 0
+    assert np.max(np.abs(got - T)) <= 1e-11 * np.max(np.abs(T))
+    h1 = m.history()
+    assert np.all(h1 >= h0) and np.any(h1 > h0)  # melted powder consolidated
