@@ -253,24 +253,27 @@ pbf_status pbf_estimate_dt_noalloc(pbf_ctx* ctx, double* x_dev, double* y_dev, i
 pbf_status pbf_cheb_bounds(pbf_ctx* ctx, double dt, const double* b_dev, int n_iter, double* out,
                            pbf_stream stream);
 
-/* nsteps backward-Euler steps (Eq. backward_euler_nonlinear, no surface terms, no laser; the
+/* nsteps backward-Euler steps (Eq. backward_euler_nonlinear, no laser; the
  * capacity is the consistent one with the plain c, the latent heat's apparent capacity is
  * not part of it). Constant k: (C/dt + K) dT = f(T_n), T_{n+1} = T_n + dT, by CG with a
  * Chebyshev(cheb_degree)-Jacobi preconditioner on bounds {lmin, lmax} (NULL: pbf_cheb_bounds
  * with 30 steps, lmax x 1.1), FP64 dot products, stop at ||r||_2 <= rtol ||r_0||_2 on the CG
- * recurrence; iters_out (host, nullable) [nsteps] CG iterations. A T-dependent k: Newton's
- * method, pbf_implicit_newton with newton_rtol = rtol, 50 corrections, lin_rtol = 1e-4 and
- * lin_max = max_it, iters_out the BiCGStab iterations of each step. Instance 0 only (batch
+ * recurrence; iters_out (host, nullable) [nsteps] CG iterations. A T-dependent k, the phase
+ * model or a surface loss: Newton's method, pbf_implicit_newton with newton_rtol = rtol, 50
+ * corrections, lin_rtol = 1e-4 and lin_max = max_it, iters_out the BiCGStab iterations. Instance 0 only (batch
  * must be 1). Synchronises once per CG iteration. PBF_ENOCONV when a step missed rtol (T holds
  * the last iterate). */
 pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt, int nsteps, double rtol, int max_it,
                               int cheb_degree, const double* cheb_bounds, int* iters_out, pbf_stream stream);
 
-/* Nonlinear backward Euler (Sec. 3.2, Eq. backward_euler_nonlinear, no surface terms, no
- * laser) by Newton-Raphson (Eqs. Newton_1, Newton_2): residual
- *   r(T) = C (T - T_n)/dt - f_diff(T)  on free dofs (T = T_D on Dirichlet dofs),
- * C the consistent capacity with the plain c; Jacobian J(T) w = C w/dt + int k(T) grad N .
- * grad w + int k'(T) w grad N . grad T (the L_e term of Eq. matrix_free_eval). From
+/* Nonlinear backward Euler (Sec. 3.2, Eq. backward_euler_nonlinear, no laser) by
+ * Newton-Raphson (Eqs. Newton_1, Newton_2): residual
+ *   r(T) = C (T - T_n)/dt - f_diff(T) - f_RE(T_n)  on free dofs (T = T_D on Dirichlet dofs),
+ * C the consistent capacity with the plain c, f_RE the context's surface loss (if set) at the
+ * previous state; Jacobian J(T) w = C w/dt + int k(T) grad N . grad w + int k'(T) w grad N .
+ * grad T (the L_e term of Eq. matrix_free_eval), k from the material ramp or, with the phase
+ * model, k(T, r_c) with r_c = max(stored, g(T)) and k' along the branch of the max; after
+ * each step the phase model stores r_c = max(r_c, g(T_{n+1})). From
  * T^0 = T_n each correction solves J(T^i) dT = -r(T^i) by BiCGStab to lin_rtol (relative to
  * ||r(T^i)||_2, at most lin_max iterations) with the Chebyshev(cheb_degree)-Jacobi
  * preconditioner of the linear operator C/dt + K(k0) on bounds {lmin, lmax} (NULL: estimated
@@ -375,8 +378,9 @@ typedef struct {
 
 /* Sets (q != NULL) or clears (NULL) the surface loss of a context for its later residual
  * evaluations (added to fvol_dev) and explicit steps. With a surface loss the explicit steps
- * run the per-cell form (shapes 4-9 act as shape 1), and pbf_implicit_solve and
- * pbf_adjoint_sweep return PBF_EINVAL. Bad parameters: PBF_EINVAL. Host only. */
+ * run the per-cell form (shapes 4-9 act as shape 1), the implicit solves evaluate it at the
+ * previous state (Newton's method), and pbf_adjoint_sweep returns PBF_EINVAL. Bad parameters:
+ * PBF_EINVAL. Host only. */
 pbf_status pbf_ctx_set_surface_loss(pbf_ctx* ctx, const pbf_surface_loss* q);
 
 /* Phase-dependent conductivity with history (Sec. 2, Eqs. liquid_fraction,
@@ -393,7 +397,8 @@ typedef struct {
 
 /* Sets (ph != NULL; the history restarts from the cell materials) or clears (NULL) the phase
  * model of a context. With it the explicit steps run the per-cell form (shapes 4-9 act as
- * shape 1), and pbf_implicit_solve and pbf_adjoint_sweep return PBF_EINVAL. PBF_EINVAL for
+ * shape 1), the implicit solves use it (Newton's method, storing r_c after each step), and
+ * pbf_adjoint_sweep returns PBF_EINVAL. PBF_EINVAL for
  * bad parameters or the quadrature-point capacity. Allocates the history once
  * ((p+1)^3 n_cells batch values); synchronises. */
 pbf_status pbf_ctx_set_phase(pbf_ctx* ctx, const pbf_phase* ph);

@@ -16,7 +16,24 @@
 namespace pbf {
 namespace {
 
-template <int P, typename R, bool JAC, bool NLK>
+template <typename R>
+__device__ __forceinline__ const PhaseR<R>& phase_of(const CellLaunch& L);
+template <>
+__device__ __forceinline__ const PhaseR<float>& phase_of<float>(const CellLaunch& L) { return L.phf; }
+template <>
+__device__ __forceinline__ const PhaseR<double>& phase_of<double>(const CellLaunch& L) { return L.phd; }
+
+// The stored consolidated fraction of quadrature point q of a cell ([q][n_cells], batch 1),
+// kept in the context's operator precision.
+__device__ __forceinline__ double stored_rc(const CellLaunch& L, int q, int cell) {
+  const int64_t j = (int64_t)q * L.mesh.n_cells + cell;
+  return L.f32 ? (double)static_cast<const float*>(L.rc_in)[j] : static_cast<const double*>(L.rc_in)[j];
+}
+
+// PH: the phase model's k(T, r_c) with r_c = max(stored, g(T)) and its branch-wise k'(T)
+// instead of the material ramp (Eq. material_parameter_interp); with L.rc_out set, the
+// residual pass also stores r_c = max(stored, g(T)) (the history of the converged state).
+template <int P, typename R, bool JAC, bool NLK, bool PH>
 __global__ void __launch_bounds__(128) k_newton(const CellLaunch L, const double* __restrict__ T,
                                                 const double* __restrict__ w, double* __restrict__ y) {
   constexpr int N = P + 1, NP = N * N * N;
@@ -55,7 +72,23 @@ __global__ void __launch_bounds__(128) k_newton(const CellLaunch L, const double
   }
   const int lev = M.cell_level[cell];
   const R detJ = geo.detJ[lev];
-  const R scale = (M.cell_mat[cell] == 1 ? mt.powder_scale : R(1)) * (kscale_of<R>(L) ? kscale_of<R>(L)[0] : R(1));
+  const R ks = kscale_of<R>(L) ? kscale_of<R>(L)[0] : R(1);
+  const R scale = PH ? ks : (M.cell_mat[cell] == 1 ? mt.powder_scale : R(1)) * ks;
+  if (PH && !JAC && L.rc_out) {  // store the history of this state
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const PhaseR<R>& ph = phase_of<R>(L);
+      const R gq = clamp01((vT[q] + ph.t_off) * ph.inv_dT);
+      const int64_t j = (int64_t)q * M.n_cells + cell;
+      if (L.f32) {
+        float* o = static_cast<float*>(L.rc_out);
+        o[j] = fmaxf(o[j], (float)gq);
+      } else {
+        double* o = static_cast<double*>(L.rc_out);
+        o[j] = fmax(o[j], (double)gq);
+      }
+    }
+  }
   R r[NP];
 #pragma unroll
   for (int q = 0; q < NP; ++q) r[q] = mt.m_impl * vw[q] * (R(wq3<P>(q)) * detJ);
@@ -75,9 +108,16 @@ __global__ void __launch_bounds__(128) k_newton(const CellLaunch L, const double
     }
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
-      const R z = (vT[q] + mt.tk_off) * mt.inv_dT;
       R k = mt.k0, kd = R(0);
-      if (NLK) {
+      if (PH) {  // scale: the instance's conductivity scale only (the powder factor is not used)
+        const PhaseR<R>& ph = phase_of<R>(L);
+        const R z = (vT[q] + ph.t_off) * ph.inv_dT;
+        const R gq = clamp01(z), st = R(stored_rc(L, q, cell));
+        const R rc = st > gq ? st : gq;
+        k = ph.kp + rc * ph.dks + gq * ph.dkm;
+        kd = (z > R(0) && z < R(1)) ? (gq > st ? ph.dks + ph.dkm : ph.dkm) * ph.inv_dT : R(0);
+      } else if (NLK) {
+        const R z = (vT[q] + mt.tk_off) * mt.inv_dT;
         k = mt.k0 + mt.dk * clamp01(z);
         kd = (z > R(0) && z < R(1)) ? mt.dk * mt.inv_dT : R(0);
       }
@@ -108,8 +148,9 @@ template <int P, typename R, bool JAC>
 cudaError_t go_newton(const CellLaunch& L, const double* T, const double* w, double* y, cudaStream_t s) {
   const int bs = 128;
   const unsigned grid = (unsigned)((L.mesh.n_cells + bs - 1) / bs);
-  if (L.nonlin_k) k_newton<P, R, JAC, true><<<grid, bs, 0, s>>>(L, T, w, y);
-  else k_newton<P, R, JAC, false><<<grid, bs, 0, s>>>(L, T, w, y);
+  if (L.phase) k_newton<P, R, JAC, false, true><<<grid, bs, 0, s>>>(L, T, w, y);
+  else if (L.nonlin_k) k_newton<P, R, JAC, true, false><<<grid, bs, 0, s>>>(L, T, w, y);
+  else k_newton<P, R, JAC, false, false><<<grid, bs, 0, s>>>(L, T, w, y);
   return cudaGetLastError();
 }
 

@@ -227,8 +227,6 @@ void splitmix_vector(std::vector<double>& v, uint64_t seed) {
 // solved by Newton's method.
 pbf_status check_implicit(pbf_ctx* c) {
   if (c->batch != 1) return err(PBF_EINVAL, "the implicit solve runs one instance (batch 1)");
-  if (c->has_loss) return err(PBF_EINVAL, "the implicit solve covers no radiation / evaporation surface loss");
-  if (c->has_phase) return err(PBF_EINVAL, "the implicit solve covers no phase-dependent conductivity");
   return PBF_OK;
 }
 
@@ -300,7 +298,7 @@ extern "C" pbf_status pbf_implicit_solve(pbf_ctx* ctx, double* T_dev, double dt,
   pbf_status st = ctx->check_usable();
   if (st) return st;
   if ((st = check_implicit(ctx))) return st;
-  if (ctx->nonlin)  // a T-dependent conductivity: Newton's method (iters_out: BiCGStab iterations)
+  if (ctx->nonlin || ctx->has_phase || ctx->has_loss)  // Newton's method (iters_out: BiCGStab iterations)
     return pbf_implicit_newton(ctx, T_dev, dt, nsteps, rtol, 50, 1e-4, max_it, cheb_degree, cheb_bounds, nullptr,
                                iters_out, nullptr, stream);
   if ((st = ctx->ensure_vectors(8))) return st;
@@ -415,6 +413,7 @@ struct Newton {
   CellLaunch Lr, Lj;  // residual (FP64) and Jacobian (operator precision) launches
   double* T = nullptr;
   double* diff = nullptr;
+  double* fre = nullptr;  // f_RE(T_n), the surface loss at the previous state (null: none)
 
   Newton(pbf_ctx* ctx, Implicit& imp, double dt) : c(ctx), I(imp), n(ctx->n_dofs) {
     Lj = ctx->base;
@@ -424,8 +423,19 @@ struct Newton {
     Lj.latent = 0;
     Lj.md.m_impl = ctx->mat.rho * ctx->mat.c / dt;
     Lj.mf.m_impl = (float)Lj.md.m_impl;
+    ctx->set_phase(Lj, false);  // the stored history is read, not changed, while iterating
     Lr = Lj;
     Lr.f32 = 0;
+  }
+
+  // fre = f_RE(Tn): the radiation / evaporation term at the previous state (Eq.
+  // backward_euler_nonlinear evaluates it there)
+  void surface_loss(const double* Tn) {
+    if (I.e != cudaSuccess || !fre) return;
+    I.e = cudaMemsetAsync(fre, 0, (size_t)n * 8, I.s);
+    if (I.e == cudaSuccess)
+      I.e = launch_surface_loss(c->degree, false, c->lsetup, Lr.mesh, Tn, 0.0, c->loss, fre, I.s);
+    ++c->launches;
   }
 
   // R = r(T) on free dofs, 0 on Dirichlet dofs (Tn: the state of the previous step)
@@ -434,8 +444,21 @@ struct Newton {
     I.e = launch_sub(n, T, Tn, diff, I.s);
     if (I.e == cudaSuccess) I.e = cudaMemsetAsync(R, 0, (size_t)n * 8, I.s);
     if (I.e == cudaSuccess) I.e = launch_newton(Lr, false, T, diff, R, I.s);
+    if (I.e == cudaSuccess && fre) I.e = launch_sub(n, R, fre, R, I.s);
     if (I.e == cudaSuccess) I.e = launch_zero_masked(n, R, c->dirichlet, I.s);
-    c->launches += 3;
+    c->launches += fre ? 4 : 3;
+  }
+
+  // the history of the converged state: r_c = max(r_c, g(T)) at every quadrature point (a
+  // residual pass that stores it; its vector goes to scratch)
+  void store_history(const double* Tn, double* scratch) {
+    if (I.e != cudaSuccess || !c->has_phase) return;
+    CellLaunch Ls = Lr;
+    c->set_phase(Ls, true);
+    I.e = launch_sub(n, T, Tn, diff, I.s);
+    if (I.e == cudaSuccess) I.e = cudaMemsetAsync(scratch, 0, (size_t)n * 8, I.s);
+    if (I.e == cudaSuccess) I.e = launch_newton(Ls, false, T, diff, scratch, I.s);
+    c->launches += 2;
   }
 
   // y = J(T) w, identity rows on Dirichlet dofs
@@ -512,7 +535,7 @@ extern "C" pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt
   pbf_status st = ctx->check_usable();
   if (st) return st;
   if ((st = check_implicit(ctx))) return st;
-  if ((st = ctx->ensure_vectors(15))) return st;
+  if ((st = ctx->ensure_vectors(16))) return st;
   cudaStream_t s = (cudaStream_t)stream;
   Implicit I(ctx, dt, s);
   double bounds[2];
@@ -530,6 +553,7 @@ extern "C" pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt
   Newton N(ctx, I, dt);
   N.T = T_dev;
   N.diff = v[10];
+  N.fre = ctx->has_loss ? v[15] : nullptr;
   double *Tn = v[11], *R = v[12], *b = v[13], *x = v[14];
   bool converged = true;
   double worst = 0.0;
@@ -537,6 +561,7 @@ extern "C" pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt
     I.e = cudaMemcpyAsync(Tn, T_dev, (size_t)n * 8, cudaMemcpyDeviceToDevice, s);
     if (I.e == cudaSuccess) I.e = launch_set_masked(n, T_dev, ctx->dirichlet, ctx->mat.T_dirichlet, s);
     ctx->launches += 1;
+    N.surface_loss(Tn);
     N.residual(Tn, R);
     const double r0 = std::sqrt(I.dot(R, R));
     double rn = r0;
@@ -557,6 +582,7 @@ extern "C" pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt
       done = !(rn > newton_rtol * r0) || xn <= 1e-13 * tn;
     }
     if (!done) converged = false;
+    N.store_history(Tn, b);
     if (r0 > 0.0) worst = std::max(worst, rn / r0);
     if (!(rn == rn)) worst = rn;
     if (newton_iters_out) newton_iters_out[step] = it;

@@ -275,3 +275,42 @@ def melt_pool_field(coords, center, peak=2600.0, width=50e-6, base=T0, seed=None
 def start_vector(n, seed=7):
     rng = np.random.default_rng(seed)
     return rng.uniform(-1.0, 1.0, size=n)
+
+
+# ---------------------------------------------------------------------------------------
+# temporal-convergence experiment (Appendix A): a 1.0 x 0.2 x 0.2 mm plate with two powder
+# layers of 40 um, one track per layer along +x through the middle of the plate's width, the
+# explicit scan, an interlayer cool-down (explicit, then implicit) and the second layer.
+# Material and loss constants are the paper's (Table mat_params: phase model, radiation and
+# evaporation, T_0 = T_inf = 303 K; no latent heat), the scan speed and beam radius those of
+# the cantilever (Table scan_params_cantilever: 960 mm/s, R = 60 um) with the paper's
+# cylinder source. The paper states no power: W_eff = 100 W is a reading.
+# ---------------------------------------------------------------------------------------
+
+APPA_T0 = 303.0
+APPA_PLATE_TOP = 0.2e-3
+APPA_LAYER = 40e-6
+APPA_MATERIAL = dict(rho=7430.0, c=965.0, k0=20.0, k1=20.0, Tk0=303.0, Tk1=303.0, latent=0.0, Tm=1700.0,
+                     sigma=0.0, powder_k_scale=0.01, T_dirichlet=APPA_T0, T_ref=APPA_T0)
+APPA_PHASE = dict(T_s=1500.0, T_l=1900.0, k_p=0.2, k_m=20.0, k_s=20.0)
+APPA_LOSS = dict(emissivity=0.7, T_amb=APPA_T0, C_P=54.0e3, C_T=5.0e4, C_M=1.0e-3, T_v=3000.0, h_v=6.0e6,
+                 c_h=965.0, T_h0=663.0, T_max=4000.0)
+APPA_OBS = (0.5e-3, 0.0, APPA_PLATE_TOP + APPA_LAYER)  # top of the first layer, middle of the track
+APPA_DT_EXPLICIT = 2e-5  # the paper's reference steps
+APPA_DT_IMPLICIT = 2e-2
+APPA_COOL = 0.06  # s between the layers
+APPA_COOL_EXPLICIT = 0.02  # s of it (1000 reference steps) explicit, as in the paper's examples
+
+
+def appa_mesh(layers=1):
+    """Q1 trees of 40 um (25 x 5 x 7 on y in [-0.1, 0.1] mm), refined once (20 um cells);
+    `layers` powder layers active; Dirichlet bottom."""
+    return mesh_desc((25, 5, 7), (40e-6,) * 3, 1, 1, [uniform_region(1)], origin=(0.0, -0.1e-3, 0.0),
+                     active_top_z=APPA_PLATE_TOP + layers * APPA_LAYER, powder_z0=APPA_PLATE_TOP,
+                     powder_z1=APPA_PLATE_TOP + 2 * APPA_LAYER)
+
+
+def appa_laser(t0=0.0, power=200.0, eta=0.5, v=0.96):
+    """The track of one layer (x from 0 to 1 mm at y = 0) starting at t0; W_eff = eta P."""
+    return laser([track(0.0, 0.0, 1.0e-3, v, t0)], [power], eta=eta, radius=60e-6, volumetric=True,
+                 h_powder=APPA_LAYER)

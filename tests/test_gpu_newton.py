@@ -126,3 +126,43 @@ def test_fp32_operator_refinement_reaches_the_fp64_linear_solution(P, oracle_mod
     assert st == 0 and worst <= 1e-10 and nit[0] >= 2
     print(f"C3 FP32-operator refinement: corrections {list(nit)}, BiCGStab {list(lit)}, residual {worst:.1e}")
     assert rel(Td.cpu().numpy(), ref) < 1e-9
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_newton_with_phase_model_and_surface_loss_matches_oracle(P, oracle_mod, prec):
+    """The paper's material in the cool-down: phase-dependent conductivity with the stored
+    history (k(T, r_c), r_c = max(stored, g(T)), stored after each step) and radiation /
+    evaporation evaluated at the previous state (Eq. backward_euler_nonlinear). A hot powder
+    band over a consolidated part: two steps, FP64 1e-10 (FP32 operator 1e-9) on T and on the
+    stored history."""
+    regions = [I.uniform_region(1), (I.BALL, (0.3e-3, 0.25e-3, 0.25e-3), (0, 0, 0), 100e-6, 3)]
+    desc = I.mesh_desc((8, 4, 2), (125e-6,) * 3, 2, 3, regions, powder_z0=0.2e-3, powder_z1=0.3e-3)
+    om = oracle_mod.Mesh(desc)
+    om.set_phase(I.PHASE)
+    om.set_surface_loss(I.SURFACE_LOSS)
+    mat = dict(I.TI64_CONST, k0=20.0, k1=20.0)
+    T = I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 1950.0, 80e-6, seed=33, noise=0.01)
+    T[om.tables()["dirichlet"] != 0] = mat["T_dirichlet"]
+    dt = 2e-4
+    lmin, lmax = om.lanczos_bounds(mat, dt, I.start_vector(om.n_dofs, seed=3), 30)
+    bounds = np.array([lmin, 1.1 * lmax])
+    ref, nit, _, st = om.implicit_newton(mat, T, dt, 2, NEWTON_RTOL, 30, 1e-6, 800, 5, *bounds)
+    assert st == 0
+    h_ref = om.history()
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
+    P.pbf_ctx_set_phase(ctx.h, I.PHASE)
+    P.pbf_ctx_set_surface_loss(ctx.h, I.SURFACE_LOSS)
+    Td = to_dev(T)
+    st, gnit, lit, worst = P.pbf_implicit_newton(ctx.h, Td, dt, 2, NEWTON_RTOL, 30, 1e-6, 800, 5, bounds)
+    assert st == 0
+    tol = 1e-10 if prec == "f64" else 1e-9
+    err = rel(Td.cpu().numpy(), ref)
+    print(f"phase + loss Newton, {prec}: rel err {err:.2e}, corrections {list(gnit)} (oracle {list(nit)})")
+    assert err < tol
+    nq = 27
+    hist = torch.zeros(nq * om.n_active, dtype=torch.float64, device="cuda")
+    P.pbf_ctx_get_history(ctx.h, hist)
+    h = hist.cpu().numpy().reshape(nq, om.n_active).T
+    assert np.max(np.abs(h - h_ref)) < (1e-9 if prec == "f64" else 1e-5)
+    assert np.any(h_ref > 0.0) and np.any(h_ref < 1.0)
