@@ -77,6 +77,7 @@ def lib():
         L.or_capp.restype = C.c_double
         L.or_cond.restype = C.c_double
         L.or_surface_flux.restype = C.c_double
+        L.or_surface_flux_deriv.restype = C.c_double
         L.or_implicit.restype = C.c_int
         L.or_implicit_newton.restype = C.c_int
         L.or_gate_pins.restype = C.c_int
@@ -333,6 +334,10 @@ def transfer_history(old: Mesh, rc_old, new: Mesh):
 
 def surface_flux(q, T):
     return lib().or_surface_flux(C.byref(surface_loss(q)), C.c_double(T))
+
+
+def surface_flux_deriv(q, T):
+    return lib().or_surface_flux_deriv(C.byref(surface_loss(q)), C.c_double(T))
 
 
 def capp(mat, T):

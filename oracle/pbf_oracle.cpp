@@ -646,6 +646,7 @@ int laser_segment(const or_laser& ls, double t) {
 
 struct Fields {
   std::vector<double> fdiff, fvol, C;
+  std::vector<double> fre;  // the surface loss's part of fvol (with a surface loss)
 };
 
 const double kStefanBoltzmann = 5.670374419e-8;  // W m^-2 K^-4
@@ -659,6 +660,18 @@ double surface_flux(const or_surface_loss& q, double T) {
     flux += mdot * (q.h_v + q.c_h * (Tc - q.T_h0));
   }
   return flux;
+}
+
+// dq/dT of surface_flux: radiation 4 eps sigma T^3; evaporation, for T_v < T < T_max,
+// mdot(T) (C_T / T^2 - 1 / (2 T)) (h_v + c_h (T - T_h0)) + mdot(T) c_h; above T_max the
+// evaporation part is constant (the cap). At T_v and T_max the one-sided value below.
+double surface_flux_deriv(const or_surface_loss& q, double T) {
+  double d = 4.0 * q.emissivity * kStefanBoltzmann * T * T * T;
+  if (q.C_P > 0.0 && T < q.T_max && T > q.T_v) {
+    const double mdot = 0.82 * q.C_P * std::exp(-q.C_T * (1.0 / T - 1.0 / q.T_v)) * std::sqrt(q.C_M / T);
+    d += mdot * (q.C_T / (T * T) - 0.5 / T) * (q.h_v + q.c_h * (T - q.T_h0)) + mdot * q.c_h;
+  }
+  return d;
 }
 
 // f_diff, f_vol and the row-sum lumped capacity C~ = P^T int rho c_app(T_h) N_i at T.
@@ -675,12 +688,13 @@ void residual(const Mesh& m, const or_material& mt, double s, const double* T, c
   const int p = m.p, npc = m.npc(), nq = p + 1;
   F.fdiff.assign((size_t)m.n_dofs, 0.0);
   F.fvol.assign((size_t)m.n_dofs, 0.0);
+  F.fre.assign(m.has_loss ? (size_t)m.n_dofs : 0, 0.0);
   if (with_C) F.C.assign((size_t)m.n_dofs, 0.0);
   double gx[3], gw[3];
   gauss(nq, gx, gw);
   double lx = 0, ly = 0, P = 0;
   bool on = ls && laser_spot(*ls, t, &lx, &ly, &P);
-  std::vector<double> Te(npc), fe(npc), ce(npc), ve(npc), N(npc);
+  std::vector<double> Te(npc), fe(npc), ce(npc), ve(npc), re(npc), N(npc);
   std::vector<double> dN((size_t)npc * 3);
   for (int c = 0; c < (int)m.acell.size(); ++c) {
     CellGeo g = cell_geo(m, c);
@@ -690,6 +704,7 @@ void residual(const Mesh& m, const or_material& mt, double s, const double* T, c
     std::fill(fe.begin(), fe.end(), 0.0);
     std::fill(ce.begin(), ce.end(), 0.0);
     std::fill(ve.begin(), ve.end(), 0.0);
+    std::fill(re.begin(), re.end(), 0.0);
     for (int qz = 0; qz < nq; ++qz)
       for (int qy = 0; qy < nq; ++qy)
         for (int qx = 0; qx < nq; ++qx) {
@@ -751,8 +766,12 @@ void residual(const Mesh& m, const or_material& mt, double s, const double* T, c
           double Tq = 0.0;
           for (int a = 0; a < npc; ++a) Tq += N[a] * Te[a];
           const double q = surface_flux(m.loss, Tq);
-          for (int i = 0; i < npc; ++i) ve[i] -= W * q * N[i];
+          for (int i = 0; i < npc; ++i) {
+            ve[i] -= W * q * N[i];
+            re[i] -= W * q * N[i];
+          }
         }
+      scatter(m, c, re.data(), F.fre.data());
     }
     scatter(m, c, fe.data(), F.fdiff.data());
     scatter(m, c, ve.data(), F.fvol.data());
@@ -1052,6 +1071,23 @@ void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, con
             ge[j] += W * (-kq * gjv - dk * gvgT * N[j] - cap_term * N[j]);
           }
         }
+    // the surface loss f_RE,i = -int_top N_i q(T_h) dA (explicit, at the state T):
+    // df_RE,i/dT_j = -int_top N_i q'(T_h) N_j dA, so g_j gets -int_top q'(T_h) v_h N_j dA
+    if (M.has_loss && M.top[(size_t)c]) {
+      for (int qy = 0; qy < nq; ++qy)
+        for (int qx = 0; qx < nq; ++qx) {
+          double xi[3] = {gx[qx], gx[qy], 1.0};
+          double W = gw[qx] * gw[qy] * geo.h[0] * geo.h[1];
+          basis(p, xi, N.data(), dN.data());
+          double Tq = 0.0, vq = 0.0;
+          for (int a = 0; a < npc; ++a) {
+            Tq += N[a] * Te[a];
+            vq += N[a] * ve[a];
+          }
+          const double dq = surface_flux_deriv(M.loss, Tq);
+          for (int j = 0; j < npc; ++j) ge[j] -= W * dq * vq * N[j];
+        }
+    }
     scatter(M, c, ge.data(), g.data());
   }
   // nodal lumping: dC~_i/dT_j = delta_ij rho M_i c_app'(T_i), M the lumped mass
@@ -1249,6 +1285,7 @@ void or_set_surface_loss(void* h, const or_surface_loss* q) {
 }
 
 double or_surface_flux(const or_surface_loss* q, double T) { return surface_flux(*q, T); }
+double or_surface_flux_deriv(const or_surface_loss* q, double T) { return surface_flux_deriv(*q, T); }
 
 // Phase-dependent conductivity with history for later residuals and explicit steps (null:
 // off). Setting it (re)starts the history: r_c = 0 in powder cells (material 1), 1 elsewhere.
@@ -1499,15 +1536,17 @@ int or_implicit_newton(void* h, const or_material* mt, double* T, double dt, int
 //   J = (1/N) sum_{n=1..N} (M_n - T_target)^2,
 //   T_{n+1} = T_n + dt u(T_n), u = C~(T)^-1 f(T) on free dofs,
 //   lambda_N = dJ/dT_N,  lambda_n = lambda_{n+1} + dt (du/dT(T_n))^T lambda_{n+1} + dJ/dT_n,
-//   dJ/dP_k = sum_n dt lambda_{n+1}^T C~^-1 f_vol(t_n) / P_k   (segment k active at t_n),
-//   dJ/ds   = sum_n dt lambda_{n+1}^T C~^-1 f_diff(T_n) / s.
-// du/dT follows the linearisation of Eq. (matrix_free_eval): the k term, the k'(T) term L_e
-// and the derivative of the lumped capacity through c_app'(T). All states are stored.
+//   dJ/dP_k = sum_n dt lambda_{n+1}^T C~^-1 f_las(t_n) / P_k   (segment k active at t_n),
+//   dJ/ds   = sum_n dt lambda_{n+1}^T C~^-1 f_diff(T_n) / s,
+// with f_las the laser's part of f_vol. du/dT follows the linearisation of Eq.
+// (matrix_free_eval): the k term, the k'(T) term L_e and the derivative of the lumped capacity
+// through c_app'(T); with a surface loss also its face term -int N_i q'(T_h) N_j dA. All states
+// are stored. The phase model (history) is not covered: NaN.
 // grad[n_seg + 1]: dJ/dP_0..dJ/dP_{n_seg-1}, dJ/ds.
 double or_adjoint(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0, double dt,
                   int nsteps, double T_target, double p_exp, double* grad) {
   Mesh* m = (Mesh*)h;
-  if (m->has_loss || m->has_phase) return std::nan("");  // the adjoint covers neither
+  if (m->has_phase) return std::nan("");  // the adjoint does not cover the phase model
   const Mesh& M = *m;
   size_t n = (size_t)M.n_dofs;
   Objective obj;
@@ -1547,7 +1586,9 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
     for (size_t i = 0; i < n; ++i) {
       if (M.dirichlet[i]) continue;
       gs += dt * lam[i] * F.fdiff[i] / F.C[i] / s;
-      if (seg >= 0) gp += dt * lam[i] * F.fvol[i] / F.C[i] / ls->power[seg];
+      // the laser's part of f_vol (the surface loss does not depend on the power)
+      const double flas = F.fvol[i] - (M.has_loss ? F.fre[i] : 0.0);
+      if (seg >= 0) gp += dt * lam[i] * flas / F.C[i] / ls->power[seg];
     }
     grad[nseg] += gs;
     if (seg >= 0) grad[seg] += gp;
@@ -1590,7 +1631,7 @@ void or_step_transpose(void* h, const or_material* mt, double s, const double* T
 double or_objective(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0,
                     double dt, int nsteps, double T_target, double p_exp) {
   Mesh* m = (Mesh*)h;
-  if (m->has_loss || m->has_phase) return std::nan("");  // as the adjoint
+  if (m->has_phase) return std::nan("");  // as the adjoint
   size_t n = (size_t)m->n_dofs;
   Objective obj;
   obj.T_target = T_target;

@@ -393,6 +393,63 @@ def test_surface_flux_branches(oracle_mod):
     assert oracle_mod.surface_flux(dict(q, emissivity=0.0), 2900.0) == 0.0
 
 
+def test_surface_flux_derivative_matches_differences(oracle_mod):
+    """q'(T) of the adjoint's face term against Richardson-extrapolated central differences of
+    the transcribed Eqs. bc_radiation and bc_evaporation, inside each branch: radiation only,
+    radiation with evaporation, and above the evaporation cap (radiation only again)."""
+    q = I.SURFACE_LOSS
+
+    def cd(T, h):
+        return (paper_surface_flux(q, T + h) - paper_surface_flux(q, T - h)) / (2 * h)
+
+    for T in (353.0, 1500.0, 2900.0, 3100.0, 3500.0, 3900.0, 4200.0, 5000.0):
+        # 1 K: Richardson is exact for T^4, the evaporation part varies on T^2 / C_T ~ 200 K,
+        # and a smaller step loses digits to the large capped flux above T_max
+        h = 1.0
+        ref = (4 * cd(T, h / 2) - cd(T, h)) / 3
+        got = oracle_mod.surface_flux_deriv(q, T)
+        assert abs(got - ref) <= 1e-8 * abs(ref), (T, got, ref)
+    # the evaporation part dominates the derivative between T_v and T_max
+    assert oracle_mod.surface_flux_deriv(q, 3500.0) > 100 * oracle_mod.surface_flux_deriv(dict(q, C_P=0.0), 3500.0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_adjoint_with_surface_loss_matches_central_differences(oracle_mod, p):
+    """With radiation and evaporation on the top surface (explicit, at each step's state) the
+    adjoint gradient (dJ/dP per segment and dJ/ds) equals central differences of the objective
+    to 1e-5, on a brick whose top reaches 3600 K under the laser track, so that evaporation is
+    active; the loss's face term moves every gradient component by a large fraction of itself,
+    so a dropped or wrong term fails. The step, 5 us, stays inside the loss term's own
+    stability limit (dt q'(T) 2 / (rho c h) below 1 at 3600 K)."""
+    d = I.mesh_desc((4, 2, 2), (125e-6,) * 3, p, 1, [I.uniform_region(1)])
+    m = oracle_mod.Mesh(d)
+    mat = dict(I.TI64_NONLIN, lumping=I.LUMP_QUADRATURE if p == 1 else I.LUMP_NODAL)
+    dt, nst, s, Tt = 5e-6, 12, 1.05, 3000.0
+    T0 = I.melt_pool_field(m.dof_xyz(), (0.25e-3, 0.125e-3, 0.25e-3), 3600.0, 90e-6, seed=11, noise=0.01)
+    ls = I.c4_laser([[180.0, 220.0, 240.0]], n_seg=3, steps_per_seg=4, dt=dt, v=0.5, y=0.125e-3)
+    _, g0 = m.adjoint(mat, T0, ls, 0.0, dt, nst, s=s, T_target=Tt)
+    m.set_surface_loss(I.SURFACE_LOSS)
+    J, g = m.adjoint(mat, T0, ls, 0.0, dt, nst, s=s, T_target=Tt)
+    assert J > 0 and np.all(np.isfinite(g))
+
+    def obj(ls_, s_):
+        return m.objective(mat, T0, ls_, 0.0, dt, nst, s=s_, T_target=Tt)
+
+    for k in range(4):
+        pw = ls["power"].copy()
+        if k < 3:
+            h = 1e-4 * pw[0, k]
+            lp, lm = dict(ls, power=pw.copy()), dict(ls, power=pw.copy())
+            lp["power"][0, k] += h
+            lm["power"][0, k] -= h
+            fd = (obj(lp, s) - obj(lm, s)) / (2 * h)
+        else:
+            h = 1e-4 * s
+            fd = (obj(ls, s + h) - obj(ls, s - h)) / (2 * h)
+        assert abs(g[k] - fd) < 1e-5 * abs(fd), (k, g[k], fd)
+        assert abs(g[k] - g0[k]) > 0.05 * abs(fd), (k, g[k], g0[k])
+
+
 @pytest.mark.parametrize("p", [1, 2])
 def test_surface_loss_of_a_constant_field(oracle_mod, p):
     """Constant T: the boundary term is -q(T) int_top N_i dA: it sums to -q(T) times the top

@@ -317,6 +317,41 @@ def test_step_transpose_dot_product(oracle_mod, p, mat):
     assert np.max(np.abs(Jv - v)) >= 0.1 * np.max(np.abs(v))
 
 
+@pytest.mark.parametrize("p", [1, 2])
+def test_step_transpose_dot_product_with_surface_loss(oracle_mod, p):
+    """The dot-product test of the transposed step with radiation and evaporation on the top
+    surface (field 2600-3700 K: evaporation active, below the cap), hanging nodes on the top:
+    <(J - I) v, w> = <v, (J^T - I) w>, and the loss's face term contributes far more than the
+    test's tolerance (a dropped term fails)."""
+    regions = [(I.BALL, (0.3e-3, 0.25e-3, 0.25e-3), (0, 0, 0), 100e-6, 2)]
+    desc = I.mesh_desc((4, 2, 2), (125e-6,) * 3, p, 2, regions)
+    m = oracle_mod.Mesh(desc)
+    assert m.n_hanging > 0
+    mat = I.TI64_CONST
+    rng = np.random.default_rng(15)
+    T = I.smooth_field(m.dof_xyz(), seed=19, lo=2600.0, hi=3700.0)
+    free = m.tables()["dirichlet"] == 0
+    T[~free] = mat["T_dirichlet"]
+    v = rng.normal(size=m.n_dofs) * free
+    w = rng.normal(size=m.n_dofs) * free
+    ls = I.laser([(0.1e-3, 0.25e-3, 0.4e-3, 0.25e-3, 0.0, 1e-3)], [200.0])
+    lam, _ = m.lambda_max(mat, rng.normal(size=m.n_dofs))
+    dt, t = 0.3 * 2.0 / lam, 3e-8
+    JTw0 = m.step_transpose(mat, T, ls, t, dt, w)
+    m.set_surface_loss(I.SURFACE_LOSS)
+
+    def cd(eps):
+        return (m.explicit(mat, T + eps * v, ls, t, dt, 1) - m.explicit(mat, T - eps * v, ls, t, dt, 1)) / (2 * eps)
+
+    eps = 1e-2
+    Jv = (4 * cd(eps / 2) - cd(eps)) / 3
+    JTw = m.step_transpose(mat, T, ls, t, dt, w)
+    lhs, rhs = np.dot(Jv - v, w), np.dot(v, JTw - w)
+    scale = np.sum(np.abs((Jv - v) * w))
+    assert abs(lhs - rhs) <= 1e-8 * scale, (lhs, rhs, scale)
+    assert abs(np.dot(v, JTw - JTw0)) > 1e3 * 1e-8 * scale
+
+
 # ---- objective ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("p", [1, 2])
