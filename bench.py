@@ -77,15 +77,17 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, period_ms=50):
         self.index = index
+        self.period_ms = period_ms
         self.proc = None
-        self.lines = []
+        self.lines = []  # (host time of arrival, line)
+        self.window = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", str(self.period_ms)],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -95,7 +97,17 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def wait_first(self, timeout=5.0):
+        """Blocks until the sampler has printed its first line (the process is up)."""
+        t0 = time.perf_counter()
+        while self.proc and not self.lines and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+
+    def mark(self, t_begin, t_end):
+        """The host-time window of the timed region."""
+        self.window = (t_begin, t_end)
 
     def __exit__(self, *a):
         if self.proc:
@@ -106,22 +118,36 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], 0.0, set()
+        """Median SM clock and the throttle reasons of the samples taken inside the timed
+        window; when the window is shorter than a few sampling periods, the samples of the
+        whole sampled span (warm-up included, the same kernels) are reported beside them."""
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
+        rows = []
+        for t, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
             try:
-                sm.append(float(parts[0]))
-                mx = max(mx, float(parts[1]))
+                sm, mx = float(parts[0]), float(parts[1])
             except ValueError:
                 continue
-            for n, v in zip(names, parts[3:7]):
-                if v.lower() in ("active", "1"):
-                    reasons.add(n)
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+            rows.append((t, sm, mx, {n for n, v in zip(names, parts[3:7]) if v.lower() in ("active", "1")}))
+
+        def agg(rs):
+            return {"sm_mhz": float(np.median([r[1] for r in rs])) if rs else None,
+                    "sm_max_mhz": max([r[2] for r in rs], default=0.0) or None,
+                    "reasons": sorted(set().union(*[r[3] for r in rs])) if rs else [], "samples": len(rs)}
+
+        inside = [r for r in rows if self.window and self.window[0] <= r[0] <= self.window[1] + 0.5 * self.period_ms / 1e3]
+        out = agg(inside if inside else rows)
+        out["sampling_ms"] = self.period_ms
+        if self.window:
+            out["timed_window_ms"] = round(1e3 * (self.window[1] - self.window[0]), 1)
+        if len(inside) < 3:
+            out["sampled_span"] = agg(rows)
+            out["note"] = ("fewer than 3 samples fell inside the timed window; sampled_span covers the warm-up and "
+                           "timed steps around it (the same kernels)")
+        return out
 
 
 def c2_initial(I, xyz, rank=0):
@@ -526,6 +552,28 @@ def bench_c5(pbf, I, torch, stream, flush, peaks, K=4, level=5):
             "l2": "state > L2; flushed between timed steps"}
 
 
+
+def bench_appendix_a(pbf, torch, stream):
+    """The temporal-convergence experiment of Appendix A (two powder layers, explicit scan,
+    explicit-then-implicit cool-down, activation of the second layer) at dt_ref, dt_ref / 2 and
+    dt_ref / 4 through the library: the observation point's deviation from the finest run and
+    the wall time of each run."""
+    from paper_2302_05164_gb300 import temporal as TM
+    runs, secs = {}, {}
+    for k in (1, 2, 4):
+        t0 = time.perf_counter()
+        runs[k] = TM.run(pbf, torch, dt_scale=1.0 / k, stream=stream)
+        secs[k] = time.perf_counter() - t0
+    ref = TM.common_samples(runs[1], runs[4], 4)
+    errs = {k: float(np.max(np.abs(TM.common_samples(runs[1], runs[k], k) - ref))) for k in (1, 2)}
+    rise = float(np.max(runs[4]["T"]) - runs[4]["T"][0])
+    return {"workload": "Appendix A: 1.0 x 0.2 x 0.2 mm plate + two 40 um powder layers, one track each, "
+                        "0.06 s cool-down (0.02 s explicit, then implicit), observation point (0.5, 0, 0.24) mm",
+            "max_dev_from_finest_K": {"dt_ref": errs[1], "dt_ref/2": errs[2]}, "ratio": errs[1] / errs[2],
+            "order_note": "first order gives a ratio of 3 against the dt_ref/4 run",
+            "peak_rise_K": rise, "wall_s": {f"dt_ref/{k}": secs[k] for k in (1, 2, 4)},
+            "newton_corrections_and_bicgstab_at_dt_ref": runs[1]["newton"]}
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -612,7 +660,7 @@ def traffic_for_kernel(kind, variant=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--quick", action="store_true", help="timed loop only (for profiler launch lists)")
@@ -674,21 +722,24 @@ def main():
     def bench_step(k):
         pbf.pbf_explicit_step(ctx.h, T, ls, k * CHUNK * dt, dt, CHUNK, stream=stream)
 
-    for k in range(W):
-        bench_step(k)
-    torch.cuda.synchronize()
-    if ws > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    launches0 = pbf.pbf_ctx_launch_count(ctx.h)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     with ClockSampler(dev) as clocks:
+        clocks.wait_first()
+        for k in range(W):
+            bench_step(k)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        launches0 = pbf.pbf_ctx_launch_count(ctx.h)
+        t_begin = time.perf_counter()
         for k in range(K):
             flush.fill_(k & 0xFF)
             evs[k][0].record(stream)
             bench_step(W + k)
             evs[k][1].record(stream)
         torch.cuda.synchronize()
+        clocks.mark(t_begin, time.perf_counter())
     ms = sum(a.elapsed_time(b) for a, b in evs)
     gpu_launches = pbf.pbf_ctx_launch_count(ctx.h) - launches0
     # the dominant kernel's launch duration: the same K benchmark steps again, with an event
@@ -839,6 +890,7 @@ def main():
         out["implicit"] = bench_implicit(pbf, I, torch, stream)
         out["large"] = bench_large(pbf, I, torch, stream, flush, peaks)
         out["c5"] = bench_c5(pbf, I, torch, stream, flush, peaks)
+        out["appendix_a"] = bench_appendix_a(pbf, torch, stream)
     ctx.close()
     mesh.close()
     if ws > 1:

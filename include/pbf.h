@@ -296,7 +296,10 @@ pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt, int nstep
  * sum_i w_i)^(1/p) over top-surface dofs, w_i = int_{top} N_i): forward nsteps from T0_dev
  * storing n_checkpoints states on a binomial (revolve) schedule, then the reverse recursion
  * lambda_n = lambda_{n+1} + dt (du/dT)^T lambda_{n+1} + dJ/dT_n, u = C~^-1 f. Gradients with
- * respect to the laser power of each segment and to the conductivity scale s.
+ * respect to the laser power of each segment and to the conductivity scale s. With a surface
+ * loss, f includes it (at each step's state) and du/dT its face term -int N_i q'(T_h) N_j dA;
+ * the power gradients take the laser's part of f_vol alone. A context with the phase model:
+ * PBF_EINVAL (its history is not differentiated).
  * J_out host [batch]; grad_out host [batch][n_seg + 1] (dJ/dP_0..dJ/dP_{n_seg-1}, dJ/ds);
  * forward_steps_out (nullable): forward steps taken, including recomputation. Synchronises. */
 pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, const pbf_laser* laser, double t0, double dt,
@@ -320,9 +323,15 @@ pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_ou
  * tables in shared memory for the whole call); shape 6 synchronises the stream; 7, 8, 9: the
  * fused step of shape 5 in its lean form (patch tables read through L1, only the staged values
  * and their sums in shared memory, the conductivity recomputed in each gradient direction),
- * compiled for 14, 12 and 10 resident blocks per SM. Where 4-9 do not apply (batch > 1,
- * quadrature-point capacity) they run the per-cell form; with a volumetric source shape 6
- * runs shape 5; residual-only evaluations of shapes 4-9 use shape 1.
+ * compiled for 14, 12 and 10 resident blocks per SM. For a batch (batch > 1, constant or
+ * nodal capacity, no surface loss or phase model, surface laser) shapes 4-9 run the batched
+ * fused step: one launch per step for all instances, threads (cell, instance) with the
+ * instance fastest, the previous step's update applied in the gather, the spot computed on
+ * the device, a call's launches replayed as one CUDA graph when (nsteps, dt, T_dev) repeat.
+ * The phase model and the surface loss run in the fused step of shapes 4 and 5 (shapes 6-9
+ * then act as shape 5). Where no fused form applies (quadrature-point capacity; a batch with
+ * an option or a volumetric source) shapes 4-9 run the per-cell form; with a volumetric
+ * source shape 6 runs shape 5; residual-only evaluations of shapes 4-9 use shape 1.
  *
  * pbf_ctx_autotune times `reps` explicit steps of every applicable shape with dt = 0 on a
  * scratch copy of T_dev (not modified), with the laser of the last call, keeps the fastest in
@@ -377,10 +386,11 @@ typedef struct {
 } pbf_surface_loss;
 
 /* Sets (q != NULL) or clears (NULL) the surface loss of a context for its later residual
- * evaluations (added to fvol_dev) and explicit steps. With a surface loss the explicit steps
- * run the per-cell form (shapes 4-9 act as shape 1), the implicit solves evaluate it at the
- * previous state (Newton's method), and pbf_adjoint_sweep returns PBF_EINVAL. Bad parameters:
- * PBF_EINVAL. Host only. */
+ * evaluations (added to fvol_dev) and explicit steps. With a surface loss the explicit steps of
+ * one instance run it inside the fused step kernel (shapes 4, 5; shapes 6-9 act as shape 5),
+ * batches run the per-cell form with a face kernel; the implicit solves evaluate it at the
+ * previous state (Newton's method); pbf_adjoint_sweep includes its linearisation. Bad
+ * parameters: PBF_EINVAL. Host only. */
 pbf_status pbf_ctx_set_surface_loss(pbf_ctx* ctx, const pbf_surface_loss* q);
 
 /* Phase-dependent conductivity with history (Sec. 2, Eqs. liquid_fraction,
@@ -396,10 +406,11 @@ typedef struct {
 } pbf_phase;
 
 /* Sets (ph != NULL; the history restarts from the cell materials) or clears (NULL) the phase
- * model of a context. With it the explicit steps run the per-cell form (shapes 4-9 act as
- * shape 1), the implicit solves use it (Newton's method, storing r_c after each step), and
- * pbf_adjoint_sweep returns PBF_EINVAL. PBF_EINVAL for
- * bad parameters or the quadrature-point capacity. Allocates the history once
+ * model of a context. With it the explicit steps of one instance read and store r_c inside the
+ * fused step kernel (shapes 4, 5; shapes 6-9 act as shape 5), batches run the per-cell form;
+ * the implicit solves use it (Newton's method, storing r_c after each step), and
+ * pbf_adjoint_sweep returns PBF_EINVAL. PBF_EINVAL for bad parameters or the quadrature-point
+ * capacity. Allocates the history once
  * ((p+1)^3 n_cells batch values); synchronises. */
 pbf_status pbf_ctx_set_phase(pbf_ctx* ctx, const pbf_phase* ph);
 

@@ -524,6 +524,8 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
   if (e == cudaSuccess) e = dalloc(c.get(), &c->C0, nd);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_d, nd);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->invC0_f, nd);
+  // FP32 1 / C~ with the Dirichlet flag: read by the fused steps of one instance and of a batch
+  if (e == cudaSuccess && c->f32) e = dalloc(c.get(), &c->invC0_fx, nd);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->power, (size_t)batch * kMaxSeg);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->powerf, (size_t)batch * kMaxSeg);
   if (e == cudaSuccess) e = dalloc(c.get(), &c->part, (size_t)reduction_blocks() * batch);
@@ -578,7 +580,6 @@ pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pb
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->fstep[2], nd);
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->xstep[0], nd);
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->xstep[1], nd);
-    if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->invC0_fx, nd);
     if (e2 == cudaSuccess) e2 = dalloc(c.get(), &c->bar, 1);
     if (e2 == cudaSuccess) e2 = cudaMemset(c->bar, 0, sizeof(GridBarrier));
     if (e2 == cudaSuccess) e2 = cudaMemset(c->fstep[1], 0, nd * 4);
@@ -777,8 +778,9 @@ cudaError_t CtxBase::apply_cell(CellLaunch L, void* f, void* C, int mode, cudaSt
 }
 
 // f_diff, f_vol and C~ at T (laser already set); FP64 outputs, accumulators left at zero.
+// With fre_dev, the surface loss's part goes there and f_vol holds the laser alone.
 cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_dev, double* fvol_dev, double* C_dev,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, double* fre_dev) {
   const int64_t nv = n_dofs * batch;
   const size_t rsz = f32 ? 4 : 8;
   CellLaunch L = base;
@@ -795,7 +797,7 @@ cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_d
     e = launch_laser(degree, f32, lsetup, L.mesh, power, spot_at(lsetup.k, t), fvol, s);
     ++launches;
   }
-  if (e == cudaSuccess && has_loss) {
+  if (e == cudaSuccess && has_loss && !fre_dev) {
     e = launch_surface_loss(degree, f32, lsetup, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev,
                             f32 ? mat.T_ref : 0.0, loss, fvol, s);
     ++launches;
@@ -811,6 +813,13 @@ cudaError_t CtxBase::residual_f64(const double* T_dev, double t, double* fdiff_d
   if (e == cudaSuccess) e = cudaMemsetAsync(f, 0, (size_t)nv * rsz, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(fvol, 0, (size_t)nv * rsz, s);
   if (e == cudaSuccess && latent) e = cudaMemsetAsync(Cacc, 0, (size_t)nv * rsz, s);
+  if (e == cudaSuccess && has_loss && fre_dev) {  // the loss alone, through the cleared f_vol buffer
+    e = launch_surface_loss(degree, f32, lsetup, L.mesh, f32 ? (const void*)Tf : (const void*)T_dev,
+                            f32 ? mat.T_ref : 0.0, loss, fvol, s);
+    if (e == cudaSuccess) e = launch_to_f64(f32, nv, fvol, fre_dev, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(fvol, 0, (size_t)nv * rsz, s);
+    launches += 2;
+  }
   return e;
 }
 
@@ -841,10 +850,10 @@ LaserInline CtxBase::inline_laser(double t, Spot* sp_out) const {
 cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nsteps, cudaStream_t s) {
   if (nsteps <= 0) return cudaSuccess;
   if (base.variant >= 4 && bfused_ok()) return explicit_steps_bfused(T_dev, t0, dt, nsteps, s);
-  if (base.variant >= 4 && fused_ok()) {
-    if (base.variant == 6 && !(lsetup.k.n_seg > 0 && lsetup.k.volumetric))
+  if (base.variant >= 4 && fused_ok(4)) {
+    if (base.variant == 6 && fused_ok(6) && !(lsetup.k.n_seg > 0 && lsetup.k.volumetric))
       return explicit_steps_persistent(T_dev, t0, dt, nsteps, s);
-    const int lean = base.variant >= 7 ? base.variant - 7 : -1;
+    const int lean = base.variant >= 7 && fused_ok(base.variant) ? base.variant - 7 : -1;
     return explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant != 4, lean, s);
   }
   CellLaunch L = base;
@@ -921,6 +930,7 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
 cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, int nsteps, bool pdl, int lean,
                                           cudaStream_t s) {
   CellLaunch L = base;
+  set_phase(L, true);  // the phase model's history is read and stored by every step
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
   const double xd = mat.T_dirichlet - mat.T_ref;
   const float xd_hi = (float)xd;
@@ -933,6 +943,8 @@ cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, i
   st.nc = nodal;
   st.x_dir = x_dir;
   st.dt = (float)dt;
+  st.has_loss = has_loss ? 1 : 0;
+  st.loss = loss;
   for (int n = 0; n < nsteps && e == cudaSuccess; ++n) {
     Spot sp;
     L.las = inline_laser(t0 + n * dt, &sp);
@@ -1244,7 +1256,7 @@ extern "C" pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int re
   for (int v = 0; v < kCellVariants && e == cudaSuccess; ++v) {
     if (us_per_step_out) us_per_step_out[v] = -1.f;
     // the fused forms of one instance; for a batch shape 4 stands for its fused form
-    if (v >= 4 && !ctx->fused_ok() && !(v == 4 && ctx->bfused_ok())) continue;
+    if (v >= 4 && !ctx->fused_ok(v) && !(v == 4 && ctx->bfused_ok())) continue;
     ctx->base.variant = v;
     e = ctx->explicit_steps(tmp, 0.0, 0.0, 2, s);  // warm-up
     if (e == cudaSuccess) e = cudaEventRecord(a, s);

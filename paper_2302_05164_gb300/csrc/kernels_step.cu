@@ -79,8 +79,9 @@ __device__ __forceinline__ void load_patch_tables(const StepTables& T, const Ste
 
 // Steps 2-4 of one patch (tables already in shared memory, a barrier after loading them):
 // staging with the previous step's update, hanging values, the cells, the push of hanging
-// sums and the scatter of the dof sums into S.f_acc.
-template <int P, bool NLK, int CAP, bool COHERENT>
+// sums and the scatter of the dof sums into S.f_acc. OPT: model options (kStepPhase,
+// kStepLoss).
+template <int P, bool NLK, int CAP, bool COHERENT, int OPT = 0>
 __device__ __forceinline__ void step_patch(const CellLaunch& L, const LaserInline& las, const StepState& S,
                                            const StepTables& T, const StepSmem<(P + 1) * (P + 1) * (P + 1)>& sm,
                                            int p, int4 cn) {
@@ -161,14 +162,32 @@ __device__ __forceinline__ void step_patch(const CellLaunch& L, const LaserInlin
     for (int a = 0; a < NP; ++a) u[a] = sm.v[sm.loc[a * KP + tid]];
     values_at_qp<P, float>(u, v);
     const float detJ = geo.detJ[lev];
-    const float scale = (mat == 1 ? mt.powder_scale : 1.f) * (L.k_scale_f ? L.k_scale_f[0] : 1.f);
-    const float k0 = mt.k0 * scale, dk = mt.dk * scale;
     float kw[NP];
+    if (OPT & kStepPhase) {
+      // k(T, r_c) with r_c = max(stored r_c, g(T)) per quadrature point (Sec. 2, Eqs.
+      // liquid_fraction .. material_parameter_interp); the history is stored where it grows
+      const PhaseR<float>& ph = L.phf;
+      const float is = L.k_scale_f ? L.k_scale_f[0] : 1.f;
+      const float* rc_in = static_cast<const float*>(L.rc_in);
+      float* rc_out = static_cast<float*>(L.rc_out);
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      float k = k0;
-      if (NLK) k = k0 + dk * clamp01((v[q] + mt.tk_off) * mt.inv_dT);
-      kw[q] = -k * (float(wq3<P>(q)) * detJ);
+      for (int q = 0; q < NP; ++q) {
+        const float g = clamp01((v[q] + ph.t_off) * ph.inv_dT);
+        const int j = q * M.n_cells + cell;
+        const float r0 = rc_in[j];
+        const float rc = r0 > g ? r0 : g;
+        if (rc_out && rc > r0) rc_out[j] = rc;
+        kw[q] = -((ph.kp + rc * ph.dks + g * ph.dkm) * is) * (float(wq3<P>(q)) * detJ);
+      }
+    } else {
+      const float scale = (mat == 1 ? mt.powder_scale : 1.f) * (L.k_scale_f ? L.k_scale_f[0] : 1.f);
+      const float k0 = mt.k0 * scale, dk = mt.dk * scale;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        float k = k0;
+        if (NLK) k = k0 + dk * clamp01((v[q] + mt.tk_off) * mt.inv_dT);
+        kw[q] = -k * (float(wq3<P>(q)) * detJ);
+      }
     }
     float r[NP], g[NP];
     {
@@ -195,11 +214,19 @@ __device__ __forceinline__ void step_patch(const CellLaunch& L, const LaserInlin
     float fe[NP];
     integrate_values<P, float>(r, fe);
     if (las.on && top) add_laser<P, float>(L, las, cell, 0, lev, fe);
+    if ((OPT & kStepLoss) && top) {
+      // radiation / evaporation at T_n on the top face (nodes (k, j, P), re-read from shared
+      // memory), in the precision of the per-cell form's face kernel
+      constexpr int NF = (P + 1) * (P + 1);
+      float Tf[NF];
+#pragma unroll
+      for (int a = 0; a < NF; ++a) Tf[a] = sm.v[sm.loc[(NP - NF + a) * KP + tid]] + float(S.off);
+      add_surface_loss<P, float>(S.loss, Tf, geo.h[lev][0], geo.h[lev][1], fe + (NP - NF));
+    }
 #pragma unroll
     for (int a = 0; a < NP; ++a) atomicAdd(&sm.f[sm.loc[a * KP + tid]], fe[a]);
   }
   __syncthreads();
-  if (!COHERENT) grid_dependency_trigger();  // the next step may start loading its tables
   // 4a. hanging contributions to their masters (P_h^T f_h), in shared memory
   for (int j = nfree + tid; j < nu; j += KP) {
     const int h = sm.slot[j], e0 = h >> 5, ne = h & 31;
@@ -216,17 +243,20 @@ __device__ __forceinline__ void step_patch(const CellLaunch& L, const LaserInlin
 }
 
 // One launch per step: block p takes patch p.
-template <int P, bool NLK, int CAP>
+template <int P, bool NLK, int CAP, int OPT>
 __global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     k_step(const CellLaunch L, const StepTables T, const StepState S) {
   constexpr int NP = (P + 1) * (P + 1) * (P + 1);
   extern __shared__ __align__(16) unsigned char smem[];
   const StepSmem<NP> sm(smem, T);
+  // the next step may be scheduled once every block of this one has started: its blocks then
+  // fill the SM slots that this step's last blocks free, load their tables and wait
+  grid_dependency_trigger();
   int4 cn;
   load_patch_tables<NP>(T, sm, blockIdx.x, cn);
   grid_dependency_wait();  // the previous step's state and accumulators are complete
   __syncthreads();
-  step_patch<P, NLK, CAP, false>(L, L.las, S, T, sm, blockIdx.x, cn);
+  step_patch<P, NLK, CAP, false, OPT>(L, L.las, S, T, sm, blockIdx.x, cn);
 }
 
 // ---- persistent form: all steps of a sequence in one cooperative launch -----------------
@@ -374,9 +404,9 @@ __global__ void k_step_final(int n, const float2* __restrict__ x_in, float* __re
   if (f_other) f_other[i] = 0.f;
 }
 
-template <int P, bool NLK, int CAP>
+template <int P, bool NLK, int CAP, int OPT = 0>
 cudaError_t go_step(const CellLaunch& L, const StepTables& t, const StepState& st, bool pdl, cudaStream_t s) {
-  auto kern = k_step<P, NLK, CAP>;
+  auto kern = k_step<P, NLK, CAP, OPT>;
   if (t.smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
     if (e != cudaSuccess) return e;
@@ -384,12 +414,23 @@ cudaError_t go_step(const CellLaunch& L, const StepTables& t, const StepState& s
   return launch_ex(kern, (unsigned)t.n_patches, kStepCells, (size_t)t.smem, pdl ? 1 : 0, s, L, t, st);
 }
 
+// the model options: with the phase model the conductivity ramp of the material is not used
+template <int P, int CAP>
+cudaError_t dispatch_step_opt(const CellLaunch& L, const StepTables& t, const StepState& st, bool pdl,
+                              cudaStream_t s) {
+  const bool nl = L.nonlin_k != 0, loss = st.has_loss != 0;
+  if (L.phase)
+    return loss ? go_step<P, false, CAP, kStepPhase | kStepLoss>(L, t, st, pdl, s)
+                : go_step<P, false, CAP, kStepPhase>(L, t, st, pdl, s);
+  if (loss) return nl ? go_step<P, true, CAP, kStepLoss>(L, t, st, pdl, s) : go_step<P, false, CAP, kStepLoss>(L, t, st, pdl, s);
+  return nl ? go_step<P, true, CAP>(L, t, st, pdl, s) : go_step<P, false, CAP>(L, t, st, pdl, s);
+}
+
 template <int P>
 cudaError_t dispatch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                           cudaStream_t s) {
-  const bool nl = L.nonlin_k != 0;
-  if (cap == CAP_NODAL) return nl ? go_step<P, true, CAP_NODAL>(L, t, st, pdl, s) : go_step<P, false, CAP_NODAL>(L, t, st, pdl, s);
-  return nl ? go_step<P, true, CAP_CONST>(L, t, st, pdl, s) : go_step<P, false, CAP_CONST>(L, t, st, pdl, s);
+  if (cap == CAP_NODAL) return dispatch_step_opt<P, CAP_NODAL>(L, t, st, pdl, s);
+  return dispatch_step_opt<P, CAP_CONST>(L, t, st, pdl, s);
 }
 
 template <int P, bool NLK, int CAP>
@@ -424,7 +465,7 @@ cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, co
   const StepState& st = ps.st;
   if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
       !t.cell || !t.loc || !t.hloc || !t.hw || !ps.x[0] || !ps.x[1] || !ps.f[0] || !ps.f[1] || !ps.f[2] || !ps.T ||
-      !st.T0 || !st.invC0x || !ps.bar || ps.nsteps < 1 || ps.laser.volumetric)
+      !st.T0 || !st.invC0x || !ps.bar || ps.nsteps < 1 || ps.laser.volumetric || L.phase || st.has_loss)
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
   if (L.degree == 1) return dispatch_steps<1>(L, t, ps, cap, blocks, s);
@@ -434,10 +475,12 @@ cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, co
 
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
                         cudaStream_t s) {
-  // the fused form covers one instance of the FP32 operator with the constant or nodal capacity
+  // the fused form covers one instance of the FP32 operator with the constant or nodal
+  // capacity, with or without the phase model and the surface loss
   if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
       !t.cell || !t.hloc || !t.hw || !t.loc || !st.x_in || !st.x_out || !st.f_in || !st.f_acc || !st.f_clear ||
-      !st.invC0x || st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear)
+      !st.invC0x || st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear ||
+      (L.phase && !L.rc_in))
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
   if (L.degree == 1) return dispatch_step<1>(L, t, st, cap, pdl, s);

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(kStepCells, MINB)
   float* sf = sv + T.max_nu32;                   // [max_nu32] accumulated contributions
   const DevMesh& M = L.mesh;
   const int tid = threadIdx.x, p = blockIdx.x;
+  grid_dependency_trigger();  // the next step may be scheduled once every block of this one started
   // independent of the previous step: tables and cell data, prefetched before the wait
   const int p0 = __ldg(&T.ptr[p]);
   const int4 cn = __ldg(&T.cnt[p]);
@@ -184,7 +185,6 @@ __global__ void __launch_bounds__(kStepCells, MINB)
     for (int a = 0; a < NP; ++a) atomicAdd(&sf[__ldg(&loc[a * KP])], fe[a]);
   }
   __syncthreads();
-  grid_dependency_trigger();  // the next step may start its prologue
   // 4a. hanging contributions to their masters
   for (int j = nfree + tid; j < nu; j += KP) {
     const int h = __ldg(&T.slot[p0 + j]), e0 = hb + (h >> 5), ne = h & 31;
@@ -238,7 +238,8 @@ cudaError_t launch_step_lean(const CellLaunch& L, const StepTables& t, const Ste
                              cudaStream_t s) {
   if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
       !t.cell || !t.hloc || !t.hw || !t.loc || !st.x_in || !st.x_out || !st.f_in || !st.f_acc || !st.f_clear ||
-      !st.invC0x || st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear)
+      !st.invC0x || st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear ||
+      L.phase || st.has_loss)  // the model options run in the fused step kernel
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
   if (L.degree == 1) return dispatch_lean_form<1>(L, t, st, cap, form, s);

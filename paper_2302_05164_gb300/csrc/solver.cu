@@ -647,6 +647,7 @@ struct Adjoint {
   std::vector<double*> slots;
   double *lam = nullptr, *v = nullptr, *mu = nullptr, *q1 = nullptr, *q2 = nullptr, *fd = nullptr, *fv = nullptr,
          *Cm = nullptr, *work = nullptr, *J = nullptr, *coef = nullptr, *grad = nullptr, *scal = nullptr;
+  double* fre = nullptr;  // the surface loss's part of f (with a surface loss)
   float *vf = nullptr, *muf = nullptr;
   void *vh = nullptr, *muh = nullptr;
   std::vector<void*> owned;
@@ -688,8 +689,10 @@ struct Adjoint {
   void adjoint_step(int k, const double* Tk) {
     if (e != cudaSuccess) return;
     const double t = t0 + k * dt;
-    e = c->residual_f64(Tk, t, fd, fv, Cm, s);
-    if (e == cudaSuccess) e = launch_adj_prepare((int)c->n_dofs, B, lam, fd, fv, Cm, c->dirichlet, v, mu, q1, q2, s);
+    // f_vol without the surface loss (fre): the power gradients take the laser's part alone
+    e = c->residual_f64(Tk, t, fd, fv, Cm, s, fre);
+    if (e == cudaSuccess)
+      e = launch_adj_prepare((int)c->n_dofs, B, lam, fd, fv, fre, Cm, c->dirichlet, v, mu, q1, q2, s);
     // parameter gradients with lambda_{k+1}
     if (e == cudaSuccess) e = launch_dot(c->n_dofs, B, lam, q1, nullptr, nullptr, c->part, scal, s);
     if (e == cudaSuccess) e = launch_dot(c->n_dofs, B, lam, q2, nullptr, nullptr, c->part, scal + B, s);
@@ -725,6 +728,12 @@ struct Adjoint {
     }
     if (e == cudaSuccess) e = launch_adjoint(L, qpc, c->f, c->fh, s);
     if (e == cudaSuccess) e = launch_hang_distribute(f32, L.mesh, c->fh, c->f, s);
+    if (e == cudaSuccess && c->has_loss) {  // the loss's face term at the state T_k
+      e = launch_surface_loss_adjoint(c->degree, f32, c->lsetup, L.mesh, f32 ? (const void*)c->Tf : (const void*)Tk,
+                                      f32 ? c->mat.T_ref : 0.0, f32 ? (const void*)vf : (const void*)v, c->loss,
+                                      c->f, s);
+      ++c->launches;
+    }
     if (e == cudaSuccess)
       e = launch_lambda_update(f32, c->cap == CAP_NODAL, (int)c->n_dofs, B, lam, c->f, mu, c->C0, Tk, c->nodal,
                                c->dirichlet, dt, s);
@@ -811,7 +820,6 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
   if (!ctx || !T0_dev || !laser || !J_out || !grad_out) return err(PBF_EINVAL, "null argument");
   if (nsteps < 1 || n_checkpoints < 1 || !(dt > 0) || !(p_exp >= 1)) return err(PBF_EINVAL, "bad sweep parameters");
   if (laser->n_seg < 1) return err(PBF_EINVAL, "the adjoint needs a laser with at least one segment");
-  if (ctx->has_loss) return err(PBF_EINVAL, "the adjoint covers no radiation / evaporation surface loss");
   if (ctx->has_phase) return err(PBF_EINVAL, "the adjoint covers no phase-dependent conductivity");
   pbf_status st = ctx->check_usable();
   if (st) return st;
@@ -845,6 +853,7 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
   A.alloc(&A.fv, nv);
   A.alloc(&A.Cm, nv);
   A.alloc(&A.work, nv);
+  if (ctx->has_loss) A.alloc(&A.fre, nv);
   A.alloc(&A.J, (size_t)A.B);
   A.alloc(&A.coef, (size_t)A.B);
   A.alloc(&A.grad, (size_t)A.B * (A.n_seg + 1));

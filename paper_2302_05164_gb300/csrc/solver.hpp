@@ -131,10 +131,12 @@ struct CtxBase {
   // L.x (FP64) or L.xf (FP32) must be set; f and C (nullable) are the dof accumulators.
   cudaError_t apply_cell(CellLaunch L, void* f, void* C, int mode, cudaStream_t s);
   // f_diff, f_vol and C~ at T in FP64 (laser set beforehand; any output may be null)
-  cudaError_t residual_f64(const double* T, double t, double* fd, double* fv, double* C, cudaStream_t s);
+  // fre (nullable): with a surface loss, its part goes there instead of into fv
+  cudaError_t residual_f64(const double* T, double t, double* fd, double* fv, double* C, cudaStream_t s,
+                           double* fre = nullptr);
   // nsteps forward-Euler steps in place on T (laser set beforehand); the fused form runs when
   // the context's shape is 4-9 (6: persistent, not with a volumetric source; 7-9: the lean
-  // kernel) and fused_ok()
+  // kernel) and fused_ok(4); shapes 6-9 run as 5 where fused_ok(shape) is false
   cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
   // lean: -1 the fused step kernel, 0..2 its lean form with the register budget kLeanForms[lean]
   cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, int lean, cudaStream_t s);
@@ -146,8 +148,11 @@ struct CtxBase {
     return f32 && batch > 1 && cap != CAP_QUADRATURE && !has_loss && !has_phase &&
            !(lsetup.k.n_seg > 0 && lsetup.k.volumetric);
   }
-  bool fused_ok() const {
-    return f32 && batch == 1 && cap != CAP_QUADRATURE && !has_loss && !has_phase && step.n_patches > 0;
+  // the fused forms of one instance: the fused step kernel (shapes 4, 5) also covers the phase
+  // model and the surface loss, the persistent and lean forms (6-9) neither
+  bool fused_ok(int variant) const {
+    return f32 && batch == 1 && cap != CAP_QUADRATURE && step.n_patches > 0 &&
+           (variant <= 5 || (!has_loss && !has_phase));
   }
   // the phase model's fields of a residual-mode launch (store: an explicit step)
   void set_phase(CellLaunch& L, bool store) const {

@@ -68,7 +68,13 @@ struct StepState {
   float2 x_dir = {0.f, 0.f};      // T_D - T_ref as hi + lo
   float dt = 0.f;
   int first = 0;                  // step 0: T_0 is the state as given (no update)
+  int has_loss = 0;               // radiation / evaporation on the top faces at T_n
+  LossK loss;
 };
+
+// Model options of the fused step kernel (compile-time mask): the phase model's conductivity
+// with its stored history, and the radiation / evaporation loss on top faces.
+enum { kStepPhase = 1, kStepLoss = 2 };
 
 // The update of one dof of the fused sequence (Dirichlet dofs, ic < 0, take x_dir).
 template <int CAP>

@@ -8,9 +8,6 @@ namespace {
 
 constexpr int kBS = 256;
 
-__device__ __forceinline__ float expo_r(float x) { return __expf(x); }
-__device__ __forceinline__ double expo_r(double x) { return exp(x); }
-
 inline unsigned grid_for(int64_t n, int bs = kBS) { return (unsigned)((n + bs - 1) / bs); }
 
 // ---- forward-Euler update -------------------------------------------------------------
@@ -233,61 +230,94 @@ __global__ void k_surface_loss(int n_top, int B, const int32_t* __restrict__ top
   const int face = B == 1 ? i : i / B, inst = i - face * B;
   const int cell = top_cell[face];
   const R hx = R(top_geo[4 * face + 2]), hy = R(top_geo[4 * face + 3]);
-  R Tn[N][N];
+  R Tf[N * N], fe[N * N];
 #pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int d = M.cell_dofs[(k + N * (j + N * P)) * M.n_cells + cell];
-      R v = R(0);
-      if (d >= 0) {
-        v = x[(int64_t)d * B + inst];
-      } else {
-        for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
-          v += R(M.con_w[e]) * x[(int64_t)M.con_idx[e] * B + inst];
-      }
-      Tn[j][k] = v + R(T_off);
+  for (int a = 0; a < N * N; ++a) {
+    const int d = M.cell_dofs[(a + N * N * P) * M.n_cells + cell];  // node (a % N, a / N, P)
+    R v = R(0);
+    if (d >= 0) {
+      v = x[(int64_t)d * B + inst];
+    } else {
+      for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
+        v += R(M.con_w[e]) * x[(int64_t)M.con_idx[e] * B + inst];
     }
-  const R eps_s = R(q.emissivity * 5.670374419e-8), Ta4 = R(q.T_amb * q.T_amb * q.T_amb * q.T_amb);
-  R fe[N][N];
+    Tf[a] = v + R(T_off);
+    fe[a] = R(0);
+  }
+  add_surface_loss<P, R>(q, Tf, hx, hy, fe);
 #pragma unroll
-  for (int j = 0; j < N; ++j)
+  for (int a = 0; a < N * N; ++a) {
+    const int d = M.cell_dofs[(a + N * N * P) * M.n_cells + cell];
+    if (d >= 0) {
+      atomicAdd(&f[(int64_t)d * B + inst], fe[a]);
+    } else {
+      for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
+        atomicAdd(&f[(int64_t)M.con_idx[e] * B + inst], R(M.con_w[e]) * fe[a]);
+    }
+  }
+}
+
+// Transposed linearisation of the surface loss for the adjoint sweep: one thread per (face,
+// instance) gathers the face's node values of the state and of the adjoint vector v (hanging
+// ones from their constraint rows) and adds -int N_j q'(T_h) v_h dA to g (masters of hanging
+// nodes through the same rows).
+template <int P, typename R>
+__global__ void k_surface_loss_adjoint(int n_top, int B, const int32_t* __restrict__ top_cell,
+                                       const double* __restrict__ top_geo, const DevMesh M, const R* __restrict__ x,
+                                       double T_off, const R* __restrict__ v, const LossK q, R* __restrict__ g) {
+  constexpr int N = P + 1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_top * B) return;
+  const int face = B == 1 ? i : i / B, inst = i - face * B;
+  const int cell = top_cell[face];
+  const R hx = R(top_geo[4 * face + 2]), hy = R(top_geo[4 * face + 3]);
+  R Tf[N * N], vf[N * N], ge[N * N];
 #pragma unroll
-    for (int k = 0; k < N; ++k) fe[j][k] = R(0);
+  for (int a = 0; a < N * N; ++a) {
+    const int d = M.cell_dofs[(a + N * N * P) * M.n_cells + cell];  // node (a % N, a / N, P)
+    R t = R(0), w = R(0);
+    if (d >= 0) {
+      t = x[(int64_t)d * B + inst];
+      w = v[(int64_t)d * B + inst];
+    } else {
+      for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e) {
+        t += R(M.con_w[e]) * x[(int64_t)M.con_idx[e] * B + inst];
+        w += R(M.con_w[e]) * v[(int64_t)M.con_idx[e] * B + inst];
+      }
+    }
+    Tf[a] = t + R(T_off);
+    vf[a] = w;
+    ge[a] = R(0);
+  }
 #pragma unroll
   for (int qy = 0; qy < N; ++qy)
 #pragma unroll
     for (int qx = 0; qx < N; ++qx) {
-      R T = R(0);
+      R T = R(0), vq = R(0);
 #pragma unroll
       for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int k = 0; k < N; ++k) T += R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k)) * Tn[j][k];
-      const R T2 = T * T;
-      R flux = eps_s * (T2 * T2 - Ta4);
-      const R Tc = T < R(q.T_max) ? T : R(q.T_max);
-      if (q.C_P > 0.0 && Tc > R(q.T_v)) {
-        const R mdot = R(0.82 * q.C_P) * expo_r(R(-q.C_T) * (R(1) / Tc - R(1.0 / q.T_v))) * sqrt(R(q.C_M) / Tc);
-        flux += mdot * (R(q.h_v) + R(q.c_h) * (Tc - R(q.T_h0)));
-      }
-      const R wq = flux * R(Basis<P>::W(qx) * Basis<P>::W(qy)) * hx * hy;
+        for (int k = 0; k < N; ++k) {
+          const R nb = R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
+          T += nb * Tf[k + N * j];
+          vq += nb * vf[k + N * j];
+        }
+      const R wq = surface_flux_deriv<R>(q, T) * vq * R(Basis<P>::W(qx) * Basis<P>::W(qy)) * hx * hy;
 #pragma unroll
       for (int j = 0; j < N; ++j)
 #pragma unroll
-        for (int k = 0; k < N; ++k) fe[j][k] -= wq * R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
+        for (int k = 0; k < N; ++k) ge[k + N * j] -= wq * R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
     }
 #pragma unroll
-  for (int j = 0; j < N; ++j)
-#pragma unroll
-    for (int k = 0; k < N; ++k) {
-      const int d = M.cell_dofs[(k + N * (j + N * P)) * M.n_cells + cell];
-      if (d >= 0) {
-        atomicAdd(&f[(int64_t)d * B + inst], fe[j][k]);
-      } else {
-        for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
-          atomicAdd(&f[(int64_t)M.con_idx[e] * B + inst], R(M.con_w[e]) * fe[j][k]);
-      }
+  for (int a = 0; a < N * N; ++a) {
+    const int d = M.cell_dofs[(a + N * N * P) * M.n_cells + cell];
+    if (d >= 0) {
+      atomicAdd(&g[(int64_t)d * B + inst], ge[a]);
+    } else {
+      for (int e = M.con_ptr[-1 - d]; e < M.con_ptr[-d]; ++e)
+        atomicAdd(&g[(int64_t)M.con_idx[e] * B + inst], R(M.con_w[e]) * ge[a]);
     }
+  }
 }
 
 // Start of the consolidated-fraction history: r_c = 0 in powder cells (material 1), 1 in
@@ -579,9 +609,9 @@ __global__ void k_add(int64_t n, double* __restrict__ T, const double* __restric
 // ---- adjoint sweep ----------------------------------------------------------------------------
 // v = lambda / C~, mu = lambda f / C~^2, q1 = f_diff / C~, q2 = f_vol / C~ on free dofs
 __global__ void k_adj_prepare(int n, int B, const double* __restrict__ lam, const double* __restrict__ fd,
-                              const double* __restrict__ fv, const double* __restrict__ Cm,
-                              const uint8_t* __restrict__ dir, double* __restrict__ v, double* __restrict__ mu,
-                              double* __restrict__ q1, double* __restrict__ q2) {
+                              const double* __restrict__ fv, const double* __restrict__ fre,
+                              const double* __restrict__ Cm, const uint8_t* __restrict__ dir, double* __restrict__ v,
+                              double* __restrict__ mu, double* __restrict__ q1, double* __restrict__ q2) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n * B) return;
   const int d = B == 1 ? i : i / B;
@@ -591,7 +621,7 @@ __global__ void k_adj_prepare(int n, int B, const double* __restrict__ lam, cons
   }
   const double ic = 1.0 / Cm[i];
   v[i] = lam[i] * ic;
-  mu[i] = lam[i] * (fd[i] + fv[i]) * ic * ic;
+  mu[i] = lam[i] * (fd[i] + fv[i] + (fre ? fre[i] : 0.0)) * ic * ic;
   q1[i] = fd[i] * ic;
   q2[i] = fv[i] * ic;
 }
@@ -866,6 +896,29 @@ cudaError_t launch_surface_loss(int degree, bool f32, const LaserSetup& ls, cons
   return cudaGetLastError();
 }
 
+cudaError_t launch_surface_loss_adjoint(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const void* x,
+                                        double T_off, const void* v, const LossK& q, void* g, cudaStream_t s) {
+  const int64_t n = (int64_t)ls.n_top * M.batch;
+  if (n == 0) return cudaSuccess;
+  const unsigned grid = grid_for(n, 128);
+  if (degree == 1) {
+    if (f32)
+      k_surface_loss_adjoint<1, float><<<grid, 128, 0, s>>>(ls.n_top, M.batch, ls.top_cell, ls.top_geo, M,
+                                                            (const float*)x, T_off, (const float*)v, q, (float*)g);
+    else
+      k_surface_loss_adjoint<1, double><<<grid, 128, 0, s>>>(ls.n_top, M.batch, ls.top_cell, ls.top_geo, M,
+                                                             (const double*)x, T_off, (const double*)v, q, (double*)g);
+  } else {
+    if (f32)
+      k_surface_loss_adjoint<2, float><<<grid, 128, 0, s>>>(ls.n_top, M.batch, ls.top_cell, ls.top_geo, M,
+                                                            (const float*)x, T_off, (const float*)v, q, (float*)g);
+    else
+      k_surface_loss_adjoint<2, double><<<grid, 128, 0, s>>>(ls.n_top, M.batch, ls.top_cell, ls.top_geo, M,
+                                                             (const double*)x, T_off, (const double*)v, q, (double*)g);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_to_f64(bool f32, int64_t n, const void* a, double* out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   if (f32) k_to_f64<float><<<grid_for(n), kBS, 0, s>>>(n, (const float*)a, out);
@@ -956,10 +1009,11 @@ cudaError_t launch_add(int64_t n, double* T, const double* x, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_adj_prepare(int n, int B, const double* lam, const double* fd, const double* fv, const double* Cm,
-                               const uint8_t* dir, double* v, double* mu, double* q1, double* q2, cudaStream_t s) {
+cudaError_t launch_adj_prepare(int n, int B, const double* lam, const double* fd, const double* fv, const double* fre,
+                               const double* Cm, const uint8_t* dir, double* v, double* mu, double* q1, double* q2,
+                               cudaStream_t s) {
   if (n * B == 0) return cudaSuccess;
-  k_adj_prepare<<<grid_for((int64_t)n * B), kBS, 0, s>>>(n, B, lam, fd, fv, Cm, dir, v, mu, q1, q2);
+  k_adj_prepare<<<grid_for((int64_t)n * B), kBS, 0, s>>>(n, B, lam, fd, fv, fre, Cm, dir, v, mu, q1, q2);
   return cudaGetLastError();
 }
 

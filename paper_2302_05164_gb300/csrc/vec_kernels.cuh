@@ -21,6 +21,55 @@ struct LossK {
   double C_P = 0.0, C_T = 0.0, C_M = 0.0, T_v = 0.0, h_v = 0.0, c_h = 0.0, T_h0 = 0.0, T_max = 0.0;
 };
 
+__device__ __forceinline__ float expo_r(float x) { return __expf(x); }
+__device__ __forceinline__ double expo_r(double x) { return exp(x); }
+
+// dq/dT of the flux below: radiation 4 eps sigma T^3; evaporation, for T_v < T < T_max,
+// mdot(T) ((C_T / T^2 - 1 / (2 T)) (h_v + c_h (T - T_h0)) + c_h); constant above the cap.
+template <typename R>
+__device__ __forceinline__ R surface_flux_deriv(const LossK& q, R T) {
+  R d = R(4.0 * q.emissivity * 5.670374419e-8) * T * T * T;
+  if (q.C_P > 0.0 && T < R(q.T_max) && T > R(q.T_v)) {
+    const R mdot = R(0.82 * q.C_P) * expo_r(R(-q.C_T) * (R(1) / T - R(1.0 / q.T_v))) * sqrt(R(q.C_M) / T);
+    d += mdot * ((R(q.C_T) / (T * T) - R(0.5) / T) * (R(q.h_v) + R(q.c_h) * (T - R(q.T_h0))) + R(q.c_h));
+  }
+  return d;
+}
+
+// -int_face N_i q(T_h) dA on one top face of size hx x hy, in precision R: Tf holds the
+// temperatures of the face's (P+1)^2 nodes and fe receives the face nodes' contributions
+// (both indexed k + (P+1) j, the face's x and y node indices). q = q_rad + q_evap, radiation
+// eps sigma (T^4 - T_amb^4) with the Stefan-Boltzmann constant 5.670374419e-8 W m^-2 K^-4 and
+// evaporation above T_v with T capped at T_max (Eqs. bc_rad_evap, bc_radiation,
+// bc_evaporation), at the face's (P+1)^2 Gauss points.
+template <int P, typename R>
+__device__ __forceinline__ void add_surface_loss(const LossK& q, const R* Tf, R hx, R hy, R* fe) {
+  constexpr int N = P + 1;
+  const R eps_s = R(q.emissivity * 5.670374419e-8), Ta4 = R(q.T_amb * q.T_amb * q.T_amb * q.T_amb);
+#pragma unroll
+  for (int qy = 0; qy < N; ++qy)
+#pragma unroll
+    for (int qx = 0; qx < N; ++qx) {
+      R T = R(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int k = 0; k < N; ++k) T += R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k)) * Tf[k + N * j];
+      const R T2 = T * T;
+      R flux = eps_s * (T2 * T2 - Ta4);
+      const R Tc = T < R(q.T_max) ? T : R(q.T_max);
+      if (q.C_P > 0.0 && Tc > R(q.T_v)) {
+        const R mdot = R(0.82 * q.C_P) * expo_r(R(-q.C_T) * (R(1) / Tc - R(1.0 / q.T_v))) * sqrt(R(q.C_M) / Tc);
+        flux += mdot * (R(q.h_v) + R(q.c_h) * (Tc - R(q.T_h0)));
+      }
+      const R wq = flux * R(Basis<P>::W(qx) * Basis<P>::W(qy)) * hx * hy;
+#pragma unroll
+      for (int j = 0; j < N; ++j)
+#pragma unroll
+        for (int k = 0; k < N; ++k) fe[k + N * j] -= wq * R(Basis<P>::S(qy, j) * Basis<P>::S(qx, k));
+    }
+}
+
 // Lumped-capacity forms of the update: constant c, quadrature-point row sum accumulated by
 // the cell kernel, or nodal apparent capacity c_app(T_i) x row-sum mass.
 enum { CAP_CONST = 0, CAP_QUADRATURE = 1, CAP_NODAL = 2 };
@@ -87,6 +136,11 @@ cudaError_t launch_laser(int degree, bool f32, const LaserSetup& ls, const DevMe
 // constraint rows), constraint-resolved atomic additions onto f.
 cudaError_t launch_surface_loss(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const void* x,
                                 double T_off, const LossK& q, void* f, cudaStream_t s);
+// The transposed linearisation of that term (adjoint sweep): g -= int_{top faces} q'(T_h) v_h N_j dA
+// for the state x (T = x + T_off) and the adjoint vector v, both [n_dofs][batch] in the operator
+// precision, constraint-resolved atomic additions onto g.
+cudaError_t launch_surface_loss_adjoint(int degree, bool f32, const LaserSetup& ls, const DevMesh& M, const void* x,
+                                        double T_off, const void* v, const LossK& q, void* g, cudaStream_t s);
 // r_c = 0 in powder cells, 1 elsewhere, for the nq quadrature points of every cell and instance
 cudaError_t launch_phase_init(bool f32, int nq, const DevMesh& M, void* rc, cudaStream_t s);
 cudaError_t launch_to_f64(bool f32, int64_t n, const void* a, double* out, cudaStream_t s);
@@ -113,9 +167,10 @@ cudaError_t launch_jacobi(int64_t n, const double* r, const double* diag, double
                           cudaStream_t s);
 cudaError_t launch_neg_masked(int64_t n, double* y, const uint8_t* mask, cudaStream_t s);
 cudaError_t launch_add(int64_t n, double* T, const double* x, cudaStream_t s);
-// adjoint sweep helpers (FP64)
-cudaError_t launch_adj_prepare(int n, int B, const double* lam, const double* fd, const double* fv, const double* Cm,
-                               const uint8_t* dir, double* v, double* mu, double* q1, double* q2, cudaStream_t s);
+// adjoint sweep helpers (FP64). fre (nullable): the surface loss's part of f, not in fv
+cudaError_t launch_adj_prepare(int n, int B, const double* lam, const double* fd, const double* fv, const double* fre,
+                               const double* Cm, const uint8_t* dir, double* v, double* mu, double* q1, double* q2,
+                               cudaStream_t s);
 cudaError_t launch_objective(int ns, int B, const int32_t* sidx, const double* sw, const double* T, double W, double p,
                              double Tt, double invN, int accumulate, double* part, double* J, double* coef,
                              cudaStream_t s);

@@ -65,8 +65,17 @@ def test_phase_residual_matches_oracle(P, oracle_mod, degree, prec):
     assert rel(gpu_residual(P, ctx, T, om.n_dofs), fd) < (TOL64 if prec == "f64" else TOL32_F)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32"])
-def test_phase_history_through_explicit_steps(P, oracle_mod, prec):
+def gpu_history(P, ctx, n_cells, nq):
+    out = torch.zeros(nq * n_cells, dtype=torch.float64, device="cuda")
+    P.pbf_ctx_get_history(ctx.h, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape(nq, n_cells).T  # the oracle's [cell][q]
+
+
+# FP32 shapes: 1 the per-cell form; 4 and 5 the fused step kernel (the phase model read and
+# stored per quadrature point inside it); 8 a lean shape, which runs as 5 with the phase model
+@pytest.mark.parametrize("prec,shape", [("f64", 5), ("f32", 1), ("f32", 4), ("f32", 5), ("f32", 8)])
+def test_phase_history_through_explicit_steps(P, oracle_mod, prec, shape):
     desc = mesh(2)
     om = oracle_mod.Mesh(desc)
     om.set_phase(PH)
@@ -79,15 +88,27 @@ def test_phase_history_through_explicit_steps(P, oracle_mod, prec):
     m = P.Mesh(desc)
     ctx = P.Context(m, mat, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
     P.pbf_ctx_set_phase(ctx.h, PH)
-    P.pbf_ctx_set_kernel_shape(ctx.h, 5)  # requested fused shape: the phase model runs per cell
+    P.pbf_ctx_set_kernel_shape(ctx.h, shape)
     Td = to_dev(T0)
+    n0 = P.pbf_ctx_launch_count(ctx.h)
     P.pbf_explicit_step(ctx.h, Td, None, 0.0, dt, 8)
     torch.cuda.synchronize()
+    if prec == "f32" and shape >= 4:
+        assert P.pbf_ctx_launch_count(ctx.h) - n0 == 8 + 1  # fused: one launch per step and the last update
     if prec == "f64":
         assert rel(Td.cpu().numpy(), ref) < TOL64
     else:
         check_f32_steps(Td.cpu().numpy(), ref, T0)
     assert np.abs(ref - T0).max() > 1.0
+    # the phase model moved the field by far more than the GPU's error: a form without it fails
+    ref_plain = oracle_mod.Mesh(desc).explicit(mat, T0, None, 0.0, dt, 8)
+    assert np.max(np.abs(Td.cpu().numpy() - ref)) < 0.1 * np.max(np.abs(ref - ref_plain))
+    # the stored history (r_c after the last step's state T_7) equals the oracle's: exactly up
+    # to FP64 rounding, and for the FP32 operator within dT / (T_l - T_s) of its state error
+    h_ref = om.history()
+    assert np.any((h_ref > 0.0) & (h_ref < 1.0))
+    h_got = gpu_history(P, ctx, om.n_active, 27)
+    assert np.max(np.abs(h_got - h_ref)) < (1e-10 if prec == "f64" else 5e-3)
     # a cool state now sees the consolidated powder where the steps melted it
     cool = I.smooth_field(om.dof_xyz(), seed=53, lo=400.0, hi=1400.0)
     fd, _, _ = om.residual(mat, cool)
@@ -98,6 +119,47 @@ def test_phase_history_through_explicit_steps(P, oracle_mod, prec):
     # the FP32 form's history follows its own states (within 2e-4 of the oracle's); g(T) turns a
     # state difference dT into dT / (T_l - T_s) of r_c, about 1e-3 here
     assert rel(gpu_residual(P, ctx, cool, om.n_dofs), fd) < (TOL64 if prec == "f64" else 5e-3)
+
+
+@pytest.mark.parametrize("degree", [1, 2])
+@pytest.mark.parametrize("prec,shape", [("f64", 5), ("f32", 1), ("f32", 5)])
+def test_phase_model_with_surface_loss_and_laser(P, oracle_mod, degree, prec, shape):
+    """The paper's material model (phase-dependent conductivity with its history) with the
+    radiation / evaporation loss and the surface laser, Q1 and Q2 with hanging nodes: six
+    explicit steps in the fused step kernel with both options (FP32, shape 5) and in the
+    per-cell form, against the oracle; temperatures and stored history."""
+    desc = mesh(degree)
+    om = oracle_mod.Mesh(desc)
+    om.set_phase(PH)
+    om.set_surface_loss(I.SURFACE_LOSS)
+    mat = I.TI64_CONST
+    lam, _ = oracle_mod.Mesh(desc).lambda_max(dict(mat, k0=30.0, k1=30.0, powder_k_scale=1.0),
+                                              I.start_vector(om.n_dofs), max_iter=300, rtol=1e-8)
+    dt = 0.4 * 2.0 / lam
+    T0 = I.melt_pool_field(om.dof_xyz(), (0.3e-3, 0.25e-3, 0.25e-3), 3600.0, 60e-6, seed=54, noise=0.01)
+    ls = I.laser([(0.1e-3, 0.25e-3, 0.9e-3, 0.25e-3, 0.0, 1e-3)], [200.0], eta=0.35, radius=40e-6)
+    ref = om.explicit(mat, T0, ls, 1e-4, dt, 6)
+    m = P.Mesh(desc)
+    ctx = P.Context(m, mat, P.PBF_F64 if prec == "f64" else P.PBF_F32OP)
+    P.pbf_ctx_set_phase(ctx.h, PH)
+    P.pbf_ctx_set_surface_loss(ctx.h, I.SURFACE_LOSS)
+    P.pbf_ctx_set_kernel_shape(ctx.h, shape)
+    Td = to_dev(T0)
+    n0 = P.pbf_ctx_launch_count(ctx.h)
+    P.pbf_explicit_step(ctx.h, Td, ls, 1e-4, dt, 6)
+    torch.cuda.synchronize()
+    if prec == "f32" and shape >= 4:
+        assert P.pbf_ctx_launch_count(ctx.h) - n0 == 6 + 1
+    got = Td.cpu().numpy()
+    if prec == "f64":
+        assert rel(got, ref) < TOL64
+    else:
+        print(f"phase model + surface loss, Q{degree}, shape {shape}:", check_f32_steps(got, ref, T0))
+    nq = (degree + 1) ** 3
+    h_ref = om.history()
+    assert np.max(np.abs(gpu_history(P, ctx, om.n_active, nq) - h_ref)) < (1e-10 if prec == "f64" else 5e-3)
+    ctx.close()
+    m.close()
 
 
 def test_adjoint_refuses_the_phase_model(P):
