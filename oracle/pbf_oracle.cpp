@@ -1016,13 +1016,29 @@ void plain_capacity(const Mesh& M, const or_material& mt, double s, const double
   plainC = G.C;
 }
 
+// The adjoint of the phase model's history across one step (reading: r_n = max(r_{n-1}, g(T_n))
+// per quadrature point is a state of the stepper; f_n uses k(T_n, r_n)). With M.rc holding the
+// history entering the step, r_{n-1}, and b = [g(T_n) > r_{n-1}] (the max takes g):
+//   rho_n = dt (du/dr_n)^T lam_{n+1} + rho_in,  (du/dr)^T lam at q = -W (k_s - k_p) s grad v . grad T,
+//   rho_out = (1 - b) rho_n                      (dr_n/dr_{n-1}, carried to the earlier step),
+//   g_hist_j = sum_q rho_n,q b_q g'(T_q) N_j(x_q) (dr_n/dT_n, added to lambda_n).
+// rho arrays are [active cell][quadrature point] like the history.
+struct HistAdj {
+  const std::vector<double>* rho_in = nullptr;
+  std::vector<double>* rho_out = nullptr;
+  std::vector<double>* g_hist = nullptr;
+  double dt = 0.0;
+};
+
 // g = (du/dT (T))^T lam for u = C~(T)^-1 f(T) on free dofs, u = 0 on Dirichlet dofs: the
 // transposed linearisation of Eq. (matrix_free_eval), with the conductivity term, the k'(T)
 // term L_e and the derivative of the lumped capacity (through c_app'(T) at the quadrature
 // points, or at the node for the nodal capacity). F holds f and C~ at T, plainC comes from
-// plain_capacity.
+// plain_capacity. With the phase model (ha non-null) k = k(T, r_n) with the history held fixed
+// in g (k'(T) = (k_m - k_s) g'(T) s), its dependence on the history through ha.
 void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, const double* T, const Fields& F,
-                             const std::vector<double>& plainC, const std::vector<double>& lam, std::vector<double>& g) {
+                             const std::vector<double>& plainC, const std::vector<double>& lam, std::vector<double>& g,
+                             HistAdj* ha = nullptr) {
   const size_t n = (size_t)M.n_dofs;
   const int p = M.p, npc = M.npc(), nq = p + 1;
   double gx[3], gw[3];
@@ -1031,8 +1047,13 @@ void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, con
   std::vector<double> Te(npc), ve(npc), me(npc), ge(npc), N(npc);
   std::vector<double> dN((size_t)npc * 3);
   // v = lambda/C~, mu = lambda f / C~^2 on free dofs
-  std::vector<double> v(n, 0.0), mu(n, 0.0);
+  std::vector<double> v(n, 0.0), mu(n, 0.0), he(npc);
   g.assign(n, 0.0);
+  const bool hist = ha && M.has_phase;
+  if (hist) {
+    ha->rho_out->assign(ha->rho_in->size(), 0.0);
+    ha->g_hist->assign(n, 0.0);
+  }
   for (size_t i = 0; i < n; ++i) {
     if (M.dirichlet[i]) continue;
     v[i] = lam[i] / F.C[i];
@@ -1047,6 +1068,7 @@ void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, con
     gather(M, c, v.data(), ve.data());
     gather(M, c, mu.data(), me.data());
     std::fill(ge.begin(), ge.end(), 0.0);
+    std::fill(he.begin(), he.end(), 0.0);
     for (int qz = 0; qz < nq; ++qz)
       for (int qy = 0; qy < nq; ++qy)
         for (int qx = 0; qx < nq; ++qx) {
@@ -1064,6 +1086,22 @@ void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, con
           }
           double kq = cond(mt, Tq, mat, s), dk = cond_deriv(mt, Tq, mat, s);
           double gvgT = gv[0] * gT[0] + gv[1] * gT[1] + gv[2] * gT[2];
+          if (hist) {
+            const or_phase& ph = M.phase;
+            const size_t iq = ((size_t)c * nq + (size_t)qz) * (size_t)(nq * nq) + (size_t)(qy * nq + qx);
+            const double z = (Tq - ph.T_s) / (ph.T_l - ph.T_s);
+            const double gz = std::min(1.0, std::max(0.0, z));
+            const double stored = M.rc[iq];
+            const double rc = std::max(stored, gz);
+            const bool b = gz > stored;
+            const double gp = (z > 0.0 && z < 1.0) ? 1.0 / (ph.T_l - ph.T_s) : 0.0;
+            kq = ((1.0 - rc) * ph.k_p + gz * ph.k_m + (rc - gz) * ph.k_s) * s;
+            dk = (ph.k_m - ph.k_s) * gp * s;
+            const double rho = ha->dt * (-W * (ph.k_s - ph.k_p) * s * gvgT) + (*ha->rho_in)[iq];
+            (*ha->rho_out)[iq] = b ? 0.0 : rho;
+            if (b)
+              for (int j = 0; j < npc; ++j) he[j] += rho * gp * N[j];
+          }
           double cap_term = nodal ? 0.0 : mt.rho * capp_deriv(mt, Tq) * muq;
           for (int j = 0; j < npc; ++j) {
             double gjv = 0.0;
@@ -1089,6 +1127,7 @@ void step_jacobian_transpose(const Mesh& M, const or_material& mt, double s, con
         }
     }
     scatter(M, c, ge.data(), g.data());
+    if (hist) scatter(M, c, he.data(), ha->g_hist->data());
   }
   // nodal lumping: dC~_i/dT_j = delta_ij rho M_i c_app'(T_i), M the lumped mass
   if (nodal)
@@ -1541,12 +1580,12 @@ int or_implicit_newton(void* h, const or_material* mt, double* T, double dt, int
 // with f_las the laser's part of f_vol. du/dT follows the linearisation of Eq.
 // (matrix_free_eval): the k term, the k'(T) term L_e and the derivative of the lumped capacity
 // through c_app'(T); with a surface loss also its face term -int N_i q'(T_h) N_j dA. All states
-// are stored. The phase model (history) is not covered: NaN.
+// are stored. With the phase model the history entering each step is stored too and its
+// adjoint is carried backward (HistAdj); the history is restored on return.
 // grad[n_seg + 1]: dJ/dP_0..dJ/dP_{n_seg-1}, dJ/ds.
 double or_adjoint(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0, double dt,
                   int nsteps, double T_target, double p_exp, double* grad) {
   Mesh* m = (Mesh*)h;
-  if (m->has_phase) return std::nan("");  // the adjoint does not cover the phase model
   const Mesh& M = *m;
   size_t n = (size_t)M.n_dofs;
   Objective obj;
@@ -1554,12 +1593,14 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
   obj.p_exp = p_exp;
   surface_weights(M, obj.w);
   for (double v : obj.w) obj.W += v;
-  std::vector<std::vector<double>> states;
+  std::vector<std::vector<double>> states, hists;  // hists[k]: the history entering step k
   states.emplace_back(T0, T0 + n);
   double J = 0.0;
   Fields F;
+  const std::vector<double> h_start = M.rc;  // restored on return: J and grad are functions of it
   for (int k = 0; k < nsteps; ++k) {
     std::vector<double> T = states.back();
+    if (M.has_phase) hists.push_back(M.rc);
     euler_step(M, *mt, s, T.data(), ls, t0 + k * dt, dt, F);
     states.push_back(T);
     double Mn = pnorm_max(obj, T.data(), nullptr);
@@ -1576,10 +1617,18 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
   std::vector<double> plainC;
   plain_capacity(M, *mt, s, T0, plainC);
   std::vector<double> g;
+  // the history's adjoint, carried from the later steps (zero after the last one)
+  std::vector<double> rho(M.has_phase ? M.rc.size() : 0, 0.0), rho_next, g_hist;
+  HistAdj ha;
+  ha.rho_in = &rho;
+  ha.rho_out = &rho_next;
+  ha.g_hist = &g_hist;
+  ha.dt = dt;
   for (int k = nsteps - 1; k >= 0; --k) {
     const double* T = states[(size_t)k].data();
     double t = t0 + k * dt;
-    residual(M, *mt, s, T, ls, t, F);
+    if (M.has_phase) M.rc = hists[(size_t)k];
+    residual(M, *mt, s, T, ls, t, F, true, M.has_phase ? 1 : 0);
     // parameter terms with lambda_{k+1}
     int seg = laser_segment(*ls, t);
     double gs = 0.0, gp = 0.0;
@@ -1592,7 +1641,7 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
     }
     grad[nseg] += gs;
     if (seg >= 0) grad[seg] += gp;
-    step_jacobian_transpose(M, *mt, s, T, F, plainC, lam, g);
+    step_jacobian_transpose(M, *mt, s, T, F, plainC, lam, g, M.has_phase ? &ha : nullptr);
     std::vector<double> lam_new(n, 0.0);
     if (k > 0) {
       double Mn = pnorm_max(obj, T, &gM);
@@ -1600,11 +1649,13 @@ double or_adjoint(void* h, const or_material* mt, double s, const double* T0, co
     }
     for (size_t i = 0; i < n; ++i) {
       double keep = M.dirichlet[i] ? 0.0 : lam[i];
-      lam_new[i] += keep + dt * g[i];
+      lam_new[i] += keep + dt * g[i] + (M.has_phase ? g_hist[i] : 0.0);
       if (M.dirichlet[i]) lam_new[i] = 0.0;
     }
     lam.swap(lam_new);
+    if (M.has_phase) rho.swap(rho_next);
   }
+  M.rc = h_start;
   return J;
 }
 
@@ -1618,6 +1669,10 @@ void or_step_transpose(void* h, const or_material* mt, double s, const double* T
   Mesh* m = (Mesh*)h;
   const Mesh& M = *m;
   const size_t n = (size_t)M.n_dofs;
+  if (M.has_phase) {  // the step's map also has the history as a state: not this test's map
+    std::fill(out, out + n, std::nan(""));
+    return;
+  }
   Fields F;
   residual(M, *mt, s, T, ls, t, F);
   std::vector<double> plainC, g, lam(n, 0.0);
@@ -1631,7 +1686,7 @@ void or_step_transpose(void* h, const or_material* mt, double s, const double* T
 double or_objective(void* h, const or_material* mt, double s, const double* T0, const or_laser* ls, double t0,
                     double dt, int nsteps, double T_target, double p_exp) {
   Mesh* m = (Mesh*)h;
-  if (m->has_phase) return std::nan("");  // as the adjoint
+  const std::vector<double> h_start = m->rc;  // restored on return, as in the adjoint
   size_t n = (size_t)m->n_dofs;
   Objective obj;
   obj.T_target = T_target;
@@ -1646,6 +1701,7 @@ double or_objective(void* h, const or_material* mt, double s, const double* T0, 
     double Mn = pnorm_max(obj, T.data(), nullptr);
     J += (Mn - T_target) * (Mn - T_target) / nsteps;
   }
+  m->rc = h_start;
   return J;
 }
 

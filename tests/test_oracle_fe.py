@@ -451,6 +451,57 @@ def test_adjoint_with_surface_loss_matches_central_differences(oracle_mod, p):
 
 
 @pytest.mark.parametrize("p", [1, 2])
+def test_adjoint_with_phase_model_matches_central_differences(oracle_mod, p):
+    """With the phase model (k(T, r_c), r_c = max(r_c, g(T)) stored by every step) the adjoint
+    carries the history's own adjoint backward (through the max where the stored value wins,
+    into lambda through g'(T) where g wins) and the gradient equals central differences of the
+    objective to 1e-5, on a brick with a powder top layer that the laser track partly melts (the
+    history grows at about a hundred quadrature points). The phase model moves every gradient
+    component by a large fraction; dropping the history term moves them by 1e-3 to 5e-2 (checked
+    when the pin was written). The adjoint and the objective leave the stored history as they
+    found it."""
+    ph = dict(I.PHASE, k_m=30.0, k_s=25.0)
+    d = I.mesh_desc((4, 2, 2), (125e-6,) * 3, p, 1, [I.uniform_region(1)], powder_z0=0.19e-3, powder_z1=1.0)
+    m = oracle_mod.Mesh(d)
+    mat = dict(I.TI64_CONST)
+    lam, _ = m.lambda_max(dict(mat, k0=30.0, k1=30.0, powder_k_scale=1.0), I.start_vector(m.n_dofs), max_iter=300,
+                          rtol=1e-8)
+    dt, nst, s, Tt = 0.3 * 2.0 / lam, 12, 1.05, 1800.0
+    T0 = I.melt_pool_field(m.dof_xyz(), (0.2e-3, 0.125e-3, 0.25e-3), 1950.0, 110e-6, seed=11, noise=0.01)
+    ls = I.c4_laser([[180.0, 220.0, 240.0]], n_seg=3, steps_per_seg=4, dt=dt, v=1.0, y=0.125e-3)
+    ls["seg"][:, 0] += 0.15e-3
+    ls["seg"][:, 2] += 0.15e-3
+    _, g0 = m.adjoint(mat, T0, ls, 0.0, dt, nst, s=s, T_target=Tt)
+    m.set_phase(ph)
+    h0 = m.history()
+    J, g = m.adjoint(mat, T0, ls, 0.0, dt, nst, s=s, T_target=Tt)
+    assert J > 0 and np.all(np.isfinite(g))
+    assert np.array_equal(m.history(), h0)
+    stepped = oracle_mod.Mesh(d)
+    stepped.set_phase(ph)
+    stepped.explicit(mat, T0, ls, 0.0, dt, nst, s=s)
+    assert np.sum(stepped.history() > h0) > 50  # the track melts powder: the history grows
+
+    def obj(ls_, s_):
+        return m.objective(mat, T0, ls_, 0.0, dt, nst, s=s_, T_target=Tt)
+
+    for k in range(4):
+        pw = ls["power"].copy()
+        if k < 3:
+            h = 1e-4 * pw[0, k]
+            lp, lm = dict(ls, power=pw.copy()), dict(ls, power=pw.copy())
+            lp["power"][0, k] += h
+            lm["power"][0, k] -= h
+            fd = (obj(lp, s) - obj(lm, s)) / (2 * h)
+        else:
+            h = 1e-4 * s
+            fd = (obj(ls, s + h) - obj(ls, s - h)) / (2 * h)
+        assert abs(g[k] - fd) < 1e-5 * abs(fd), (k, g[k], fd)
+        assert abs(g[k] - g0[k]) > 0.05 * abs(fd), (k, g[k], g0[k])
+    assert np.array_equal(m.history(), h0)
+
+
+@pytest.mark.parametrize("p", [1, 2])
 def test_surface_loss_of_a_constant_field(oracle_mod, p):
     """Constant T: the boundary term is -q(T) int_top N_i dA: it sums to -q(T) times the top
     area (partition of unity, constraint rows summing to 1 across hanging faces), vanishes off
