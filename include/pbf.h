@@ -298,8 +298,11 @@ pbf_status pbf_implicit_newton(pbf_ctx* ctx, double* T_dev, double dt, int nstep
  * lambda_n = lambda_{n+1} + dt (du/dT)^T lambda_{n+1} + dJ/dT_n, u = C~^-1 f. Gradients with
  * respect to the laser power of each segment and to the conductivity scale s. With a surface
  * loss, f includes it (at each step's state) and du/dT its face term -int N_i q'(T_h) N_j dA;
- * the power gradients take the laser's part of f_vol alone. A context with the phase model:
- * PBF_EINVAL (its history is not differentiated).
+ * the power gradients take the laser's part of f_vol alone. With the phase model the history
+ * r_n = max(r_{n-1}, g(T_n)) is a state of the stepper: every snapshot stores it with T, the
+ * reverse pass carries its adjoint (through the max where the stored value wins, into lambda
+ * through g'(T) where g wins), and the context's history is as on entry when the call returns
+ * (one more history-sized buffer per snapshot, and one for the adjoint).
  * J_out host [batch]; grad_out host [batch][n_seg + 1] (dJ/dP_0..dJ/dP_{n_seg-1}, dJ/ds);
  * forward_steps_out (nullable): forward steps taken, including recomputation. Synchronises. */
 pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, const pbf_laser* laser, double t0, double dt,
@@ -409,8 +412,8 @@ typedef struct {
  * model of a context. With it the explicit steps of one instance read and store r_c inside the
  * fused step kernel (shapes 4, 5; shapes 6-9 act as shape 5), batches run the per-cell form;
  * the implicit solves use it (Newton's method, storing r_c after each step), and
- * pbf_adjoint_sweep returns PBF_EINVAL. PBF_EINVAL for bad parameters or the quadrature-point
- * capacity. Allocates the history once
+ * pbf_adjoint_sweep differentiates it with its history. PBF_EINVAL for bad parameters or the
+ * quadrature-point capacity. Allocates the history once
  * ((p+1)^3 n_cells batch values); synchronises. */
 pbf_status pbf_ctx_set_phase(pbf_ctx* ctx, const pbf_phase* ph);
 

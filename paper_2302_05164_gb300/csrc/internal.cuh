@@ -212,6 +212,9 @@ struct CellLaunch {
   PhaseR<double> phd;
   const void* rc_in = nullptr;
   void* rc_out = nullptr;
+  // adjoint sweep with the phase model: the history's adjoint divided by dt, [q][n_cells][batch]
+  // in the operator precision, read and replaced by the adjoint kernel
+  void* sig = nullptr;
 };
 
 // Explicit-step shapes the autotuner chooses from for the FP32 operator. 0-3: the per-cell

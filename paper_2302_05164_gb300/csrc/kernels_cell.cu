@@ -247,9 +247,12 @@ __global__ void __launch_bounds__(64) k_diag(const CellLaunch L, double* __restr
 //   g_j = sum_e [ -int k(T_h) grad v_h . grad N_j - int k'(T_h) N_j grad v_h . grad T_h
 //                 - int rho c_app'(T_h) mu_h N_j ]
 // i.e. the transpose of the linearised operator of Eq. matrix_free_eval (the D_e and L_e
-// parts) plus, for the quadrature-point capacity, the transposed capacity derivative.
-template <int P, typename R, bool NLK, bool QPC>
+// parts) plus, for the quadrature-point capacity, the transposed capacity derivative. PH: the
+// phase model's k(T, r) with the history r = max(r_{n-1}, g(T)) as a state of the stepper; the
+// kernel also updates the history's adjoint L.sig and adds its path into g through g'(T).
+template <int P, typename R, bool NLK, bool QPC, bool PH>
 __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restrict__ g, R* __restrict__ gh) {
+  static_assert(!(PH && (NLK || QPC)), "the phase model replaces the conductivity ramp; no quadrature capacity");
   constexpr int NP = (P + 1) * (P + 1) * (P + 1);
   const DevMesh& M = L.mesh;
   const MatR<R>& mt = mat_of<R>(L);
@@ -270,15 +273,33 @@ __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restri
   const R* ks = kscale_of<R>(L);
   const R scale = (mat == 1 ? mt.powder_scale : R(1)) * (ks ? ks[inst] : R(1));
   R kw[NP], val[NP];
+  if (PH) {
+    // k(T, r) with r = max(r_{n-1}, g(T)), r_{n-1} the history entering the step; val holds
+    // -dk/dT W at fixed r: (k_m - k_s) g'(T)
+    const PhaseR<R>& ph = phase_of<R>(L);
+    const R is = ks ? ks[inst] : R(1);
+    const R* rc_in = static_cast<const R*>(L.rc_in);
 #pragma unroll
-  for (int q = 0; q < NP; ++q) {
-    const R W = R(wq3<P>(q)) * detJ;
-    const R sx = (Tq[q] + mt.tk_off) * mt.inv_dT;
-    R k = mt.k0 * scale;
-    if (NLK) k = k + mt.dk * scale * clamp01(sx);
-    kw[q] = -k * W;
-    // k'(T): slope inside the open ramp, zero outside (and at its ends)
-    val[q] = (NLK && sx > R(0) && sx < R(1)) ? -(mt.dk * scale * mt.inv_dT) * W : R(0);
+    for (int q = 0; q < NP; ++q) {
+      const R W = R(wq3<P>(q)) * detJ;
+      const R z = (Tq[q] + ph.t_off) * ph.inv_dT;
+      const R gz = clamp01(z);
+      const R st = rc_in[((int64_t)q * M.n_cells + cell) * B + inst];
+      const R rc = st > gz ? st : gz;
+      kw[q] = -((ph.kp + rc * ph.dks + gz * ph.dkm) * is) * W;
+      val[q] = (z > R(0) && z < R(1)) ? -(ph.dkm * is * ph.inv_dT) * W : R(0);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const R W = R(wq3<P>(q)) * detJ;
+      const R sx = (Tq[q] + mt.tk_off) * mt.inv_dT;
+      R k = mt.k0 * scale;
+      if (NLK) k = k + mt.dk * scale * clamp01(sx);
+      kw[q] = -k * W;
+      // k'(T): slope inside the open ramp, zero outside (and at its ends)
+      val[q] = (NLK && sx > R(0) && sx < R(1)) ? -(mt.dk * scale * mt.inv_dT) * W : R(0);
+    }
   }
   if (QPC) {
     if (sizeof(R) == 4) gather_sel<P, R, float>(M, L.muf, L.mufh, cell, inst, 0.0, u);
@@ -298,16 +319,20 @@ __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restri
 #pragma unroll
     for (int q = 0; q < NP; ++q) u[q] = R(0);
   }
-  R r[NP], gv[NP], gT[NP];
+  R r[NP], gv[NP], gT[NP], gg[NP];  // gg (phase model): grad v . grad T per quadrature point
 #pragma unroll
-  for (int q = 0; q < NP; ++q) r[q] = R(0);
+  for (int q = 0; q < NP; ++q) {
+    r[q] = R(0);
+    gg[q] = R(0);
+  }
 #define ADJ_DIR(DIR)                                                         \
   {                                                                          \
     const R cd = geo.ih2[lev][DIR];                                          \
     apply1d<P, 1, DIR, false, false>(vq, gv);                                \
-    if (NLK) apply1d<P, 1, DIR, false, false>(Tq, gT);                       \
+    if (NLK || PH) apply1d<P, 1, DIR, false, false>(Tq, gT);                 \
     _Pragma("unroll") for (int q = 0; q < NP; ++q) {                         \
       if (NLK) u[q] += val[q] * cd * gv[q] * gT[q];                          \
+      if (PH) gg[q] += cd * gv[q] * gT[q];                                   \
       gv[q] *= kw[q] * cd;                                                   \
     }                                                                        \
     apply1d<P, 1, DIR, true, true>(gv, r);                                   \
@@ -316,6 +341,26 @@ __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restri
   ADJ_DIR(1)
   ADJ_DIR(2)
 #undef ADJ_DIR
+  if (PH) {
+    // the history's adjoint (divided by dt): sig_n = -W (k_s - k_p) s grad v . grad T + sig_in;
+    // where the max takes g (b) it reaches lambda through g'(T) and is not carried further back,
+    // else it is carried unchanged (r_n = r_{n-1})
+    const PhaseR<R>& ph = phase_of<R>(L);
+    const R is = ks ? ks[inst] : R(1);
+    const R* rc_in = static_cast<const R*>(L.rc_in);
+    R* sig = static_cast<R*>(L.sig);
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const R W = R(wq3<P>(q)) * detJ;
+      const int64_t j = ((int64_t)q * M.n_cells + cell) * B + inst;
+      const R z = (Tq[q] + ph.t_off) * ph.inv_dT;
+      const R gz = clamp01(z);
+      const bool b = gz > rc_in[j];
+      const R sg = -W * ph.dks * is * gg[q] + sig[j];
+      sig[j] = b ? R(0) : sg;
+      u[q] += val[q] * gg[q] + ((b && z < R(1)) ? ph.inv_dT * sg : R(0));
+    }
+  }
 #pragma unroll
   for (int q = 0; q < NP; ++q) r[q] += u[q];
   R fe[NP];
@@ -323,17 +368,21 @@ __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restri
   scatter<P, R>(M, g, gh, cell, inst, fe);
 }
 
-template <int P, typename R, bool NLK, bool QPC>
+template <int P, typename R, bool NLK, bool QPC, bool PH = false>
 cudaError_t go_adj(const CellLaunch& L, void* g, void* gh, cudaStream_t s) {
   const int64_t n = (int64_t)L.mesh.n_cells * L.mesh.batch;
   if (n == 0) return cudaSuccess;
-  k_adjoint<P, R, NLK, QPC><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(L, (R*)g, (R*)gh);
+  k_adjoint<P, R, NLK, QPC, PH><<<(unsigned)((n + 127) / 128), 128, 0, s>>>(L, (R*)g, (R*)gh);
   return cudaGetLastError();
 }
 
 template <int P, typename R>
 cudaError_t dispatch_adj(const CellLaunch& L, bool qpc, void* g, void* gh, cudaStream_t s) {
   const bool nl = L.nonlin_k != 0;
+  if (L.phase) {  // the phase model: its history and the history's adjoint are needed
+    if (qpc || !L.rc_in || !L.sig) return cudaErrorInvalidValue;
+    return go_adj<P, R, false, false, true>(L, g, gh, s);
+  }
   if (nl && qpc) return go_adj<P, R, true, true>(L, g, gh, s);
   if (nl) return go_adj<P, R, true, false>(L, g, gh, s);
   if (qpc) return go_adj<P, R, false, true>(L, g, gh, s);

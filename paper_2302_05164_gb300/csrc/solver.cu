@@ -650,6 +650,11 @@ struct Adjoint {
   double* fre = nullptr;  // the surface loss's part of f (with a surface loss)
   float *vf = nullptr, *muf = nullptr;
   void *vh = nullptr, *muh = nullptr;
+  // phase model: the history at each snapshot (beside slots) and the history's adjoint
+  bool ph = false;
+  size_t hbytes = 0;
+  std::vector<char*> hslots;
+  char* sig = nullptr;
   std::vector<void*> owned;
 
   template <typename X>
@@ -668,6 +673,18 @@ struct Adjoint {
 
   void copy(double* dst, const double* src) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, src, (size_t)nv * 8, cudaMemcpyDeviceToDevice, s);
+  }
+  // the context's live history to / from the snapshot kept beside `slot` (phase model)
+  char* hist_of(const double* slot) {
+    for (size_t i = 0; i < slots.size(); ++i)
+      if (slots[i] == slot) return hslots[i];
+    return nullptr;
+  }
+  void put_hist(const double* slot) {
+    if (ph && e == cudaSuccess) e = cudaMemcpyAsync(hist_of(slot), c->rc, hbytes, cudaMemcpyDeviceToDevice, s);
+  }
+  void get_hist(const double* slot) {
+    if (ph && e == cudaSuccess) e = cudaMemcpyAsync(c->rc, hist_of(slot), hbytes, cudaMemcpyDeviceToDevice, s);
   }
   // advance T from step k by m steps
   void advance(double* T, int k, int m) {
@@ -698,8 +715,11 @@ struct Adjoint {
     if (e == cudaSuccess) e = launch_dot(c->n_dofs, B, lam, q2, nullptr, nullptr, c->part, scal + B, s);
     const Spot sp = spot_at(c->lsetup.k, t);
     if (e == cudaSuccess) e = launch_grad_accum(B, n_seg, sp.seg, scal, scal + B, c->k_scale_d, c->power, dt, grad, s);
-    // transposed linearisation
+    // transposed linearisation (with the phase model: the history entering step k, read only,
+    // and the history's adjoint)
     CellLaunch L = c->base;
+    c->set_phase(L, false);
+    L.sig = sig;
     const bool qpc = c->cap == CAP_QUADRATURE;
     if (c->f32) {
       if (e == cudaSuccess) e = launch_prepare_f32(nv, Tk, c->mat.T_ref, c->Tf, nullptr, s);
@@ -745,12 +765,14 @@ struct Adjoint {
     if (e != cudaSuccess) return;
     const int l = b - a;
     if (l == 1) {
+      get_hist(slot);
       adjoint_step(a, slot);
       return;
     }
     if (free == 0) {
       for (int k = b - 1; k >= a && e == cudaSuccess; --k) {
         copy(work, slot);
+        get_hist(slot);
         advance(work, a, k - a);
         adjoint_step(k, work);
       }
@@ -759,7 +781,9 @@ struct Adjoint {
     const int m = rv.M(l, free);
     double* mid = slots[(size_t)free_base];
     copy(mid, slot);
+    get_hist(slot);
     advance(mid, a, m);
+    put_hist(mid);
     reverse(a + m, b, mid, free - 1, free_base + 1);
     reverse(a, a + m, slot, free, free_base);
   }
@@ -820,7 +844,6 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
   if (!ctx || !T0_dev || !laser || !J_out || !grad_out) return err(PBF_EINVAL, "null argument");
   if (nsteps < 1 || n_checkpoints < 1 || !(dt > 0) || !(p_exp >= 1)) return err(PBF_EINVAL, "bad sweep parameters");
   if (laser->n_seg < 1) return err(PBF_EINVAL, "the adjoint needs a laser with at least one segment");
-  if (ctx->has_phase) return err(PBF_EINVAL, "the adjoint covers no phase-dependent conductivity");
   pbf_status st = ctx->check_usable();
   if (st) return st;
   cudaStream_t s = (cudaStream_t)stream;
@@ -844,6 +867,15 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
   const size_t rsz = ctx->f32 ? 4 : 8;
   A.slots.resize((size_t)free_slots + 1);
   for (auto& sl : A.slots) A.alloc(&sl, nv);
+  if (ctx->has_phase) {  // the history travels with every snapshot; its adjoint starts at zero
+    const int p1 = ctx->degree + 1;
+    A.ph = true;
+    A.hbytes = (size_t)p1 * p1 * p1 * (size_t)ctx->n_cells * (size_t)ctx->batch * rsz;
+    A.hslots.resize(A.slots.size());
+    for (auto& hs : A.hslots) A.alloc(&hs, A.hbytes);
+    A.alloc(&A.sig, A.hbytes);
+    if (A.e == cudaSuccess) A.e = cudaMemsetAsync(A.sig, 0, A.hbytes, s);
+  }
   A.alloc(&A.lam, nv);
   A.alloc(&A.v, nv);
   A.alloc(&A.mu, nv);
@@ -872,6 +904,7 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
   // forward sweep along the right spine of the schedule: store its snapshots, accumulate J
   double* start = A.slots[0];
   A.copy(start, T0_dev);
+  A.put_hist(start);  // the history at T0 (restored on return)
   struct Node { int a; double* slot; int free; int base; };
   std::vector<Node> spine;
   int a = 0, free = free_slots, base = 1;
@@ -886,6 +919,7 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
       A.objective(A.work, 1);
     }
     A.copy(nxt, A.work);
+    A.put_hist(nxt);
     a += m;
     cur = nxt;
     --free;
@@ -903,6 +937,7 @@ extern "C" pbf_status pbf_adjoint_sweep(pbf_ctx* ctx, const double* T0_dev, cons
     const int b = (i + 1 < (int)spine.size()) ? spine[(size_t)i + 1].a : a;
     A.reverse(spine[(size_t)i].a, b, spine[(size_t)i].slot, spine[(size_t)i].free, spine[(size_t)i].base);
   }
+  A.get_hist(start);  // the context's history as it was on entry
   if (A.e == cudaSuccess) A.e = cudaMemcpyAsync(J_out, A.J, (size_t)A.B * 8, cudaMemcpyDeviceToHost, s);
   if (A.e == cudaSuccess)
     A.e = cudaMemcpyAsync(grad_out, A.grad, (size_t)A.B * (A.n_seg + 1) * 8, cudaMemcpyDeviceToHost, s);

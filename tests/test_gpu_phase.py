@@ -3,7 +3,8 @@
 material_parameter_interp) with the oracle, through the C ABI: residual terms at the initial
 history, explicit steps that melt part of a powder layer (history stored per quadrature point),
 and a residual at a cool state afterwards that must see the consolidated material; FP64 and
-FP32 operators, Q1 and Q2 with hanging nodes. Calls that do not cover the model refuse it.
+FP32 operators, Q1 and Q2 with hanging nodes; the fused step kernel with the model; the adjoint
+sweep with the history against the oracle's adjoint.
 
 Tolerances: FP64 1e-10 relative; FP32 operator 2e-5 of max|f| (residual terms), 2e-4 relative
 max-norm on temperatures, and 5e-3 of max|f| for a residual that reads a history built by FP32
@@ -162,7 +163,53 @@ def test_phase_model_with_surface_loss_and_laser(P, oracle_mod, degree, prec, sh
     m.close()
 
 
-def test_adjoint_refuses_the_phase_model(P):
+@pytest.mark.parametrize("p,prec,ckpt", [(1, "f64", 3), (2, "f64", 4), (2, "f32", 3)])
+def test_adjoint_with_phase_model_matches_oracle(P, oracle_mod, p, prec, ckpt):
+    """The adjoint sweep with the phase model (the history as a state of the stepper, stored
+    with every snapshot, its adjoint carried backward) equals the oracle's adjoint, which
+    stores every state and history, for a batch of two instances with their own powers,
+    conductivity scales and initial fields; the laser track partly melts the powder layer.
+    FP64 1e-10, FP32 operator 1e-3; the phase model moves the gradients by far more than the
+    tolerance; the context's history is as before the call."""
+    d = I.mesh_desc((4, 2, 2), (125e-6,) * 3, p, 1, [I.uniform_region(1)], powder_z0=0.19e-3, powder_z1=1.0)
+    om = oracle_mod.Mesh(d)
+    mat = dict(I.TI64_CONST)
+    lam, _ = om.lambda_max(dict(mat, k0=30.0, k1=30.0, powder_k_scale=1.0), I.start_vector(om.n_dofs), max_iter=300,
+                           rtol=1e-8)
+    dt, nsteps, Tt, B = 0.3 * 2.0 / lam, 12, 1800.0, 2
+    P_, s = I.c4_params(B, n_seg=3, seed=2304)
+    ls = I.c4_laser(P_, n_seg=3, steps_per_seg=4, dt=dt, v=1.0, y=0.125e-3)
+    ls["seg"][:, 0] += 0.15e-3
+    ls["seg"][:, 2] += 0.15e-3
+    xyz = om.dof_xyz()
+    T0 = np.stack([I.melt_pool_field(xyz, (0.2e-3, 0.125e-3, 0.25e-3), 1950.0 + 30 * b, 110e-6, seed=11 + b,
+                                     noise=0.01) for b in range(B)], axis=1)
+    ref0 = [om.adjoint(mat, T0[:, b], ls, 0.0, dt, nsteps, T_target=Tt, s=s[b], instance=b) for b in range(B)]
+    om.set_phase(PH)
+    ref = [om.adjoint(mat, T0[:, b], ls, 0.0, dt, nsteps, T_target=Tt, s=s[b], instance=b) for b in range(B)]
+    m = P.Mesh(d)
+    ctx = P.Context(m, mat, P.PBF_F64 if prec == "f64" else P.PBF_F32OP, B)
+    P.pbf_ctx_set_k_scale(ctx.h, s)
+    P.pbf_ctx_set_phase(ctx.h, PH)
+    nq = (p + 1) ** 3
+    h_before = torch.zeros(nq * om.n_active * B, dtype=torch.float64, device="cuda")
+    P.pbf_ctx_get_history(ctx.h, h_before)
+    J, g, fwd = P.pbf_adjoint_sweep(ctx.h, to_dev(T0), ls, 0.0, dt, nsteps, ckpt, T_target=Tt, batch=B)
+    tol = 1e-10 if prec == "f64" else 1e-3
+    for b in range(B):
+        Jr, gr = ref[b]
+        assert abs(J[b] - Jr) < tol * abs(Jr)
+        assert np.max(np.abs(g[b] - gr)) < tol * np.max(np.abs(gr)), (g[b], gr)
+        assert np.max(np.abs(gr - ref0[b][1])) > 100 * tol * np.max(np.abs(gr))
+    assert fwd > nsteps
+    h_after = torch.zeros_like(h_before)
+    P.pbf_ctx_get_history(ctx.h, h_after)
+    assert torch.equal(h_before, h_after)
+    ctx.close()
+    m.close()
+
+
+def test_implicit_covers_the_phase_model_and_bad_parameters_refused(P):
     m = P.Mesh(mesh(1))
     ctx = P.Context(m, I.TI64_CONST, P.PBF_F64)
     with pytest.raises(P.PbfError):
@@ -172,7 +219,5 @@ def test_adjoint_refuses_the_phase_model(P):
     T = torch.full((n,), 500.0, dtype=torch.float64, device="cuda")
     status, _ = P.pbf_implicit_solve(ctx.h, T, 1e-2, 1, 1e-8, 200, 5, np.array([0.5, 2.0]))
     assert status == 0  # the implicit solve covers it by Newton's method (tests/test_gpu_newton.py)
-    ls = I.laser([(0.1e-3, 0.25e-3, 0.9e-3, 0.25e-3, 0.0, 1e-3)], [200.0])
-    with pytest.raises(P.PbfError) as e:
-        P.pbf_adjoint_sweep(ctx.h, T, ls, 0.0, 1e-8, 4, 2)
-    assert e.value.status == 1
+    with pytest.raises(P.PbfError):  # the phase model needs the constant or nodal capacity
+        P.pbf_ctx_set_phase(P.Context(m, I.TI64_NONLIN, P.PBF_F64).h, PH)
