@@ -203,11 +203,12 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10, sh
     T0 = I.melt_pool_field(xyz, (0.05e-3, 0.25e-3, 0.25e-3), 2500.0, 50e-6, seed=5)
     T = torch.tensor(np.repeat(T0[:, None], batch, axis=1), dtype=torch.float64, device="cuda")
     dt = 2e-8
+    shape_us = [-1.0] * len(SHAPES)
     if shape >= 0:
         variant = shape
         pbf.pbf_ctx_set_kernel_shape(ctx.h, shape)
     else:
-        variant = pbf.pbf_ctx_autotune(ctx.h, T, reps=3, stream=stream)
+        variant, shape_us = pbf.pbf_ctx_autotune(ctx.h, T, reps=3, stream=stream, times=True)
     for k in range(3):
         pbf.pbf_explicit_step(ctx.h, T, ls, k * chunk * dt, dt, chunk, batch=batch, stream=stream)
     pbf.pbf_ctx_kernel_time(ctx.h)
@@ -235,7 +236,9 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=10, sh
     mesh.close()
     return {"workload": f"C4: Q2 1.0x0.5x0.25 mm, {n} dofs x {batch} instances (own powers and k scales)",
             "value": rate, "unit": "GDoF/s", "explicit_steps_per_step": chunk, "steps": K,
-            "cell_kernel_avg_us": cell_us, "step_shape": SHAPES[variant],
+            "cell_kernel_avg_us": cell_us, "step_shape": SHAPES[variant] if variant < 4 else "batched fused step",
+            "autotune_us_per_step": {("batched fused step" if i == 4 else SHAPES[i]): round(u, 2)
+                                     for i, u in enumerate(shape_us) if u > 0},
             "cell_kernel_roofline": {"bound": "alu", "achieved": cell_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                                      "frac": cell_tflops / fp32_peak, "cells_x_instances": n_cells * batch},
             "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / hbm, "l2": "state > L2; flushed between timed steps"}

@@ -206,8 +206,11 @@ struct CellLaunch {
   int variant = 0;  // launch shape of the FP32 residual kernel (see kCellVariants)
   LaserInline las;
   // phase-dependent conductivity (residual mode): r_c per quadrature point, [q][n_cells][batch]
-  // in the operator precision, read from rc_in and stored to rc_out (null: read only)
+  // in the context's precision (rc_f32: FP32 elements, else FP64; a launch's arithmetic may
+  // differ, as in the FP64 Newton residual of an FP32 context), read from rc_in and stored to
+  // rc_out (null: read only); kernels access it through rc_load / rc_store only
   int phase = 0;
+  int rc_f32 = 0;
   PhaseR<float> phf;
   PhaseR<double> phd;
   const void* rc_in = nullptr;
@@ -216,6 +219,17 @@ struct CellLaunch {
   // in the operator precision, read and replaced by the adjoint kernel
   void* sig = nullptr;
 };
+
+// Element j of the phase model's history, in the element type the context keeps it in.
+template <typename R>
+__device__ __forceinline__ R rc_load(const CellLaunch& L, int64_t j) {
+  return L.rc_f32 ? R(static_cast<const float*>(L.rc_in)[j]) : R(static_cast<const double*>(L.rc_in)[j]);
+}
+template <typename R>
+__device__ __forceinline__ void rc_store(const CellLaunch& L, int64_t j, R v) {
+  if (L.rc_f32) static_cast<float*>(L.rc_out)[j] = float(v);
+  else static_cast<double*>(L.rc_out)[j] = double(v);
+}
 
 // Explicit-step shapes the autotuner chooses from for the FP32 operator. 0-3: the per-cell
 // residual kernel {threads per block, minimum resident blocks per SM} = {128, 1}, {128, 5},

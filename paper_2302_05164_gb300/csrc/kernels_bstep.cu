@@ -20,7 +20,10 @@
 namespace pbf {
 namespace {
 
-// value of one dof and instance at step n: the previous state completed by its update
+// value of one dof and instance at step n: the previous state completed by its update. The
+// previous state and accumulator are written by earlier launches only (this launch writes the
+// other buffers), so they are read through the read-only path, where the re-reads of a dof by
+// its other adjacent cells can hit L1.
 template <int CAP>
 __device__ __forceinline__ float2 staged(const BStepArgs& A, int d, int idx) {
   if (A.first) {
@@ -28,7 +31,7 @@ __device__ __forceinline__ float2 staged(const BStepArgs& A, int d, int idx) {
     const float hi = d2f_rn(v);
     return make_float2(hi, d2f_rn(v - f2d(hi)));
   }
-  return euler_ff<CAP>(__ldcg(&A.x_in[idx]), __ldcg(&A.f_in[idx]), __ldg(&A.invC0x[d]), A.nc, A.x_dir, A.dt);
+  return euler_ff<CAP>(__ldg(&A.x_in[idx]), __ldg(&A.f_in[idx]), __ldg(&A.invC0x[d]), A.nc, A.x_dir, A.dt);
 }
 
 template <int P, bool NLK, int CAP>

@@ -130,15 +130,13 @@ __global__ void __launch_bounds__(BS, MINB) k_cell(const CellLaunch L, R* __rest
     // k(T, r_c) with r_c = max(stored r_c, g(T)) per quadrature point; stored in explicit steps
     const PhaseR<R>& ph = phase_of<R>(L);
     const R is = ks ? ks[inst] : R(1);
-    const R* rc_in = static_cast<const R*>(L.rc_in);
-    R* rc_out = static_cast<R*>(L.rc_out);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       const R g = clamp01((v[q] + ph.t_off) * ph.inv_dT);
       const int64_t j = ((int64_t)q * M.n_cells + cell) * B + inst;
-      R rc = rc_in[j];
+      R rc = rc_load<R>(L, j);
       rc = rc > g ? rc : g;
-      if (rc_out) rc_out[j] = rc;
+      if (L.rc_out) rc_store<R>(L, j, rc);
       kw[q] = sgn * ((ph.kp + rc * ph.dks + g * ph.dkm) * is) * (R(wq3<P>(q)) * detJ);
     }
   } else {
@@ -278,13 +276,12 @@ __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restri
     // -dk/dT W at fixed r: (k_m - k_s) g'(T)
     const PhaseR<R>& ph = phase_of<R>(L);
     const R is = ks ? ks[inst] : R(1);
-    const R* rc_in = static_cast<const R*>(L.rc_in);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
       const R W = R(wq3<P>(q)) * detJ;
       const R z = (Tq[q] + ph.t_off) * ph.inv_dT;
       const R gz = clamp01(z);
-      const R st = rc_in[((int64_t)q * M.n_cells + cell) * B + inst];
+      const R st = rc_load<R>(L, ((int64_t)q * M.n_cells + cell) * B + inst);
       const R rc = st > gz ? st : gz;
       kw[q] = -((ph.kp + rc * ph.dks + gz * ph.dkm) * is) * W;
       val[q] = (z > R(0) && z < R(1)) ? -(ph.dkm * is * ph.inv_dT) * W : R(0);
@@ -347,7 +344,6 @@ __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restri
     // else it is carried unchanged (r_n = r_{n-1})
     const PhaseR<R>& ph = phase_of<R>(L);
     const R is = ks ? ks[inst] : R(1);
-    const R* rc_in = static_cast<const R*>(L.rc_in);
     R* sig = static_cast<R*>(L.sig);
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -355,7 +351,7 @@ __global__ void __launch_bounds__(128) k_adjoint(const CellLaunch L, R* __restri
       const int64_t j = ((int64_t)q * M.n_cells + cell) * B + inst;
       const R z = (Tq[q] + ph.t_off) * ph.inv_dT;
       const R gz = clamp01(z);
-      const bool b = gz > rc_in[j];
+      const bool b = gz > rc_load<R>(L, j);
       const R sg = -W * ph.dks * is * gg[q] + sig[j];
       sig[j] = b ? R(0) : sg;
       u[q] += val[q] * gg[q] + ((b && z < R(1)) ? ph.inv_dT * sg : R(0));

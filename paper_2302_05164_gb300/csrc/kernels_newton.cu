@@ -23,11 +23,10 @@ __device__ __forceinline__ const PhaseR<float>& phase_of<float>(const CellLaunch
 template <>
 __device__ __forceinline__ const PhaseR<double>& phase_of<double>(const CellLaunch& L) { return L.phd; }
 
-// The stored consolidated fraction of quadrature point q of a cell ([q][n_cells], batch 1),
-// kept in the context's operator precision.
+// The stored consolidated fraction of quadrature point q of a cell ([q][n_cells], batch 1), in
+// the context's element type (the residual pass runs in FP64 in an FP32 context too).
 __device__ __forceinline__ double stored_rc(const CellLaunch& L, int q, int cell) {
-  const int64_t j = (int64_t)q * L.mesh.n_cells + cell;
-  return L.f32 ? (double)static_cast<const float*>(L.rc_in)[j] : static_cast<const double*>(L.rc_in)[j];
+  return rc_load<double>(L, (int64_t)q * L.mesh.n_cells + cell);
 }
 
 // PH: the phase model's k(T, r_c) with r_c = max(stored, g(T)) and its branch-wise k'(T)
@@ -80,13 +79,8 @@ __global__ void __launch_bounds__(128) k_newton(const CellLaunch L, const double
       const PhaseR<R>& ph = phase_of<R>(L);
       const R gq = clamp01((vT[q] + ph.t_off) * ph.inv_dT);
       const int64_t j = (int64_t)q * M.n_cells + cell;
-      if (L.f32) {
-        float* o = static_cast<float*>(L.rc_out);
-        o[j] = fmaxf(o[j], (float)gq);
-      } else {
-        double* o = static_cast<double*>(L.rc_out);
-        o[j] = fmax(o[j], (double)gq);
-      }
+      const double st = rc_load<double>(L, j);
+      if ((double)gq > st) rc_store<double>(L, j, (double)gq);
     }
   }
   R r[NP];

@@ -480,7 +480,7 @@ cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepStat
   if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
       !t.cell || !t.hloc || !t.hw || !t.loc || !st.x_in || !st.x_out || !st.f_in || !st.f_acc || !st.f_clear ||
       !st.invC0x || st.x_in == st.x_out || st.f_in == st.f_acc || st.f_in == st.f_clear || st.f_acc == st.f_clear ||
-      (L.phase && !L.rc_in))
+      (L.phase && (!L.rc_in || !L.rc_f32)))  // the fused step reads and stores an FP32 history
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
   if (L.degree == 1) return dispatch_step<1>(L, t, st, cap, pdl, s);

@@ -159,6 +159,7 @@ struct CtxBase {
     L.phase = has_phase ? 1 : 0;
     L.phf = phf;
     L.phd = phd;
+    L.rc_f32 = f32 ? 1 : 0;  // the history is kept in the context's precision
     L.rc_in = has_phase ? rc : nullptr;
     L.rc_out = has_phase && store ? rc : nullptr;
   }

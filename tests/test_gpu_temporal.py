@@ -4,7 +4,9 @@ activation of the second layer): the GPU run at the reference steps equals the o
 of the same sequence (FP64, 1e-9 relative on the observation point's series and the final
 field), and the temperature at the observation point converges at first order as the steps
 shrink (dt_ref, dt_ref / 2, dt_ref / 4; Sec. 3.2: forward and backward Euler are first-order
-schemes), to within a few percent of the temperature rise at dt_ref as the paper reports."""
+schemes): the differences to the finest run, maximum and root mean square over the sample
+times, shrink by about 3 when the steps halve. The paper shows the series as a figure and
+prints no error value."""
 import numpy as np
 import pytest
 
@@ -98,7 +100,14 @@ def test_two_layer_sequence_converges_in_time(runs):
         errs[k] = np.max(np.abs(samples - ref))
     rise = np.max(finest["T"]) - I.APPA_T0
     ratio = errs[1] / errs[2]
+    rms = {k: float(np.sqrt(np.mean((TM.common_samples(runs[1], runs[k], k) - TM.common_samples(runs[1], finest, 4)) ** 2)))
+           for k in (1, 2)}
     print(f"Appendix A: max |T_obs(dt) - T_obs(dt_ref/4)| over the reference sample times: dt_ref {errs[1]:.2f} K, "
-          f"dt_ref/2 {errs[2]:.2f} K (ratio {ratio:.2f}, first order gives 3); peak rise {rise:.0f} K")
-    assert ratio > 2.0
-    assert errs[1] < 0.05 * rise
+          f"dt_ref/2 {errs[2]:.2f} K (ratio {ratio:.2f}, first order gives 3); rms {rms[1]:.2f} K, {rms[2]:.2f} K; "
+          f"peak rise {rise:.0f} K")
+    # first order: the differences to the finest run shrink by 3 when the steps halve
+    assert 2.0 < ratio < 4.5
+    assert 2.0 < rms[1] / rms[2] < 4.5
+    # the paper prints no error value (a figure); the pointwise maximum sits on the heating front,
+    # where the spot advances 19 um per reference step, so only a loose bound is checked on it
+    assert errs[1] < 0.2 * rise
