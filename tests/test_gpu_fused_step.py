@@ -173,9 +173,11 @@ def test_autotune_times_every_step_form(P):
     v, us = P.pbf_ctx_autotune(ctx.h, T, reps=3, times=True)
     assert len(us) == 10 and all(u > 0 for u in us) and us[v] == min(us)
     assert torch.equal(T, T0)  # the state is not modified
-    bctx = P.Context(m, I.TI64_NONLIN_Q2, P.PBF_F32OP, 2)  # batches have no fused form
+    print(f"autotune, one instance ({m.info()['n_dofs']} dofs), us per step by shape:", [round(u, 1) for u in us])
+    bctx = P.Context(m, I.TI64_NONLIN_Q2, P.PBF_F32OP, 2)  # a batch: the per-cell shapes and shape 4
     Tb = torch.full((2 * m.info()["n_dofs"],), 900.0, dtype=torch.float64, device="cuda")
     v, us = P.pbf_ctx_autotune(bctx.h, Tb, reps=2, times=True)
+    print("autotune, batch of 2, us per step by shape:", [round(u, 1) for u in us])
     assert us[4] > 0 and all(u < 0 for u in us[5:]) and v <= 4  # shape 4: the batched fused form
 
 
