@@ -40,12 +40,10 @@ SHAPES = ["per-cell kernel, 128 threads", "per-cell kernel, 128 threads, 5 block
           "fused step, 64-cell patches", "fused step, 64-cell patches, programmatic dependent launch",
           "fused steps, one persistent cooperative launch per call",
           "lean fused step (tables through L1), 14 blocks/SM", "lean fused step (tables through L1), 12 blocks/SM",
-          "lean fused step (tables through L1), 10 blocks/SM",
-          "fused step, 64-cell patches, programmatic dependent launch, 12 blocks/SM"]
+          "lean fused step (tables through L1), 10 blocks/SM"]
 KERNELS = ["k_cell<2,float,RESIDUAL,nonlinear>"] * 4 + ["k_step<2,nonlinear,nodal> (fused step)"] * 2 + \
     ["k_steps<2,nonlinear,nodal> (persistent fused steps)"] + \
-    [f"k_step_lean<2,nonlinear,nodal,{b}> (lean fused step)" for b in (14, 12, 10)] + \
-    ["k_step<2,nonlinear,nodal,12 blocks/SM> (fused step)"]
+    [f"k_step_lean<2,nonlinear,nodal,{b}> (lean fused step)" for b in (14, 12, 10)]
 BYTES_PER_DOF_UPDATE = 16  # read T_n and write T_{n+1} in FP64 (c_app(T) recomputed in-kernel)
 
 
@@ -287,7 +285,7 @@ def bench_large(pbf, I, torch, stream, flush, peaks, K=5, chunk=20):
            "value": rate, "unit": "GDoF/s", "us_per_explicit_step": 1e3 * ms / (K * chunk), "step_shape": SHAPES[variant],
            "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / peaks.get("hbm_gbs", 6800.0), "finite": ok,
            "host_setup_s": setup_s, "l2": "state and tables > L2; flushed between timed steps"}
-    if 7 <= variant <= 9:  # measured DRAM bytes per launch of the lean step on this mesh (ncu record)
+    if variant >= 7:  # measured DRAM bytes per launch of the lean step on this mesh (ncu record)
         t = traffic_for_kernel("lean_large", variant)
         out["traffic_bytes_per_launch"] = t
         if t:
@@ -685,7 +683,7 @@ def main():
     ap.add_argument("--workload", default="c2", choices=["c2", "c4", "large"],
                     help="c4 / large: only the batched C4 steps / the 18 M-dof single instance (profiler runs)")
     ap.add_argument("--shape", type=int, default=-1,
-                    help="explicit-step kernel shape to use instead of the autotuner's pick (0-10)")
+                    help="explicit-step kernel shape to use instead of the autotuner's pick (0-6)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -798,7 +796,7 @@ def main():
     bytes_launch = BYTES_PER_DOF_UPDATE * n * (CHUNK if variant == 6 else 1)
     hbm = peaks.get("hbm_gbs", 6800.0)
     achieved = bytes_launch / launch_s / 1e9
-    kind = "lean" if 7 <= variant <= 9 else ("step" if variant >= 4 else "cell")
+    kind = "lean" if variant >= 7 else ("step" if variant >= 4 else "cell")
     out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                        "traffic": traffic_for_kernel(kind, variant), "kernel": KERNELS[variant],
                        "algorithmic_bytes_per_launch": bytes_launch,

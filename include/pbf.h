@@ -326,21 +326,19 @@ pbf_status pbf_revolve_cost(int nsteps, int n_snaps, long long* forward_steps_ou
  * tables in shared memory for the whole call); shape 6 synchronises the stream; 7, 8, 9: the
  * fused step of shape 5 in its lean form (patch tables read through L1, only the staged values
  * and their sums in shared memory, the conductivity recomputed in each gradient direction),
- * compiled for 14, 12 and 10 resident blocks per SM; 10: the fused step of shape 5 compiled for
- * 12 resident blocks per SM (80 registers, a few spills; the patches hold at most 512
- * hanging-table entries, so that 12 blocks fit in shared memory). For a batch (batch > 1,
- * constant or nodal capacity, no surface loss or phase model, surface laser) shapes 4-10 run the
- * batched fused step: one launch per step for all instances, threads (cell, instance) with the
+ * compiled for 14, 12 and 10 resident blocks per SM. For a batch (batch > 1, constant or
+ * nodal capacity, no surface loss or phase model, surface laser) shapes 4-9 run the batched
+ * fused step: one launch per step for all instances, threads (cell, instance) with the
  * instance fastest, the previous step's update applied in the gather, the spot computed on
  * the device, a call's launches replayed as one CUDA graph when (nsteps, dt, T_dev) repeat.
- * The phase model and the surface loss run in the fused step of shapes 4 and 5 (shapes 6-10
+ * The phase model and the surface loss run in the fused step of shapes 4 and 5 (shapes 6-9
  * then act as shape 5). Where no fused form applies (quadrature-point capacity; a batch with
- * an option or a volumetric source) shapes 4-10 run the per-cell form; with a volumetric
- * source shape 6 runs shape 5; residual-only evaluations of shapes 4-10 use shape 1.
+ * an option or a volumetric source) shapes 4-9 run the per-cell form; with a volumetric
+ * source shape 6 runs shape 5; residual-only evaluations of shapes 4-9 use shape 1.
  *
  * pbf_ctx_autotune times `reps` explicit steps of every applicable shape with dt = 0 on a
  * scratch copy of T_dev (not modified), with the laser of the last call, keeps the fastest in
- * the context and returns its index; us_per_step_out (nullable, 11 entries) receives each
+ * the context and returns its index; us_per_step_out (nullable, 10 entries) receives each
  * shape's microseconds per step, -1 where it does not apply. FP64 contexts keep shape 0.
  * Allocates one scratch vector; synchronises. */
 pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* variant_out, float* us_per_step_out,

@@ -247,14 +247,10 @@ static uint64_t spread_bits3(uint64_t v) {
   return r;
 }
 
-// Hanging-table entries a patch may hold: the largest patch sets every block's shared memory,
-// and without a bound it is one at a refinement interface (C2: 1,137 entries against 106 on
-// average, 6.8 KB of the 21.8 KB); with 512 the blocks need at most 18 KB, room for 12 per SM.
-constexpr int64_t kStepMaxHent = 512;
-
 static void build_step_tables(const HostMesh& m, StepHost& out) {
   const size_t nc = m.leaf_of_active.size(), npc = (size_t)m.npc;
   const int32_t nd32 = (int32_t)m.n_dofs;
+  const size_t np = (nc + kStepCells - 1) / kStepCells;
   std::vector<std::pair<uint64_t, int32_t>> order(nc);
   for (size_t c = 0; c < nc; ++c) {
     const Octant& o = m.oct[(size_t)m.leaf_of_active[c]];
@@ -263,45 +259,6 @@ static void build_step_tables(const HostMesh& m, StepHost& out) {
     order[c] = {k, (int32_t)c};
   }
   std::sort(order.begin(), order.end());
-  // patches: runs of consecutive cells in that order, at most kStepCells cells and at most
-  // kStepMaxHent hanging-table entries each (a cell with more starts a patch of its own)
-  std::vector<size_t> pb{0};
-  {
-    const size_t n_rows = m.con_ptr.empty() ? 0 : m.con_ptr.size() - 1;
-    std::vector<uint8_t> in_patch(n_rows, 0);
-    std::vector<int32_t> rows, cell_rows;
-    int64_t hent = 0;
-    for (size_t c = 0; c < nc; ++c) {
-      cell_rows.clear();
-      for (size_t a = 0; a < npc; ++a) {
-        const int32_t d = m.cell_dofs[(size_t)order[c].second * npc + a];
-        if (d < 0 && std::find(cell_rows.begin(), cell_rows.end(), -1 - d) == cell_rows.end()) cell_rows.push_back(-1 - d);
-      }
-      auto added = [&]() {
-        int64_t h = 0;
-        for (int32_t r : cell_rows)
-          if (!in_patch[(size_t)r]) h += m.con_ptr[(size_t)r + 1] - m.con_ptr[(size_t)r];
-        return h;
-      };
-      int64_t add = added();
-      const size_t len = c - pb.back();
-      if (len > 0 && (len == (size_t)kStepCells || hent + add > kStepMaxHent)) {
-        for (int32_t r : rows) in_patch[(size_t)r] = 0;
-        rows.clear();
-        hent = 0;
-        pb.push_back(c);
-        add = added();
-      }
-      for (int32_t r : cell_rows)
-        if (!in_patch[(size_t)r]) {
-          in_patch[(size_t)r] = 1;
-          rows.push_back(r);
-        }
-      hent += add;
-    }
-    if (nc > 0) pb.push_back(nc);
-  }
-  const size_t np = pb.size() - 1;
   // unique slot keys of every patch (dof d, or n_dofs + r for hanging row r), and its work
   std::vector<size_t> kptr(np + 1, 0);
   std::vector<int32_t> keys, tmp;
@@ -309,7 +266,7 @@ static void build_step_tables(const HostMesh& m, StepHost& out) {
   for (size_t p = 0; p < np; ++p) {
     tmp.clear();
     int64_t hent = 0;
-    for (size_t c = pb[p]; c < pb[p + 1]; ++c)
+    for (size_t c = p * kStepCells; c < std::min(nc, (p + 1) * kStepCells); ++c)
       for (size_t a = 0; a < npc; ++a) {
         const int32_t d = m.cell_dofs[(size_t)order[c].second * npc + a];
         if (d >= 0) {
@@ -342,8 +299,8 @@ static void build_step_tables(const HostMesh& m, StepHost& out) {
     const int32_t nu = (int32_t)(kptr[p + 1] - kptr[p]);
     const int32_t nfree = (int32_t)(std::lower_bound(kb, kb + nu, nd32) - kb);
     auto pos = [&](int32_t key) { return step_swizzle((int)(std::lower_bound(kb, kb + nu, key) - kb)); };
-    for (size_t c = pb[p]; c < pb[p + 1]; ++c) {
-      const size_t lane = c - pb[p], cell = (size_t)order[c].second;
+    for (size_t c = p * kStepCells; c < std::min(nc, (p + 1) * kStepCells); ++c) {
+      const size_t lane = c - p * kStepCells, cell = (size_t)order[c].second;
       o.cell[q * kStepCells + lane] = (int32_t)cell;
       for (size_t a = 0; a < npc; ++a) {
         const int32_t d = m.cell_dofs[cell * npc + a];
@@ -896,9 +853,8 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
   if (base.variant >= 4 && fused_ok(4)) {
     if (base.variant == 6 && fused_ok(6) && !(lsetup.k.n_seg > 0 && lsetup.k.volumetric))
       return explicit_steps_persistent(T_dev, t0, dt, nsteps, s);
-    const bool ok = fused_ok(base.variant);
-    const int lean = is_lean(base.variant) && ok ? base.variant - 7 : -1;
-    return explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant != 4, lean, s, base.variant == 10 && ok);
+    const int lean = base.variant >= 7 && fused_ok(base.variant) ? base.variant - 7 : -1;
+    return explicit_steps_fused(T_dev, t0, dt, nsteps, base.variant != 4, lean, s);
   }
   CellLaunch L = base;
   set_phase(L, true);
@@ -972,7 +928,7 @@ cudaError_t CtxBase::explicit_steps(double* T_dev, double t0, double dt, int nst
 // fstep[(n + 2) % 3] (f_{n-1}, read); the state, T - T_ref as an FP32 pair hi + lo, alternates
 // between xstep[0] and xstep[1].
 cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, int nsteps, bool pdl, int lean,
-                                          cudaStream_t s, bool dense) {
+                                          cudaStream_t s) {
   CellLaunch L = base;
   set_phase(L, true);  // the phase model's history is read and stored by every step
   const bool volumetric = lsetup.k.n_seg > 0 && lsetup.k.volumetric;
@@ -999,7 +955,7 @@ cudaError_t CtxBase::explicit_steps_fused(double* T_dev, double t0, double dt, i
     st.f_clear = fstep[(n + 1) % 3];
     st.first = n == 0;
     const auto ev = timing ? timing_begin(s) : std::pair<cudaEvent_t, cudaEvent_t>{};
-    e = lean >= 0 ? launch_step_lean(L, step, st, cap, lean, s) : launch_step(L, step, st, cap, pdl, s, dense);
+    e = lean >= 0 ? launch_step_lean(L, step, st, cap, lean, s) : launch_step(L, step, st, cap, pdl, s);
     ++launches;
     if (ev.first) timing_end(ev, s);
     if (e == cudaSuccess && volumetric && sp.seg >= 0) {

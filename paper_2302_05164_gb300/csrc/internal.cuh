@@ -237,9 +237,8 @@ __device__ __forceinline__ void rc_store(const CellLaunch& L, int64_t j, R v) {
 // 4: the fused step kernel (one instance, constant or nodal capacity), 5: the same launched
 // with programmatic dependent launch, 6: all steps in one persistent cooperative launch,
 // 7-9: the lean fused step kernel (tables through L1) compiled for 14, 12 and 10 resident
-// blocks per SM, 10: the fused step kernel of shape 5 compiled for 12 resident blocks per SM.
-// Residual-only launches of shapes 4-10 use shape 1.
-constexpr int kCellVariants = 11;
+// blocks per SM. Residual-only launches of shapes 4-9 use shape 1.
+constexpr int kCellVariants = 10;
 
 template <typename R>
 __host__ __device__ inline const GeoR<R>& geo_of(const CellLaunch& L);

@@ -405,7 +405,7 @@ cudaError_t go(const CellLaunch& L, void* f, void* fh, void* C, void* Ch, cudaSt
       case 0: return go_shape<P, R, MODE, NLK, LAT>(L, f, fh, C, Ch, s);
       case 2: return go_shape<P, R, MODE, NLK, LAT, 128, 6>(L, f, fh, C, Ch, s);
       case 3: return go_shape<P, R, MODE, NLK, LAT, 64, 10>(L, f, fh, C, Ch, s);
-      default:  // 1, and 4-10 (forms of the fused explicit step: residual-only launches use shape 1)
+      default:  // 1, and 4-9 (forms of the fused explicit step: residual-only launches use shape 1)
         return go_shape<P, R, MODE, NLK, LAT, 128, 5>(L, f, fh, C, Ch, s);
     }
   }

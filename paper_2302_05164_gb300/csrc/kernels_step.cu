@@ -25,8 +25,7 @@
 namespace pbf {
 namespace {
 
-constexpr int kStepMinBlocks = 10;       // 64-thread blocks: at most 102 registers per thread
-constexpr int kStepMinBlocksDense = 12;  // the dense form: at most 85 (80 allocated), some spills
+constexpr int kStepMinBlocks = 10;  // 64-thread blocks: at most 102 registers per thread
 constexpr int kStageUnroll = 14;    // dof slots each thread has in flight while staging
 
 // Loads of data that changes between steps: through the read-only path when each step is its
@@ -243,10 +242,9 @@ __device__ __forceinline__ void step_patch(const CellLaunch& L, const LaserInlin
   }
 }
 
-// One launch per step: block p takes patch p. MINB: the resident blocks per SM it is compiled
-// for (the register budget).
-template <int P, bool NLK, int CAP, int OPT, int MINB>
-__global__ void __launch_bounds__(kStepCells, MINB)
+// One launch per step: block p takes patch p.
+template <int P, bool NLK, int CAP, int OPT>
+__global__ void __launch_bounds__(kStepCells, kStepMinBlocks)
     k_step(const CellLaunch L, const StepTables T, const StepState S) {
   constexpr int NP = (P + 1) * (P + 1) * (P + 1);
   extern __shared__ __align__(16) unsigned char smem[];
@@ -406,9 +404,9 @@ __global__ void k_step_final(int n, const float2* __restrict__ x_in, float* __re
   if (f_other) f_other[i] = 0.f;
 }
 
-template <int P, bool NLK, int CAP, int OPT = 0, int MINB = kStepMinBlocks>
+template <int P, bool NLK, int CAP, int OPT = 0>
 cudaError_t go_step(const CellLaunch& L, const StepTables& t, const StepState& st, bool pdl, cudaStream_t s) {
-  auto kern = k_step<P, NLK, CAP, OPT, MINB>;
+  auto kern = k_step<P, NLK, CAP, OPT>;
   if (t.smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, t.smem);
     if (e != cudaSuccess) return e;
@@ -418,12 +416,9 @@ cudaError_t go_step(const CellLaunch& L, const StepTables& t, const StepState& s
 
 // the model options: with the phase model the conductivity ramp of the material is not used
 template <int P, int CAP>
-cudaError_t dispatch_step_opt(const CellLaunch& L, const StepTables& t, const StepState& st, bool pdl, bool dense,
+cudaError_t dispatch_step_opt(const CellLaunch& L, const StepTables& t, const StepState& st, bool pdl,
                               cudaStream_t s) {
   const bool nl = L.nonlin_k != 0, loss = st.has_loss != 0;
-  if (dense && !L.phase && !loss)  // the dense form: plain step only
-    return nl ? go_step<P, true, CAP, 0, kStepMinBlocksDense>(L, t, st, pdl, s)
-              : go_step<P, false, CAP, 0, kStepMinBlocksDense>(L, t, st, pdl, s);
   if (L.phase)
     return loss ? go_step<P, false, CAP, kStepPhase | kStepLoss>(L, t, st, pdl, s)
                 : go_step<P, false, CAP, kStepPhase>(L, t, st, pdl, s);
@@ -433,9 +428,9 @@ cudaError_t dispatch_step_opt(const CellLaunch& L, const StepTables& t, const St
 
 template <int P>
 cudaError_t dispatch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
-                          bool dense, cudaStream_t s) {
-  if (cap == CAP_NODAL) return dispatch_step_opt<P, CAP_NODAL>(L, t, st, pdl, dense, s);
-  return dispatch_step_opt<P, CAP_CONST>(L, t, st, pdl, dense, s);
+                          cudaStream_t s) {
+  if (cap == CAP_NODAL) return dispatch_step_opt<P, CAP_NODAL>(L, t, st, pdl, s);
+  return dispatch_step_opt<P, CAP_CONST>(L, t, st, pdl, s);
 }
 
 template <int P, bool NLK, int CAP>
@@ -479,7 +474,7 @@ cudaError_t launch_steps_persistent(const CellLaunch& L, const StepTables& t, co
 }
 
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
-                        cudaStream_t s, bool dense) {
+                        cudaStream_t s) {
   // the fused form covers one instance of the FP32 operator with the constant or nodal
   // capacity, with or without the phase model and the surface loss
   if (!L.f32 || L.mesh.batch != 1 || !(cap == CAP_CONST || cap == CAP_NODAL) || !t.ptr || !t.cnt || !t.slot ||
@@ -488,8 +483,8 @@ cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepStat
       (L.phase && (!L.rc_in || !L.rc_f32)))  // the fused step reads and stores an FP32 history
     return cudaErrorInvalidValue;
   if (t.n_patches == 0) return cudaSuccess;
-  if (L.degree == 1) return dispatch_step<1>(L, t, st, cap, pdl, dense, s);
-  if (L.degree == 2) return dispatch_step<2>(L, t, st, cap, pdl, dense, s);
+  if (L.degree == 1) return dispatch_step<1>(L, t, st, cap, pdl, s);
+  if (L.degree == 2) return dispatch_step<2>(L, t, st, cap, pdl, s);
   return cudaErrorInvalidValue;
 }
 

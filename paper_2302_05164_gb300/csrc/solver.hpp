@@ -135,14 +135,11 @@ struct CtxBase {
   cudaError_t residual_f64(const double* T, double t, double* fd, double* fv, double* C, cudaStream_t s,
                            double* fre = nullptr);
   // nsteps forward-Euler steps in place on T (laser set beforehand); the fused form runs when
-  // the context's shape is 4-10 (6: persistent, not with a volumetric source; 7-9: the lean
-  // kernel; 10: the dense fused kernel) and fused_ok(4); shapes 6-10 run as 5 where
-  // fused_ok(shape) is false
+  // the context's shape is 4-9 (6: persistent, not with a volumetric source; 7-9: the lean
+  // kernel) and fused_ok(4); shapes 6-9 run as 5 where fused_ok(shape) is false
   cudaError_t explicit_steps(double* T, double t0, double dt, int nsteps, cudaStream_t s);
-  // lean: -1 the fused step kernel, 0..2 its lean form with the register budget kLeanForms[lean];
-  // dense: the fused step kernel compiled for 12 resident blocks per SM (shape 10)
-  cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, int lean, cudaStream_t s,
-                                   bool dense = false);
+  // lean: -1 the fused step kernel, 0..2 its lean form with the register budget kLeanForms[lean]
+  cudaError_t explicit_steps_fused(double* T, double t0, double dt, int nsteps, bool pdl, int lean, cudaStream_t s);
   cudaError_t explicit_steps_persistent(double* T, double t0, double dt, int nsteps, cudaStream_t s);
   // the batched fused form: buffers allocated on first use; surface lasers only
   pbf_status ensure_bfused();
@@ -157,7 +154,6 @@ struct CtxBase {
     return f32 && batch == 1 && cap != CAP_QUADRATURE && step.n_patches > 0 &&
            (variant <= 5 || (!has_loss && !has_phase));
   }
-  static bool is_lean(int variant) { return variant >= 7 && variant <= 9; }
   // the phase model's fields of a residual-mode launch (store: an explicit step)
   void set_phase(CellLaunch& L, bool store) const {
     L.phase = has_phase ? 1 : 0;

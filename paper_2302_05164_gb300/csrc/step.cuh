@@ -109,10 +109,8 @@ inline cudaError_t launch_ex(void (*kernel)(KArgs...), unsigned grid, unsigned b
 
 // cap: CAP_CONST or CAP_NODAL. pdl: launch with programmatic stream serialisation, so that
 // the block prologue (table loads) overlaps the tail of the previous kernel in the stream.
-// dense: the kernel compiled for 12 resident blocks per SM (80 registers, a few spills) instead
-// of 10; the plain step only (with a model option the 10-block kernel runs).
 cudaError_t launch_step(const CellLaunch& L, const StepTables& t, const StepState& st, int cap, bool pdl,
-                        cudaStream_t s, bool dense = false);
+                        cudaStream_t s);
 
 // The lean form of the same step (kernels_step_lean.cu): patch tables read through L1, only
 // the staged values and their sums in shared memory, launched with programmatic stream

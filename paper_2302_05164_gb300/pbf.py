@@ -335,7 +335,7 @@ def pbf_widen_to_f64(x, y, n, stream=None):
     _check(lib().pbf_widen_to_f64(_ptr(x), _ptr(y), int(n), _stream(stream)))
 
 
-N_SHAPES = 11
+N_SHAPES = 10
 
 
 def pbf_ctx_autotune(h, T, reps=5, stream=None, times=False):

@@ -171,7 +171,7 @@ def test_autotune_times_every_step_form(P):
     T = torch.full((m.info()["n_dofs"],), 900.0, dtype=torch.float64, device="cuda")
     T0 = T.clone()
     v, us = P.pbf_ctx_autotune(ctx.h, T, reps=3, times=True)
-    assert len(us) == 11 and all(u > 0 for u in us) and us[v] == min(us)
+    assert len(us) == 10 and all(u > 0 for u in us) and us[v] == min(us)
     assert torch.equal(T, T0)  # the state is not modified
     print(f"autotune, one instance ({m.info()['n_dofs']} dofs), us per step by shape:", [round(u, 1) for u in us])
     bctx = P.Context(m, I.TI64_NONLIN_Q2, P.PBF_F32OP, 2)  # a batch: the per-cell shapes and shape 4
