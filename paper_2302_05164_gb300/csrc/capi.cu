@@ -248,11 +248,13 @@ static uint64_t spread_bits3(uint64_t v) {
 }
 
 // Hanging-table entries a patch may hold. Without a bound the patches at refinement
-// interfaces carry about ten times the average (C2: up to 1,137 entries against 106), and
-// since the largest patch sets every block's shared memory and the heavy blocks the step's
-// critical path, those patches are split: with 512, C2 has 2,183 patches instead of 2,070, the
-// blocks need at most 18 KB instead of 21.8 KB, and a step takes 23.8 instead of 25.9 us.
-constexpr int64_t kStepMaxHent = 512;
+// interfaces carry about ten times the average (C2: up to 1,137 entries against 106); the
+// largest patch sets every block's shared memory, and the heavy blocks set the step's critical
+// path. Measured on C2 (us per step, fused step with programmatic dependent launch): no bound
+// 25.9, 768: 25.8, 704: 25.7, 640: 22.85, 576: 23.0, 512: 23.8, 384: 24.5, 256: 26.3, 192: 27.0.
+// Below about 640 the extra patches and re-staged slots cost more than the balance gains;
+// from about 700 on the step is as slow as without a bound.
+constexpr int64_t kStepMaxHent = 640;
 
 static void build_step_tables(const HostMesh& m, StepHost& out) {
   const size_t nc = m.leaf_of_active.size(), npc = (size_t)m.npc;
