@@ -48,6 +48,7 @@ uint64_t HostMesh::morton_key(const int64_t q[3]) const {
 
 int64_t HostMesh::locate(const int64_t q[3]) const {
   if (!inside(q)) return -1;
+  if (fine_leaf) return fine_leaf[(size_t)(q[0] + ext[0] * (q[1] + ext[1] * q[2]))];
   uint64_t k = morton_key(q);
   auto it = std::upper_bound(key.begin(), key.end(), k);
   if (it == key.begin()) return -1;
@@ -132,13 +133,15 @@ static void rekey(HostMesh& m) {
 static void balance(HostMesh& m) {
   for (;;) {
     // mark the leaves that are more than one level coarser than a vertex neighbour (the
-    // leaves are scanned in parallel; a mark is only ever set to 1)
+    // leaves are scanned in parallel; a mark is only ever set to 1). Only a leaf of level 2 or
+    // finer can have such a neighbour.
     std::vector<uint8_t> split(m.oct.size(), 0);
     int any = 0;
     const int64_t nl = (int64_t)m.oct.size();
 #pragma omp parallel for schedule(static, 4096) reduction(| : any)
     for (int64_t i = 0; i < nl; ++i) {
       const Octant& o = m.oct[(size_t)i];
+      if (o.level < 2) continue;
       int64_t s = m.size(o);
       for (int nb = 0; nb < 27; ++nb) {
         if (nb == 13) continue;
@@ -241,9 +244,25 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
         if (m.inside(root.a)) refine_tree(m, root, m.oct);
       }
   if (m.oct.empty()) return *err = "no trees exist", PBF_EINVAL;
+  m.fine_leaf.reset();
   rekey(m);
   balance(m);
   size_t nl = m.oct.size();
+  // the finest-cell index of the balanced leaves, for constant-time locate from here on
+  if (m.ext[0] * m.ext[1] * m.ext[2] <= HostMesh::kFineGridMax) {
+    std::shared_ptr<int32_t[]> fl(new int32_t[(size_t)(m.ext[0] * m.ext[1] * m.ext[2])]);
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t i = 0; i < (int64_t)nl; ++i) {
+      const Octant& o = m.oct[(size_t)i];
+      const int64_t s = m.size(o);
+      for (int64_t z = o.a[2]; z < o.a[2] + s; ++z)
+        for (int64_t y = o.a[1]; y < o.a[1] + s; ++y) {
+          int32_t* row = fl.get() + (size_t)(m.ext[0] * (y + m.ext[1] * z));
+          for (int64_t x = o.a[0]; x < o.a[0] + s; ++x) row[x] = (int32_t)i;
+        }
+    }
+    m.fine_leaf = std::move(fl);
+  }
   // activity and material
   m.active.assign(nl, 0);
   m.material.assign(nl, 0);

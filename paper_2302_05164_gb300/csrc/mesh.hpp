@@ -3,6 +3,8 @@
 // dof numbering, hanging-node constraints, colouring, top faces and transfer maps.
 #pragma once
 
+#include <memory>
+
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -34,6 +36,12 @@ struct HostMesh {
 
   std::vector<Octant> oct;    // canonical order
   std::vector<uint64_t> key;  // global Morton key of each anchor (strictly increasing)
+  // leaf holding each finest cell of the brick, x fastest (cells of trees that do not exist
+  // are not written: locate checks inside() first); built after balancing when the brick has
+  // at most kFineGridMax finest cells (null otherwise: locate searches the keys). Not
+  // value-initialised, so that the parallel fill is the first touch of its pages.
+  std::shared_ptr<int32_t[]> fine_leaf;
+  static constexpr int64_t kFineGridMax = (int64_t)1 << 26;
   std::vector<uint8_t> active, material;
   std::vector<int32_t> active_of_leaf;  // leaf -> active index or -1
   std::vector<int32_t> leaf_of_active;
