@@ -636,17 +636,15 @@ def run_reference(args):
                       "e2e": {"value": value, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
-# dominant kernel -> (ncu traffic record, sources it was captured from; the fused steps' patch
-# tables are built in capi.cu)
+# dominant kernel -> (ncu traffic record, sources it was captured from: the kernel, its
+# headers, and the host builder of the fused steps' patch tables)
+_STEP_SRC = ["cell_ops.cuh", "step.cuh", "step_layout.hpp", "vec_kernels.cuh", "internal.cuh", "step_tables.cpp"]
 TRAFFIC_RECORDS = {
     "cell": ("cell_kernel_c2_traffic.txt", ["kernels_cell.cu", "cell_ops.cuh", "internal.cuh"]),
-    "step": ("step_kernel_c2_traffic.txt", ["kernels_step.cu", "cell_ops.cuh", "step.cuh", "vec_kernels.cuh",
-                                             "internal.cuh", "capi.cu"]),
-    "lean": ("step_lean_kernel_c2_traffic.txt", ["kernels_step_lean.cu", "cell_ops.cuh", "step.cuh",
-                                                  "vec_kernels.cuh", "internal.cuh", "capi.cu"]),
+    "step": ("step_kernel_c2_traffic.txt", ["kernels_step.cu"] + _STEP_SRC),
+    "lean": ("step_lean_kernel_c2_traffic.txt", ["kernels_step_lean.cu"] + _STEP_SRC),
     # the lean step on the 18.2 M-dof mesh (the `large` entry), beyond L2
-    "lean_large": ("step_lean_kernel_large_traffic.txt", ["kernels_step_lean.cu", "cell_ops.cuh", "step.cuh",
-                                                          "vec_kernels.cuh", "internal.cuh", "capi.cu"]),
+    "lean_large": ("step_lean_kernel_large_traffic.txt", ["kernels_step_lean.cu"] + _STEP_SRC),
 }
 
 

@@ -16,6 +16,7 @@
 #include "mesh.hpp"
 #include "pbf.h"
 #include "solver.hpp"
+#include "step_layout.hpp"
 #include "vec_kernels.cuh"
 
 using namespace pbf;
@@ -224,172 +225,6 @@ extern "C" pbf_status pbf_mesh_transfer(pbf_mesh* mesh, const double* T_old_dev,
 // ======================================================================================
 // context
 // ======================================================================================
-
-// Patch tables of the fused step kernel. A patch is kStepCells cells that are consecutive in
-// the global Morton order of their anchors (over the whole brick, not tree by tree), so that
-// coarse regions give compact 4 x 4 x 4 blocks instead of rows of trees and a patch shares
-// as few nodes as possible with its neighbours. Each patch lists its unique node slots: the
-// dofs of its cells and the masters of its hanging nodes, ascending, then its hanging nodes.
-// Patches are numbered by decreasing work (slots plus twice the hanging-table entries), so
-// the blocks of the expensive patches at refinement interfaces start first instead of
-// forming the tail of a launch. Every dof is owned by the first patch in that numbering
-// that lists it. Leaves `out` empty when the fused form does not apply.
-struct StepHost {
-  std::vector<int32_t> ptr, cnt, slot, cell;
-  std::vector<uint16_t> loc, hloc;
-  std::vector<float> hw;
-  int max_nu = 0, max_hent = 0;
-};
-
-static uint64_t spread_bits3(uint64_t v) {
-  uint64_t r = 0;
-  for (int b = 0; b < 21; ++b) r |= ((v >> b) & 1u) << (3 * b);
-  return r;
-}
-
-// Hanging-table entries a patch may hold. Without a bound the patches at refinement
-// interfaces carry about ten times the average (C2: up to 1,137 entries against 106); the
-// largest patch sets every block's shared memory, and the heavy blocks set the step's critical
-// path. Measured on C2 (us per step, fused step with programmatic dependent launch): no bound
-// 25.9, 768: 25.8, 704: 25.7, 640: 22.85, 576: 23.0, 512: 23.8, 384: 24.5, 256: 26.3, 192: 27.0.
-// Below about 640 the extra patches and re-staged slots cost more than the balance gains;
-// from about 700 on the step is as slow as without a bound.
-constexpr int64_t kStepMaxHent = 640;
-
-static void build_step_tables(const HostMesh& m, StepHost& out) {
-  const size_t nc = m.leaf_of_active.size(), npc = (size_t)m.npc;
-  const int32_t nd32 = (int32_t)m.n_dofs;
-  std::vector<std::pair<uint64_t, int32_t>> order(nc);
-  for (size_t c = 0; c < nc; ++c) {
-    const Octant& o = m.oct[(size_t)m.leaf_of_active[c]];
-    const uint64_t k = spread_bits3((uint64_t)o.a[0]) | (spread_bits3((uint64_t)o.a[1]) << 1) |
-                       (spread_bits3((uint64_t)o.a[2]) << 2);
-    order[c] = {k, (int32_t)c};
-  }
-  std::sort(order.begin(), order.end());
-  // patches: runs of consecutive cells in that order, at most kStepCells cells and at most
-  // kStepMaxHent hanging-table entries each (a cell with more starts a patch of its own)
-  std::vector<size_t> pb{0};
-  {
-    const size_t n_rows = m.con_ptr.empty() ? 0 : m.con_ptr.size() - 1;
-    std::vector<uint8_t> in_patch(n_rows, 0);
-    std::vector<int32_t> rows, cell_rows;
-    int64_t hent = 0;
-    for (size_t c = 0; c < nc; ++c) {
-      cell_rows.clear();
-      for (size_t a = 0; a < npc; ++a) {
-        const int32_t d = m.cell_dofs[(size_t)order[c].second * npc + a];
-        if (d < 0 && std::find(cell_rows.begin(), cell_rows.end(), -1 - d) == cell_rows.end()) cell_rows.push_back(-1 - d);
-      }
-      auto added = [&]() {
-        int64_t h = 0;
-        for (int32_t r : cell_rows)
-          if (!in_patch[(size_t)r]) h += m.con_ptr[(size_t)r + 1] - m.con_ptr[(size_t)r];
-        return h;
-      };
-      int64_t add = added();
-      const size_t len = c - pb.back();
-      if (len > 0 && (len == (size_t)kStepCells || hent + add > kStepMaxHent)) {
-        for (int32_t r : rows) in_patch[(size_t)r] = 0;
-        rows.clear();
-        hent = 0;
-        pb.push_back(c);
-        add = added();
-      }
-      for (int32_t r : cell_rows)
-        if (!in_patch[(size_t)r]) {
-          in_patch[(size_t)r] = 1;
-          rows.push_back(r);
-        }
-      hent += add;
-    }
-    if (nc > 0) pb.push_back(nc);
-  }
-  const size_t np = pb.size() - 1;
-  // unique slot keys of every patch (dof d, or n_dofs + r for hanging row r), and its work
-  std::vector<size_t> kptr(np + 1, 0);
-  std::vector<int32_t> keys, tmp;
-  std::vector<int64_t> work(np, 0);
-  for (size_t p = 0; p < np; ++p) {
-    tmp.clear();
-    int64_t hent = 0;
-    for (size_t c = pb[p]; c < pb[p + 1]; ++c)
-      for (size_t a = 0; a < npc; ++a) {
-        const int32_t d = m.cell_dofs[(size_t)order[c].second * npc + a];
-        if (d >= 0) {
-          tmp.push_back(d);
-        } else {
-          const int32_t r = -1 - d;
-          tmp.push_back(nd32 + r);
-          for (int32_t e = m.con_ptr[(size_t)r]; e < m.con_ptr[(size_t)r + 1]; ++e) tmp.push_back(m.con_idx[(size_t)e]);
-        }
-      }
-    std::sort(tmp.begin(), tmp.end());
-    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
-    for (int32_t k : tmp)
-      if (k >= nd32) hent += m.con_ptr[(size_t)(k - nd32) + 1] - m.con_ptr[(size_t)(k - nd32)];
-    keys.insert(keys.end(), tmp.begin(), tmp.end());
-    kptr[p + 1] = keys.size();
-    work[p] = (int64_t)tmp.size() + 2 * hent;
-  }
-  std::vector<int32_t> porder(np);
-  for (size_t p = 0; p < np; ++p) porder[p] = (int32_t)p;
-  std::stable_sort(porder.begin(), porder.end(), [&](int32_t a, int32_t b) { return work[(size_t)a] > work[(size_t)b]; });
-  StepHost& o = out;
-  o.loc.assign(np * npc * kStepCells, 0);
-  o.cell.assign(np * kStepCells, -1);
-  std::vector<uint8_t> owned((size_t)m.n_dofs, 0);
-  bool ok = true;
-  for (size_t q = 0; q < np && ok; ++q) {
-    const size_t p = (size_t)porder[q];
-    const int32_t* kb = keys.data() + kptr[p];
-    const int32_t nu = (int32_t)(kptr[p + 1] - kptr[p]);
-    const int32_t nfree = (int32_t)(std::lower_bound(kb, kb + nu, nd32) - kb);
-    auto pos = [&](int32_t key) { return step_swizzle((int)(std::lower_bound(kb, kb + nu, key) - kb)); };
-    for (size_t c = pb[p]; c < pb[p + 1]; ++c) {
-      const size_t lane = c - pb[p], cell = (size_t)order[c].second;
-      o.cell[q * kStepCells + lane] = (int32_t)cell;
-      for (size_t a = 0; a < npc; ++a) {
-        const int32_t d = m.cell_dofs[cell * npc + a];
-        o.loc[(q * npc + a) * kStepCells + lane] = (uint16_t)pos(d >= 0 ? d : nd32 + (-1 - d));
-      }
-    }
-    const int32_t hbegin = (int32_t)o.hloc.size();
-    o.ptr.push_back((int32_t)o.slot.size());
-    for (int32_t j = 0; j < nu; ++j) {
-      const int32_t k = kb[j];
-      if (k < nd32) {
-        int32_t v = k;
-        if (!owned[(size_t)k]) {
-          owned[(size_t)k] = 1;
-          v = (int32_t)((uint32_t)k | 0x80000000u);
-        }
-        o.slot.push_back(v);
-      } else {
-        const int32_t r = k - nd32, e0 = m.con_ptr[(size_t)r], e1 = m.con_ptr[(size_t)r + 1];
-        const int32_t start = (int32_t)o.hloc.size() - hbegin;
-        if (e1 - e0 > 31 || start >= (1 << 26)) ok = false;
-        for (int32_t e = e0; e < e1; ++e) {
-          o.hloc.push_back((uint16_t)pos(m.con_idx[(size_t)e]));
-          o.hw.push_back((float)m.con_w[(size_t)e]);
-        }
-        o.slot.push_back((start << 5) | (e1 - e0));
-      }
-    }
-    while (o.slot.size() % 4) o.slot.push_back(0);
-    o.cnt.push_back(nfree);
-    o.cnt.push_back(nu);
-    o.cnt.push_back(hbegin);
-    o.cnt.push_back((int32_t)o.hloc.size());
-    o.max_nu = std::max(o.max_nu, (int)nu);
-    o.max_hent = std::max(o.max_hent, (int)o.hloc.size() - hbegin);
-  }
-  // every dof needs an owner (each lies in an active cell), and shared-memory positions
-  // are 16-bit; otherwise the context has no fused form
-  if (ok && std::find(owned.begin(), owned.end(), (uint8_t)0) != owned.end()) ok = false;
-  if (ok && ((o.max_nu + 31) & ~31) > 65536) ok = false;
-  if (!ok) out = StepHost();
-}
 
 pbf_status pbf_ctx_impl_create(const pbf_mesh* mesh, const pbf_material* mat, pbf_precision prec, int batch,
                                pbf_ctx** out);

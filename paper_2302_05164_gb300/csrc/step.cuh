@@ -3,6 +3,7 @@
 
 #include <utility>
 
+#include "step_layout.hpp"
 #include "vec_kernels.cuh"
 
 namespace pbf {
@@ -13,10 +14,8 @@ __device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepco
 __device__ __forceinline__ void grid_dependency_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 
-constexpr int kStepCells = 64;  // cells per patch = threads per block of the fused step kernel
-
-// Patches of kStepCells cells, built once per context on the host (cells consecutive in the
-// global Morton order, patches numbered by decreasing work). Each patch lists its unique node
+// Patches of up to kStepCells cells (step_layout.hpp), built once per context on the host
+// (cells consecutive in the global Morton order, patches numbered by decreasing work). Each patch lists its unique node
 // slots: first the dofs of its cells and the masters of its hanging nodes, in ascending
 // order, then its hanging nodes, padded to a multiple of 4 entries so that a block can load
 // its list with 16-byte loads. Every dof is owned by exactly one patch, the first that lists
@@ -36,12 +35,6 @@ struct StepTables {
   const uint16_t* hloc = nullptr; // hanging tables: master positions ...
   const float* hw = nullptr;      // ... and constraint weights
 };
-
-// Shared-memory position of slot j of a patch: an XOR swizzle within each 32-slot block.
-// Slots of consecutive Morton-order cells are about 8 apart (the new nodes per Q2 cell), so the
-// same local node of the 32 cells of a warp would fall into 4 banks; the swizzle spreads them
-// over all 32, and keeps a warp's 32 consecutive slots conflict-free.
-__host__ __device__ inline int step_swizzle(int j) { return j ^ ((j >> 5) & 31); }
 
 // loc table, slot list, staged values and contributions, hanging tables
 inline int step_smem_bytes(int npc, int max_nu32, int max_hent8) {
