@@ -8,6 +8,10 @@
 // the repository exactly (bit for bit), including the floating-point geometry tests.
 #include "mesh.hpp"
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #include <algorithm>
 #ifdef _OPENMP
 #include <parallel/algorithm>
@@ -131,13 +135,28 @@ static void rekey(HostMesh& m) {
 }
 
 static void balance(HostMesh& m) {
+  const int64_t n_fine = m.ext[0] * m.ext[1] * m.ext[2];
+  const bool use_grid = n_fine <= HostMesh::kFineGridMax;
+  std::unique_ptr<uint8_t[]> level_of;  // the level of the leaf holding each finest cell
+  if (use_grid) level_of.reset(new uint8_t[(size_t)n_fine]);
   for (;;) {
+    const int64_t nl = (int64_t)m.oct.size();
+    if (use_grid) {
+#pragma omp parallel for schedule(dynamic, 256)
+      for (int64_t i = 0; i < nl; ++i) {
+        const Octant& o = m.oct[(size_t)i];
+        const int64_t s = m.size(o);
+        for (int64_t z = o.a[2]; z < o.a[2] + s; ++z)
+          for (int64_t y = o.a[1]; y < o.a[1] + s; ++y)
+            std::memset(level_of.get() + (size_t)(o.a[0] + m.ext[0] * (y + m.ext[1] * z)), o.level, (size_t)s);
+      }
+    }
     // mark the leaves that are more than one level coarser than a vertex neighbour (the
     // leaves are scanned in parallel; a mark is only ever set to 1). Only a leaf of level 2 or
-    // finer can have such a neighbour.
+    // finer can have such a neighbour; the level grid answers whether a neighbour is too
+    // coarse, and only such a neighbour is looked up by its key.
     std::vector<uint8_t> split(m.oct.size(), 0);
     int any = 0;
-    const int64_t nl = (int64_t)m.oct.size();
 #pragma omp parallel for schedule(static, 4096) reduction(| : any)
     for (int64_t i = 0; i < nl; ++i) {
       const Octant& o = m.oct[(size_t)i];
@@ -146,6 +165,8 @@ static void balance(HostMesh& m) {
       for (int nb = 0; nb < 27; ++nb) {
         if (nb == 13) continue;
         int64_t q[3] = {o.a[0] + (nb % 3 - 1) * s, o.a[1] + ((nb / 3) % 3 - 1) * s, o.a[2] + (nb / 9 - 1) * s};
+        if (use_grid && (!m.inside(q) || level_of[(size_t)(q[0] + m.ext[0] * (q[1] + m.ext[1] * q[2]))] >= o.level - 1))
+          continue;
         int64_t j = m.locate(q);
         if (j >= 0 && m.oct[(size_t)j].level < o.level - 1) {
 #pragma omp atomic write
@@ -443,13 +464,27 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
   out.n_old = om.n_dofs;
   out.n_new = nm.n_dofs;
   out.fill = fill;
-  // the rows are built in parallel (one per new dof) and concatenated in dof order
-  std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nm.n_dofs);
-#pragma omp parallel
+  // the rows are built in parallel, each thread a contiguous range of new dofs into its own
+  // buffers, and concatenated in dof order (the same result for any number of threads)
+  const int64_t n_new = nm.n_dofs;
+  int n_threads = 1;
+#ifdef _OPENMP
+  n_threads = omp_get_max_threads();
+#endif
+  std::vector<std::vector<int32_t>> t_idx((size_t)n_threads);
+  std::vector<std::vector<double>> t_w((size_t)n_threads);
+  std::vector<int32_t> row_len((size_t)n_new, 0);
+#pragma omp parallel num_threads(n_threads)
   {
+    int t = 0;
+#ifdef _OPENMP
+    t = omp_get_thread_num();
+#endif
+    const int64_t lo = n_new * t / n_threads, hi = n_new * (t + 1) / n_threads;
     std::vector<std::pair<int32_t, double>> acc;
-#pragma omp for schedule(static, 1024)
-    for (int64_t i = 0; i < nm.n_dofs; ++i) {
+    std::vector<int32_t>& my_idx = t_idx[(size_t)t];
+    std::vector<double>& my_w = t_w[(size_t)t];
+    for (int64_t i = lo; i < hi; ++i) {
       const int64_t* n = &nm.dof_xyz[(size_t)i * 3];
       // first old active cell (cell order) whose closure holds the point
       int32_t best = -1;
@@ -485,25 +520,30 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
       }
       std::stable_sort(acc.begin(), acc.end(),
                        [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
-      auto& row = rows[(size_t)i];
+      int32_t len = 0;
       for (size_t e = 0; e < acc.size();) {
         size_t f = e;
         double sum = 0.0;
         while (f < acc.size() && acc[f].first == acc[e].first) sum += acc[f++].second;
-        if (sum != 0.0) row.push_back({acc[e].first, sum});
+        if (sum != 0.0) {
+          my_idx.push_back(acc[e].first);
+          my_w.push_back(sum);
+          ++len;
+        }
         e = f;
       }
+      row_len[(size_t)i] = len;
     }
   }
-  out.ptr.assign(1, 0);
+  out.ptr.assign((size_t)n_new + 1, 0);
+  for (int64_t i = 0; i < n_new; ++i) out.ptr[(size_t)i + 1] = out.ptr[(size_t)i] + row_len[(size_t)i];
   out.idx.clear();
   out.w.clear();
-  for (const auto& row : rows) {
-    for (const auto& e : row) {
-      out.idx.push_back(e.first);
-      out.w.push_back(e.second);
-    }
-    out.ptr.push_back((int32_t)out.idx.size());
+  out.idx.reserve((size_t)out.ptr.back());
+  out.w.reserve((size_t)out.ptr.back());
+  for (int t = 0; t < n_threads; ++t) {
+    out.idx.insert(out.idx.end(), t_idx[(size_t)t].begin(), t_idx[(size_t)t].end());
+    out.w.insert(out.w.end(), t_w[(size_t)t].begin(), t_w[(size_t)t].end());
   }
 }
 
