@@ -254,6 +254,30 @@ static void sort_pairs(std::vector<std::pair<uint64_t, int64_t>>& v) {
 #endif
 }
 
+// out[i] = the number of j < i with pred(j), for i in [0, n): a prefix sum over fixed chunks,
+// on all host cores (the result does not depend on the number of threads).
+template <typename Pred>
+static void exclusive_count(int64_t n, Pred pred, int32_t* out) {
+  const int64_t chunk = 1 << 16;
+  const int64_t nch = (n + chunk - 1) / chunk;
+  std::vector<int32_t> base((size_t)nch + 1, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nch; ++c) {
+    int32_t k = 0;
+    for (int64_t i = c * chunk; i < std::min(n, (c + 1) * chunk); ++i) k += pred(i) ? 1 : 0;
+    base[(size_t)c + 1] = k;
+  }
+  for (int64_t c = 0; c < nch; ++c) base[(size_t)c + 1] += base[(size_t)c];
+#pragma omp parallel for schedule(static)
+  for (int64_t c = 0; c < nch; ++c) {
+    int32_t k = base[(size_t)c];
+    for (int64_t i = c * chunk; i < std::min(n, (c + 1) * chunk); ++i) {
+      out[(size_t)i] = k;
+      k += pred(i) ? 1 : 0;
+    }
+  }
+}
+
 pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::string* err) {
   const int p = m.p;
   // forest
@@ -317,38 +341,70 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
     }
   }
   sort_pairs(ents);  // a total order (the slots are distinct): the same result in parallel
+  // unique nodes: entry e starts a node when its key differs from the previous one, and the
+  // node's index is the number of starts up to e (a prefix sum); the entries of a node are
+  // sorted by slot, so its first entry holds its first slot
+  const int64_t ne = (int64_t)ents.size();
+  auto starts = [&](int64_t e) { return e == 0 || ents[(size_t)e].first != ents[(size_t)e - 1].first; };
+  std::vector<int32_t> starts_before((size_t)ne);
+  exclusive_count(ne, starts, starts_before.data());
+  const size_t nn = ne == 0 ? 0 : (size_t)starts_before.back() + (starts(ne - 1) ? 1 : 0);
   NodeTable nodes;
+  nodes.keys.resize(nn);
+  nodes.xyz.resize(3 * nn);
+  std::vector<int32_t> first_slot(nn);
   std::vector<int32_t> node_of_slot(na * (size_t)npc);
-  for (size_t e = 0; e < ents.size(); ++e) {
-    if (e == 0 || ents[e].first != ents[e - 1].first) {
-      nodes.keys.push_back(ents[e].first);
-      uint64_t k = ents[e].first;
-      nodes.xyz.push_back((int64_t)(k & 0x1FFFFF));
-      nodes.xyz.push_back((int64_t)((k >> 21) & 0x1FFFFF));
-      nodes.xyz.push_back((int64_t)(k >> 42));
+#pragma omp parallel for schedule(static)
+  for (int64_t e = 0; e < ne; ++e) {
+    const bool st = starts(e);
+    const size_t nd = (size_t)(starts_before[(size_t)e] + (st ? 1 : 0) - 1);
+    if (st) {
+      const uint64_t k = ents[(size_t)e].first;
+      nodes.keys[nd] = k;
+      nodes.xyz[3 * nd] = (int64_t)(k & 0x1FFFFF);
+      nodes.xyz[3 * nd + 1] = (int64_t)((k >> 21) & 0x1FFFFF);
+      nodes.xyz[3 * nd + 2] = (int64_t)(k >> 42);
+      first_slot[nd] = (int32_t)ents[(size_t)e].second;
     }
-    node_of_slot[(size_t)ents[e].second] = (int32_t)nodes.keys.size() - 1;
+    node_of_slot[(size_t)ents[(size_t)e].second] = (int32_t)nd;
   }
-  size_t nn = nodes.keys.size();
   std::vector<int32_t> holder(nn);
 #pragma omp parallel for schedule(static, 4096)
   for (int64_t i = 0; i < (int64_t)nn; ++i) holder[(size_t)i] = first_coarse_holder(m, &nodes.xyz[(size_t)i * 3]);
-  // first-touch numbering of dofs and of constraint rows
+  // first-touch numbering of dofs and of constraint rows: a node is numbered at its first slot,
+  // so its number is the count of first slots of its kind (free or hanging) before that one.
+  // Kind of each slot: 0 not its node's first, 1 the first of a free node, 2 of a hanging one.
+  const int64_t ns = (int64_t)node_of_slot.size();
+  std::vector<uint8_t> kind((size_t)ns);
+#pragma omp parallel for schedule(static)
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    const int32_t nd = node_of_slot[(size_t)sl];
+    kind[(size_t)sl] = first_slot[(size_t)nd] != (int32_t)sl ? 0 : (holder[(size_t)nd] < 0 ? 1 : 2);
+  }
+  std::vector<int32_t> dof_before((size_t)ns), row_before((size_t)ns);
+  exclusive_count(ns, [&](int64_t sl) { return kind[(size_t)sl] == 1; }, dof_before.data());
+  exclusive_count(ns, [&](int64_t sl) { return kind[(size_t)sl] == 2; }, row_before.data());
   std::vector<int32_t> dof(nn, -1), row(nn, -1);
-  m.n_dofs = 0;
-  int32_t n_rows = 0;
-  std::vector<int32_t> row_node;
-  m.dof_xyz.clear();
-  for (size_t slot = 0; slot < node_of_slot.size(); ++slot) {
-    int32_t nd = node_of_slot[slot];
-    if (holder[(size_t)nd] >= 0) {
-      if (row[(size_t)nd] < 0) {
-        row[(size_t)nd] = n_rows++;
-        row_node.push_back(nd);
-      }
-    } else if (dof[(size_t)nd] < 0) {
-      dof[(size_t)nd] = (int32_t)m.n_dofs++;
-      for (int a = 0; a < 3; ++a) m.dof_xyz.push_back(nodes.xyz[(size_t)nd * 3 + a]);
+  int64_t n_dofs = 0, n_rows64 = 0;
+  if (ns > 0) {
+    n_dofs = dof_before[(size_t)ns - 1] + (kind[(size_t)ns - 1] == 1 ? 1 : 0);
+    n_rows64 = row_before[(size_t)ns - 1] + (kind[(size_t)ns - 1] == 2 ? 1 : 0);
+  }
+  m.n_dofs = n_dofs;
+  const int32_t n_rows = (int32_t)n_rows64;
+  std::vector<int32_t> row_node((size_t)n_rows);
+  m.dof_xyz.assign((size_t)n_dofs * 3, 0);
+#pragma omp parallel for schedule(static)
+  for (int64_t sl = 0; sl < ns; ++sl) {
+    if (kind[(size_t)sl] == 0) continue;
+    const int32_t nd = node_of_slot[(size_t)sl];
+    if (kind[(size_t)sl] == 2) {
+      row[(size_t)nd] = row_before[(size_t)sl];
+      row_node[(size_t)row_before[(size_t)sl]] = nd;
+    } else {
+      const int32_t d = dof_before[(size_t)sl];
+      dof[(size_t)nd] = d;
+      for (int a = 0; a < 3; ++a) m.dof_xyz[(size_t)d * 3 + (size_t)a] = nodes.xyz[(size_t)nd * 3 + (size_t)a];
     }
   }
   if (m.n_dofs >= ((int64_t)1 << 31)) return *err = "too many dofs", PBF_EINVAL;
