@@ -408,18 +408,20 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
     }
   }
   if (m.n_dofs >= ((int64_t)1 << 31)) return *err = "too many dofs", PBF_EINVAL;
-  // constraint rows, with chains substituted (memoised by node)
-  std::map<int32_t, std::vector<std::pair<int32_t, double>>> memo;
-  std::vector<std::pair<int32_t, double>> stackbuf;
-  std::function<const std::vector<std::pair<int32_t, double>>&(int32_t)> expand;
-  expand = [&](int32_t nd) -> const std::vector<std::pair<int32_t, double>>& {
-    auto it = memo.find(nd);
-    if (it != memo.end()) return it->second;
+  // constraint rows, with chains substituted: rows whose masters are all free are expanded on
+  // all host cores, the others (chains through hanging masters) afterwards in row order,
+  // reusing the expanded rows; each row's arithmetic is the same either way
+  using Row = std::vector<std::pair<int32_t, double>>;
+  std::vector<Row> memo((size_t)n_rows);
+  std::vector<uint8_t> done((size_t)n_rows, 0);
+  // the expansion of hanging node nd into `out`; sub(r) gives row r's expansion or null when it
+  // is not available (then nothing is written and false is returned)
+  auto expand_row = [&](int32_t nd, const auto& sub, Row& out) -> bool {
     const Octant& c = m.oct[(size_t)m.leaf_of_active[(size_t)holder[(size_t)nd]]];
     int64_t s = m.size(c);
     double w1[3][3];
     for (int a = 0; a < 3; ++a) weights_1d(p, nodes.xyz[(size_t)nd * 3 + a] - p * c.a[a], s, w1[a]);
-    std::vector<std::pair<int32_t, double>> acc;
+    Row acc;
     for (int l = 0; l < npc; ++l) {
       int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
       double w = w1[0][ijk[0]] * w1[1][ijk[1]] * w1[2][ijk[2]];
@@ -428,15 +430,16 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
       for (int a = 0; a < 3; ++a) q[a] = p * c.a[a] + ijk[a] * s;
       int32_t mn = (int32_t)nodes.find(q);
       if (holder[(size_t)mn] >= 0) {
-        const auto& sub = expand(mn);
-        for (const auto& e : sub) acc.push_back({e.first, w * e.second});
+        const Row* r = sub(row[(size_t)mn]);
+        if (!r) return false;
+        for (const auto& e : *r) acc.push_back({e.first, w * e.second});
       } else {
         acc.push_back({dof[(size_t)mn], w});
       }
     }
     std::stable_sort(acc.begin(), acc.end(),
                      [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
-    std::vector<std::pair<int32_t, double>> out;
+    out.clear();
     for (size_t e = 0; e < acc.size();) {
       size_t f = e;
       double sum = 0.0;
@@ -444,15 +447,28 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
       if (sum != 0.0) out.push_back({acc[e].first, sum});
       e = f;
     }
-    return memo[nd] = out;
+    return true;
   };
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t r = 0; r < (int64_t)n_rows; ++r) {
+    auto none = [](int32_t) -> const Row* { return nullptr; };
+    if (expand_row(row_node[(size_t)r], none, memo[(size_t)r])) done[(size_t)r] = 1;
+  }
+  std::function<const Row*(int32_t)> chain = [&](int32_t r) -> const Row* {
+    if (!done[(size_t)r]) {
+      expand_row(row_node[(size_t)r], chain, memo[(size_t)r]);
+      done[(size_t)r] = 1;
+    }
+    return &memo[(size_t)r];
+  };
+  for (int32_t r = 0; r < n_rows; ++r) chain(r);
   m.con_ptr.assign(1, 0);
   m.con_idx.clear();
   m.con_w.clear();
   m.hang_xyz.clear();
   for (int32_t r = 0; r < n_rows; ++r) {
     int32_t nd = row_node[(size_t)r];
-    for (const auto& e : expand(nd)) {
+    for (const auto& e : memo[(size_t)r]) {
       m.con_idx.push_back(e.first);
       m.con_w.push_back(e.second);
     }
