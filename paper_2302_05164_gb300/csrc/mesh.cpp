@@ -20,7 +20,6 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
-#include <map>
 
 namespace pbf {
 
