@@ -128,6 +128,41 @@ pbf_status pbf_mesh_destroy(pbf_mesh* mesh);
 pbf_status pbf_mesh_info(const pbf_mesh* mesh, pbf_mesh_info_t* out);
 pbf_status pbf_mesh_export(const pbf_mesh* mesh, const pbf_mesh_tables* out);
 
+/* Patch tables of the fused explicit step (the one-pass step of Sec. 4.2: a block loads its
+ * cells' nodal values once, evaluates f and updates the state), built on the host as
+ * pbf_ctx_create builds them for an FP32-operator context of batch 1. A patch is up to
+ * cells_per_patch active cells consecutive in the Morton order of their anchors over the whole
+ * brick, with at most 640 hanging-table entries unless it holds one cell; patches are numbered
+ * by decreasing work (slots + 2 x hanging entries); each dof is owned by the first patch in
+ * that numbering that lists it. Shared-memory positions are s(j) = j ^ ((j >> 5) & 31) of
+ * slot index j.
+ *  ptr    [n_patches]                          first entry of patch q in slot
+ *  cnt    [n_patches][4]                       dof slots, all slots, hanging table begin, end
+ *  slot   [n_slots]  per patch, ascending keys: dof d (bit 31 set where q owns d) for the
+ *                    dofs of its cells and the masters of its hanging nodes, then one entry
+ *                    (start << 5) | count per hanging row in ascending row order (start
+ *                    relative to the patch's hanging table); zero-padded to a multiple of 4
+ *  cell   [n_patches][cells_per_patch]          active cell of each lane, -1 past the end
+ *  loc    [n_patches][nodes_per_cell][cells_per_patch]  s(slot index) of each lane's node
+ *  hloc   [n_hent], hw [n_hent]                s(slot index) of each master, its weight
+ * Sizes are outputs. With every array NULL the call only reports the sizes; otherwise the
+ * sizes passed in must equal the mesh's (from a sizes-only call on the same mesh generation)
+ * and each non-NULL array is filled. n_patches = 0 when the fused form does not apply (a
+ * constraint row of more than 31 entries, or a patch of more than 65,536 slots). Host only.
+ * Errors: PBF_EINVAL (null mesh or tables, sizes that differ), PBF_ENOMEM. */
+typedef struct {
+  int64_t n_patches, n_slots, n_hent;
+  int32_t cells_per_patch, max_slots, max_hent;
+  int32_t* ptr;
+  int32_t* cnt;
+  int32_t* slot;
+  int32_t* cell;
+  uint16_t* loc;
+  uint16_t* hloc;
+  float* hw;
+} pbf_step_tables;
+pbf_status pbf_mesh_step_tables(const pbf_mesh* mesh, pbf_step_tables* tables);
+
 /* Layer activation (Sec. 4.1; initial condition of Sec. 2 for later-activated parts): raises
  * the activation height to z_new_top; newly active cells take `material`. Host topology
  * change only; it records a pending transfer (old dofs -> new dofs) that pbf_mesh_transfer

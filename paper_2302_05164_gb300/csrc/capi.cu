@@ -112,6 +112,36 @@ extern "C" pbf_status pbf_mesh_export(const pbf_mesh* mesh, const pbf_mesh_table
   return PBF_OK;
 }
 
+extern "C" pbf_status pbf_mesh_step_tables(const pbf_mesh* mesh, pbf_step_tables* t) {
+  if (!mesh || !t) return fail(PBF_EINVAL, "null argument");
+  try {
+    StepHost sh;
+    build_step_tables(mesh->m, sh);
+    const int64_t np = (int64_t)sh.ptr.size(), ns = (int64_t)sh.slot.size(), nh = (int64_t)sh.hloc.size();
+    const bool fill = t->ptr || t->cnt || t->slot || t->cell || t->loc || t->hloc || t->hw;
+    if (fill && (t->n_patches != np || t->n_slots != ns || t->n_hent != nh))
+      return fail(PBF_EINVAL, "table sizes (%lld, %lld, %lld) differ from the mesh's (%lld, %lld, %lld)",
+                  (long long)t->n_patches, (long long)t->n_slots, (long long)t->n_hent, (long long)np,
+                  (long long)ns, (long long)nh);
+    t->n_patches = np;
+    t->n_slots = ns;
+    t->n_hent = nh;
+    t->cells_per_patch = kStepCells;
+    t->max_slots = sh.max_nu;
+    t->max_hent = sh.max_hent;
+    if (t->ptr) std::memcpy(t->ptr, sh.ptr.data(), sh.ptr.size() * 4);
+    if (t->cnt) std::memcpy(t->cnt, sh.cnt.data(), sh.cnt.size() * 4);
+    if (t->slot) std::memcpy(t->slot, sh.slot.data(), sh.slot.size() * 4);
+    if (t->cell) std::memcpy(t->cell, sh.cell.data(), sh.cell.size() * 4);
+    if (t->loc) std::memcpy(t->loc, sh.loc.data(), sh.loc.size() * 2);
+    if (t->hloc) std::memcpy(t->hloc, sh.hloc.data(), sh.hloc.size() * 2);
+    if (t->hw) std::memcpy(t->hw, sh.hw.data(), sh.hw.size() * 4);
+    return PBF_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(PBF_ENOMEM, "host allocation failed");
+  }
+}
+
 extern "C" pbf_status pbf_mesh_activate_layer(pbf_mesh* mesh, double z_new_top, int material, double T_init) {
   if (!mesh) return fail(PBF_EINVAL, "null mesh");
   if (material < 0 || material > 1) return fail(PBF_EINVAL, "material must be 0 or 1");

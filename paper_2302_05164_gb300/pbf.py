@@ -57,6 +57,12 @@ class MeshTables(C.Structure):
                                           "hang_coord", "dof_coord", "dirichlet", "colour", "top")]
 
 
+class StepTables(C.Structure):
+    _fields_ = [("n_patches", C.c_int64), ("n_slots", C.c_int64), ("n_hent", C.c_int64),
+                ("cells_per_patch", C.c_int32), ("max_slots", C.c_int32), ("max_hent", C.c_int32)] + \
+               [(n, C.c_void_p) for n in ("ptr", "cnt", "slot", "cell", "loc", "hloc", "hw")]
+
+
 class Material(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("rho", "c", "k0", "k1", "Tk0", "Tk1", "latent", "Tm", "sigma",
                                           "powder_k_scale", "T_dirichlet", "T_ref")] + [("lumping", C.c_int)]
@@ -76,6 +82,7 @@ _SIGS = {
     "pbf_mesh_destroy": ([C.c_void_p], C.c_int),
     "pbf_mesh_info": ([C.c_void_p, C.POINTER(MeshInfo)], C.c_int),
     "pbf_mesh_export": ([C.c_void_p, C.POINTER(MeshTables)], C.c_int),
+    "pbf_mesh_step_tables": ([C.c_void_p, C.POINTER(StepTables)], C.c_int),
     "pbf_mesh_activate_layer": ([C.c_void_p, C.c_double, C.c_int, C.c_double], C.c_int),
     "pbf_mesh_adapt": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pbf_mesh_adapt_gated": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double], C.c_int),
@@ -222,6 +229,23 @@ def pbf_mesh_export(h) -> dict:
     tab = MeshTables(*[_ptr(t[n]) for n, _ in MeshTables._fields_])
     _check(lib().pbf_mesh_export(h, C.byref(tab)))
     return t
+
+
+def pbf_mesh_step_tables(h) -> dict:
+    """Patch tables of the fused explicit step (host only): sizes first, then the arrays."""
+    t = StepTables()
+    _check(lib().pbf_mesh_step_tables(h, C.byref(t)))
+    npc = pbf_mesh_info(h)["nodes_per_cell"]
+    npat, cpp = int(t.n_patches), int(t.cells_per_patch)
+    out = dict(ptr=np.zeros(npat, np.int32), cnt=np.zeros((npat, 4), np.int32), slot=np.zeros(t.n_slots, np.int32),
+               cell=np.zeros((npat, cpp), np.int32), loc=np.zeros((npat, npc, cpp), np.uint16),
+               hloc=np.zeros(t.n_hent, np.uint16), hw=np.zeros(t.n_hent, np.float32))
+    if npat:
+        for n in ("ptr", "cnt", "slot", "cell", "loc", "hloc", "hw"):
+            setattr(t, n, _ptr(out[n]))
+        _check(lib().pbf_mesh_step_tables(h, C.byref(t)))
+    out.update(cells_per_patch=cpp, max_slots=int(t.max_slots), max_hent=int(t.max_hent))
+    return out
 
 
 def pbf_mesh_activate_layer(h, z_new_top, material, T_init):
