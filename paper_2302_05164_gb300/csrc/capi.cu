@@ -252,6 +252,25 @@ extern "C" pbf_status pbf_mesh_transfer(pbf_mesh* mesh, const double* T_old_dev,
   return PBF_OK;
 }
 
+extern "C" pbf_status pbf_mesh_transfer_map(const pbf_mesh* mesh, pbf_transfer_map* t) {
+  if (!mesh || !t) return fail(PBF_EINVAL, "null argument");
+  const TransferMap& tr = mesh->m.transfer;
+  if (!tr.pending) return fail(PBF_ESTATE, "no pending transfer");
+  const int64_t ne = (int64_t)tr.idx.size();
+  if ((t->ptr || t->idx || t->w) && (t->n_old != tr.n_old || t->n_new != tr.n_new || t->n_entries != ne))
+    return fail(PBF_EINVAL, "map sizes (%lld, %lld, %lld) differ from the mesh's (%lld, %lld, %lld)",
+                (long long)t->n_old, (long long)t->n_new, (long long)t->n_entries, (long long)tr.n_old,
+                (long long)tr.n_new, (long long)ne);
+  t->n_old = tr.n_old;
+  t->n_new = tr.n_new;
+  t->n_entries = ne;
+  t->fill = tr.fill;
+  if (t->ptr) std::memcpy(t->ptr, tr.ptr.data(), tr.ptr.size() * 4);
+  if (t->idx) std::memcpy(t->idx, tr.idx.data(), tr.idx.size() * 4);
+  if (t->w) std::memcpy(t->w, tr.w.data(), tr.w.size() * 8);
+  return PBF_OK;
+}
+
 // ======================================================================================
 // context
 // ======================================================================================

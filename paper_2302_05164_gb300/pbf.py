@@ -63,6 +63,11 @@ class StepTables(C.Structure):
                [(n, C.c_void_p) for n in ("ptr", "cnt", "slot", "cell", "loc", "hloc", "hw")]
 
 
+class TransferMapC(C.Structure):
+    _fields_ = [("n_old", C.c_int64), ("n_new", C.c_int64), ("n_entries", C.c_int64), ("fill", C.c_double),
+                ("ptr", C.c_void_p), ("idx", C.c_void_p), ("w", C.c_void_p)]
+
+
 class Material(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("rho", "c", "k0", "k1", "Tk0", "Tk1", "latent", "Tm", "sigma",
                                           "powder_k_scale", "T_dirichlet", "T_ref")] + [("lumping", C.c_int)]
@@ -83,6 +88,7 @@ _SIGS = {
     "pbf_mesh_info": ([C.c_void_p, C.POINTER(MeshInfo)], C.c_int),
     "pbf_mesh_export": ([C.c_void_p, C.POINTER(MeshTables)], C.c_int),
     "pbf_mesh_step_tables": ([C.c_void_p, C.POINTER(StepTables)], C.c_int),
+    "pbf_mesh_transfer_map": ([C.c_void_p, C.POINTER(TransferMapC)], C.c_int),
     "pbf_mesh_activate_layer": ([C.c_void_p, C.c_double, C.c_int, C.c_double], C.c_int),
     "pbf_mesh_adapt": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pbf_mesh_adapt_gated": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double], C.c_int),
@@ -245,6 +251,18 @@ def pbf_mesh_step_tables(h) -> dict:
             setattr(t, n, _ptr(out[n]))
         _check(lib().pbf_mesh_step_tables(h, C.byref(t)))
     out.update(cells_per_patch=cpp, max_slots=int(t.max_slots), max_hent=int(t.max_hent))
+    return out
+
+
+def pbf_mesh_transfer_map(h) -> dict:
+    """The pending transfer's map (host only): sizes first, then the arrays."""
+    t = TransferMapC()
+    _check(lib().pbf_mesh_transfer_map(h, C.byref(t)))
+    out = dict(ptr=np.zeros(t.n_new + 1, np.int32), idx=np.zeros(t.n_entries, np.int32),
+               w=np.zeros(t.n_entries, np.float64))
+    t.ptr, t.idx, t.w = (_ptr(out[n]) for n in ("ptr", "idx", "w"))
+    _check(lib().pbf_mesh_transfer_map(h, C.byref(t)))
+    out.update(n_old=int(t.n_old), n_new=int(t.n_new), fill=float(t.fill))
     return out
 
 

@@ -1,6 +1,6 @@
 """The host mesh builder runs its independent work on all host cores (balance, node table,
-numbering, constraint rows, holders, the fused step's patch tables); its tables must not depend
-on the number of threads.
+numbering, constraint rows, holders, the fused step's patch tables, the transfer map); its
+tables must not depend on the number of threads.
 Two processes, one with a single OpenMP thread and one with four, build a Q2 mesh with nested
 refinement, hanging nodes and an inactive layer, adapt it twice (the spot moves), and export
 the tables after each step: all arrays are equal. No GPU is needed."""
@@ -30,6 +30,8 @@ out = {{}}
 for step, x in enumerate((None, 0.45e-3, 0.6e-3)):
     if x is not None:
         pbf.pbf_mesh_adapt(m.h, regions(x))
+        for k, v in pbf.pbf_mesh_transfer_map(m.h).items():
+            out[f"{{step}}_map_{{k}}"] = np.asarray(v)
     for k, v in m.tables().items():
         out[f"{{step}}_{{k}}"] = np.asarray(v)
     for k, v in pbf.pbf_mesh_step_tables(m.h).items():
@@ -51,6 +53,8 @@ def test_mesh_tables_do_not_depend_on_the_thread_count(tmp_path):
     assert any(k.endswith("_con_idx") and one[k].size > 0 for k in one.files)  # hanging nodes exist
     assert one["0_cell_dofs"].size > 2 * 65536  # three or more chunks of the prefix sums over slots
     assert all(one[f"{s}_step_ptr"].size > 8 for s in range(3))  # patches for several threads
+    # rows of every thread, with prolongation (several entries) among them
+    assert all(one[f"{s}_map_ptr"].size > 10000 and one[f"{s}_map_idx"].size > one[f"{s}_map_ptr"].size for s in (1, 2))
     for k in one.files:
         assert one[k].shape == four[k].shape, k
         assert np.array_equal(one[k], four[k]), k
