@@ -415,7 +415,14 @@ pbf_status pbf_ctx_autotune(pbf_ctx* ctx, const double* T_dev, int reps, int* va
  * takes the value of the nearest (per axis) quadrature point of the first old active cell, in
  * cell order, whose closure holds it (a copy on refinement, injection on coarsening); points
  * outside the old active domain start as new cells do (0 in powder, 1 elsewhere). PBF_ESTATE
- * when `from` is not of the mesh before its last change. Synchronises. */
+ * when `from` is not of the mesh before its last change. Synchronises.
+ * pbf_mesh_history_map: the map pbf_ctx_transfer_history applies, on the host, for inspection:
+ * map [n_active][(p+1)^3] (nullable; quadrature point index x fastest) receives, for each
+ * quadrature point of the mesh, the old cell x (p+1)^3 + old point whose r_c it takes, or -1
+ * (it starts at 0: powder) or -2 (it starts at 1); n_old_cells_out (nullable) the old mesh's
+ * active cells. Host only. PBF_EINVAL for a null mesh, PBF_ESTATE when the mesh has not
+ * changed since it was created. */
+pbf_status pbf_mesh_history_map(const pbf_mesh* mesh, int64_t* n_old_cells_out, int32_t* map);
 pbf_status pbf_ctx_history_cell_min(pbf_ctx* ctx, double* rc_min_host, pbf_stream stream);
 pbf_status pbf_ctx_get_history(pbf_ctx* ctx, double* rc_dev, pbf_stream stream);
 pbf_status pbf_ctx_set_history(pbf_ctx* ctx, const double* rc_dev, pbf_stream stream);

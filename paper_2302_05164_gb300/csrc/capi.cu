@@ -252,6 +252,15 @@ extern "C" pbf_status pbf_mesh_transfer(pbf_mesh* mesh, const double* T_old_dev,
   return PBF_OK;
 }
 
+extern "C" pbf_status pbf_mesh_history_map(const pbf_mesh* mesh, int64_t* n_old_cells_out, int32_t* map) {
+  if (!mesh) return fail(PBF_EINVAL, "null mesh");
+  const HostMesh& m = mesh->m;
+  if (m.generation <= 1) return fail(PBF_ESTATE, "no mesh change recorded");
+  if (n_old_cells_out) *n_old_cells_out = m.history_old_cells;
+  if (map) std::memcpy(map, m.history_map.data(), m.history_map.size() * 4);
+  return PBF_OK;
+}
+
 extern "C" pbf_status pbf_mesh_transfer_map(const pbf_mesh* mesh, pbf_transfer_map* t) {
   if (!mesh || !t) return fail(PBF_EINVAL, "null argument");
   const TransferMap& tr = mesh->m.transfer;

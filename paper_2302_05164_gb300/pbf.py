@@ -89,6 +89,7 @@ _SIGS = {
     "pbf_mesh_export": ([C.c_void_p, C.POINTER(MeshTables)], C.c_int),
     "pbf_mesh_step_tables": ([C.c_void_p, C.POINTER(StepTables)], C.c_int),
     "pbf_mesh_transfer_map": ([C.c_void_p, C.POINTER(TransferMapC)], C.c_int),
+    "pbf_mesh_history_map": ([C.c_void_p, C.POINTER(C.c_int64), C.c_void_p], C.c_int),
     "pbf_mesh_activate_layer": ([C.c_void_p, C.c_double, C.c_int, C.c_double], C.c_int),
     "pbf_mesh_adapt": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "pbf_mesh_adapt_gated": ([C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double], C.c_int),
@@ -264,6 +265,16 @@ def pbf_mesh_transfer_map(h) -> dict:
     _check(lib().pbf_mesh_transfer_map(h, C.byref(t)))
     out.update(n_old=int(t.n_old), n_new=int(t.n_new), fill=float(t.fill))
     return out
+
+
+def pbf_mesh_history_map(h):
+    """The history map of the mesh's last change (host only): ([n_active][(p+1)^3] int32, the old
+    mesh's active cells)."""
+    i = pbf_mesh_info(h)
+    out = np.zeros((i["n_active"], i["nodes_per_cell"]), np.int32)
+    n_old = C.c_int64()
+    _check(lib().pbf_mesh_history_map(h, C.byref(n_old), _ptr(out)))
+    return out, int(n_old.value)
 
 
 def pbf_mesh_activate_layer(h, z_new_top, material, T_init):

@@ -1,6 +1,6 @@
 """The host mesh builder runs its independent work on all host cores (balance, node table,
-numbering, constraint rows, holders, the fused step's patch tables, the transfer map); its
-tables must not depend on the number of threads.
+numbering, constraint rows, holders, the fused step's patch tables, the transfer and history
+maps); its tables must not depend on the number of threads.
 Two processes, one with a single OpenMP thread and one with four, build a Q2 mesh with nested
 refinement, hanging nodes and an inactive layer, adapt it twice (the spot moves), and export
 the tables after each step: all arrays are equal. No GPU is needed."""
@@ -32,6 +32,7 @@ for step, x in enumerate((None, 0.45e-3, 0.6e-3)):
         pbf.pbf_mesh_adapt(m.h, regions(x))
         for k, v in pbf.pbf_mesh_transfer_map(m.h).items():
             out[f"{{step}}_map_{{k}}"] = np.asarray(v)
+        out[f"{{step}}_history_map"] = pbf.pbf_mesh_history_map(m.h)[0]
     for k, v in m.tables().items():
         out[f"{{step}}_{{k}}"] = np.asarray(v)
     for k, v in pbf.pbf_mesh_step_tables(m.h).items():
