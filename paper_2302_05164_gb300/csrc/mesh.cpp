@@ -476,43 +476,50 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
   }
   // cell table
   m.cell_dofs.resize(na * (size_t)npc);
-  for (size_t slot = 0; slot < node_of_slot.size(); ++slot) {
-    int32_t nd = node_of_slot[slot];
-    m.cell_dofs[slot] = holder[(size_t)nd] >= 0 ? -1 - row[(size_t)nd] : dof[(size_t)nd];
+#pragma omp parallel for schedule(static)
+  for (int64_t slot = 0; slot < ns; ++slot) {
+    const int32_t nd = node_of_slot[(size_t)slot];
+    m.cell_dofs[(size_t)slot] = holder[(size_t)nd] >= 0 ? -1 - row[(size_t)nd] : dof[(size_t)nd];
   }
   // Dirichlet dofs
   m.dirichlet.assign((size_t)m.n_dofs, 0);
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < m.n_dofs; ++i)
     for (int a = 0; a < 3; ++a) {
       int64_t v = m.dof_xyz[(size_t)i * 3 + a];
       if ((m.desc.dirichlet_faces & (1u << (2 * a))) && v == 0) m.dirichlet[(size_t)i] = 1;
       if ((m.desc.dirichlet_faces & (1u << (2 * a + 1))) && v == p * m.ext[a]) m.dirichlet[(size_t)i] = 1;
     }
-  // greedy colouring with per-dof colour masks (up to 256 colours)
-  const int W = 4;
-  std::vector<uint64_t> used((size_t)m.n_dofs * W, 0);
-  m.colour.assign(na, 0);
-  m.n_colours = 0;
-  std::vector<int32_t> touched;
-  for (size_t c = 0; c < na; ++c) {
-    touched.clear();
-    for (int l = 0; l < npc; ++l) {
-      int32_t v = m.cell_dofs[c * (size_t)npc + (size_t)l];
-      if (v >= 0) touched.push_back(v);
-      else
-        for (int32_t e = m.con_ptr[(size_t)(-1 - v)]; e < m.con_ptr[(size_t)(-v)]; ++e) touched.push_back(m.con_idx[(size_t)e]);
+  // greedy colouring with per-dof colour masks of W 64-bit words: one word while 64 colours
+  // suffice (the meshes here need at most about 32), else again with four (up to 256 colours);
+  // the colours are the same either way
+  auto colour_cells = [&](const int W) -> bool {
+    std::vector<uint64_t> used((size_t)m.n_dofs * (size_t)W, 0);
+    m.colour.assign(na, 0);
+    m.n_colours = 0;
+    std::vector<int32_t> touched;
+    for (size_t c = 0; c < na; ++c) {
+      touched.clear();
+      for (int l = 0; l < npc; ++l) {
+        int32_t v = m.cell_dofs[c * (size_t)npc + (size_t)l];
+        if (v >= 0) touched.push_back(v);
+        else
+          for (int32_t e = m.con_ptr[(size_t)(-1 - v)]; e < m.con_ptr[(size_t)(-v)]; ++e) touched.push_back(m.con_idx[(size_t)e]);
+      }
+      uint64_t busy[4] = {0, 0, 0, 0};
+      for (int32_t t : touched)
+        for (int w = 0; w < W; ++w) busy[w] |= used[(size_t)t * (size_t)W + (size_t)w];
+      int col = -1;
+      for (int w = 0; w < W && col < 0; ++w)
+        if (~busy[w]) col = 64 * w + __builtin_ctzll(~busy[w]);
+      if (col < 0) return false;
+      m.colour[c] = col;
+      if (col + 1 > m.n_colours) m.n_colours = col + 1;
+      for (int32_t t : touched) used[(size_t)t * (size_t)W + (size_t)(col / 64)] |= 1ull << (col % 64);
     }
-    uint64_t busy[W] = {0, 0, 0, 0};
-    for (int32_t t : touched)
-      for (int w = 0; w < W; ++w) busy[w] |= used[(size_t)t * W + w];
-    int col = -1;
-    for (int w = 0; w < W && col < 0; ++w)
-      if (~busy[w]) col = 64 * w + __builtin_ctzll(~busy[w]);
-    if (col < 0) return *err = "colouring needs more than 256 colours", PBF_EINVAL;
-    m.colour[c] = col;
-    if (col + 1 > m.n_colours) m.n_colours = col + 1;
-    for (int32_t t : touched) used[(size_t)t * W + (size_t)(col / 64)] |= 1ull << (col % 64);
-  }
+    return true;
+  };
+  if (!colour_cells(1) && !colour_cells(4)) return *err = "colouring needs more than 256 colours", PBF_EINVAL;
   // top faces
   m.top.assign(na, 0);
   m.n_top = 0;
