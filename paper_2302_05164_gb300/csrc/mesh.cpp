@@ -542,75 +542,103 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
   out.n_old = om.n_dofs;
   out.n_new = nm.n_dofs;
   out.fill = fill;
-  // the rows are built in parallel, each thread a contiguous range of new dofs into its own
-  // buffers, and concatenated in dof order (the same result for any number of threads)
+  // the rows are built in parallel over fixed chunks of new dofs, each chunk into its own
+  // buffers (taken by the threads as they come free: the rows that interpolate cluster in the
+  // refined region), and concatenated in dof order (the same result for any number of threads)
   const int64_t n_new = nm.n_dofs;
-  int n_threads = 1;
-#ifdef _OPENMP
-  n_threads = omp_get_max_threads();
-#endif
-  std::vector<std::vector<int32_t>> t_idx((size_t)n_threads);
-  std::vector<std::vector<double>> t_w((size_t)n_threads);
+  constexpr int64_t kChunk = 4096;
+  const int64_t n_chunks = (n_new + kChunk - 1) / kChunk;
+  std::vector<std::vector<int32_t>> t_idx((size_t)n_chunks);
+  std::vector<std::vector<double>> t_w((size_t)n_chunks);
   std::vector<int32_t> row_len((size_t)n_new, 0);
-#pragma omp parallel num_threads(n_threads)
+#pragma omp parallel
   {
-    int t = 0;
-#ifdef _OPENMP
-    t = omp_get_thread_num();
-#endif
-    const int64_t lo = n_new * t / n_threads, hi = n_new * (t + 1) / n_threads;
     std::vector<std::pair<int32_t, double>> acc;
-    std::vector<int32_t>& my_idx = t_idx[(size_t)t];
-    std::vector<double>& my_w = t_w[(size_t)t];
-    for (int64_t i = lo; i < hi; ++i) {
-      const int64_t* n = &nm.dof_xyz[(size_t)i * 3];
-      // first old active cell (cell order) whose closure holds the point
-      int32_t best = -1;
-      for (int o = 0; o < 8; ++o) {
-        int64_t q[3];
-        bool ok = true;
-        for (int a = 0; a < 3; ++a) {
-          int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);
-          if (h2 < 0) { ok = false; break; }
-          q[a] = h2 / (2 * p);
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t ch = 0; ch < n_chunks; ++ch) {
+      const int64_t lo = ch * kChunk, hi = std::min(n_new, lo + kChunk);
+      std::vector<int32_t>& my_idx = t_idx[(size_t)ch];
+      std::vector<double>& my_w = t_w[(size_t)ch];
+      for (int64_t i = lo; i < hi; ++i) {
+        const int64_t* n = &nm.dof_xyz[(size_t)i * 3];
+        // first old active cell (cell order) whose closure holds the point
+        int32_t best = -1;
+        for (int o = 0; o < 8; ++o) {
+          int64_t q[3];
+          bool ok = true;
+          for (int a = 0; a < 3; ++a) {
+            int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);
+            if (h2 < 0) { ok = false; break; }
+            q[a] = h2 / (2 * p);
+          }
+          if (!ok) continue;
+          int64_t leaf = om.locate(q);
+          if (leaf < 0 || !om.active[(size_t)leaf]) continue;
+          int32_t ai = om.active_of_leaf[(size_t)leaf];
+          if (best < 0 || ai < best) best = ai;
         }
-        if (!ok) continue;
-        int64_t leaf = om.locate(q);
-        if (leaf < 0 || !om.active[(size_t)leaf]) continue;
-        int32_t ai = om.active_of_leaf[(size_t)leaf];
-        if (best < 0 || ai < best) best = ai;
-      }
-      if (best < 0) continue;
-      const Octant& c = om.oct[(size_t)om.leaf_of_active[(size_t)best]];
-      int64_t s = om.size(c);
-      double w1[3][3];
-      for (int a = 0; a < 3; ++a) weights_1d(p, n[a] - p * c.a[a], s, w1[a]);
-      acc.clear();
-      for (int l = 0; l < npc; ++l) {
-        int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
-        double w = w1[0][ijk[0]] * w1[1][ijk[1]] * w1[2][ijk[2]];
-        if (w == 0.0) continue;
-        int32_t v = om.cell_dofs[(size_t)best * (size_t)npc + (size_t)l];
-        if (v >= 0) acc.push_back({v, w});
-        else
-          for (int32_t e = om.con_ptr[(size_t)(-1 - v)]; e < om.con_ptr[(size_t)(-v)]; ++e)
-            acc.push_back({om.con_idx[(size_t)e], w * om.con_w[(size_t)e]});
-      }
-      std::stable_sort(acc.begin(), acc.end(),
-                       [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) { return x.first < y.first; });
-      int32_t len = 0;
-      for (size_t e = 0; e < acc.size();) {
-        size_t f = e;
-        double sum = 0.0;
-        while (f < acc.size() && acc[f].first == acc[e].first) sum += acc[f++].second;
-        if (sum != 0.0) {
-          my_idx.push_back(acc[e].first);
-          my_w.push_back(sum);
-          ++len;
+        if (best < 0) continue;
+        const Octant& c = om.oct[(size_t)om.leaf_of_active[(size_t)best]];
+        int64_t s = om.size(c);
+        // a nodal point of that cell: its one weight is exactly 1, so its row is the node's own
+        // (a dof, or its constraint row, whose masters are sorted and merged already)
+        int loc = 0, stride = 1;
+        bool nodal = true;
+        for (int a = 0; a < 3 && nodal; ++a) {
+          const int64_t u = n[a] - p * c.a[a];
+          nodal = u % s == 0;
+          loc += (int)(u / s) * stride;
+          stride *= p + 1;
         }
-        e = f;
+        if (nodal) {
+          const int32_t v = om.cell_dofs[(size_t)best * (size_t)npc + (size_t)loc];
+          if (v >= 0) {
+            my_idx.push_back(v);
+            my_w.push_back(1.0);
+            row_len[(size_t)i] = 1;
+          } else {
+            const int32_t e0 = om.con_ptr[(size_t)(-1 - v)], e1 = om.con_ptr[(size_t)(-v)];
+            my_idx.insert(my_idx.end(), om.con_idx.begin() + e0, om.con_idx.begin() + e1);
+            my_w.insert(my_w.end(), om.con_w.begin() + e0, om.con_w.begin() + e1);
+            row_len[(size_t)i] = e1 - e0;
+          }
+          continue;
+        }
+        double w1[3][3];
+        for (int a = 0; a < 3; ++a) weights_1d(p, n[a] - p * c.a[a], s, w1[a]);
+        acc.clear();
+        for (int l = 0; l < npc; ++l) {
+          int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
+          double w = w1[0][ijk[0]] * w1[1][ijk[1]] * w1[2][ijk[2]];
+          if (w == 0.0) continue;
+          int32_t v = om.cell_dofs[(size_t)best * (size_t)npc + (size_t)l];
+          if (v >= 0) acc.push_back({v, w});
+          else
+            for (int32_t e = om.con_ptr[(size_t)(-1 - v)]; e < om.con_ptr[(size_t)(-v)]; ++e)
+              acc.push_back({om.con_idx[(size_t)e], w * om.con_w[(size_t)e]});
+        }
+        // by old dof, entries of one dof in the order above (a stable insertion sort: the lists
+        // are short)
+        for (size_t e = 1; e < acc.size(); ++e) {
+          const std::pair<int32_t, double> x = acc[e];
+          size_t f = e;
+          for (; f > 0 && acc[f - 1].first > x.first; --f) acc[f] = acc[f - 1];
+          acc[f] = x;
+        }
+        int32_t len = 0;
+        for (size_t e = 0; e < acc.size();) {
+          size_t f = e;
+          double sum = 0.0;
+          while (f < acc.size() && acc[f].first == acc[e].first) sum += acc[f++].second;
+          if (sum != 0.0) {
+            my_idx.push_back(acc[e].first);
+            my_w.push_back(sum);
+            ++len;
+          }
+          e = f;
+        }
+        row_len[(size_t)i] = len;
       }
-      row_len[(size_t)i] = len;
     }
   }
   out.ptr.assign((size_t)n_new + 1, 0);
@@ -619,9 +647,9 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
   out.w.clear();
   out.idx.reserve((size_t)out.ptr.back());
   out.w.reserve((size_t)out.ptr.back());
-  for (int t = 0; t < n_threads; ++t) {
-    out.idx.insert(out.idx.end(), t_idx[(size_t)t].begin(), t_idx[(size_t)t].end());
-    out.w.insert(out.w.end(), t_w[(size_t)t].begin(), t_w[(size_t)t].end());
+  for (int64_t ch = 0; ch < n_chunks; ++ch) {
+    out.idx.insert(out.idx.end(), t_idx[(size_t)ch].begin(), t_idx[(size_t)ch].end());
+    out.w.insert(out.w.end(), t_w[(size_t)ch].begin(), t_w[(size_t)ch].end());
   }
 }
 
