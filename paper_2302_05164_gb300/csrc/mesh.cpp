@@ -216,31 +216,43 @@ struct NodeTable {
   }
 };
 
-// The active cells whose closure holds node n, found by probing the eight octants around it;
-// returns the smallest active index among those that do not have n as a nodal point (-1:
-// none, i.e. the node is a proper dof).
+// Calls f(q) for the finest cells q around node n (node-lattice units): along each axis the
+// cells on either side of the node's position half a node spacing away (one cell where the
+// node lies inside a finest cell; none below 0). These are the cells whose closure may hold n.
+template <typename F>
+static void for_each_cell_around(int p, const int64_t n[3], F f) {
+  int64_t c[3][2];
+  int nc[3];
+  for (int a = 0; a < 3; ++a) {
+    nc[a] = 0;
+    const int64_t lo = 2 * n[a] - 1, hi = 2 * n[a] + 1;  // half node-lattice units
+    if (lo >= 0) c[a][nc[a]++] = lo / (2 * p);
+    if (nc[a] == 0 || c[a][0] != hi / (2 * p)) c[a][nc[a]++] = hi / (2 * p);
+  }
+  for (int k = 0; k < nc[2]; ++k)
+    for (int j = 0; j < nc[1]; ++j)
+      for (int i = 0; i < nc[0]; ++i) {
+        const int64_t q[3] = {c[0][i], c[1][j], c[2][k]};
+        f(q);
+      }
+}
+
+// The active cells whose closure holds node n; returns the smallest active index among those
+// that do not have n as a nodal point (-1: none, i.e. the node is a proper dof).
 static int32_t first_coarse_holder(const HostMesh& m, const int64_t n[3]) {
   int32_t best = -1;
-  for (int o = 0; o < 8; ++o) {
-    int64_t q[3];
-    bool ok = true;
-    for (int a = 0; a < 3; ++a) {
-      int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);  // half node-lattice units
-      if (h2 < 0) { ok = false; break; }
-      q[a] = h2 / (2 * m.p);
-    }
-    if (!ok) continue;
+  for_each_cell_around(m.p, n, [&](const int64_t q[3]) {
     int64_t leaf = m.locate(q);
-    if (leaf < 0 || !m.active[(size_t)leaf]) continue;
+    if (leaf < 0 || !m.active[(size_t)leaf]) return;
     const Octant& c = m.oct[(size_t)leaf];
     int64_t s = m.size(c);
     bool nodal = true;
     for (int a = 0; a < 3; ++a)
       if ((n[a] - m.p * c.a[a]) % s != 0) nodal = false;
-    if (nodal) continue;
+    if (nodal) return;
     int32_t ai = m.active_of_leaf[(size_t)leaf];
     if (best < 0 || ai < best) best = ai;
-  }
+  });
   return best;
 }
 
@@ -563,20 +575,12 @@ void make_transfer(const HostMesh& om, const HostMesh& nm, double fill, Transfer
         const int64_t* n = &nm.dof_xyz[(size_t)i * 3];
         // first old active cell (cell order) whose closure holds the point
         int32_t best = -1;
-        for (int o = 0; o < 8; ++o) {
-          int64_t q[3];
-          bool ok = true;
-          for (int a = 0; a < 3; ++a) {
-            int64_t h2 = 2 * n[a] + (((o >> a) & 1) ? 1 : -1);
-            if (h2 < 0) { ok = false; break; }
-            q[a] = h2 / (2 * p);
-          }
-          if (!ok) continue;
+        for_each_cell_around(p, n, [&](const int64_t q[3]) {
           int64_t leaf = om.locate(q);
-          if (leaf < 0 || !om.active[(size_t)leaf]) continue;
+          if (leaf < 0 || !om.active[(size_t)leaf]) return;
           int32_t ai = om.active_of_leaf[(size_t)leaf];
           if (best < 0 || ai < best) best = ai;
-        }
+        });
         if (best < 0) continue;
         const Octant& c = om.oct[(size_t)om.leaf_of_active[(size_t)best]];
         int64_t s = om.size(c);
