@@ -55,6 +55,41 @@ void patch_keys(const HostMesh& m, const std::vector<std::pair<uint64_t, int32_t
     if (k >= nd32) hent += m.con_ptr[(size_t)(k - nd32) + 1] - m.con_ptr[(size_t)(k - nd32)];
 }
 
+// The index of each key in a patch's sorted key list, by open addressing (a patch lists at
+// most a few thousand keys; one table per thread, rebuilt for each patch). find() returns -1
+// for a key that is not listed.
+class KeyIndex {
+ public:
+  void build(const int32_t* kb, int32_t nu) {
+    int bits = 6;
+    while ((1 << bits) < 2 * nu) ++bits;
+    shift_ = 32 - bits;
+    mask_ = (1u << bits) - 1;
+    key_.assign((size_t)1 << bits, -1);
+    pos_.resize((size_t)1 << bits);
+    for (int32_t j = 0; j < nu; ++j) {
+      uint32_t h = slot(kb[j]);
+      while (key_[h] >= 0) h = (h + 1) & mask_;
+      key_[h] = kb[j];
+      pos_[h] = j;
+    }
+  }
+  int32_t find(int32_t k) const {
+    uint32_t h = slot(k);
+    for (uint32_t n = 0; n <= mask_; ++n, h = (h + 1) & mask_) {
+      if (key_[h] == k) return pos_[h];
+      if (key_[h] < 0) return -1;
+    }
+    return -1;
+  }
+
+ private:
+  uint32_t slot(int32_t k) const { return ((uint32_t)k * 2654435761u) >> shift_; }
+  std::vector<int32_t> key_, pos_;
+  uint32_t mask_ = 0;
+  int shift_ = 26;
+};
+
 }  // namespace
 
 void build_step_tables(const HostMesh& m, StepHost& out) {
@@ -143,39 +178,48 @@ void build_step_tables(const HostMesh& m, StepHost& out) {
   std::vector<std::vector<float>> phw(np);
   std::vector<int32_t> pnfree(np);
   int bad = 0;
-#pragma omp parallel for schedule(dynamic, 8) reduction(| : bad)
-  for (int64_t qq = 0; qq < (int64_t)np; ++qq) {
-    const size_t q = (size_t)qq, p = (size_t)porder[q];
-    const int32_t* kb = keys[p].data();
-    const int32_t nu = (int32_t)keys[p].size();
-    pnfree[q] = (int32_t)(std::lower_bound(kb, kb + nu, nd32) - kb);
-    auto pos = [&](int32_t key) { return step_swizzle((int)(std::lower_bound(kb, kb + nu, key) - kb)); };
-    for (size_t c = pb[p]; c < pb[p + 1]; ++c) {
-      const size_t lane = c - pb[p], cell = (size_t)order[c].second;
-      o.cell[q * kStepCells + lane] = (int32_t)cell;
-      for (size_t a = 0; a < npc; ++a) {
-        const int32_t d = m.cell_dofs[cell * npc + a];
-        o.loc[(q * npc + a) * kStepCells + lane] = (uint16_t)pos(d >= 0 ? d : nd32 + (-1 - d));
-      }
-    }
-    std::vector<int32_t>& sl = pslot[q];
-    sl.reserve((size_t)nu + 3);
-    for (int32_t j = 0; j < nu; ++j) {
-      const int32_t k = kb[j];
-      if (k < nd32) {
-        sl.push_back(owner[(size_t)k] == (int32_t)q ? (int32_t)((uint32_t)k | 0x80000000u) : k);
-      } else {
-        const int32_t r = k - nd32, e0 = m.con_ptr[(size_t)r], e1 = m.con_ptr[(size_t)r + 1];
-        const int32_t start = (int32_t)phloc[q].size();
-        if (e1 - e0 > 31 || start >= (1 << 26)) bad = 1;
-        for (int32_t e = e0; e < e1; ++e) {
-          phloc[q].push_back((uint16_t)pos(m.con_idx[(size_t)e]));
-          phw[q].push_back((float)m.con_w[(size_t)e]);
+#pragma omp parallel reduction(| : bad)
+  {
+    KeyIndex index;
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t qq = 0; qq < (int64_t)np; ++qq) {
+      const size_t q = (size_t)qq, p = (size_t)porder[q];
+      const int32_t* kb = keys[p].data();
+      const int32_t nu = (int32_t)keys[p].size();
+      pnfree[q] = (int32_t)(std::lower_bound(kb, kb + nu, nd32) - kb);
+      index.build(kb, nu);
+      auto pos = [&](int32_t key) {
+        const int32_t j = index.find(key);
+        if (j < 0) bad = 1;  // every key looked up is listed: a miss means no fused form
+        return step_swizzle(j < 0 ? 0 : (int)j);
+      };
+      for (size_t c = pb[p]; c < pb[p + 1]; ++c) {
+        const size_t lane = c - pb[p], cell = (size_t)order[c].second;
+        o.cell[q * kStepCells + lane] = (int32_t)cell;
+        for (size_t a = 0; a < npc; ++a) {
+          const int32_t d = m.cell_dofs[cell * npc + a];
+          o.loc[(q * npc + a) * kStepCells + lane] = (uint16_t)pos(d >= 0 ? d : nd32 + (-1 - d));
         }
-        sl.push_back((start << 5) | (e1 - e0));
       }
+      std::vector<int32_t>& sl = pslot[q];
+      sl.reserve((size_t)nu + 3);
+      for (int32_t j = 0; j < nu; ++j) {
+        const int32_t k = kb[j];
+        if (k < nd32) {
+          sl.push_back(owner[(size_t)k] == (int32_t)q ? (int32_t)((uint32_t)k | 0x80000000u) : k);
+        } else {
+          const int32_t r = k - nd32, e0 = m.con_ptr[(size_t)r], e1 = m.con_ptr[(size_t)r + 1];
+          const int32_t start = (int32_t)phloc[q].size();
+          if (e1 - e0 > 31 || start >= (1 << 26)) bad = 1;
+          for (int32_t e = e0; e < e1; ++e) {
+            phloc[q].push_back((uint16_t)pos(m.con_idx[(size_t)e]));
+            phw[q].push_back((float)m.con_w[(size_t)e]);
+          }
+          sl.push_back((start << 5) | (e1 - e0));
+        }
+      }
+      while (sl.size() % 4) sl.push_back(0);
     }
-    while (sl.size() % 4) sl.push_back(0);
   }
   // concatenation in the patch numbering
   size_t ns = 0, nh = 0;
