@@ -338,8 +338,26 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
   }
   size_t na = m.leaf_of_active.size();
   const int npc = m.npc;
-  // node table: sort (node key, slot)
-  std::vector<std::pair<uint64_t, int64_t>> ents(na * (size_t)npc);
+  // node table: the (node, slot) entries sorted by node, then slot. When the node's index on
+  // the node lattice (z, y, x lexicographic: the order of pack_node) and the slot fit in one
+  // 64-bit word together, an entry is that word (half the bytes to sort); otherwise a
+  // (pack_node key, slot) pair. Either way the order is total, so the result is the same in
+  // parallel.
+  const int64_t nsl = (int64_t)(na * (size_t)npc);
+  const int64_t NX = p * m.ext[0] + 1, NY = p * m.ext[1] + 1, NZ = p * m.ext[2] + 1;
+  auto bit_length = [](uint64_t v) {
+    int b = 0;
+    while (b < 64 && (v >> b) != 0) ++b;
+    return b;
+  };
+  const int sbits = bit_length((uint64_t)std::max<int64_t>(nsl - 1, 0));
+  const bool packed = bit_length((uint64_t)NX) + bit_length((uint64_t)NY) + bit_length((uint64_t)NZ) <= 62 &&
+                      bit_length((uint64_t)(NX * NY * NZ - 1)) + sbits <= 64;
+  const uint64_t smask = sbits == 0 ? 0 : (~0ull >> (64 - sbits));
+  std::vector<uint64_t> word;
+  std::vector<std::pair<uint64_t, int64_t>> ents;
+  if (packed) word.resize((size_t)nsl);
+  else ents.resize((size_t)nsl);
 #pragma omp parallel for schedule(static, 1024)
   for (int64_t c = 0; c < (int64_t)na; ++c) {
     const Octant& o = m.oct[(size_t)m.leaf_of_active[(size_t)c]];
@@ -348,15 +366,41 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
       int ijk[3] = {l % (p + 1), (l / (p + 1)) % (p + 1), l / ((p + 1) * (p + 1))};
       int64_t n[3];
       for (int a = 0; a < 3; ++a) n[a] = p * o.a[a] + ijk[a] * s;
-      ents[(size_t)c * (size_t)npc + (size_t)l] = {pack_node(n), (int64_t)((size_t)c * (size_t)npc + (size_t)l)};
+      const size_t slot = (size_t)c * (size_t)npc + (size_t)l;
+      if (packed) word[slot] = ((uint64_t)(n[0] + NX * (n[1] + NY * n[2])) << sbits) | (uint64_t)slot;
+      else ents[slot] = {pack_node(n), (int64_t)slot};
     }
   }
-  sort_pairs(ents);  // a total order (the slots are distinct): the same result in parallel
+  if (packed) {
+#ifdef _OPENMP
+    __gnu_parallel::sort(word.begin(), word.end());
+#else
+    std::sort(word.begin(), word.end());
+#endif
+  } else {
+    sort_pairs(ents);
+  }
+  // entry e: a key equal for the entries of one node, its slot, and the node's position
+  auto node_of = [&](int64_t e) { return packed ? word[(size_t)e] >> sbits : ents[(size_t)e].first; };
+  auto slot_of = [&](int64_t e) { return packed ? (int64_t)(word[(size_t)e] & smask) : ents[(size_t)e].second; };
+  auto position = [&](int64_t e, int64_t* xyz) {
+    if (packed) {
+      const int64_t i = (int64_t)(word[(size_t)e] >> sbits);
+      xyz[0] = i % NX;
+      xyz[1] = (i / NX) % NY;
+      xyz[2] = i / (NX * NY);
+    } else {
+      const uint64_t k = ents[(size_t)e].first;
+      xyz[0] = (int64_t)(k & 0x1FFFFF);
+      xyz[1] = (int64_t)((k >> 21) & 0x1FFFFF);
+      xyz[2] = (int64_t)(k >> 42);
+    }
+  };
   // unique nodes: entry e starts a node when its key differs from the previous one, and the
   // node's index is the number of starts up to e (a prefix sum); the entries of a node are
   // sorted by slot, so its first entry holds its first slot
-  const int64_t ne = (int64_t)ents.size();
-  auto starts = [&](int64_t e) { return e == 0 || ents[(size_t)e].first != ents[(size_t)e - 1].first; };
+  const int64_t ne = nsl;
+  auto starts = [&](int64_t e) { return e == 0 || node_of(e) != node_of(e - 1); };
   std::vector<int32_t> starts_before((size_t)ne);
   exclusive_count(ne, starts, starts_before.data());
   const size_t nn = ne == 0 ? 0 : (size_t)starts_before.back() + (starts(ne - 1) ? 1 : 0);
@@ -369,15 +413,14 @@ pbf_status build_mesh(HostMesh& m, const std::vector<uint8_t>* mat_hint, std::st
   for (int64_t e = 0; e < ne; ++e) {
     const bool st = starts(e);
     const size_t nd = (size_t)(starts_before[(size_t)e] + (st ? 1 : 0) - 1);
+    const int64_t sl = slot_of(e);
     if (st) {
-      const uint64_t k = ents[(size_t)e].first;
-      nodes.keys[nd] = k;
-      nodes.xyz[3 * nd] = (int64_t)(k & 0x1FFFFF);
-      nodes.xyz[3 * nd + 1] = (int64_t)((k >> 21) & 0x1FFFFF);
-      nodes.xyz[3 * nd + 2] = (int64_t)(k >> 42);
-      first_slot[nd] = (int32_t)ents[(size_t)e].second;
+      int64_t* xyz = &nodes.xyz[3 * nd];
+      position(e, xyz);
+      nodes.keys[nd] = pack_node(xyz);
+      first_slot[nd] = (int32_t)sl;
     }
-    node_of_slot[(size_t)ents[(size_t)e].second] = (int32_t)nd;
+    node_of_slot[(size_t)sl] = (int32_t)nd;
   }
   std::vector<int32_t> holder(nn);
 #pragma omp parallel for schedule(static, 4096)
