@@ -1,6 +1,6 @@
 """Benchmark of the explicit hot path on the adaptive Q2 multi-track workload.
 
-Workload (configuration 2 of the scope): Q2 octree mesh on a 2 x 2 x 1 mm block (40 um trees,
+Workload C2: Q2 octree mesh on a 2 x 2 x 1 mm block (40 um trees,
 3 refinement levels -> 5 um cells inside a 150 um ball around the laser spot, 2:1 balanced
 with hanging nodes; 1,066,531 dofs, 132,423 cells), k(T) linear 6.7 -> 28 W/mK over
 300-1928 K, apparent capacity with latent heat 2.86e5 J/kg (Gaussian around 1903 K, nodal
@@ -234,6 +234,7 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=50, sh
     n_sm = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
     fp32_peak = n_sm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     cell_tflops = flops_per_cell_q2_nonlinear() * n_cells * batch / (cell_us * 1e-6) / 1e12
+    meta = metadata_bytes(pbf, mesh, False, batch)  # both batched forms read the per-cell tables
     ctx.close()
     mesh.close()
     return {"workload": f"C4: Q2 1.0x0.5x0.25 mm, {n} dofs x {batch} instances (own powers and k scales)",
@@ -243,7 +244,8 @@ def bench_batched(pbf, I, torch, stream, flush, peaks, K, batch=64, chunk=50, sh
                                      for i, u in enumerate(shape_us) if u > 0},
             "cell_kernel_roofline": {"bound": "alu", "achieved": cell_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                                      "frac": cell_tflops / fp32_peak, "cells_x_instances": n_cells * batch},
-            "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / hbm, "l2": "state > L2; flushed between timed steps"}
+            "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / hbm, "l2": "state > L2; flushed between timed steps",
+            "metadata": meta}
 
 
 def bench_large(pbf, I, torch, stream, flush, peaks, K=5, chunk=20):
@@ -482,6 +484,27 @@ def bench_c2_adapt(pbf, I, torch, stream, T0, dt, shape, cycles=8):
             "context_rebuild_ms_per_cycle": 1e3 * ctx_s / cycles,
             "with_adaptation_value": updates / (step_ms * 1e-3 + adapt_s + transfer_ms * 1e-3 + ctx_s) / 1e9,
             "finite": ok}
+
+
+def metadata_bytes(pbf, mesh, fused, batch=1):
+    """Mesh metadata an explicit step reads at least once, the same whatever the number of
+    instances in a batch (so it is amortised by batching and counted apart from the 16 B of
+    state per dof-update). Every form reads, per active cell, its level, material and top flag
+    (3 B) and, on the top surface, its FP32 corner (12 B), and per dof the FP32 inverse lumped
+    mass (4 B). The fused step adds its patch tables. The per-cell form adds its cell-to-dof
+    table (4 B per cell node) and the hanging-node rows (offsets, masters and FP32 weights)."""
+    info = mesh.info()
+    n_cells, n_dofs = info["n_active"], info["n_dofs"]
+    common = 3 * n_cells + 12 * info["n_top_faces"] + 4 * n_dofs
+    if fused:
+        st = pbf.pbf_mesh_step_tables(mesh.h)
+        tables = int(sum(st[k].nbytes for k in ("ptr", "cnt", "slot", "cell", "loc", "hloc", "hw")))
+    else:
+        tables = 4 * info["nodes_per_cell"] * n_cells + 4 * (info["n_hanging"] + 1) + 8 * info["n_con_entries"]
+    total = common + tables
+    return {"form": "fused step" if fused else "per-cell", "tables_bytes": tables, "cell_and_dof_bytes": common,
+            "bytes_per_step": total, "bytes_per_dof_update": total / (n_dofs * batch), "instances": batch,
+            "algorithmic_state_bytes_per_dof_update": BYTES_PER_DOF_UPDATE}
 
 
 def bench_laplace(pbf, I, torch, stream, flush, mesh, T0, dt, variant, K, full_gdofs):
@@ -854,6 +877,8 @@ def main():
                            "achieved_gbs": value * BYTES_PER_DOF_UPDATE,
                            "peak_gbs": hbm, "frac": value * BYTES_PER_DOF_UPDATE / hbm,
                            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})"}
+    # shapes 4-9 read the patch tables (the lean forms through L1), shapes 0-3 the per-cell tables
+    out["metadata"] = metadata_bytes(pbf, mesh, variant >= 4)
     out["device"] = {"name": props.name, "sms": n_sm}
     out["clocks"] = clocks.summary()
     if not args.quick:

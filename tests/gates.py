@@ -2,7 +2,7 @@
 
 FP64 operator: 1e-10 relative max-norm, max |gpu - oracle| / max |oracle|.
 FP32 operator, temperatures after explicit steps, three gates at once:
-  - relative max-norm max |gpu - oracle| / max |oracle| <= 2e-4 (the scope's stated gate);
+  - relative max-norm max |gpu - oracle| / max |oracle| <= 2e-4 (the stated FP32-operator gate);
   - relative to the change the steps made, max |gpu - oracle| / max |oracle - T_0| <= 1e-3,
     so that a small increment cannot hide a large error in it behind the size of T itself;
   - relative L2 error ||gpu - oracle||_2 / ||oracle||_2, reported (and held to 2e-4).
