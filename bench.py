@@ -872,7 +872,7 @@ def main():
                            "peak_basis": f"{n_sm} SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (nominal)",
                            "note": "the ALU roof (338 GDoF/s at 238 flops per dof-update) lies below the HBM roof "
                                    "(423 GDoF/s); the kernel reaches neither: it is bound by latency and instruction "
-                                   "issue within each patch (ncu: issue active ~32%, FP32 pipe ~17%)"}
+                                   "issue within each patch (ncu: issue active ~37%, FMA pipe ~19%)"}
     out["hbm_fraction"] = {"algorithmic_bytes_per_dof_update": BYTES_PER_DOF_UPDATE,
                            "achieved_gbs": value * BYTES_PER_DOF_UPDATE,
                            "peak_gbs": hbm, "frac": value * BYTES_PER_DOF_UPDATE / hbm,
