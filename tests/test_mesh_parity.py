@@ -85,3 +85,19 @@ def test_adapt_topology(oracle_mod):
     pbf.pbf_mesh_adapt(lm.h, regs)
     d1 = I.c2_mesh(spot=(0.6e-3, 0.55e-3))
     compare(oracle_mod.Mesh(d1).tables(), lm.tables())
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_wide_lattice_mesh_bit_exact(oracle_mod, p):
+    """A forest whose node lattice needs more than 64 bits together with the slot index (255 x 64
+    trees at up to 12 levels: the library sorts its node entries as (key, slot) pairs instead of
+    single words), refined to level 2 in a ball, with hanging nodes."""
+    regions = [(I.BALL, (16e-3, 4e-3, 0.06e-3), (0, 0, 0), 0.4e-3, 2)]
+    d = I.mesh_desc((255, 64, 1), (125e-6,) * 3, p, 12, regions)
+    om, lm = oracle_mod.Mesh(d), pbf.Mesh(d)
+    info = lm.info()
+    ext = np.array([255, 64, 1]) << 12
+    lattice_bits = int(np.ceil(np.log2(float(np.prod(p * ext + 1)))))
+    slot_bits = int(np.ceil(np.log2(info["n_active"] * info["nodes_per_cell"])))
+    assert lattice_bits + slot_bits > 64 and info["n_hanging"] > 0
+    compare(om.tables(), lm.tables())
