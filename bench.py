@@ -281,12 +281,13 @@ def bench_large(pbf, I, torch, stream, flush, peaks, K=5, chunk=20):
         ms += a.elapsed_time(b)
     rate = n * chunk * K / (ms * 1e-3) / 1e9
     ok = bool(torch.isfinite(T).all().item())
+    meta = metadata_bytes(pbf, mesh, variant >= 4)
     ctx.close()
     mesh.close()
     out = {"workload": f"C2 block and material, 500 um refinement ball: {info['n_active']} cells, {n} dofs, one instance",
            "value": rate, "unit": "GDoF/s", "us_per_explicit_step": 1e3 * ms / (K * chunk), "step_shape": SHAPES[variant],
            "hbm_fraction": rate * BYTES_PER_DOF_UPDATE / peaks.get("hbm_gbs", 6800.0), "finite": ok,
-           "host_setup_s": setup_s, "l2": "state and tables > L2; flushed between timed steps"}
+           "host_setup_s": setup_s, "l2": "state and tables > L2; flushed between timed steps", "metadata": meta}
     if variant >= 7:  # measured DRAM bytes per launch of the lean step on this mesh (ncu record)
         t = traffic_for_kernel("lean_large", variant)
         out["traffic_bytes_per_launch"] = t
@@ -493,14 +494,17 @@ def metadata_bytes(pbf, mesh, fused, batch=1):
     (3 B) and, on the top surface, its FP32 corner (12 B), and per dof the FP32 inverse lumped
     mass (4 B). The fused step adds its patch tables. The per-cell form adds its cell-to-dof
     table (4 B per cell node) and the hanging-node rows (offsets, masters and FP32 weights)."""
-    info = mesh.info()
-    n_cells, n_dofs = info["n_active"], info["n_dofs"]
-    common = 3 * n_cells + 12 * info["n_top_faces"] + 4 * n_dofs
-    if fused:
-        st = pbf.pbf_mesh_step_tables(mesh.h)
-        tables = int(sum(st[k].nbytes for k in ("ptr", "cnt", "slot", "cell", "loc", "hloc", "hw")))
-    else:
-        tables = 4 * info["nodes_per_cell"] * n_cells + 4 * (info["n_hanging"] + 1) + 8 * info["n_con_entries"]
+    try:
+        info = mesh.info()
+        n_cells, n_dofs = info["n_active"], info["n_dofs"]
+        common = 3 * n_cells + 12 * info["n_top_faces"] + 4 * n_dofs
+        if fused:
+            st = pbf.pbf_mesh_step_tables(mesh.h)
+            tables = int(sum(st[k].nbytes for k in ("ptr", "cnt", "slot", "cell", "loc", "hloc", "hw")))
+        else:
+            tables = 4 * info["nodes_per_cell"] * n_cells + 4 * (info["n_hanging"] + 1) + 8 * info["n_con_entries"]
+    except Exception as e:  # a side record: its failure is reported, the measurements stand
+        return {"error": repr(e)}
     total = common + tables
     return {"form": "fused step" if fused else "per-cell", "tables_bytes": tables, "cell_and_dof_bytes": common,
             "bytes_per_step": total, "bytes_per_dof_update": total / (n_dofs * batch), "instances": batch,
@@ -605,6 +609,7 @@ def bench_c5(pbf, I, torch, stream, flush, peaks, K=4, level=5):
             "bicgstab_iterations": [int(v) for v in lit], "rel_residual": worst, "dt_s": 5e-2,
             "bounds": "from 30 Lanczos steps (included in the first step's time)"}
     ok = bool(torch.isfinite(T).all().item())
+    meta = metadata_bytes(pbf, mesh, variant >= 4)
     ctx.close()
     mesh.close()
     return {"workload": f"C5 stand-in, first layer: ribbed part on a baseplate, Q2 level {level}, "
@@ -615,7 +620,7 @@ def bench_c5(pbf, I, torch, stream, flush, peaks, K=4, level=5):
             "fp64": {"value": v64, "unit": "GDoF/s", "f32op_speedup": value / v64},
             "error_f32op_vs_f64_after_steps": dict(err, steps=K * CHUNK), "cooldown": cool,
             "host_mesh_s": host_mesh_s, "context_setup_s": ctx_s, "finite": ok,
-            "l2": "state > L2; flushed between timed steps"}
+            "l2": "state > L2; flushed between timed steps", "metadata": meta}
 
 
 

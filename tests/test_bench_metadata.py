@@ -29,3 +29,12 @@ def test_metadata_bytes_are_the_array_sizes():
         assert rec["instances"] == batch
         assert np.isclose(rec["bytes_per_dof_update"], rec["bytes_per_step"] / (batch * info["n_dofs"]))
     assert fused["form"] == "fused step" and per_cell["form"] == "per-cell"
+
+
+def test_a_failure_is_reported_not_raised():
+    class Broken:
+        h = None
+
+        def info(self):
+            raise RuntimeError("no mesh")
+    assert "no mesh" in bench.metadata_bytes(pbf, Broken(), True)["error"]
