@@ -181,9 +181,10 @@ pbf_status pbf_mesh_adapt(pbf_mesh* mesh, int n_regions, const pbf_region* regio
 pbf_status pbf_mesh_transfer(pbf_mesh* mesh, const double* T_old_dev, double* T_new_dev, int batch,
                              pbf_stream stream);
 
-/* The pending transfer's map on the host, for inspection; pbf_mesh_transfer applies it. New
- * dof i takes T_new[i] = sum over e in [ptr[i], ptr[i+1]) of w[e] T_old[idx[e]], or `fill` when
- * its row is empty (a dof outside the old active domain).
+/* The pending transfer's map (the state moved onto a changed mesh, Sec. 4.1) on the host, for
+ * inspection; pbf_mesh_transfer applies it. New dof i takes T_new[i] = sum over e in
+ * [ptr[i], ptr[i+1]) of w[e] T_old[idx[e]], or `fill` when its row is empty (a dof outside
+ * the old active domain).
  *  ptr [n_new + 1], idx [n_entries] (old dofs, ascending within a row), w [n_entries]
  * Sizes and fill are outputs. With every array NULL only they are reported; otherwise the
  * sizes passed in must equal the map's and each non-NULL array is filled. Host only. Errors:
