@@ -30,49 +30,33 @@ uint64_t spread_bits3(uint64_t v) {
   return r;
 }
 
-// The slot keys of one patch, sorted and unique: dof d, or n_dofs + r for hanging row r, with
-// the masters of its hanging rows; hent = the hanging-table entries of its rows.
-void patch_keys(const HostMesh& m, const std::vector<std::pair<uint64_t, int32_t>>& order, size_t c0, size_t c1,
-                std::vector<int32_t>& keys, int64_t& hent) {
-  const size_t npc = (size_t)m.npc;
-  const int32_t nd32 = (int32_t)m.n_dofs;
-  keys.clear();
-  for (size_t c = c0; c < c1; ++c)
-    for (size_t a = 0; a < npc; ++a) {
-      const int32_t d = m.cell_dofs[(size_t)order[c].second * npc + a];
-      if (d >= 0) {
-        keys.push_back(d);
-      } else {
-        const int32_t r = -1 - d;
-        keys.push_back(nd32 + r);
-        for (int32_t e = m.con_ptr[(size_t)r]; e < m.con_ptr[(size_t)r + 1]; ++e) keys.push_back(m.con_idx[(size_t)e]);
-      }
-    }
-  std::sort(keys.begin(), keys.end());
-  keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-  hent = 0;
-  for (int32_t k : keys)
-    if (k >= nd32) hent += m.con_ptr[(size_t)(k - nd32) + 1] - m.con_ptr[(size_t)(k - nd32)];
-}
-
-// The index of each key in a patch's sorted key list, by open addressing (a patch lists at
-// most a few thousand keys; one table per thread, rebuilt for each patch). find() returns -1
-// for a key that is not listed.
+// Keys of a patch (dofs, and n_dofs + r for hanging row r) with a position each, by open
+// addressing (a patch lists at most a few thousand keys; one table per thread, reset for each
+// use). find() returns -1 for a key that is not present.
 class KeyIndex {
  public:
-  void build(const int32_t* kb, int32_t nu) {
+  void reset(size_t n) {
     int bits = 6;
-    while ((1 << bits) < 2 * nu) ++bits;
+    while (((size_t)1 << bits) < 2 * n) ++bits;
     shift_ = 32 - bits;
     mask_ = (1u << bits) - 1;
     key_.assign((size_t)1 << bits, -1);
     pos_.resize((size_t)1 << bits);
-    for (int32_t j = 0; j < nu; ++j) {
-      uint32_t h = slot(kb[j]);
-      while (key_[h] >= 0) h = (h + 1) & mask_;
-      key_[h] = kb[j];
-      pos_[h] = j;
+  }
+  // adds k with position j; false (and nothing changes) when k is present already
+  bool insert(int32_t k, int32_t j) {
+    uint32_t h = slot(k);
+    while (key_[h] >= 0) {
+      if (key_[h] == k) return false;
+      h = (h + 1) & mask_;
     }
+    key_[h] = k;
+    pos_[h] = j;
+    return true;
+  }
+  void build(const int32_t* kb, int32_t nu) {
+    reset((size_t)nu);
+    for (int32_t j = 0; j < nu; ++j) insert(kb[j], j);
   }
   int32_t find(int32_t k) const {
     uint32_t h = slot(k);
@@ -89,6 +73,36 @@ class KeyIndex {
   uint32_t mask_ = 0;
   int shift_ = 26;
 };
+
+// The slot keys of one patch, sorted and unique: dof d, or n_dofs + r for hanging row r, with
+// the masters of its hanging rows; hent = the hanging-table entries of its rows. raw and seen
+// are the calling thread's work space.
+void patch_keys(const HostMesh& m, const std::vector<std::pair<uint64_t, int32_t>>& order, size_t c0, size_t c1,
+                std::vector<int32_t>& keys, int64_t& hent, std::vector<int32_t>& raw, KeyIndex& seen) {
+  const size_t npc = (size_t)m.npc;
+  const int32_t nd32 = (int32_t)m.n_dofs;
+  raw.clear();
+  for (size_t c = c0; c < c1; ++c)
+    for (size_t a = 0; a < npc; ++a) {
+      const int32_t d = m.cell_dofs[(size_t)order[c].second * npc + a];
+      if (d >= 0) {
+        raw.push_back(d);
+      } else {
+        const int32_t r = -1 - d;
+        raw.push_back(nd32 + r);
+        for (int32_t e = m.con_ptr[(size_t)r]; e < m.con_ptr[(size_t)r + 1]; ++e) raw.push_back(m.con_idx[(size_t)e]);
+      }
+    }
+  // the distinct keys (each key of a patch recurs in up to eight of its cells), then sorted
+  seen.reset(raw.size());
+  keys.clear();
+  for (int32_t k : raw)
+    if (seen.insert(k, 0)) keys.push_back(k);
+  std::sort(keys.begin(), keys.end());
+  hent = 0;
+  for (int32_t k : keys)
+    if (k >= nd32) hent += m.con_ptr[(size_t)(k - nd32) + 1] - m.con_ptr[(size_t)(k - nd32)];
+}
 
 }  // namespace
 
@@ -153,11 +167,16 @@ void build_step_tables(const HostMesh& m, StepHost& out) {
   // slot keys and work of every patch
   std::vector<std::vector<int32_t>> keys(np);
   std::vector<int64_t> work(np, 0);
-#pragma omp parallel for schedule(dynamic, 8)
-  for (int64_t p = 0; p < (int64_t)np; ++p) {
-    int64_t hent = 0;
-    patch_keys(m, order, pb[(size_t)p], pb[(size_t)p + 1], keys[(size_t)p], hent);
-    work[(size_t)p] = (int64_t)keys[(size_t)p].size() + 2 * hent;
+#pragma omp parallel
+  {
+    std::vector<int32_t> raw;
+    KeyIndex seen;
+#pragma omp for schedule(dynamic, 8)
+    for (int64_t p = 0; p < (int64_t)np; ++p) {
+      int64_t hent = 0;
+      patch_keys(m, order, pb[(size_t)p], pb[(size_t)p + 1], keys[(size_t)p], hent, raw, seen);
+      work[(size_t)p] = (int64_t)keys[(size_t)p].size() + 2 * hent;
+    }
   }
   std::vector<int32_t> porder(np);
   for (size_t p = 0; p < np; ++p) porder[p] = (int32_t)p;
