@@ -713,7 +713,7 @@ void make_history_map(const HostMesh& om, const HostMesh& nm, std::vector<int32_
   out.assign(ncell * (size_t)nq3, -1);
   double g[3];
   for (int q = 0; q < nq; ++q) g[q] = gauss_point(nm.p, q);
-#pragma omp parallel for schedule(static, 256)
+#pragma omp parallel for schedule(dynamic, 256)
   for (int64_t ci = 0; ci < (int64_t)ncell; ++ci) {
     const size_t c = (size_t)ci;
     const size_t leaf = (size_t)nm.leaf_of_active[c];
